@@ -1,0 +1,269 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+brute-force Jordan-Wigner operators, dense diagonalisation, finite differences,
+closed forms, LAPACK, and the sector sizes printed in the paper's Table 1."""
+import math
+import os
+from decimal import ROUND_HALF_UP, Decimal
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+import synth
+from oracle import fock, irl, lm, native
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sector_matrix(n, na, nb, h, eri):
+    dets = fock.sector_dets(n, na, nb)
+    idx = {int(d): i for i, d in enumerate(dets)}
+    H = np.zeros((len(dets), len(dets)))
+    for i, d in enumerate(dets):
+        od, oh, _ = native.connections(n, na, nb, h, eri, int(d))
+        for dd, hh in zip(od, oh):
+            H[idx[int(dd)], i] += hh
+    return dets, H
+
+
+def test_table1_sector_sizes():
+    """Sector enumeration reproduces Table 1's PVC counts (2 significant digits)."""
+    with open(os.path.join(GOLDEN, "table1_sector_sizes.txt")) as f:
+        lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    for mol, no, ne, pvc, note in lines:
+        no, ne, pvc = int(no), int(ne), float(pvc)
+        n = no // 2
+        count = math.comb(n, ne // 2) ** 2
+        e = len(str(count)) - 2   # keep 2 significant digits, halves rounded up as printed
+        printed = float((Decimal(count) / Decimal(10) ** e).quantize(Decimal(1), ROUND_HALF_UP)
+                        * Decimal(10) ** e) if e > 0 else float(count)
+        if note == "ok":
+            assert printed == pytest.approx(pvc, rel=1e-12), mol
+        else:
+            assert printed != pytest.approx(pvc, rel=0.05), mol
+        if count <= 5000:
+            assert len(fock.sector_dets(n, ne // 2, ne // 2)) == count
+
+
+@pytest.mark.parametrize("n,na,nb,seed", [(3, 1, 1, 1), (4, 2, 1, 5), (4, 2, 2, 7), (5, 2, 2, 9)])
+def test_slater_condon_equals_jordan_wigner(n, na, nb, seed):
+    """Slater-Condon elements and connectivity equal the literal JW operator sum."""
+    h, eri = synth.integrals(n, seed)
+    dets, Hjw = fock.sector_matrix_from_jw(h, eri, na, nb)
+    _, Hsc = _sector_matrix(n, na, nb, h, eri)
+    assert np.abs(Hsc - Hjw).max() <= 1e-13 * max(1.0, np.abs(Hjw).max())
+    # identical sparsity: every spin-conserving single/double is listed, nothing else
+    nz_jw = np.abs(Hjw) > 1e-12
+    nz_sc = np.abs(Hsc) > 1e-12
+    assert (nz_jw == nz_sc).all()
+
+
+def test_connection_counts_closed_form():
+    """conn = 1 + singles + doubles for the shapes of the benchmark workloads."""
+    for n, na, nb, want in [(6, 3, 3, 117), (10, 7, 7, 609), (14, 7, 7, 3381)]:
+        h, eri = synth.integrals(n, 3)
+        x = int(fock.sector_dets(n, na, nb)[0])
+        od, _, _ = native.connections(n, na, nb, h, eri, x)
+        va, vb = n - na, n - nb
+        singles = na * va + nb * vb
+        doubles = (math.comb(na, 2) * math.comb(va, 2) + math.comb(nb, 2) * math.comb(vb, 2)
+                   + na * va * nb * vb)
+        assert len(od) - 1 == singles + doubles == want
+        assert len(set(od.tolist())) == len(od)
+
+
+def test_one_body_only_fci_closed_form():
+    """With (pq|rs) = 0 the ground energy is the sum of the lowest N_a and N_b orbital energies."""
+    n, na, nb = 6, 3, 2
+    h, _ = synth.integrals(n, 11)
+    eri = np.zeros((n,) * 4)
+    _, H = _sector_matrix(n, na, nb, h, eri)
+    e = np.linalg.eigvalsh(h)
+    assert np.linalg.eigvalsh(H)[0] == pytest.approx(e[:na].sum() + e[:nb].sum(), abs=1e-12)
+
+
+def _exact_energy_and_eloc(theta, n, na, nb, nh, h, eri):
+    dets = fock.sector_dets(n, na, nb)
+    lnpsi, _, eloc, _ = native.rows(n, na, nb, nh, h, eri, theta, dets, want_o=False, want_g=False)
+    w = lm.weights_exact(lnpsi)
+    return float(w @ eloc), lnpsi, eloc
+
+
+def test_O_matches_finite_differences():
+    n, na, nb, nh = 4, 2, 2, 5
+    h, eri = synth.integrals(n, 2)
+    theta = synth.rbm_theta(n, nh, 2, sigma=0.3)
+    dets = fock.sector_dets(n, na, nb)
+    lnpsi, O, _, _ = native.rows(n, na, nb, nh, h, eri, theta, dets, want_g=False)
+    step = 1e-5
+    for k in range(theta.size):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += step
+        tm[k] -= step
+        lp = native.rows(n, na, nb, nh, h, eri, tp, dets, False, False)[0]
+        lmn = native.rows(n, na, nb, nh, h, eri, tm, dets, False, False)[0]
+        fd = (lp - lmn) / (2 * step)
+        assert np.abs(fd - O[:, k + 1]).max() <= 1e-8 * max(1.0, np.abs(O[:, k + 1]).max())
+    assert (O[:, 0] == 1.0).all()
+
+
+def test_G_identity_with_finite_differences():
+    """G_k = E_loc O_k + d E_loc / d theta_k (the connected derivative of the local energy)."""
+    n, na, nb, nh = 4, 2, 1, 4
+    h, eri = synth.integrals(n, 4)
+    theta = synth.rbm_theta(n, nh, 4, sigma=0.3)
+    dets = fock.sector_dets(n, na, nb)
+    _, O, eloc, G = native.rows(n, na, nb, nh, h, eri, theta, dets)
+    step = 1e-5
+    for k in range(theta.size):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += step
+        tm[k] -= step
+        ep = native.rows(n, na, nb, nh, h, eri, tp, dets, False, False)[2]
+        em = native.rows(n, na, nb, nh, h, eri, tm, dets, False, False)[2]
+        rhs = eloc * O[:, k + 1] + (ep - em) / (2 * step)
+        assert np.abs(G[:, k + 1] - rhs).max() <= 1e-7 * max(1.0, np.abs(G[:, k + 1]).max())
+    assert np.abs(G[:, 0] - eloc).max() <= 1e-13 * np.abs(eloc).max()
+
+
+def test_pencil_equals_phi_route():
+    """Exact enumeration: H~' = Phi^T (H - E) Phi with Phi = psi O_c / |psi| (no G involved)."""
+    w0 = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, theta, _, _ = w0.inputs()
+    pd = lm.build_pencil(6, 3, 3, 24, h, eri, theta)
+    S, Hp = lm.pencil_matrices(pd.Oc, pd.Gpc, pd.w)
+    _, Hdet = _sector_matrix(6, 3, 3, h, eri)
+    psi = np.exp(pd.lnpsi - pd.lnpsi.max())
+    psi /= np.linalg.norm(psi)
+    Phi = psi[:, None] * pd.Oc
+    H2 = Phi.T @ Hdet @ Phi - pd.E * (Phi.T @ Phi)
+    assert np.abs(H2 - Hp).max() <= 1e-12 * np.abs(Hp).max()
+    assert np.abs(Phi.T @ Phi - S).max() <= 1e-12 * np.abs(S).max()
+    assert pd.E == pytest.approx(float(psi @ Hdet @ psi), rel=1e-13)
+
+
+def test_pencil_structure_and_null_space():
+    w0 = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, theta, _, _ = w0.inputs()
+    theta = synth.rbm_theta(6, 24, 5, sigma=0.2)
+    pd = lm.build_pencil(6, 3, 3, 24, h, eri, theta)
+    S, Hp = lm.pencil_matrices(pd.Oc, pd.Gpc, pd.w)
+    nrm = np.abs(S).max()
+    assert np.abs(S - S.T).max() <= 1e-14 * nrm
+    assert np.linalg.eigvalsh(S)[0] >= -1e-13 * nrm
+    assert S[0, 0] == pytest.approx(1.0, abs=1e-14)
+    assert np.abs(S[0, 1:]).max() <= 1e-13
+    assert abs(Hp[0, 0]) <= 1e-12 * np.abs(Hp).max()
+    assert np.abs(Hp - Hp.T).max() <= 1e-12 * np.abs(Hp).max()
+    nb = lm.null_vectors(6, 3, 3, 24)
+    assert nb.shape[1] == 2 * 25
+    assert np.abs(S @ nb).max() <= 1e-12 * nrm
+    assert np.abs(Hp @ nb).max() <= 1e-11 * np.abs(Hp).max()
+
+
+def test_gradient_row_is_energy_gradient():
+    """2 H~'_{k0} = dE/dtheta_k for exact enumeration (central differences of E(theta))."""
+    n, na, nb, nh = 4, 2, 2, 3
+    h, eri = synth.integrals(n, 8)
+    theta = synth.rbm_theta(n, nh, 8, sigma=0.3)
+    pd = lm.build_pencil(n, na, nb, nh, h, eri, theta)
+    _, Hp = lm.pencil_matrices(pd.Oc, pd.Gpc, pd.w)
+    step = 1e-5
+    for k in range(theta.size):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += step
+        tm[k] -= step
+        fd = (_exact_energy_and_eloc(tp, n, na, nb, nh, h, eri)[0]
+              - _exact_energy_and_eloc(tm, n, na, nb, nh, h, eri)[0]) / (2 * step)
+        assert 2 * Hp[k + 1, 0] == pytest.approx(fd, rel=1e-8, abs=1e-9)
+
+
+def test_gevp_is_variational_and_shep_nonpositive():
+    w0 = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, theta, _, _ = w0.inputs()
+    r = lm.lm_step(6, 3, 3, 24, h, eri, theta)
+    _, Hdet = _sector_matrix(6, 3, 3, h, eri)
+    efci = np.linalg.eigvalsh(Hdet)[0]
+    assert efci - 1e-10 <= r["E"] + r["lam_gen"] <= r["E"] + 1e-12
+    assert r["lam"] <= 1e-14
+    assert r["lam"] == pytest.approx(np.linalg.eigvalsh(0.5 * (r["Hp"] + r["Hp"].T))[0], rel=1e-13)
+
+
+@pytest.mark.parametrize("n,na,nb,nh,sigma,tol", [(2, 1, 1, 2, 0.5, 1e-10),
+                                                  (4, 2, 2, 8, 0.3, 1e-10),
+                                                  (6, 2, 2, 24, 0.2, 1e-9)])
+def test_gevp_exact_when_tangent_space_spans_sector(n, na, nb, nh, sigma, tol):
+    """If the kept range of S~ spans the whole sector, E + lambda_gen is the FCI energy.
+
+    The LiH-shaped case (6 orbitals, 4 electrons, 225 determinants, 325 columns)
+    has S~ condition ~1e8 on the sector, so its bound is looser."""
+    h, eri = synth.integrals(n, 21)
+    theta = synth.rbm_theta(n, nh, 21, sigma=sigma)
+    pd = lm.build_pencil(n, na, nb, nh, h, eri, theta)
+    S, _ = lm.pencil_matrices(pd.Oc, pd.Gpc, pd.w)
+    ev = np.linalg.eigvalsh(S)
+    assert (ev > 1e-12 * ev.max()).sum() == len(pd.rows)
+    r = lm.lm_step(n, na, nb, nh, h, eri, theta)
+    _, Hdet = _sector_matrix(n, na, nb, h, eri)
+    efci = np.linalg.eigvalsh(Hdet)[0]
+    assert r["E"] + r["lam_gen"] == pytest.approx(efci, abs=tol)
+
+
+def test_splitmix64_reference_value():
+    """SplitMix64 with state 0: first output 0xE220A8397B1DCDAF (published test vector)."""
+    u = irl.splitmix64_uniform(0, 1)[0]
+    z = 0xE220A8397B1DCDAF
+    assert u == 2.0 * ((z >> 11) * 2.0 ** -53) - 1.0
+
+
+def test_implicit_qr_sweep_properties():
+    rng = np.random.default_rng(0)
+    m = 12
+    a = rng.standard_normal(m)
+    b = rng.random(m - 1) + 0.1
+    T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+    ev = np.linalg.eigvalsh(T)
+    a2, b2, Q = a.copy(), b.copy(), np.eye(m)
+    irl.implicit_qr_sweep(a2, b2, ev[-1], Q)
+    T2 = np.diag(a2) + np.diag(b2, 1) + np.diag(b2, -1)
+    assert np.abs(Q.T @ Q - np.eye(m)).max() < 1e-14
+    assert np.abs(Q.T @ T @ Q - T2).max() < 1e-13
+    # an exact shift deflates the last row: T2[m-1, m-2] ~ 0 and T2[m-1, m-1] = shift
+    assert abs(b2[-1]) < 1e-9 and a2[-1] == pytest.approx(ev[-1], abs=1e-9)
+    # the first column of Q is proportional to (T - nu I) e_1
+    q1 = (T - ev[-1] * np.eye(m))[:, 0]
+    q1 /= np.linalg.norm(q1)
+    assert abs(abs(q1 @ Q[:, 0]) - 1.0) < 1e-13
+
+
+def test_irl_laplacian_closed_form():
+    """1-D Laplacian tridiag(-1, 2, -1): lowest eigenvalue 2 - 2 cos(pi / (N+1))."""
+    N = 120
+    A = 2 * np.eye(N) - np.eye(N, k=1) - np.eye(N, k=-1)
+    r = irl.irl_lowest(lambda v: A @ v, N, m=40, k=8, tol=1e-12, max_restarts=2000)
+    assert r["status"] == irl.IRL_OK
+    assert r["lam"] == pytest.approx(2 - 2 * math.cos(math.pi / (N + 1)), abs=1e-12)
+    assert np.linalg.norm(A @ r["y"] - r["lam"] * r["y"]) < 1e-11
+
+
+def test_irl_diagonal_with_gap_and_random_symmetric():
+    rng = np.random.default_rng(3)
+    d = np.concatenate([[-5.0], rng.uniform(0, 10, 299)])
+    r = irl.irl_lowest(lambda v: d * v, 300, m=20, k=1)
+    assert r["lam"] == pytest.approx(-5.0, abs=1e-12)
+    X = rng.standard_normal((200, 200))
+    A = (X + X.T) / 2
+    r = irl.irl_lowest(lambda v: A @ v, 200, m=30, k=5, max_restarts=500)
+    assert r["lam"] == pytest.approx(np.linalg.eigvalsh(A)[0], abs=1e-11)
+
+
+def test_irl_on_pencil_matches_dense_shep():
+    w0 = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, theta, _, _ = w0.inputs()
+    theta = synth.rbm_theta(6, 24, 9, sigma=0.3)
+    r = lm.lm_step(6, 3, 3, 24, h, eri, theta)
+    Hs = 0.5 * (r["Hp"] + r["Hp"].T)
+    nb = lm.null_vectors(6, 3, 3, 24)
+    res = irl.irl_lowest(lambda v: Hs @ v, Hs.shape[0], m=20, k=1, null_basis=nb)
+    assert res["lam"] == pytest.approx(r["lam"], rel=1e-12)
