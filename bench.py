@@ -1,0 +1,353 @@
+"""Benchmark: LM steps/s of the IRL linear-method hot path on GB300.
+
+One step = one LM step of the F2-shaped workload (10 spatial orbitals,
+14 electrons, all 14,400 Sz=0 determinants, RBM with Nh=40 so P=860, FP64):
+rebuild O_c, G'_c from the current theta, solve the SHEP by IRL (m=30, k=10,
+tol=1e-12), refine, and apply theta += Delta theta. theta follows 5-step LM
+trajectories from the seeded start (reset every 5 steps), so every timed step
+is a real step of the optimisation.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload NAME] [--no-cpu-baseline]
+
+Under torchrun every rank runs its own replica (independent instance, seed
+111 + rank); value = all ranks' steps / max elapsed. The reference arm is the
+FP64 CPU oracle (explicit S~ and H~', dense eigensolves) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "LM steps/sec"
+UNIT = "LM steps/s"
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.20  # project probe: DFMA throughput on this machine's GB300 (FP64 ALU roofline)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="f2_10o14e")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+def algorithmic_units(w):
+    """Per-launch algorithmic work of the two dominant kernels (formulas in the design doc)."""
+    n, na, nb, nh = w.n_orb, w.n_alpha, w.n_beta, w.n_hidden
+    va, vb = n - na, n - nb
+    singles = na * va + nb * vb
+    doubles = (na * (na - 1) // 2) * (va * (va - 1) // 2) + \
+              (nb * (nb - 1) // 2) * (vb * (vb - 1) // 2) + na * va * nb * vb
+    # FP64 flops of the row build per determinant row:
+    #   singles: Nh*9 (ratio, tanh) + (Nh+1)*4 (accumulate); doubles: Nh*13 + (Nh+1)*6
+    flops_row = singles * (nh * 9 + (nh + 1) * 4) + doubles * (nh * 13 + (nh + 1) * 6)
+    build_flops = flops_row * w.n_rows
+    P1 = (nh + 1) * (2 * n + 1)
+    bytes_for = {"f64": 16, "f32": 8, "bf16": 4}
+    pencil_bytes = w.n_rows * P1 * bytes_for[w.precision] + 8 * w.n_rows
+    return build_flops, pencil_bytes
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2601_01437_gb300 import abi
+
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload]
+    if world > 1:
+        w = synth.Workload(**{**w.__dict__, "seed": w.seed + rank})
+    h, eri, th0, rows, counts = w.inputs()
+    prec = {"f64": abi.LM_FP64, "f32": abi.LM_FP32, "bf16": abi.LM_BF16}[w.precision]
+    dev = torch.device("cuda", local)
+    s = torch.cuda.Stream(device=dev)
+    h_d = torch.from_numpy(h).to(dev)
+    eri_d = torch.from_numpy(eri).to(dev)
+    th0_d = torch.from_numpy(th0).to(dev)
+    theta = th0_d.clone()
+    rows_d = None if rows is None else torch.from_numpy(rows.view(np.int64)).to(dev)
+    wts_d = None if counts is None else torch.from_numpy(counts.astype(np.float64)).to(dev)
+    dth = torch.zeros(w.n_params, dtype=torch.float64, device=dev)
+    ctx = abi.Context(local)
+    sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h_d, eri_d)
+    state = {"pen": None, "res": None}
+    torch.cuda.synchronize()
+
+    def lm_step(i):
+        if i % w.lm_steps == 0:
+            with torch.cuda.stream(s):
+                theta.copy_(th0_d)
+        state["pen"] = ctx.build_OG(sysd, theta, rows=rows_d, weights=wts_d,
+                                    n_rows=w.n_rows, prec=prec, stream=s, pencil=state["pen"])
+        state["res"] = state["pen"].irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200,
+                                             prec=prec, dtheta_out=dth, theta_inout=theta,
+                                             stream=s)
+
+    for i in range(args.warmup):
+        lm_step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.stats_reset(profile=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(s)
+    for i in range(args.steps):
+        lm_step(args.warmup + i)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    st = ctx.stats()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    res = state["res"]
+    out = {
+        "metric": METRIC, "value": args.steps * world / (ms / 1e3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": w.precision, "data": "synthetic",
+        "config": {
+            "workload": (f"{w.name}: {w.n_orb} spatial orbitals, {w.n_alpha + w.n_beta} electrons, "
+                         f"{w.n_rows} {'determinants (exact sector)' if w.exact else 'MC rows'}, "
+                         f"RBM Nh={w.n_hidden} (P={w.n_params}), {w.lm_steps}-step LM "
+                         f"trajectories, IRL m={w.m} k={w.k} tol={w.tol:g}"),
+            "l2": "inputs larger than L2: O_c+G'_c "
+                  f"{w.n_rows * (w.n_params + 1) * 16 / 1e6:.0f} MB FP64 vs 129 MB L2",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        },
+        "clocks": clk,
+        "gpu_launches": int(st.launches),
+        "last_step": {"energy": res.energy, "lambda": res.lambda_, "status": res.status,
+                      "n_matvec": res.n_matvec, "n_restart": res.n_restart,
+                      "residual": res.residual},
+    }
+    # roofline of the dominant kernel, live CUDA-event durations over the timed region
+    build_flops, pencil_bytes = algorithmic_units(w)
+    hbm, hbm_src = peaks()
+    kern = {}
+    if st.build_count:
+        d = st.build_ms / st.build_count / 1e3
+        ach = build_flops / d / 1e12
+        kern["build"] = {"kernel": "k_build_rows", "bound": "alu", "achieved": ach,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "traffic": None, "avg_ms": d * 1e3, "launches": int(st.build_count),
+                         "total_ms": st.build_ms,
+                         "peak_source": "FP64 DFMA throughput measured by the project probe"}
+    if st.pencil_count:
+        d = st.pencil_ms / st.pencil_count / 1e3
+        ach = pencil_bytes / d / 1e9
+        kern["pencil"] = {"kernel": "k_pencil", "bound": "hbm", "achieved": ach, "peak": hbm,
+                          "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                          "avg_ms": d * 1e3, "launches": int(st.pencil_count),
+                          "total_ms": st.pencil_ms, "peak_source": f"{hbm_src} hbm_gbs"}
+    if kern:
+        dom = max(kern, key=lambda k: kern[k]["total_ms"])
+        out["roofline"] = {k: v for k, v in kern[dom].items()
+                           if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+        out["roofline"]["kernel"] = kern[dom]["kernel"]
+        out["kernels"] = kern
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    if not args.no_e2e:
+        h_p = torch.from_numpy(h).pin_memory().numpy()
+        eri_p = torch.from_numpy(eri).pin_memory().numpy()
+        th_p = torch.from_numpy(th0).pin_memory().numpy()
+        th0_np = th0.copy()
+        dth_p = torch.zeros(w.n_params, dtype=torch.float64).pin_memory().numpy()
+        rows_p = None if rows is None else torch.from_numpy(rows.view(np.int64)).pin_memory().numpy()
+        wts_p = None if counts is None else torch.from_numpy(counts.astype(np.float64)).pin_memory().numpy()
+        sysh = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h_p, eri_p)
+        pen2 = None
+        last = {}
+
+        def e2e_step(i):
+            nonlocal pen2
+            if i % w.lm_steps == 0:
+                th_p[:] = th0_np
+            pen2 = ctx.build_OG(sysh, th_p, rows=rows_p, weights=wts_p, n_rows=w.n_rows,
+                                prec=prec, stream=s, pencil=pen2)
+            r = pen2.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200, prec=prec,
+                              dtheta_out=dth_p, theta_inout=th_p, stream=s)
+            last["lambda"] = r.lambda_
+
+        for i in range(args.warmup):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            e2e_step(args.warmup + i)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        h2d = h.nbytes + eri.nbytes + th0.nbytes + (0 if rows is None else rows.nbytes) + \
+            (0 if counts is None else counts.size * 8)
+        d2h = 2 * th0.nbytes + 72
+        out["e2e"] = {"value": args.steps * world / el, "unit": UNIT,
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        pen2.free()
+    state["pen"].free()
+    ctx.close()
+    return out
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+def oracle_steps(w, n_steps, rank=0):
+    """Time full oracle LM steps on the host cores; returns (steps/s, cores, seconds)."""
+    import oracle  # test infrastructure: used here only for the CPU baseline / reference arm
+    h, eri, th0, rows, counts = w.inputs()
+    theta = th0.copy()
+    t0 = time.perf_counter()
+    for i in range(n_steps):
+        if i % w.lm_steps == 0:
+            theta = th0.copy()
+        r = oracle.lm.lm_step(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, theta,
+                              rows, counts)
+        if r["dtheta"] is not None:
+            theta = theta + r["dtheta"]
+    el = time.perf_counter() - t0
+    return n_steps / el, os.cpu_count(), el
+
+
+def cpu_sample(w):
+    return (f"{w.name}: full oracle LM steps (C per-row O/G build of all {w.n_rows} rows with "
+            f"OpenMP, explicit S~ and H~' with BLAS, dense SHEP and deflated GEVP with LAPACK)")
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sps, cores, el = oracle_steps(w, args.warmup + args.steps)
+        line = {"impl": "reference", "metric": METRIC, "value": sps, "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / sps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w.name},
+                "cpu_baseline": {"value": sps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": cpu_sample(w) + f"; {args.warmup + args.steps} steps"},
+                "e2e": {"value": sps, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    out = run_gpu(args, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            n = 2 if w.n_rows <= 20000 else 1
+            sps, cores, el = oracle_steps(w, n)
+            out["cpu_baseline"] = {"value": sps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": cpu_sample(w) + f"; {n} steps in {el:.1f} s"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

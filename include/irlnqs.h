@@ -1,0 +1,227 @@
+/*
+ * irlnqs.h — C ABI of the GB300 (sm_103a) library for the data-parallel hot
+ * path of the implicitly restarted Lanczos (IRL) optimiser for shallow neural
+ * quantum states (arXiv 2601.01437).
+ *
+ * The path has two halves:
+ *   1. lm_build_OG: over bit-packed determinants of a second-quantised
+ *      molecular Hamiltonian, build the per-row log-derivative matrix
+ *      O_k(x) = d ln psi(x) / d theta_k of an RBM wavefunction and the
+ *      Hamiltonian-applied matrix G_k(x) = sum_x' H_xx' psi(x')/psi(x) O_k(x'),
+ *      then the weights, the energy E and the centred pencil factors.
+ *   2. lm_apply_pencil / irl_step: apply the centred linear-method pencil
+ *      matrix-free, y_H = O_c^T W (G'_c v) and y_S = O_c^T W (O_c v), inside
+ *      device-resident implicitly restarted Lanczos, and return the lowest
+ *      Ritz pair and the parameter update.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Determinants: uint64, bit p = occupation of spin orbital p, blocked order
+ *   (spin orbitals 0..n-1 alpha, n..2n-1 beta; spatial orbital p mod n).
+ * RBM: ln psi(x) = a.x + sum_j ln(2 cosh(b_j + W_j.x)), M = 2n visible,
+ *   Nh hidden, P = M + Nh + M*Nh parameters.
+ * Augmented index space (the linear method's basis chi_0 = psi,
+ *   chi_k = (O_k - <O_k>) psi; Methods, eqs. rayleigh_quotient/full_gevp):
+ *   dimension P+1 = (Nh+1)(M+1), row-major over the grid (r, c), r in [0,Nh],
+ *   c in [0,M]. Entry (0,0) is chi_0. theta is this grid without (0,0):
+ *   theta[0..M) = a; theta[(j+1)(M+1)-1] = b_j; theta[(j+1)(M+1)+p] = W_jp.
+ * Pointers: every input or output array may be host or device memory; the
+ *   library detects which with cudaPointerGetAttributes. The caller owns
+ *   every pointer it passes; the library owns everything behind a handle.
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   Calls enqueue their work on it; results written to host memory are valid
+ *   when the call returns (those calls synchronise the stream).
+ * Errors: every function returns an int status (0 = LM_OK). Nothing throws
+ *   across the ABI. lm_last_error gives a one-line description of the last
+ *   failure on a context.
+ * Limits: M = 2*n_orb <= 64, Nh <= 127, P+1 <= 2048, Krylov dimension m <= 64.
+ */
+#ifndef IRLNQS_H
+#define IRLNQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+    LM_OK = 0,
+    LM_ERR_ARG = -1,     /* null pointer, bad enum, rows outside the sector */
+    LM_ERR_SIZE = -2,    /* M > 64, N_alpha > n_orb, m > 64, ...            */
+    LM_ERR_OOM = -3,     /* device allocation failed                        */
+    LM_ERR_CUDA = -4,    /* a CUDA runtime call or kernel launch failed     */
+    LM_ERR_TIMEOUT = -5  /* a bounded device wait gave up                   */
+};
+
+/* irl_result.status (Algorithm 1 outcomes and the update's validity) */
+enum {
+    IRL_OK = 0,                  /* residual below tolerance                  */
+    IRL_BREAKDOWN_INVARIANT = 1, /* beta_j ~ 0: invariant subspace, exact Ritz */
+    IRL_MAX_RESTARTS = 2,        /* restart budget exhausted (best pair kept) */
+    LM_C0_TINY = 3,              /* |c_0| < 1e-8 |c|: no update written       */
+    LM_STATIONARY = 4            /* lambda_min > -tol: theta is stationary    */
+};
+
+typedef enum { LM_FP64 = 0, LM_FP32 = 1, LM_BF16 = 2 } lm_precision;
+
+/* symmetrisation of H~' inside the Lanczos operator */
+typedef enum {
+    LM_SYM_AUTO = 0, /* NONE for the full enumerated sector, HALF otherwise    */
+    LM_SYM_NONE = 1, /* y = O_c^T W G'_c v                                     */
+    LM_SYM_HALF = 2  /* y = 1/2 (O_c^T W G'_c v + G'_c^T W O_c v)              */
+} lm_sym;
+
+typedef struct lm_ctx lm_ctx;
+typedef struct lm_pencil lm_pencil;
+
+/* Second-quantised Hamiltonian (Methods, "Wave Function Ansatz"):
+ * H = sum_{pq,s} h_pq a+_ps a_qs + 1/2 sum_{pqrs,s,t} (pq|rs) a+_ps a+_rt a_st a_qs.
+ * h: n_orb x n_orb real symmetric; eri: n_orb^4 chemist (pq|rs) with 8-fold
+ * symmetry, index ((p*n+q)*n+r)*n+s. Both are read during lm_build_OG only. */
+typedef struct {
+    int n_orb, n_alpha, n_beta, n_hidden;
+    const double *h;
+    const double *eri;
+    double e_core; /* added to E and E_loc */
+} lm_system;
+
+typedef struct {
+    int64_t n_rows;       /* N_s */
+    int n_params;         /* P */
+    int ld;               /* padded row length of O_c, G'_c (>= P+1, multiple of 8) */
+    int precision;        /* lm_precision of the low-precision copy (FP64: none) */
+    int sym;              /* resolved lm_sym */
+    double energy;        /* E(theta) = sum_x w(x) E_loc(x), including e_core */
+} lm_pencil_info;
+
+/* IRL settings (Algorithm 1; the paper uses k = 1, m = 20, tol = 1e-12). */
+typedef struct {
+    int m;              /* Krylov dimension, k < m <= 64                          */
+    int k;              /* kept Ritz pairs per restart (mu = m - k shifts)        */
+    double tol;         /* absolute residual tolerance on ||H y - lambda y||      */
+    int max_restarts;   /* restart budget (the paper gives none; 200 is typical)  */
+    uint64_t seed;      /* SplitMix64 seed of the random start vector             */
+    int sym;            /* lm_sym (AUTO resolves as for the pencil)               */
+    int precision;      /* lm_precision of the Lanczos operator; a low-precision  */
+                        /* solve is refined by FP64 restarts before returning     */
+    int deflate_null;   /* 1: remove the particle-number null space of O_c        */
+    const double *v0;   /* optional start vector (P+1), NULL = random             */
+} irl_params;
+
+typedef struct {
+    double lambda;        /* lowest Ritz value of the SHEP (eq. standard_evp)     */
+    double energy;        /* E(theta)                                             */
+    double lambda_gen_rq; /* generalised Rayleigh quotient c^T H~' c / c^T S~ c   */
+    double residual;      /* explicit FP64 ||H~' c - lambda c||, |c| = 1          */
+    double c0;            /* c[0] of the unit Ritz vector (sign fixed c0 >= 0)    */
+    int status;           /* IRL_* / LM_* above                                   */
+    int n_matvec;         /* pencil applications (all precisions)                 */
+    int n_restart;        /* implicit restarts                                    */
+    int n_matvec_lowp;    /* of which in the low-precision phase                  */
+} irl_result;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (made current for every call).
+ * *out receives the handle; free it with lm_destroy. */
+int lm_create(lm_ctx **out, int device);
+int lm_destroy(lm_ctx *ctx);
+/* Description of the last failure on ctx (never NULL; "" after success). */
+const char *lm_last_error(const lm_ctx *ctx);
+
+/* ---- the hot path ------------------------------------------------------ */
+
+/*
+ * Build the centred pencil factors (Methods: E_loc, O, eqs. heff and
+ * centered_hamiltonian; the energy-centring step H' = H - E).
+ *   rows    N_s determinants, or NULL to enumerate the whole (N_alpha, N_beta)
+ *           sector in ascending order (its size must equal n_rows; pass
+ *           n_rows = 0 to let the library size it).
+ *   weights N_s non-negative sample weights (e.g. Monte Carlo multiplicities),
+ *           normalised by their sum; NULL = |psi(x)|^2 / sum |psi|^2.
+ *   prec    FP64 only, or FP64 plus an FP32 / BF16 copy of O_c and G'_c for
+ *           low-precision Lanczos.
+ * Layout on the device: O_c, G'_c row-major N_s x ld FP64 (columns >= P+1 zero),
+ *   O_c(x,0) = 1, G'_c(x,0) = E_loc(x) - E, and for k >= 1
+ *   O_c(x,k) = O_k(x) - <O_k>, G'_c(x,k) = G_k(x) - <O_k> E_loc(x) - E O_c(x,k).
+ * *inout: NULL to create a pencil, or an existing pencil of the same system
+ *   and row count to rebuild in place (buffers are reused).
+ * Errors: LM_ERR_SIZE for M > 64 or Nh > 256 or bad electron counts;
+ *   LM_ERR_ARG if a given row lies outside the sector (detected on the device,
+ *   reported by this call).
+ */
+int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *theta, const uint64_t *rows,
+                const double *weights, int64_t n_rows, lm_precision prec, void *stream,
+                lm_pencil **inout);
+
+/*
+ * Matrix-free pencil product (Methods, eq. matrix_vec_prod, with the G form of
+ * eq. heff): Hv = H~' v (symmetrised per `sym`), Sv = S~ v, both P+1 FP64.
+ * v: P+1 FP64. Either output may be NULL. `prec` selects the FP64 factors or
+ * the pencil's low-precision copy. Reads O_c and G'_c once.
+ */
+int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double *Sv, int sym, int prec,
+                    void *stream);
+
+/*
+ * Lowest eigenpair of the SHEP H~' c = lambda c (eq. standard_evp) by
+ * implicitly restarted Lanczos (Algorithms 1 and 2) with full FP64
+ * reorthogonalisation, followed by an explicit FP64 residual / Rayleigh
+ * refinement. Writes (all optional, host or device):
+ *   c_out      P+1, unit Ritz vector with c[0] >= 0;
+ *   dtheta_out P,   the update c[1:]/c[0] (linearised wavefunction, c = [1, v]);
+ *   theta_inout P,  theta += dtheta when status is IRL_OK/BREAKDOWN.
+ * out receives the result record (host memory). Returns LM_ERR_* on failure;
+ * the IRL outcome itself is out->status.
+ */
+int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, double *c_out,
+             double *dtheta_out, double *theta_inout, void *stream);
+
+int lm_pencil_info_get(lm_pencil *p, lm_pencil_info *out);
+int lm_pencil_free(lm_pencil *p);
+
+/* ---- inspection (tests and tools; not on the timed path) -------------- */
+
+/* Enumerate the (n_alpha, n_beta) sector in ascending order into out
+ * (capacity cap); *count receives the sector size. (Methods, Fock
+ * expansion restricted to fixed N_up, N_down.) */
+int lm_enumerate_sector(lm_ctx *ctx, int n_orb, int n_alpha, int n_beta, uint64_t *out,
+                        int64_t cap, int64_t *count);
+
+/* Connected determinants of each row, as the build kernel enumerates them:
+ * for row i, entries [i*cap, i*cap + count[i]) of out_det / out_sign /
+ * out_h hold x', the Jordan-Wigner sign of the excitation operator and
+ * <x'|H|x>; entry 0 is the diagonal. Slater-Condon rules with parity. */
+int lm_debug_connections(lm_ctx *ctx, const lm_system *sys, const uint64_t *rows, int64_t n_rows,
+                         int cap, uint64_t *out_det, int8_t *out_sign, double *out_h,
+                         int32_t *count);
+
+/* Copy a pencil array out as FP64 (host or device destination):
+ * what = 0 O_c (N_s x ld), 1 G'_c (N_s x ld), 2 ln psi (N_s), 3 E_loc (N_s),
+ *        4 normalised weights (N_s), 5 mean O (ld), 6 rows (N_s, as uint64 bits). */
+int lm_pencil_export(lm_pencil *p, int what, void *dst, void *stream);
+
+/* ---- counters (benchmarking; not on the math path) -------------------- */
+
+typedef struct {
+    int64_t launches;      /* kernels this context launched since the last reset */
+    double build_ms;       /* summed device time of the row-build kernel launches */
+    int64_t build_count;
+    double pencil_ms;      /* summed device time of the pencil kernel launches    */
+    int64_t pencil_count;
+    int64_t pencil_rows;   /* rows streamed by those pencil launches               */
+} lm_stats;
+
+/* Reset the counters; profile = 1 also brackets every row-build and pencil
+ * launch with CUDA events (recorded on the launch stream) until the next
+ * reset. lm_stats_get synchronises the device before reading the events. */
+int lm_stats_reset(lm_ctx *ctx, int profile);
+int lm_stats_get(lm_ctx *ctx, lm_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IRLNQS_H */

@@ -1,0 +1,248 @@
+"""ctypes binding of include/irlnqs.h: the same entry points, argument marshalling only.
+
+Every array argument may be a ``torch.Tensor`` (host or CUDA) or a NumPy
+array; the library detects host versus device memory itself. Streams are
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers, or ``None``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libirlnqs.so")
+
+LM_OK, LM_ERR_ARG, LM_ERR_SIZE, LM_ERR_OOM, LM_ERR_CUDA, LM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+IRL_OK, IRL_BREAKDOWN_INVARIANT, IRL_MAX_RESTARTS, LM_C0_TINY, LM_STATIONARY = 0, 1, 2, 3, 4
+LM_FP64, LM_FP32, LM_BF16 = 0, 1, 2
+LM_SYM_AUTO, LM_SYM_NONE, LM_SYM_HALF = 0, 1, 2
+EXPORT_O, EXPORT_G, EXPORT_LNPSI, EXPORT_ELOC, EXPORT_W, EXPORT_OBAR, EXPORT_ROWS = range(7)
+
+c_int, c_double, c_int64, c_uint64, c_vp = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                            ctypes.c_uint64, ctypes.c_void_p)
+
+
+class lm_system(ctypes.Structure):
+    _fields_ = [("n_orb", c_int), ("n_alpha", c_int), ("n_beta", c_int), ("n_hidden", c_int),
+                ("h", c_vp), ("eri", c_vp), ("e_core", c_double)]
+
+
+class lm_pencil_info(ctypes.Structure):
+    _fields_ = [("n_rows", c_int64), ("n_params", c_int), ("ld", c_int), ("precision", c_int),
+                ("sym", c_int), ("energy", c_double)]
+
+
+class irl_params(ctypes.Structure):
+    _fields_ = [("m", c_int), ("k", c_int), ("tol", c_double), ("max_restarts", c_int),
+                ("seed", c_uint64), ("sym", c_int), ("precision", c_int),
+                ("deflate_null", c_int), ("v0", c_vp)]
+
+
+class irl_result(ctypes.Structure):
+    _fields_ = [("lambda_", c_double), ("energy", c_double), ("lambda_gen_rq", c_double),
+                ("residual", c_double), ("c0", c_double), ("status", c_int),
+                ("n_matvec", c_int), ("n_restart", c_int), ("n_matvec_lowp", c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class lm_stats(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("build_ms", c_double), ("build_count", c_int64),
+                ("pencil_ms", c_double), ("pencil_count", c_int64), ("pencil_rows", c_int64)]
+
+
+_lib = None
+
+_SIGNATURES = {
+    "lm_create": (c_int, [ctypes.POINTER(c_vp), c_int]),
+    "lm_destroy": (c_int, [c_vp]),
+    "lm_last_error": (ctypes.c_char_p, [c_vp]),
+    "lm_build_OG": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_vp, c_vp, c_int64, c_int,
+                            c_vp, ctypes.POINTER(c_vp)]),
+    "lm_apply_pencil": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_vp]),
+    "irl_step": (c_int, [c_vp, ctypes.POINTER(irl_params), ctypes.POINTER(irl_result), c_vp,
+                         c_vp, c_vp, c_vp]),
+    "lm_pencil_info_get": (c_int, [c_vp, ctypes.POINTER(lm_pencil_info)]),
+    "lm_pencil_free": (c_int, [c_vp]),
+    "lm_enumerate_sector": (c_int, [c_vp, c_int, c_int, c_int, c_vp, c_int64,
+                                    ctypes.POINTER(c_int64)]),
+    "lm_debug_connections": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_int64, c_int, c_vp,
+                                     c_vp, c_vp, c_vp]),
+    "lm_pencil_export": (c_int, [c_vp, c_int, c_vp, c_vp]),
+    "lm_stats_reset": (c_int, [c_vp, c_int]),
+    "lm_stats_get": (c_int, [c_vp, ctypes.POINTER(lm_stats)]),
+}
+
+
+def lib():
+    """Load libirlnqs.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def ptr(x):
+    """Raw pointer of a tensor / array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class LMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class Context:
+    """lm_create / lm_destroy."""
+
+    def __init__(self, device: int = 0):
+        h = c_vp()
+        rc = lib().lm_create(ctypes.byref(h), device)
+        if rc != LM_OK:
+            raise LMError(rc, f"lm_create(device={device}) failed")
+        self.handle = h
+
+    def check(self, rc, what):
+        if rc != LM_OK:
+            raise LMError(rc, f"{what}: {lib().lm_last_error(self.handle).decode()}")
+
+    def close(self):
+        if self.handle:
+            lib().lm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def system(self, n_orb, n_alpha, n_beta, n_hidden, h, eri, e_core=0.0):
+        s = lm_system(n_orb, n_alpha, n_beta, n_hidden, ptr(h), ptr(eri), e_core)
+        s._keep = (h, eri)
+        return s
+
+    def build_OG(self, sys, theta, rows=None, weights=None, n_rows=0, prec=LM_FP64, stream=None,
+                 pencil=None):
+        """lm_build_OG; returns a Pencil (new, or the given one rebuilt in place)."""
+        h = c_vp(pencil.handle if pencil is not None else None)
+        if rows is not None and n_rows == 0:
+            n_rows = int(rows.shape[0])
+        rc = lib().lm_build_OG(self.handle, ctypes.byref(sys), ptr(theta), ptr(rows),
+                               ptr(weights), int(n_rows), int(prec), stream_handle(stream),
+                               ctypes.byref(h))
+        self.check(rc, "lm_build_OG")
+        if pencil is not None:
+            return pencil
+        return Pencil(self, h)
+
+    def stats_reset(self, profile=False):
+        self.check(lib().lm_stats_reset(self.handle, int(profile)), "lm_stats_reset")
+
+    def stats(self):
+        st = lm_stats()
+        self.check(lib().lm_stats_get(self.handle, ctypes.byref(st)), "lm_stats_get")
+        return st
+
+    def enumerate_sector(self, n_orb, n_alpha, n_beta):
+        cnt = c_int64()
+        self.check(lib().lm_enumerate_sector(self.handle, n_orb, n_alpha, n_beta, None, 0,
+                                             ctypes.byref(cnt)), "lm_enumerate_sector")
+        out = np.zeros(cnt.value, dtype=np.uint64)
+        self.check(lib().lm_enumerate_sector(self.handle, n_orb, n_alpha, n_beta, ptr(out),
+                                             cnt.value, ctypes.byref(cnt)), "lm_enumerate_sector")
+        return out
+
+    def debug_connections(self, sys, rows, cap):
+        rows = np.ascontiguousarray(rows, dtype=np.uint64)
+        n = rows.shape[0]
+        od = np.zeros((n, cap), dtype=np.uint64)
+        sg = np.zeros((n, cap), dtype=np.int8)
+        hv = np.zeros((n, cap))
+        cnt = np.zeros(n, dtype=np.int32)
+        self.check(lib().lm_debug_connections(self.handle, ctypes.byref(sys), ptr(rows), n, cap,
+                                              ptr(od), ptr(sg), ptr(hv), ptr(cnt)),
+                   "lm_debug_connections")
+        return od, sg, hv, cnt
+
+
+class Pencil:
+    """Handle of a built pencil: apply, irl_step, export, info, free."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle.value if isinstance(handle, c_vp) else handle
+
+    def info(self):
+        inf = lm_pencil_info()
+        self.ctx.check(lib().lm_pencil_info_get(self.handle, ctypes.byref(inf)), "info")
+        return inf
+
+    def apply(self, v, Hv=None, Sv=None, sym=LM_SYM_AUTO, prec=LM_FP64, stream=None):
+        rc = lib().lm_apply_pencil(self.handle, ptr(v), ptr(Hv), ptr(Sv), int(sym), int(prec),
+                                   stream_handle(stream))
+        self.ctx.check(rc, "lm_apply_pencil")
+
+    def irl_step(self, m=20, k=1, tol=1e-12, max_restarts=200, seed=111, sym=LM_SYM_AUTO,
+                 prec=LM_FP64, deflate_null=1, v0=None, c_out=None, dtheta_out=None,
+                 theta_inout=None, stream=None):
+        prm = irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null),
+                         ptr(v0))
+        res = irl_result()
+        rc = lib().irl_step(self.handle, ctypes.byref(prm), ctypes.byref(res), ptr(c_out),
+                            ptr(dtheta_out), ptr(theta_inout), stream_handle(stream))
+        self.ctx.check(rc, "irl_step")
+        return res
+
+    def export(self, what, out=None):
+        inf = self.info()
+        if out is None:
+            if what in (EXPORT_O, EXPORT_G):
+                out = np.zeros((inf.n_rows, inf.ld))
+            elif what == EXPORT_OBAR:
+                out = np.zeros(inf.ld)
+            elif what == EXPORT_ROWS:
+                out = np.zeros(inf.n_rows, dtype=np.uint64)
+            else:
+                out = np.zeros(inf.n_rows)
+        self.ctx.check(lib().lm_pencil_export(self.handle, int(what), ptr(out), None), "export")
+        return out
+
+    def free(self):
+        if self.handle:
+            lib().lm_pencil_free(self.handle)
+            self.handle = None

@@ -1,0 +1,703 @@
+// Build half of the hot path: rows -> O, E_loc, G -> weights, E, <O> -> centred
+// O_c and G'_c (arXiv 2601.01437, Methods: E_loc and O definitions, eqs. heff
+// and centered_hamiltonian, the energy-centring step H' = H - E).
+//
+// Layout: one determinant per uint64 (bit p = spin orbital p, alpha block
+// then beta block). O and G rows live on the augmented (Nh+1) x (M+1) grid,
+// row-major, padded to ldp columns (a multiple of 8, so every row starts on a
+// 64-byte boundary for FP64 and on 16 bytes for the low-precision copies).
+#include <cstdarg>
+
+#include "internal.cuh"
+
+namespace {
+
+// ----------------------------------------------------------------- helpers
+__device__ __forceinline__ uint64_t binom_dev(int n, int k) {
+    if (k < 0 || n < 0 || k > n) return 0;
+    uint64_t c = 1;
+    for (int i = 1; i <= k; ++i) c = c * (uint64_t)(n - k + i) / (uint64_t)i;
+    return c;
+}
+
+// k-subset of [0, n) with colex rank r (ascending bit-mask order).
+__device__ __forceinline__ uint64_t unrank_colex(int n, int k, uint64_t r) {
+    uint64_t x = 0;
+    for (int kk = k; kk >= 1; --kk) {
+        int c = kk - 1;
+        while (c + 1 < n && binom_dev(c + 1, kk) <= r) ++c;
+        x |= (1ull << c);
+        r -= binom_dev(c, kk);
+    }
+    return x;
+}
+
+// pair (lo < hi) with colex rank q
+__device__ __forceinline__ void unrank_pair(int q, int &lo, int &hi) {
+    int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)q)) * 0.5f);
+    while (y * (y - 1) / 2 > q) --y;
+    while ((y + 1) * y / 2 <= q) ++y;
+    hi = y;
+    lo = q - y * (y - 1) / 2;
+}
+
+__device__ __forceinline__ int parity_below(uint64_t x, int p) {
+    return __popcll(x & ((1ull << p) - 1ull)) & 1;
+}
+
+struct SysView {
+    int n, na, nb, nva, nvb;
+    int ns_a, ns_b, nd_aa, nd_bb, nd_ab, conn;
+    const double *h, *eri;
+};
+
+__device__ __forceinline__ double eri4(const SysView &S, int p, int q, int r, int s) {
+    return __ldg(S.eri + (((size_t)p * S.n + q) * S.n + r) * S.n + s);
+}
+
+// Occupied / empty spin orbitals of one determinant, ascending, per spin.
+struct RowLists {
+    int oa[32], va[32], ob[32], vb[32];
+};
+
+__device__ void make_lists(const SysView &S, uint64_t x, RowLists &L) {
+    int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    for (int p = 0; p < S.n; ++p) {
+        if ((x >> p) & 1ull) L.oa[c0++] = p; else L.va[c1++] = p;
+        int q = p + S.n;
+        if ((x >> q) & 1ull) L.ob[c2++] = q; else L.vb[c3++] = q;
+    }
+}
+
+struct Exc {
+    int i, j, a, b;  // removed i (< j), added a (< b); j = b = -1 for singles
+};
+
+// Connection k of the row (0 <= k < conn): singles alpha, singles beta,
+// doubles alpha-alpha, beta-beta, alpha-beta, each in a fixed nested order.
+__device__ __forceinline__ Exc decode_exc(const SysView &S, const RowLists &L, int k) {
+    Exc e;
+    e.j = -1;
+    e.b = -1;
+    if (k < S.ns_a) {
+        e.i = L.oa[k / S.nva];
+        e.a = L.va[k % S.nva];
+        return e;
+    }
+    k -= S.ns_a;
+    if (k < S.ns_b) {
+        e.i = L.ob[k / S.nvb];
+        e.a = L.vb[k % S.nvb];
+        return e;
+    }
+    k -= S.ns_b;
+    int lo, hi;
+    if (k < S.nd_aa) {
+        int nvp = S.nva * (S.nva - 1) / 2;
+        unrank_pair(k / nvp, lo, hi);
+        e.i = L.oa[lo];
+        e.j = L.oa[hi];
+        unrank_pair(k % nvp, lo, hi);
+        e.a = L.va[lo];
+        e.b = L.va[hi];
+        return e;
+    }
+    k -= S.nd_aa;
+    if (k < S.nd_bb) {
+        int nvp = S.nvb * (S.nvb - 1) / 2;
+        unrank_pair(k / nvp, lo, hi);
+        e.i = L.ob[lo];
+        e.j = L.ob[hi];
+        unrank_pair(k % nvp, lo, hi);
+        e.a = L.vb[lo];
+        e.b = L.vb[hi];
+        return e;
+    }
+    k -= S.nd_bb;
+    int nbe = S.nb * S.nvb;
+    int sa = k / nbe, sb = k % nbe;
+    e.i = L.oa[sa / S.nva];
+    e.a = L.va[sa % S.nva];
+    e.j = L.ob[sb / S.nvb];
+    e.b = L.vb[sb % S.nvb];
+    return e;
+}
+
+// Apply the excitation to x: x' and the Jordan-Wigner sign of a+_a a_i or
+// a+_a a+_b a_j a_i (operators applied right to left).
+__device__ __forceinline__ uint64_t apply_exc(uint64_t x, const Exc &e, int &sgn) {
+    int par = parity_below(x, e.i);
+    x ^= (1ull << e.i);
+    if (e.j >= 0) {
+        par += parity_below(x, e.j);
+        x ^= (1ull << e.j);
+        par += parity_below(x, e.b);
+        x |= (1ull << e.b);
+    }
+    par += parity_below(x, e.a);
+    x |= (1ull << e.a);
+    sgn = (par & 1) ? -1 : 1;
+    return x;
+}
+
+// <x'|H|x> without the sign (Slater-Condon rules, chemist integrals).
+__device__ __forceinline__ double exc_value(const SysView &S, const RowLists &L, const Exc &e) {
+    const int n = S.n;
+    if (e.j < 0) {
+        int sp = e.i >= n;
+        int ip = e.i - sp * n, ap = e.a - sp * n;
+        double v = __ldg(S.h + ap * n + ip);
+        for (int t = 0; t < S.na; ++t) {
+            int kp = L.oa[t];
+            v += eri4(S, ap, ip, kp, kp);
+            if (sp == 0) v -= eri4(S, ap, kp, kp, ip);
+        }
+        for (int t = 0; t < S.nb; ++t) {
+            int kp = L.ob[t] - n;
+            v += eri4(S, ap, ip, kp, kp);
+            if (sp == 1) v -= eri4(S, ap, kp, kp, ip);
+        }
+        return v;
+    }
+    int si = e.i >= n, sj = e.j >= n, sa = e.a >= n, sb = e.b >= n;
+    int ip = e.i - si * n, jp = e.j - sj * n, ap = e.a - sa * n, bp = e.b - sb * n;
+    double v = 0.0;
+    if (sa == si && sb == sj) v += eri4(S, ap, ip, bp, jp);
+    if (sa == sj && sb == si) v -= eri4(S, ap, jp, bp, ip);
+    return v;
+}
+
+// Diagonal <x|H|x> by one warp: sum_I h_II + 1/2 sum_{I,J} [(II|JJ) - d_s (IJ|JI)].
+__device__ double diag_value_warp(const SysView &S, const RowLists &L) {
+    const int lane = threadIdx.x & 31;
+    const int ne = S.na + S.nb;
+    double v = 0.0;
+    for (int t = lane; t < ne * ne; t += 32) {
+        int a = t / ne, b = t % ne;
+        int I = a < S.na ? L.oa[a] : L.ob[a - S.na];
+        int J = b < S.na ? L.oa[b] : L.ob[b - S.na];
+        int sI = I >= S.n, sJ = J >= S.n;
+        int ip = I - sI * S.n, jp = J - sJ * S.n;
+        double g = eri4(S, ip, ip, jp, jp);
+        if (sI == sJ) g -= eri4(S, ip, jp, jp, ip);
+        v += 0.5 * g;
+    }
+    for (int t = lane; t < ne; t += 32) {
+        int I = t < S.na ? L.oa[t] : L.ob[t - S.na];
+        int ip = I >= S.n ? I - S.n : I;
+        v += __ldg(S.h + ip * S.n + ip);
+    }
+    return warp_sum(v);
+}
+
+SysView make_view(int n, int na, int nb, const double *h, const double *eri) {
+    SysView S;
+    S.n = n;
+    S.na = na;
+    S.nb = nb;
+    S.nva = n - na;
+    S.nvb = n - nb;
+    S.ns_a = na * S.nva;
+    S.ns_b = nb * S.nvb;
+    S.nd_aa = (na * (na - 1) / 2) * (S.nva * (S.nva - 1) / 2);
+    S.nd_bb = (nb * (nb - 1) / 2) * (S.nvb * (S.nvb - 1) / 2);
+    S.nd_ab = S.ns_a * S.ns_b;
+    S.conn = S.ns_a + S.ns_b + S.nd_aa + S.nd_bb + S.nd_ab;
+    S.h = h;
+    S.eri = eri;
+    return S;
+}
+
+// --------------------------------------------------------- K1: enumeration
+// Index i = rank_beta * C(n, na) + rank_alpha gives the ascending order of
+// x = alpha_bits | beta_bits << n (colex rank = ascending mask order).
+__global__ void k_enumerate(int n, int na, int nb, uint64_t *out, int64_t count) {
+    const uint64_t ca = binom_dev(n, na);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t ra = (uint64_t)i % ca, rb = (uint64_t)i / ca;
+        out[i] = unrank_colex(n, na, ra) | (unrank_colex(n, nb, rb) << n);
+    }
+}
+
+// ------------------------------------------------------ theta-derived tables
+// tabs = [exp(W) (Nh x M) | exp(-W) (Nh x M) | exp(a) (M) | exp(-a) (M)]
+__global__ void k_tables(const double *theta, int M, int nh, double *tabs) {
+    const int M1 = M + 1;
+    const int tot = nh * M + M;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+        double w;
+        if (e < nh * M) {
+            int j = e / M, p = e % M;
+            w = theta[(j + 1) * M1 + p];
+            tabs[e] = exp(w);
+            tabs[nh * M + e] = exp(-w);
+        } else {
+            int p = e - nh * M;
+            w = theta[p];
+            tabs[2 * nh * M + p] = exp(w);
+            tabs[2 * nh * M + M + p] = exp(-w);
+        }
+    }
+}
+
+// ------------------------------------------------- K2-K6: fused row build
+struct BuildArgs {
+    SysView S;
+    int nh, M, M1, P1, ldp;
+    int ldF, ldS, nslice;
+    const double *theta, *tabs;
+    const uint64_t *rows;
+    int64_t n_rows;
+    uint64_t amask, bmask;
+    double e_core;
+    double *lnpsi, *eloc, *O, *G;
+    int *flags;
+};
+
+constexpr int BUILD_THREADS = 128;
+
+// One CTA per row (persistent over rows). Per row:
+//   z_j = b_j + W_j.x, t_j = tanh z_j, ln psi, O row = [1;t] (x) [1;x];
+//   every connection x' (Slater-Condon element with sign) contributes
+//   c = H_xx' psi(x')/psi(x), evaluated from tables as
+//   psi(x')/psi(x) = exp(a.dx) prod_j cosh(z_j + d_j)/cosh(z_j), with
+//   exp(+-d_j) products of exp(+-W_jp) over the moved orbitals, and
+//   tanh(z_j + d_j) from the same factors;
+//   G row = sum_x' c [1;t'] (x) [1;x'] accumulated sparsely: column 0 gets
+//   every term, column p+1 gets terms with x'_p = 1 (all minus those that
+//   remove p for occupied p; those that add p for empty p).
+__global__ void __launch_bounds__(BUILD_THREADS) k_build_rows(BuildArgs A) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    const int nh = A.nh, M = A.M, M1 = A.M1;
+    const int tid = threadIdx.x;
+    const int K = BUILD_THREADS;
+    // 16-byte aligned pieces first, then the FP64 arrays
+    int4 *sIdx = reinterpret_cast<int4 *>(smb);
+    RowLists *sL = reinterpret_cast<RowLists *>(sIdx + K);
+    double *sEW = reinterpret_cast<double *>(sL + 1);
+    double *sEWi = sEW + nh * M;
+    double *sea = sEWi + nh * M;
+    double *seai = sea + M;
+    double *sP = seai + M;
+    double *sQ = sP + nh;
+    double *sT = sQ + nh;
+    double *sF = sT + nh;
+    double *sC = sF + K * A.ldF;
+    double *sS = sC + K;
+    double *sA = sS + A.nslice * (nh + 1) * A.ldS;
+    double *sRed = sA + A.nslice * (nh + 1);
+    __shared__ double sDiag, sLn;
+    __shared__ int sBad;
+
+    for (int e = tid; e < 2 * nh * M + 2 * M; e += K) sEW[e] = A.tabs[e];
+    __syncthreads();
+
+    const int nsl = A.nslice;
+    const int sc_r = tid % (nh + 1), sc_s = tid / (nh + 1);
+    const bool scatter_thread = sc_s < nsl;
+
+    for (int64_t row = blockIdx.x; row < A.n_rows; row += gridDim.x) {
+        const uint64_t x = A.rows[row];
+        if (tid == 0) {
+            int bad = (__popcll(x & A.amask) != A.S.na) || (__popcll(x & A.bmask) != A.S.nb) ||
+                      (x & ~(A.amask | A.bmask)) != 0;
+            sBad = bad;
+            if (bad) atomicOr(A.flags, FLAG_ROW_OUTSIDE_SECTOR);
+            make_lists(A.S, x, *sL);
+        }
+        __syncthreads();
+        if (sBad) {
+            __syncthreads();
+            continue;
+        }
+        // hidden pre-activations
+        for (int j = tid; j < nh; j += K) {
+            double z = A.theta[(j + 1) * M1 - 1];
+            for (int p = 0; p < M; ++p)
+                if ((x >> p) & 1ull) z += A.theta[(j + 1) * M1 + p];
+            double az = fabs(z);
+            double e2 = exp(-2.0 * az);
+            double inv = 1.0 / (1.0 + e2);
+            double big = inv, small = e2 * inv;  // e^{|z|}/(2cosh z), e^{-|z|}/(2cosh z)
+            sP[j] = z >= 0.0 ? big : small;       // e^{z} / (2 cosh z)
+            sQ[j] = z >= 0.0 ? small : big;       // e^{-z} / (2 cosh z)
+            sT[j] = tanh(z);
+        }
+        for (int e = tid; e < nsl * (nh + 1) * A.ldS; e += K) sS[e] = 0.0;
+        __syncthreads();
+        if (tid < 32) {
+            // ln psi = a.x + sum_j ln(2 cosh z_j), ln(2cosh z) = |z| + log1p(e^{-2|z|})
+            double lp = 0.0;
+            for (int j = tid; j < nh; j += 32) {
+                double zz = A.theta[(j + 1) * M1 - 1];
+                for (int p = 0; p < M; ++p)
+                    if ((x >> p) & 1ull) zz += A.theta[(j + 1) * M1 + p];
+                lp += fabs(zz) + log1p(exp(-2.0 * fabs(zz)));
+            }
+            for (int p = tid; p < M; p += 32)
+                if ((x >> p) & 1ull) lp += A.theta[p];
+            lp = warp_sum(lp);
+            if (tid == 0) sLn = lp;
+        } else if (tid < 64) {
+            double d = diag_value_warp(A.S, *sL);
+            if (tid == 32) sDiag = d + A.e_core;
+        }
+        __syncthreads();
+
+        double el_part = 0.0;
+        double accA = 0.0;
+        const RowLists &L = *sL;
+        for (int k0 = 0; k0 < A.S.conn; k0 += K) {
+            const int k = k0 + tid;
+            if (k < A.S.conn) {
+                Exc e = decode_exc(A.S, L, k);
+                int sg;
+                (void)apply_exc(x, e, sg);
+                double hv = sg * exc_value(A.S, L, e);
+                const bool dbl = e.j >= 0;
+                double ead = sea[e.a] * seai[e.i];
+                if (dbl) ead *= sea[e.b] * seai[e.j];
+                double r = 1.0;
+                double *Frow = sF + tid * A.ldF;
+                for (int j = 0; j < nh; ++j) {
+                    const double *ew = sEW + j * M;
+                    const double *ewi = sEWi + j * M;
+                    double ep = ew[e.a] * ewi[e.i];
+                    double em = ewi[e.a] * ew[e.i];
+                    if (dbl) {
+                        ep *= ew[e.b] * ewi[e.j];
+                        em *= ewi[e.b] * ew[e.j];
+                    }
+                    double t1 = ep * sP[j];
+                    double q = fma(em, sQ[j], t1);   // cosh(z+d)/cosh(z)
+                    double nu = fma(-em, sQ[j], t1); // sinh(z+d)/cosh(z)
+                    r *= q;
+                    Frow[j] = nu / q;                // tanh(z+d)
+                }
+                double c = hv * ead * r;
+                sC[tid] = c;
+                sIdx[tid] = make_int4(e.i, e.j, e.a, e.b);
+                el_part += c;
+            }
+            __syncthreads();
+            if (scatter_thread) {
+                const int kend = min(K, A.S.conn - k0);
+                double *Srow = sS + (sc_s * (nh + 1) + sc_r) * A.ldS;
+                for (int kk = sc_s; kk < kend; kk += nsl) {
+                    double f = sC[kk];
+                    if (sc_r > 0) f *= sF[kk * A.ldF + sc_r - 1];
+                    int4 ix = sIdx[kk];
+                    accA += f;
+                    Srow[ix.x] += f;
+                    Srow[ix.z] += f;
+                    if (ix.y >= 0) {
+                        Srow[ix.y] += f;
+                        Srow[ix.w] += f;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (scatter_thread) sA[sc_s * (nh + 1) + sc_r] = accA;
+        // E_loc: fixed-order block reduction
+        el_part = warp_sum(el_part);
+        if ((tid & 31) == 0) sRed[32 + (tid >> 5)] = el_part;
+        __syncthreads();
+        if (tid == 0) {
+            double el = sDiag;
+            for (int w = 0; w < K / 32; ++w) el += sRed[32 + w];
+            A.eloc[row] = el;
+            A.lnpsi[row] = sLn;
+        }
+        // O row and G row
+        double *Orow = A.O + row * (int64_t)A.ldp;
+        double *Grow = A.G + row * (int64_t)A.ldp;
+        const double hd = sDiag;
+        for (int e = tid; e < A.ldp; e += K) {
+            double ov = 0.0, gv = 0.0;
+            if (e < A.P1) {
+                int r = e / M1, c = e % M1;
+                double u = (r == 0) ? 1.0 : sT[r - 1];
+                double xc = (c == 0) ? 1.0 : (double)((x >> (c - 1)) & 1ull);
+                ov = u * xc;
+                double at = hd * u;
+                for (int s = 0; s < nsl; ++s) at += sA[s * (nh + 1) + r];
+                if (c == 0) {
+                    gv = at;
+                } else {
+                    double sv = 0.0;
+                    for (int s = 0; s < nsl; ++s) sv += sS[(s * (nh + 1) + r) * A.ldS + c - 1];
+                    gv = ((x >> (c - 1)) & 1ull) ? at - sv : sv;
+                }
+            }
+            Orow[e] = ov;
+            Grow[e] = gv;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------ K7: weights and statistics
+// Max of ln psi (for the |psi|^2 weights' shift): per-CTA partial maxima.
+__global__ void k_lnpsi_max_partial(const double *lnpsi, int64_t n, double *part) {
+    double m = -INFINITY;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, lnpsi[i]);
+    m = warp_max(m);
+    __shared__ double s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s[w]);
+        m = fmax(m, s[0]);
+        part[blockIdx.x] = m;
+    }
+}
+
+// Per-CTA partial sums over a contiguous row chunk: sum w, sum w E_loc,
+// sum w O[:, c]. w = exp(2 (ln psi - max)) (|psi|^2 up to a constant) or the
+// given weight. Unnormalised weights are stored in wt.
+__global__ void k_stats_partial(const double *O, const double *lnpsi, const double *eloc,
+                                const double *given, double *wt, int64_t n, int ldp,
+                                const double *max_part, int n_max_part, double *part) {
+    __shared__ double sMax;
+    if (threadIdx.x == 0) {
+        double m = -INFINITY;
+        if (!given)
+            for (int b = 0; b < n_max_part; ++b) m = fmax(m, max_part[b]);
+        sMax = m;
+    }
+    __syncthreads();
+    const int64_t r0 = n * blockIdx.x / gridDim.x, r1 = n * (blockIdx.x + 1) / gridDim.x;
+    double *out = part + (int64_t)blockIdx.x * (ldp + 2);
+    for (int c = threadIdx.x; c < ldp; c += blockDim.x) {
+        double acc = 0.0;
+        for (int64_t r = r0; r < r1; ++r) {
+            double w = given ? given[r] : exp(2.0 * (lnpsi[r] - sMax));
+            acc = fma(w, O[r * ldp + c], acc);
+        }
+        out[c] = acc;
+    }
+    if (threadIdx.x == 0) {
+        double sw = 0.0, se = 0.0;
+        for (int64_t r = r0; r < r1; ++r) {
+            double w = given ? given[r] : exp(2.0 * (lnpsi[r] - sMax));
+            wt[r] = w;
+            sw += w;
+            se = fma(w, eloc[r], se);
+        }
+        out[ldp] = sw;
+        out[ldp + 1] = se;
+    }
+}
+
+// stats[0] = sum w, stats[1] = E, stats[8 + c] = <O_c>
+__global__ void k_stats_final(const double *part, int nparts, int ldp, double *stats) {
+    __shared__ double sw;
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int p = 0; p < nparts; ++p) {
+            a += part[(int64_t)p * (ldp + 2) + ldp];
+            b += part[(int64_t)p * (ldp + 2) + ldp + 1];
+        }
+        sw = a;
+        if (blockIdx.x == 0) {
+            stats[0] = a;
+            stats[1] = b / a;
+        }
+    }
+    __syncthreads();
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ldp) {
+        double a = 0.0;
+        for (int p = 0; p < nparts; ++p) a += part[(int64_t)p * (ldp + 2) + c];
+        stats[8 + c] = a / sw;
+    }
+}
+
+// Centre in place (FP64) and write the optional low-precision copies:
+//   O_c(x,0) = 1, G'_c(x,0) = E_loc - E,
+//   O_c(x,k) = O - <O_k>, G'_c(x,k) = G - <O_k> E_loc - E O_c(x,k),
+// and normalise the weights.
+template <typename TL>
+__global__ void k_centre(double *O, double *G, const double *eloc, double *wt,
+                         const double *stats, int64_t n, int ldp, int P1, double e_core,
+                         TL *Olo, TL *Glo) {
+    const double E = stats[1];
+    const double isw = 1.0 / stats[0];
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const double el = eloc[r];  // E_loc already includes e_core
+        double *Or = O + r * ldp;
+        double *Gr = G + r * ldp;
+        for (int c = threadIdx.x; c < ldp; c += blockDim.x) {
+            double oc, gc;
+            if (c == 0) {
+                oc = 1.0;
+                gc = el - E;
+            } else if (c < P1) {
+                double ob = stats[8 + c];
+                oc = Or[c] - ob;
+                gc = fma(-ob, el, Gr[c]);
+                gc = fma(-E, oc, gc);
+            } else {
+                oc = 0.0;
+                gc = 0.0;
+            }
+            Or[c] = oc;
+            Gr[c] = gc;
+            if (Olo) {
+                Olo[r * ldp + c] = (TL)oc;
+                Glo[r * ldp + c] = (TL)gc;
+            }
+        }
+        if (threadIdx.x == 0) wt[r] *= isw;
+    }
+}
+
+// ------------------------------------------------ debug: connection lists
+__global__ void k_connections(SysView S, const uint64_t *rows, int64_t n_rows, int cap,
+                              uint64_t *od, int8_t *osg, double *oh, int32_t *cnt,
+                              double e_core) {
+    __shared__ RowLists L;
+    for (int64_t row = blockIdx.x; row < n_rows; row += gridDim.x) {
+        const uint64_t x = rows[row];
+        if (threadIdx.x == 0) make_lists(S, x, L);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double d = diag_value_warp(S, L);
+            if (threadIdx.x == 0) {
+                od[row * cap] = x;
+                osg[row * cap] = 1;
+                oh[row * cap] = d + e_core;
+                cnt[row] = min(S.conn + 1, cap);
+            }
+        }
+        for (int k = threadIdx.x; k < S.conn; k += blockDim.x) {
+            if (k + 1 >= cap) break;
+            Exc e = decode_exc(S, L, k);
+            int sg;
+            uint64_t y = apply_exc(x, e, sg);
+            od[row * cap + k + 1] = y;
+            osg[row * cap + k + 1] = (int8_t)sg;
+            oh[row * cap + k + 1] = sg * exc_value(S, L, e);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ==========================================================================
+// host launchers
+// ==========================================================================
+int lm_launch_enumerate(lm_ctx *ctx, int n, int na, int nb, uint64_t *out, int64_t count,
+                        cudaStream_t s) {
+    int blocks = (int)std::min<int64_t>((count + 255) / 256, (int64_t)ctx->sms * 8);
+    if (blocks < 1) blocks = 1;
+    k_enumerate<<<blocks, 256, 0, s>>>(n, na, nb, out, count);
+    lm_note_launch(ctx);
+    return lm_cuda_check(ctx, cudaGetLastError(), "k_enumerate");
+}
+
+static size_t build_smem_bytes(int nh, int M, int ldF, int ldS, int nslice) {
+    size_t d = (size_t)2 * nh * M + 2 * M + 3 * nh + (size_t)BUILD_THREADS * ldF + BUILD_THREADS +
+               (size_t)nslice * (nh + 1) * ldS + (size_t)nslice * (nh + 1) + 64;
+    return d * sizeof(double) + BUILD_THREADS * sizeof(int4) + sizeof(RowLists) + 64;
+}
+
+int lm_launch_build(lm_pencil *p, cudaStream_t s) {
+    lm_ctx *ctx = p->ctx;
+    BuildArgs A;
+    A.S = make_view(p->n, p->na, p->nb, p->h, p->eri);
+    A.nh = p->nh;
+    A.M = p->M;
+    A.M1 = p->M1;
+    A.P1 = p->P1;
+    A.ldp = p->ldp;
+    A.ldF = p->nh | 1;
+    A.ldS = p->M | 1;
+    A.nslice = std::max(1, BUILD_THREADS / (p->nh + 1));
+    A.theta = p->theta;
+    A.tabs = p->tabs;
+    A.rows = p->rows;
+    A.n_rows = p->n_rows;
+    A.amask = (p->n >= 64) ? ~0ull : ((1ull << p->n) - 1ull);
+    A.bmask = A.amask << p->n;
+    A.e_core = p->e_core;
+    A.lnpsi = p->lnpsi;
+    A.eloc = p->eloc;
+    A.O = p->O;
+    A.G = p->G;
+    A.flags = ctx->d_flags;
+    if (p->nh + 1 > BUILD_THREADS)
+        return lm_fail(ctx, LM_ERR_SIZE, "n_hidden + 1 = %d exceeds %d", p->nh + 1,
+                       BUILD_THREADS);
+    size_t smem = build_smem_bytes(p->nh, p->M, A.ldF, A.ldS, A.nslice);
+    if (smem > (size_t)ctx->smem_optin)
+        return lm_fail(ctx, LM_ERR_SIZE, "build kernel needs %zu B shared memory", smem);
+    cudaError_t e = cudaFuncSetAttribute(k_build_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return lm_cuda_check(ctx, e, "build smem attribute");
+
+    int tb = 256;
+    k_tables<<<(p->nh * p->M + p->M + tb - 1) / tb, tb, 0, s>>>(p->theta, p->M, p->nh, p->tabs);
+    lm_note_launch(ctx);
+    if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_tables")) return rc;
+
+    int per_sm = std::max(1, (int)(200 * 1024 / smem));
+    per_sm = std::min(per_sm, 8);
+    int64_t grid = std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * per_sm);
+    if (grid < 1) grid = 1;
+    lm_prof_begin(ctx, PROF_BUILD, s);
+    k_build_rows<<<(unsigned)grid, BUILD_THREADS, smem, s>>>(A);
+    lm_prof_end(ctx, PROF_BUILD, s);
+    lm_note_launch(ctx);
+    if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_build_rows")) return rc;
+
+    // weights, E, <O>
+    const int nmax = std::max(1, std::min(ctx->sms, (int)((p->n_rows + 255) / 256)));
+    double *maxpart = p->part;  // reuse the partials buffer (nmax doubles first)
+    double *given = p->given_weights ? p->wt : nullptr;
+    if (!given) {
+        k_lnpsi_max_partial<<<nmax, 256, 0, s>>>(p->lnpsi, p->n_rows, maxpart);
+        lm_note_launch(ctx);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_lnpsi_max")) return rc;
+    }
+    const int nst = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_rows, ctx->sms * 2));
+    double *spart = p->part + 256;
+    k_stats_partial<<<nst, 256, 0, s>>>(p->O, p->lnpsi, p->eloc, given, p->wt, p->n_rows, p->ldp,
+                                        maxpart, nmax, spart);
+    lm_note_launch(ctx);
+    if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_stats_partial")) return rc;
+    k_stats_final<<<(p->ldp + 255) / 256, 256, 0, s>>>(spart, nst, p->ldp, p->stats);
+    lm_note_launch(ctx);
+    if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_stats_final")) return rc;
+    int cgrid = (int)std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * 16);
+    if (p->prec == LM_FP32)
+        k_centre<float><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
+                                              p->ldp, p->P1, p->e_core, (float *)p->Olo,
+                                              (float *)p->Glo);
+    else if (p->prec == LM_BF16)
+        k_centre<__nv_bfloat16><<<cgrid, 256, 0, s>>>(
+            p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows, p->ldp, p->P1, p->e_core,
+            (__nv_bfloat16 *)p->Olo, (__nv_bfloat16 *)p->Glo);
+    else
+        k_centre<double><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
+                                               p->ldp, p->P1, p->e_core, (double *)nullptr,
+                                               (double *)nullptr);
+    lm_note_launch(ctx);
+    return lm_cuda_check(ctx, cudaGetLastError(), "k_centre");
+}
+
+int lm_launch_connections(lm_ctx *ctx, int n, int na, int nb, const double *h, const double *eri,
+                          const uint64_t *rows, int64_t n_rows, int cap, uint64_t *od,
+                          int8_t *osg, double *oh, int32_t *cnt, double e_core, cudaStream_t s) {
+    SysView S = make_view(n, na, nb, h, eri);
+    int grid = (int)std::min<int64_t>(n_rows, (int64_t)ctx->sms * 4);
+    if (grid < 1) return LM_OK;
+    k_connections<<<grid, 256, 0, s>>>(S, rows, n_rows, cap, od, osg, oh, cnt, e_core);
+    lm_note_launch(ctx);
+    return lm_cuda_check(ctx, cudaGetLastError(), "k_connections");
+}

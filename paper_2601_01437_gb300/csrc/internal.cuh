@@ -1,0 +1,203 @@
+// Internal declarations shared by the library's CUDA translation units.
+// Nothing here is part of the C ABI (include/irlnqs.h is).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+
+#include "irlnqs.h"
+
+#define LM_MAXM 64      // spin orbitals
+#define LM_MAXH 256     // hidden units
+#define LM_MAXKRYLOV 64 // Krylov dimension
+
+// Bound on polls of one mbarrier phase before a kernel gives up (each
+// try_wait may itself suspend for a short, hardware-defined time).
+#define LM_SPIN_LIMIT (1u << 22)
+
+// Device error flags (lm_ctx::d_flags): bit set by kernels, read by the host.
+enum {
+    FLAG_ROW_OUTSIDE_SECTOR = 1,
+    FLAG_TIMEOUT = 2,
+    FLAG_BAD_ARG = 4,
+};
+
+// ---------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// mbarrier + 1-D bulk copy (TMA engine) wrappers, CTA scope.
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Bulk global->shared copy; dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait on one phase of an mbarrier: false once LM_SPIN_LIMIT polls or
+// two seconds of wall time have passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0; i < LM_SPIN_LIMIT; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && global_ns() - t0 > 2000000000ull) return false;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+#define LM_PROF_EVENTS 4096
+
+struct lm_ctx {
+    int device;
+    int sms;
+    int smem_optin;
+    int *d_flags;        // device error flags
+    char err[512];
+    // counters
+    int64_t launches;
+    int profile;
+    cudaEvent_t ev[2][LM_PROF_EVENTS][2];  // [class][pair][start/end]
+    int ev_ready;
+    int64_t ev_used[2];
+    int64_t ev_count[2];
+    int64_t pencil_rows;
+};
+
+enum { PROF_BUILD = 0, PROF_PENCIL = 1 };
+
+inline void lm_note_launch(lm_ctx *ctx, int n = 1) { ctx->launches += n; }
+// Event pair around one launch of a profiled kernel class (no-op unless profiling).
+inline void lm_prof_begin(lm_ctx *ctx, int cls, cudaStream_t s) {
+    if (!ctx->profile || !ctx->ev_ready) return;
+    if (ctx->ev_used[cls] < LM_PROF_EVENTS) cudaEventRecord(ctx->ev[cls][ctx->ev_used[cls]][0], s);
+}
+inline void lm_prof_end(lm_ctx *ctx, int cls, cudaStream_t s) {
+    ctx->ev_count[cls]++;
+    if (!ctx->profile || !ctx->ev_ready) return;
+    if (ctx->ev_used[cls] < LM_PROF_EVENTS) {
+        cudaEventRecord(ctx->ev[cls][ctx->ev_used[cls]][1], s);
+        ctx->ev_used[cls]++;
+    }
+}
+
+// Device-side IRL state (one per pencil), all FP64.
+struct IrlState {
+    double alpha[LM_MAXKRYLOV + 1];
+    double beta[LM_MAXKRYLOV + 1];
+    double ritz[LM_MAXKRYLOV];
+    double u[LM_MAXKRYLOV];                   // lowest eigenvector of T (final)
+    double Q[LM_MAXKRYLOV * LM_MAXKRYLOV];    // restart rotations, column-major
+    double h1[LM_MAXKRYLOV + 1];              // reduced CGS dots (pass 1)
+    double h2[LM_MAXKRYLOV + 1];              // reduced CGS dots (pass 2)
+    double lam, res, tnorm, tol_eff, bnorm;
+    double rq, rq_s, res_explicit, c0, yty;
+    int jend, broke, conv, err;
+};
+
+struct lm_pencil {
+    lm_ctx *ctx;
+    int n, na, nb, nh, M, M1, P1, ldp;
+    int64_t n_rows;
+    int enumerated;     // rows = the whole sector
+    int given_weights;  // weights from the caller
+    int prec;           // low-precision copy kind (LM_FP64 = none)
+    int sym;            // resolved default symmetrisation
+    double e_core;
+    // device buffers (FP64 unless noted)
+    uint64_t *rows;
+    double *wt, *lnpsi, *eloc;
+    double *O, *G;      // N_s x ldp, centred in place
+    void *Olo, *Glo;    // low-precision copies (float or bf16) or null
+    double *h, *eri, *theta, *tabs;
+    double *stats;      // [0] sum w, [1] E, [2] max lnpsi, [8..8+ldp) mean O
+    double *part;       // reduction partials
+    int64_t part_len;
+    int g_pencil;       // CTAs of the pencil kernel
+    // IRL workspace
+    double *V;          // ldp x (LM_MAXKRYLOV + 1), column-major
+    double *wvec, *yvec, *hy, *sy, *tvec, *dots;
+    IrlState *st;       // device
+    IrlState *st_host;  // pinned mirror
+    double E_host;
+};
+
+// ---------------------------------------------------------------------------
+// Host helpers (abi.cu)
+// ---------------------------------------------------------------------------
+int lm_fail(lm_ctx *ctx, int code, const char *fmt, ...);
+int lm_cuda_check(lm_ctx *ctx, cudaError_t e, const char *what);
+bool lm_is_device_ptr(const void *p);
+int lm_read_flags(lm_ctx *ctx, cudaStream_t s, int *flags);
+
+// build.cu
+int lm_launch_enumerate(lm_ctx *ctx, int n, int na, int nb, uint64_t *out, int64_t count,
+                        cudaStream_t s);
+int lm_launch_build(lm_pencil *p, cudaStream_t s);
+int lm_launch_connections(lm_ctx *ctx, int n, int na, int nb, const double *h,
+                          const double *eri, const uint64_t *rows, int64_t n_rows, int cap,
+                          uint64_t *od, int8_t *osg, double *oh, int32_t *cnt, double e_core,
+                          cudaStream_t s);
+
+// pencil.cu
+// partial products of the pencil over row blocks; y_H into part[b][0..ldp),
+// y_S into part[b][ldp..2ldp)
+int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_s,
+                     const int *skip, cudaStream_t s);
+int lm_launch_reduce_partials(lm_pencil *p, double *yH, double *yS, cudaStream_t s);
+int lm_pencil_grid(lm_pencil *p);

@@ -1,0 +1,841 @@
+// Implicitly restarted Lanczos on the device (arXiv 2601.01437, Methods,
+// "The Standard Lanczos Process and Implicit Restart", Algorithms 1 and 2).
+//
+// Per Lanczos step j (v_j = V[:, j]):
+//   w = H~' v_j (pencil kernel, partials per row block)
+//   lz_a: w = sum of partials; d1 = V^T w          (CGS pass 1 dots)
+//   lz_b: w -= V d1; d2 = V^T w                    (CGS pass 2 dots)
+//   lz_c: w -= V d2; alpha_j = d1_j + d2_j; remove the particle-number null
+//         space; partial |w|^2
+//   lz_d: beta_j = |w|; v_{j+1} = w / beta_j; breakdown test
+// The vector kernels use one CTA per row r of the (Nh+1) x (M+1) parameter
+// grid, so the null-space projection (which acts within a grid row) needs no
+// extra synchronisation. Reductions always run in a fixed order.
+//
+// After m steps, one CTA (k_tri) finds the Ritz values of T_m (FP32
+// multisection for brackets, FP64 Newton on the characteristic polynomial),
+// estimates the residual of the lowest pair as beta_m |u_m| with
+// u_m^2 = -p_{m-1}(theta)/p_m'(theta), and, if not converged, applies the
+// mu = m - k largest Ritz values as shifts by implicit shifted QR sweeps.
+// Consecutive bulges are chased concurrently four positions apart; the
+// rotations they apply touch disjoint entries, so the result is the same as
+// applying the sweeps one after another (the chase is latency bound in FP64).
+// k_restart then forms V_k <- V_m Q[:, :k] and the new residual
+// f = beta_hat_k V_m Q[:, k] + beta_m Q[m-1, k-1] v_{m+1}.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int LT = 256;       // threads of the Lanczos vector kernels
+constexpr int DLD = LM_MAXKRYLOV + 8;  // leading dimension of the per-CTA dot buffers
+
+struct LzArgs {
+    double *V;          // current basis, column-major ldp x (MAXK+1)
+    double *w;          // work vector (ldp)
+    const double *part; // pencil partials [nparts][2 ldp]
+    int nparts;
+    double *dots;       // [3][G2][DLD]
+    int ldp, M1, P1, nrow_grid;  // nrow_grid = Nh + 1 = number of CTAs
+    int n_orb, na, nb;
+    int deflate;
+    IrlState *st;
+};
+
+__device__ __forceinline__ void cta_range(const LzArgs &a, int &e0, int &e1) {
+    e0 = blockIdx.x * a.M1;
+    e1 = (blockIdx.x == a.nrow_grid - 1) ? a.ldp : e0 + a.M1;
+}
+
+__device__ __forceinline__ bool lz_skip(const IrlState *st) { return st->broke != 0; }
+
+// dots[i] (i <= j) of V[:, i] with w over this CTA's entries, by warps
+__device__ void cta_dots(const LzArgs &a, int e0, int e1, int j, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i <= j; i += LT / 32) {
+        const double *vi = a.V + (size_t)i * a.ldp;
+        double s = 0.0;
+        for (int e = e0 + lane; e < e1; e += 32) s = fma(vi[e], a.w[e], s);
+        s = warp_sum(s);
+        if (lane == 0) out[i] = s;
+    }
+}
+
+// h[i] = sum over CTAs of dots[region][cta][i], fixed CTA order
+__device__ void sum_dots(const LzArgs &a, int region, int j, double *h) {
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        double s = 0.0;
+        const double *d = a.dots + (size_t)region * a.nrow_grid * DLD;
+        for (int b = 0; b < a.nrow_grid; ++b) s += d[(size_t)b * DLD + i];
+        h[i] = s;
+    }
+}
+
+__global__ void __launch_bounds__(LT) k_lz_a(LzArgs a, int j) {
+    if (lz_skip(a.st)) return;
+    int e0, e1;
+    cta_range(a, e0, e1);
+    __shared__ double s[LT / 32][72];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // w = sum_b part[b][e]: 8 warps split b, fixed-order combine
+    for (int base = e0; base < e1; base += 32) {
+        const int e = base + lane;
+        double acc = 0.0;
+        if (e < e1)
+            for (int b = warp; b < a.nparts; b += LT / 32) acc += a.part[(size_t)b * 2 * a.ldp + e];
+        s[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && e < e1) {
+            double t = 0.0;
+            for (int w = 0; w < LT / 32; ++w) t += s[w][lane];
+            a.w[e] = t;
+        }
+        __syncthreads();
+    }
+    cta_dots(a, e0, e1, j, a.dots + (size_t)blockIdx.x * DLD);
+}
+
+__global__ void __launch_bounds__(LT) k_lz_b(LzArgs a, int j) {
+    if (lz_skip(a.st)) return;
+    int e0, e1;
+    cta_range(a, e0, e1);
+    __shared__ double h[LM_MAXKRYLOV + 1];
+    sum_dots(a, 0, j, h);
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) a.st->h1[i] = h[i];
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        double x = a.w[e];
+        for (int i = 0; i <= j; ++i) x = fma(-a.V[(size_t)i * a.ldp + e], h[i], x);
+        a.w[e] = x;
+    }
+    __syncthreads();
+    cta_dots(a, e0, e1, j, a.dots + ((size_t)a.nrow_grid + blockIdx.x) * DLD);
+}
+
+__global__ void __launch_bounds__(LT) k_lz_c(LzArgs a, int j) {
+    if (lz_skip(a.st)) return;
+    int e0, e1;
+    cta_range(a, e0, e1);
+    __shared__ double h[LM_MAXKRYLOV + 1];
+    __shared__ double red[LT / 32][4];
+    __shared__ double coef[2];
+    sum_dots(a, 1, j, h);
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0 && j >= 0) a.st->alpha[j] = a.st->h1[j] + h[j];
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) a.st->h2[i] = h[i];
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        double x = a.w[e];
+        for (int i = 0; i <= j; ++i) x = fma(-a.V[(size_t)i * a.ldp + e], h[i], x);
+        a.w[e] = x;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (a.deflate) {
+        // grid row r = blockIdx.x: columns 1..n alpha, n+1..2n beta, column 0
+        const int r = blockIdx.x, n = a.n_orb;
+        double sa = 0.0, sb = 0.0;
+        for (int c = 1 + threadIdx.x; c <= 2 * n; c += blockDim.x) {
+            double x = a.w[r * a.M1 + c];
+            if (c <= n) sa += x; else sb += x;
+        }
+        sa = warp_sum(sa);
+        sb = warp_sum(sb);
+        if (lane == 0) {
+            red[warp][0] = sa;
+            red[warp][1] = sb;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double A = 0.0, B = 0.0;
+            for (int w = 0; w < LT / 32; ++w) {
+                A += red[w][0];
+                B += red[w][1];
+            }
+            if (r == 0) {
+                coef[0] = A / n;
+                coef[1] = B / n;
+            } else {
+                // least squares on span{1_alpha - Na e0, 1_beta - Nb e0}
+                const double w0 = a.w[r * a.M1];
+                const double na = a.na, nb = a.nb;
+                const double g11 = n + na * na, g22 = n + nb * nb, g12 = na * nb;
+                const double r1 = A - na * w0, r2 = B - nb * w0;
+                const double det = g11 * g22 - g12 * g12;
+                coef[0] = (g22 * r1 - g12 * r2) / det;
+                coef[1] = (g11 * r2 - g12 * r1) / det;
+            }
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c <= 2 * n; c += blockDim.x) {
+            double &x = a.w[r * a.M1 + c];
+            if (c == 0) {
+                if (r > 0) x += coef[0] * a.na + coef[1] * a.nb;
+            } else if (c <= n) {
+                x -= coef[0];
+            } else {
+                x -= coef[1];
+            }
+        }
+        __syncthreads();
+    }
+    double s2 = 0.0;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) s2 = fma(a.w[e], a.w[e], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) red[warp][2] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < LT / 32; ++w) t += red[w][2];
+        a.dots[((size_t)2 * a.nrow_grid + blockIdx.x) * DLD] = t;
+    }
+}
+
+// beta = |w| (fixed-order sum of CTA partials), v_{jout} = w / beta.
+// mode 0: Lanczos step j (jout = j+1, stores beta_j, breakdown test)
+// mode 1: start vector (jout = 0)
+// mode 2: restart residual (jout = k, stores beta_{k-1})
+__global__ void __launch_bounds__(LT) k_lz_d(LzArgs a, int j, int jout, int mode) {
+    if (mode == 0 && lz_skip(a.st)) return;
+    __shared__ double sb;
+    __shared__ int sbrk;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < a.nrow_grid; ++b)
+            t += a.dots[((size_t)2 * a.nrow_grid + b) * DLD];
+        const double beta = sqrt(t);
+        int brk = 0;
+        if (mode == 0) {
+            double tn = fmax(a.st->tnorm, fmax(fabs(a.st->alpha[j]), beta));
+            if (j > 0) tn = fmax(tn, fabs(a.st->beta[j - 1]));
+            if (beta <= 1e-14 * fmax(tn, 1e-300)) brk = 1;
+            if (blockIdx.x == 0) {
+                a.st->beta[j] = beta;
+                a.st->tnorm = tn;
+                if (brk) {
+                    a.st->broke = 1;
+                    a.st->jend = j + 1;
+                }
+            }
+        } else if (mode == 2 && blockIdx.x == 0) {
+            a.st->beta[jout - 1] = beta;
+        }
+        sb = beta;
+        sbrk = brk;
+    }
+    __syncthreads();
+    if (sbrk) return;
+    int e0, e1;
+    cta_range(a, e0, e1);
+    const double inv = sb > 0.0 ? 1.0 / sb : 0.0;
+    double *vout = a.V + (size_t)jout * a.ldp;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) vout[e] = a.w[e] * inv;
+}
+
+// Random start vector: component e is 2u-1 with u the 53-bit uniform of
+// SplitMix64 at counter e (state seed + (e+1) * golden gamma), zero padding.
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t e) {
+    uint64_t z = seed + (e + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+__global__ void k_init_start(double *w, int ldp, int P1, uint64_t seed, const double *v0) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ldp; e += gridDim.x * blockDim.x) {
+        double x = 0.0;
+        if (e < P1) x = v0 ? v0[e] : splitmix_uniform(seed, (uint64_t)e);
+        w[e] = x;
+    }
+}
+
+// ---------------------------------------------------------------- k_tri
+constexpr int TT = 1024;
+
+// Sturm count (number of eigenvalues < x) of the scaled tridiagonal, FP32.
+__device__ __forceinline__ int sturm_f32(const float *a, const float *b2, int n, float x) {
+    const float pivmin = 1e-30f;
+    int cnt = 0;
+    float q = a[0] - x;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0f;
+    for (int i = 1; i < n; ++i) {
+        q = (a[i] - x) - b2[i - 1] / q;
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += q < 0.0f;
+    }
+    return cnt;
+}
+
+// p_n(x) = det(T - x I) and p_{n-1}(x), p_n'(x) by the three-term recurrence
+// (division free), on the scaled matrix.
+__device__ __forceinline__ void charpoly(const double *a, const double *b2, int n, double x,
+                                         double &pn, double &pn1, double &dpn) {
+    double pm2 = 0.0, pm1 = 1.0, dm2 = 0.0, dm1 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double bb = i > 0 ? b2[i - 1] : 0.0;
+        const double p = (a[i] - x) * pm1 - bb * pm2;
+        const double d = -pm1 + (a[i] - x) * dm1 - bb * dm2;
+        pm2 = pm1;
+        pm1 = p;
+        dm2 = dm1;
+        dm1 = d;
+    }
+    pn = pm1;
+    pn1 = pm2;
+    dpn = dm1;
+}
+
+struct TriArgs {
+    IrlState *st;
+    int m, k;
+    int final_pass;
+    double tol;  // absolute tolerance
+    double rel;  // floor relative to ||T|| (50 eps for FP64 operators)
+};
+
+__global__ void __launch_bounds__(TT) k_tri(TriArgs t) {
+    IrlState *st = t.st;
+    __shared__ double a[LM_MAXKRYLOV], b[LM_MAXKRYLOV], as[LM_MAXKRYLOV], b2s[LM_MAXKRYLOV];
+    __shared__ float af[LM_MAXKRYLOV], b2f[LM_MAXKRYLOV];
+    __shared__ double ritz[LM_MAXKRYLOV];
+    __shared__ double Q[LM_MAXKRYLOV * LM_MAXKRYLOV];
+    __shared__ double rc[LM_MAXKRYLOV], rs[LM_MAXKRYLOV];
+    __shared__ int rp[LM_MAXKRYLOV];
+    __shared__ double sscale, u0last;
+    __shared__ int je_s, conv_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        je_s = st->broke ? st->jend : t.m;
+        conv_s = 0;
+    }
+    __syncthreads();
+    const int je = je_s;
+    for (int i = tid; i < je; i += TT) {
+        a[i] = st->alpha[i];
+        b[i] = i < je - 1 ? st->beta[i] : 0.0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int i = 0; i < je; ++i) s = fmax(s, fabs(a[i]));
+        for (int i = 0; i < je - 1; ++i) s = fmax(s, fabs(b[i]));
+        sscale = s > 0.0 ? s : 1.0;
+    }
+    __syncthreads();
+    const double sc = sscale;
+    for (int i = tid; i < je; i += TT) {
+        as[i] = a[i] / sc;
+        af[i] = (float)as[i];
+        double bb = i < je - 1 ? b[i] / sc : 0.0;
+        b2s[i] = bb * bb;
+        b2f[i] = (float)(bb * bb);
+    }
+    __syncthreads();
+    // (1) brackets by 32-way multisection in FP32: warp -> eigenvalue index
+    __shared__ float blo[LM_MAXKRYLOV], bhi[LM_MAXKRYLOV];
+    for (int i = warp; i < je; i += TT / 32) {
+        float lo = -3.0f, hi = 3.0f;  // scaled Gershgorin bound
+        for (int round = 0; round < 6; ++round) {
+            const float x = lo + (hi - lo) * (float)(lane + 1) / 33.0f;
+            const int c = sturm_f32(af, b2f, je, x);
+            const unsigned above = __ballot_sync(0xffffffffu, c > i);
+            const int L = above ? __ffs(above) - 1 : 32;
+            const float nhi = L < 32 ? lo + (hi - lo) * (float)(L + 1) / 33.0f : hi;
+            const float nlo = L > 0 ? lo + (hi - lo) * (float)L / 33.0f : lo;
+            lo = nlo;
+            hi = nhi;
+        }
+        if (lane == 0) {
+            blo[i] = lo;
+            bhi[i] = hi;
+        }
+    }
+    __syncthreads();
+    // (2) FP64 safeguarded Newton on p_je inside the (widened) bracket
+    if (tid < je) {
+        const int i = tid;
+        double lo = (double)blo[i] - 4e-7, hi = (double)bhi[i] + 4e-7;
+        double x = 0.5 * ((double)blo[i] + (double)bhi[i]);
+        double pn, pn1, dpn, plo, pl1, dl;
+        charpoly(as, b2s, je, lo, plo, pl1, dl);
+        for (int it = 0; it < 8; ++it) {
+            charpoly(as, b2s, je, x, pn, pn1, dpn);
+            if (pn == 0.0) break;
+            if ((pn > 0.0) == (plo > 0.0)) lo = x; else hi = x;
+            double xn = dpn != 0.0 ? x - pn / dpn : 0.5 * (lo + hi);
+            if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+            const double dx = fabs(xn - x);
+            x = xn;
+            if (dx <= 2e-16 * fmax(fabs(x), 1e-3)) break;
+        }
+        charpoly(as, b2s, je, x, pn, pn1, dpn);
+        ritz[i] = x * sc;
+        if (i == 0) u0last = (dpn != 0.0) ? fabs(pn1 / dpn) : 1.0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double tn = 0.0;
+        for (int i = 0; i < je; ++i) tn = fmax(tn, fabs(ritz[i]));
+        const double tol_eff = fmax(t.tol, t.rel * tn);
+        const double bres = st->broke ? 0.0 : fabs(st->beta[je - 1]);
+        const double res = st->broke ? 0.0 : bres * sqrt(fmin(u0last, 1.0));
+        st->lam = ritz[0];
+        st->res = res;
+        st->tol_eff = tol_eff;
+        st->bnorm = tn;
+        const int conv = st->broke || res < tol_eff;
+        st->conv = conv;
+        conv_s = conv;
+    }
+    for (int i = tid; i < je; i += TT) st->ritz[i] = ritz[i];
+    __syncthreads();
+    if (conv_s || t.final_pass) {
+        // (3) eigenvector of the lowest Ritz value by inverse iteration (FP64,
+        // tridiagonal elimination with partial pivoting), two sweeps.
+        if (tid == 0) {
+            const double lam = ritz[0];
+            const double eps = 2.220446049250313e-16 * sc;
+            double y[LM_MAXKRYLOV], d[LM_MAXKRYLOV], du[LM_MAXKRYLOV], du2[LM_MAXKRYLOV],
+                dl[LM_MAXKRYLOV];
+            int piv[LM_MAXKRYLOV];
+            for (int i = 0; i < je; ++i) {
+                d[i] = a[i] - lam;
+                du[i] = i < je - 1 ? b[i] : 0.0;
+                dl[i] = i < je - 1 ? b[i] : 0.0;
+                du2[i] = 0.0;
+                y[i] = 1.0;
+            }
+            // LU with partial pivoting (LAPACK dgttrf layout)
+            for (int i = 0; i < je - 1; ++i) {
+                if (fabs(d[i]) >= fabs(dl[i])) {
+                    piv[i] = 0;
+                    if (d[i] == 0.0) d[i] = eps;
+                    const double f = dl[i] / d[i];
+                    dl[i] = f;
+                    d[i + 1] -= f * du[i];
+                } else {
+                    piv[i] = 1;
+                    const double f = d[i] / dl[i];
+                    d[i] = dl[i];
+                    dl[i] = f;
+                    const double tmp = du[i];
+                    du[i] = d[i + 1];
+                    d[i + 1] = tmp - f * d[i + 1];
+                    if (i < je - 2) {
+                        du2[i] = du[i + 1];
+                        du[i + 1] = -f * du[i + 1];
+                    }
+                }
+            }
+            if (d[je - 1] == 0.0) d[je - 1] = eps;
+            for (int sweep = 0; sweep < 2; ++sweep) {
+                for (int i = 0; i < je - 1; ++i) {
+                    if (piv[i] == 0) {
+                        y[i + 1] -= dl[i] * y[i];
+                    } else {
+                        const double tmp = y[i];
+                        y[i] = y[i + 1];
+                        y[i + 1] = tmp - dl[i] * y[i];
+                    }
+                }
+                y[je - 1] /= d[je - 1];
+                if (je > 1) y[je - 2] = (y[je - 2] - du[je - 2] * y[je - 1]) / d[je - 2];
+                for (int i = je - 3; i >= 0; --i)
+                    y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / d[i];
+                double nn = 0.0;
+                for (int i = 0; i < je; ++i) nn += y[i] * y[i];
+                nn = 1.0 / sqrt(nn);
+                for (int i = 0; i < je; ++i) y[i] *= nn;
+            }
+            for (int i = 0; i < je; ++i) st->u[i] = y[i];
+            st->jend = je;
+        }
+        return;
+    }
+    // (4) implicit restart: mu = m - k shifts (largest first), pipelined chase
+    const int m = je, k = t.k, mu = m - k;
+    for (int e = tid; e < m * m; e += TT) Q[e] = (e % (m + 1) == 0) ? 1.0 : 0.0;
+    __syncthreads();
+    double bx = 0.0, bz = 0.0;  // per-bulge state (thread q < mu)
+    const int nsteps = (m - 1) + 4 * (mu - 1);
+    for (int step = 0; step < nsteps; ++step) {
+        if (tid < mu) {
+            const int q = tid;
+            const int p = step - 4 * q;
+            if (p >= 0 && p <= m - 2) {
+                if (p == 0) {
+                    bx = a[0] - ritz[m - 1 - q];
+                    bz = b[0];
+                }
+                double r = hypot(bx, bz);
+                double c = 1.0, s = 0.0;
+                if (r != 0.0) {
+                    c = bx / r;
+                    s = bz / r;
+                }
+                if (p > 0) b[p - 1] = r;
+                const double ap = a[p], aq = a[p + 1], bp = b[p];
+                a[p] = c * c * ap + 2.0 * c * s * bp + s * s * aq;
+                a[p + 1] = s * s * ap - 2.0 * c * s * bp + c * c * aq;
+                b[p] = c * s * (aq - ap) + (c * c - s * s) * bp;
+                if (p < m - 2) {
+                    bz = s * b[p + 1];
+                    b[p + 1] = c * b[p + 1];
+                    bx = b[p];
+                }
+                rc[q] = c;
+                rs[q] = s;
+                rp[q] = p;
+            } else {
+                rp[q] = -1;
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < mu * m; e += TT) {
+            const int q = e / m, i = e % m;
+            const int p = rp[q];
+            if (p >= 0) {
+                const double c = rc[q], s = rs[q];
+                const double x0 = Q[p * m + i], x1 = Q[(p + 1) * m + i];
+                Q[p * m + i] = c * x0 + s * x1;
+                Q[(p + 1) * m + i] = -s * x0 + c * x1;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < m * (k + 1); e += TT) st->Q[e] = Q[e];
+    for (int i = tid; i < k; i += TT) st->alpha[i] = a[i];
+    for (int i = tid; i < k - 1; i += TT) st->beta[i] = b[i];
+    if (tid == 0) {
+        st->h1[0] = b[k - 1];                          // beta_hat_k
+        st->h2[0] = st->beta[m - 1] * Q[(k - 1) * m + (m - 1)];  // beta_m Q[m-1, k-1]
+    }
+}
+
+// V_new[:, i] = V[:, :m] Q[:, i] (i < k); w = beta_hat V Q[:, k] + sigma V[:, m];
+// per-CTA partial |w|^2 into dots region 2.
+__global__ void __launch_bounds__(LT) k_restart(LzArgs a, double *Vnew, int m, int k) {
+    __shared__ double Qs[LM_MAXKRYLOV * (LM_MAXKRYLOV + 1)];
+    __shared__ double red[LT / 32];
+    for (int e = threadIdx.x; e < m * (k + 1); e += blockDim.x) Qs[e] = a.st->Q[e];
+    __syncthreads();
+    const double bhat = a.st->h1[0], sigma = a.st->h2[0];
+    int e0, e1;
+    cta_range(a, e0, e1);
+    double s2 = 0.0;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        for (int i = 0; i <= k; ++i) {
+            double acc = 0.0;
+            for (int l = 0; l < m; ++l) acc = fma(a.V[(size_t)l * a.ldp + e], Qs[i * m + l], acc);
+            if (i < k) {
+                Vnew[(size_t)i * a.ldp + e] = acc;
+            } else {
+                const double f = fma(sigma, a.V[(size_t)m * a.ldp + e], bhat * acc);
+                a.w[e] = f;
+                s2 = fma(f, f, s2);
+            }
+        }
+    }
+    s2 = warp_sum(s2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < LT / 32; ++w) t += red[w];
+        a.dots[((size_t)2 * a.nrow_grid + blockIdx.x) * DLD] = t;
+    }
+}
+
+// y = V[:, :jend] u (the Ritz vector)
+__global__ void k_ritz_vector(const double *V, const IrlState *st, int ldp, double *y) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ldp; e += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        const int n = st->jend;
+        for (int l = 0; l < n; ++l) acc = fma(V[(size_t)l * ldp + e], st->u[l], acc);
+        y[e] = acc;
+    }
+}
+
+// One-CTA refinement: Rayleigh quotients, explicit residual, sign of c_0,
+// update Delta theta = c[1:]/c[0] (and theta += Delta theta on request).
+__global__ void __launch_bounds__(1024) k_refine(double *y, const double *hy, const double *sy,
+                                                 IrlState *st, int ldp, int P1, double *c_out,
+                                                 double *dth_out, double *theta, double tol,
+                                                 int *status_out) {
+    __shared__ double red[32][4];
+    __shared__ double sv[5];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double yy = 0.0, yh = 0.0, ys = 0.0;
+    for (int e = tid; e < P1; e += blockDim.x) {
+        yy = fma(y[e], y[e], yy);
+        yh = fma(y[e], hy[e], yh);
+        ys = fma(y[e], sy[e], ys);
+    }
+    yy = warp_sum(yy);
+    yh = warp_sum(yh);
+    ys = warp_sum(ys);
+    if (lane == 0) {
+        red[warp][0] = yy;
+        red[warp][1] = yh;
+        red[warp][2] = ys;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double A = 0, B = 0, C = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            A += red[w][0];
+            B += red[w][1];
+            C += red[w][2];
+        }
+        sv[0] = A;
+        sv[1] = B;
+        sv[2] = C;
+        sv[3] = y[0] < 0.0 ? -1.0 : 1.0;
+        sv[4] = fabs(y[0]);
+    }
+    __syncthreads();
+    const double nrm = sqrt(sv[0]);
+    const double lam = st->lam;
+    const double sgn = sv[3] / nrm;
+    double rr = 0.0;
+    for (int e = tid; e < P1; e += blockDim.x) {
+        const double r = (hy[e] - lam * y[e]) / nrm;
+        rr = fma(r, r, rr);
+    }
+    rr = warp_sum(rr);
+    if (lane == 0) red[warp][3] = rr;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][3];
+        st->res_explicit = sqrt(t);
+        st->rq = sv[1] / sv[0];
+        st->rq_s = sv[1] / sv[2];
+        st->c0 = fabs(y[0]) / nrm;
+        st->yty = sv[0];
+        int status = st->broke ? IRL_BREAKDOWN_INVARIANT : (st->conv ? IRL_OK : IRL_MAX_RESTARTS);
+        if (lam > -tol) status = LM_STATIONARY;
+        else if (fabs(y[0]) / nrm < 1e-8) status = LM_C0_TINY;
+        *status_out = status;
+        sv[0] = (double)status;
+    }
+    __syncthreads();
+    const int status = (int)sv[0];
+    const bool upd = (status == IRL_OK || status == IRL_BREAKDOWN_INVARIANT);
+    const double inv_c0 = 1.0 / (sv[4] / sqrt(sv[0] > 0.0 ? sv[0] : 1.0));
+    for (int e = tid; e < ldp; e += blockDim.x) {
+        const double c = e < P1 ? sgn * y[e] : 0.0;
+        y[e] = c;
+        if (c_out && e < P1) c_out[e] = c;
+        if (e >= 1 && e < P1) {
+            const double d = upd ? c * inv_c0 : 0.0;
+            if (dth_out) dth_out[e - 1] = d;
+            if (theta && upd) theta[e - 1] += d;
+        }
+    }
+}
+
+}  // namespace
+
+// =========================================================================
+// host side
+// =========================================================================
+namespace {
+
+struct Run {
+    lm_pencil *p;
+    cudaStream_t s;
+    LzArgs la;
+    int m, k, sym, prec;
+    int n_matvec, n_restart;
+};
+
+int lanczos_step(Run &R, int j) {
+    lm_pencil *p = R.p;
+    R.la.V = p->V;
+    const double *vj = p->V + (size_t)j * p->ldp;
+    if (int rc = lm_launch_pencil(p, vj, R.sym, R.prec, 0, &p->st->broke, R.s)) return rc;
+    const int g2 = R.la.nrow_grid;
+    k_lz_a<<<g2, LT, 0, R.s>>>(R.la, j);
+    k_lz_b<<<g2, LT, 0, R.s>>>(R.la, j);
+    k_lz_c<<<g2, LT, 0, R.s>>>(R.la, j);
+    k_lz_d<<<g2, LT, 0, R.s>>>(R.la, j, j + 1, 0);
+    lm_note_launch(p->ctx, 4);
+    R.n_matvec++;
+    return lm_cuda_check(p->ctx, cudaGetLastError(), "lanczos step");
+}
+
+// start vector from w (already filled): null projection + normalise into V[:,0]
+int start_vector(Run &R) {
+    lm_pencil *p = R.p;
+    const int g2 = R.la.nrow_grid;
+    R.la.V = p->V;
+    // reuse k_lz_c with j = -1 (no CGS terms): projection and norm only
+    k_lz_c<<<g2, LT, 0, R.s>>>(R.la, -1);
+    k_lz_d<<<g2, LT, 0, R.s>>>(R.la, 0, 0, 1);
+    lm_note_launch(p->ctx, 2);
+    return lm_cuda_check(p->ctx, cudaGetLastError(), "start vector");
+}
+
+int run_irl(Run &R, double tol, double rel, int max_restarts, const double *v0_dev,
+            uint64_t seed) {
+    lm_pencil *p = R.p;
+    lm_ctx *ctx = p->ctx;
+    cudaMemsetAsync(p->st, 0, sizeof(IrlState), R.s);
+    k_init_start<<<(p->ldp + 255) / 256, 256, 0, R.s>>>(p->wvec, p->ldp, p->P1, seed, v0_dev);
+    lm_note_launch(ctx);
+    if (int rc = start_vector(R)) return rc;
+    int j0 = 0;
+    for (int cycle = 0;; ++cycle) {
+        for (int j = j0; j < R.m; ++j)
+            if (int rc = lanczos_step(R, j)) return rc;
+        TriArgs ta;
+        ta.st = p->st;
+        ta.m = R.m;
+        ta.k = R.k;
+        ta.final_pass = cycle >= max_restarts;
+        ta.tol = tol;
+        ta.rel = rel;
+        k_tri<<<1, TT, 0, R.s>>>(ta);
+        lm_note_launch(ctx);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_tri")) return rc;
+        cudaError_t e = cudaMemcpyAsync(p->st_host, p->st, sizeof(IrlState),
+                                        cudaMemcpyDeviceToHost, R.s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(R.s);
+        if (int rc = lm_cuda_check(ctx, e, "IRL state read-back")) return rc;
+        int flags = 0;
+        if (int rc = lm_read_flags(ctx, R.s, &flags)) return rc;
+        if (flags & FLAG_TIMEOUT) return lm_fail(ctx, LM_ERR_TIMEOUT, "pencil pipeline wait timed out");
+        const IrlState &h = *p->st_host;
+        if (h.conv || h.broke || cycle >= max_restarts) break;
+        // implicit restart
+        double *Vnew = p->V + (size_t)(LM_MAXKRYLOV + 1) * p->ldp;
+        k_restart<<<R.la.nrow_grid, LT, 0, R.s>>>(R.la, Vnew, R.m, R.k);
+        lm_note_launch(ctx);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_restart")) return rc;
+        // swap halves: the kept vectors now live in Vnew
+        cudaMemcpyAsync(p->V, Vnew, (size_t)R.k * p->ldp * sizeof(double),
+                        cudaMemcpyDeviceToDevice, R.s);
+        R.la.V = p->V;
+        k_lz_d<<<R.la.nrow_grid, LT, 0, R.s>>>(R.la, 0, R.k, 2);
+        lm_note_launch(ctx);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "restart normalise")) return rc;
+        R.n_restart++;
+        j0 = R.k;
+    }
+    k_ritz_vector<<<(p->ldp + 255) / 256, 256, 0, R.s>>>(p->V, p->st, p->ldp, p->yvec);
+    lm_note_launch(ctx);
+    return lm_cuda_check(ctx, cudaGetLastError(), "k_ritz_vector");
+}
+
+}  // namespace
+
+extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, double *c_out,
+                        double *dtheta_out, double *theta_inout, void *stream) {
+    if (!p || !prm || !out) return LM_ERR_ARG;
+    lm_ctx *ctx = p->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prm->m > LM_MAXKRYLOV || prm->m < 2 || prm->k < 1 || prm->k >= prm->m || prm->m > p->P1)
+        return lm_fail(ctx, LM_ERR_SIZE, "need 1 <= k < m <= min(64, P+1); got k=%d m=%d", prm->k,
+                       prm->m);
+    if (prm->sym < 0 || prm->sym > 2 || prm->precision < 0 || prm->precision > 2)
+        return lm_fail(ctx, LM_ERR_ARG, "bad sym or precision");
+    Run R;
+    R.p = p;
+    R.s = s;
+    R.m = prm->m;
+    R.k = prm->k;
+    R.sym = prm->sym == LM_SYM_AUTO ? p->sym : prm->sym;
+    R.n_matvec = 0;
+    R.n_restart = 0;
+    R.la.V = p->V;
+    R.la.w = p->wvec;
+    R.la.part = p->part;
+    R.la.nparts = p->g_pencil;
+    R.la.dots = p->dots;
+    R.la.ldp = p->ldp;
+    R.la.M1 = p->M1;
+    R.la.P1 = p->P1;
+    R.la.nrow_grid = p->nh + 1;
+    R.la.n_orb = p->n;
+    R.la.na = p->na;
+    R.la.nb = p->nb;
+    R.la.deflate = prm->deflate_null;
+    R.la.st = p->st;
+
+    // optional start vector to the device
+    const double *v0_dev = nullptr;
+    if (prm->v0) {
+        if (lm_is_device_ptr(prm->v0)) {
+            v0_dev = prm->v0;
+        } else {
+            cudaMemcpyAsync(p->yvec, prm->v0, p->P1 * sizeof(double), cudaMemcpyHostToDevice, s);
+            v0_dev = p->yvec;
+        }
+    }
+    const int max_restarts = prm->max_restarts < 0 ? 0 : prm->max_restarts;
+    int n_lowp = 0;
+    const bool lowp = prm->precision != LM_FP64 && p->Olo != nullptr;
+    if (lowp) {
+        // Low-precision phase: stop at the relative residual the storage format
+        // supports, then continue the restarts with the FP64 operator from its
+        // Ritz vector until the requested tolerance.
+        R.prec = p->prec;
+        const double rel = p->prec == LM_FP32 ? 1e-6 : 1e-3;
+        if (int rc = run_irl(R, prm->tol, rel, max_restarts, v0_dev, prm->seed)) return rc;
+        n_lowp = R.n_matvec;
+        cudaMemcpyAsync(p->hy, p->yvec, p->ldp * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        v0_dev = p->hy;
+    }
+    R.prec = LM_FP64;
+    if (int rc = run_irl(R, prm->tol, 50.0 * 2.220446049250313e-16, max_restarts, v0_dev,
+                         prm->seed))
+        return rc;
+
+    // explicit FP64 refinement: H~' y and S~ y in one pass
+    if (int rc = lm_launch_pencil(p, p->yvec, R.sym, LM_FP64, 1, nullptr, s)) return rc;
+    if (int rc = lm_launch_reduce_partials(p, p->hy, p->sy, s)) return rc;
+    R.n_matvec++;
+    const bool c_dev = c_out && lm_is_device_ptr(c_out);
+    const bool d_dev = dtheta_out && lm_is_device_ptr(dtheta_out);
+    const bool t_dev = theta_inout && lm_is_device_ptr(theta_inout);
+    double *dth_tmp = p->dots + (size_t)3 * (p->nh + 1) * DLD;  // scratch >= ldp
+    if (theta_inout && !t_dev)
+        cudaMemcpyAsync(p->tvec, theta_inout, (p->P1 - 1) * sizeof(double),
+                        cudaMemcpyHostToDevice, s);
+    int *status_dev = reinterpret_cast<int *>(&p->st->err);
+    k_refine<<<1, 1024, 0, s>>>(p->yvec, p->hy, p->sy, p->st, p->ldp, p->P1,
+                                c_dev ? c_out : nullptr, d_dev ? dtheta_out : dth_tmp,
+                                theta_inout ? (t_dev ? theta_inout : p->tvec) : nullptr, prm->tol,
+                                status_dev);
+    lm_note_launch(ctx);
+    if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_refine")) return rc;
+    cudaMemcpyAsync(p->st_host, p->st, sizeof(IrlState), cudaMemcpyDeviceToHost, s);
+    if (c_out && !c_dev)
+        cudaMemcpyAsync(c_out, p->yvec, p->P1 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (dtheta_out && !d_dev)
+        cudaMemcpyAsync(dtheta_out, dth_tmp, (p->P1 - 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                        s);
+    if (theta_inout && !t_dev)
+        cudaMemcpyAsync(theta_inout, p->tvec, (p->P1 - 1) * sizeof(double),
+                        cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (int rc = lm_cuda_check(ctx, e, "irl_step")) return rc;
+    const IrlState &h = *p->st_host;
+    out->lambda = h.lam;
+    out->energy = p->E_host;
+    out->lambda_gen_rq = h.rq_s;
+    out->residual = h.res_explicit;
+    out->c0 = h.c0;
+    out->status = h.err;
+    out->n_matvec = R.n_matvec;
+    out->n_restart = R.n_restart;
+    out->n_matvec_lowp = n_lowp;
+    return LM_OK;
+}

@@ -1,0 +1,319 @@
+"""GPU parity: the sm_103a library through its C ABI against the FP64 oracle.
+
+Bars (stated per test): bit-exact sector enumeration, connectivity and signs;
+1e-12 relative on the FP64 build (O_c, G'_c, E_loc, ln psi, weights);
+1e-10 relative (2-norm) on FP64 pencil products and IRL eigenvalues;
+1e-8 relative on the update Delta theta; mixed precision within 1e-9 Ha of
+the FP64 eigenvalue after FP64 refinement.
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__ as entry
+import oracle
+import synth
+from oracle import fock, lm, native
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def abi():
+    entry.build()
+    from paper_2601_01437_gb300 import abi as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def ctx(abi):
+    c = abi.Context(0)
+    yield c
+    c.close()
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def _mc_rows(n, na, nb, count, seed, h):
+    return synth.proxy_mc_samples(n, na, nb, count, seed, h, walkers=512, burn_in=50)
+
+
+# ------------------------------------------------------------------ K1
+@pytest.mark.parametrize("n,na,nb", [(2, 1, 1), (6, 3, 3), (6, 2, 2), (7, 5, 5), (8, 5, 5),
+                                     (10, 7, 7), (10, 6, 6), (11, 9, 9), (9, 0, 4), (32, 1, 1)])
+def test_sector_enumeration_bit_exact(ctx, n, na, nb):
+    got = ctx.enumerate_sector(n, na, nb)
+    want = fock.sector_dets(n, na, nb)
+    assert got.dtype == np.uint64 and np.array_equal(got, want)
+
+
+# ------------------------------------------------------------------ K3/K4
+def _check_connections(ctx, n, na, nb, h, eri, rows):
+    sysd = ctx.system(n, na, nb, 1, h, eri)
+    cap = 4096
+    od, sg, hv, cnt = ctx.debug_connections(sysd, rows, cap)
+    for i, x in enumerate(rows):
+        ro_d, ro_h, ro_s = native.connections(n, na, nb, h, eri, int(x))
+        assert cnt[i] == len(ro_d)
+        assert od[i, 0] == x and sg[i, 0] == 1
+        gi = np.argsort(od[i, :cnt[i]], kind="stable")
+        oi = np.argsort(ro_d, kind="stable")
+        assert np.array_equal(od[i, :cnt[i]][gi], ro_d[oi]), "connectivity differs"
+        assert np.array_equal(sg[i, :cnt[i]][gi].astype(np.int32), ro_s[oi]), "sign differs"
+        scale = np.abs(ro_h).max()
+        assert np.abs(hv[i, :cnt[i]][gi] - ro_h[oi]).max() <= 1e-13 * scale
+
+
+def test_connections_bit_exact_tiny_all_rows(ctx):
+    h, eri = synth.integrals(6, 111)
+    _check_connections(ctx, 6, 3, 3, h, eri, fock.sector_dets(6, 3, 3))
+
+
+@pytest.mark.parametrize("n,na,nb,nrows", [(10, 7, 7, 64), (14, 7, 7, 16), (9, 0, 4, 32),
+                                           (7, 7, 3, 20)])
+def test_connections_bit_exact_sampled(ctx, n, na, nb, nrows):
+    h, eri = synth.integrals(n, 5)
+    dets = fock.sector_dets(n, na, nb) if n <= 10 else _mc_rows(n, na, nb, 400, 5, h)[0]
+    rng = np.random.default_rng(0)
+    rows = dets[rng.choice(len(dets), size=min(nrows, len(dets)), replace=False)]
+    _check_connections(ctx, n, na, nb, h, eri, rows)
+
+
+# ------------------------------------------------------------------ build
+def _build_both(ctx, abi, n, na, nb, nh, h, eri, theta, rows=None, counts=None, prec=0):
+    sysd = ctx.system(n, na, nb, nh, h, eri)
+    w = None if counts is None else counts.astype(np.float64)
+    pen = ctx.build_OG(sysd, theta, rows=rows, weights=w, prec=prec)
+    pd = lm.build_pencil(n, na, nb, nh, h, eri, theta, rows, counts)
+    return pen, pd
+
+
+def _check_build(abi, pen, pd):
+    P1 = pd.Oc.shape[1]
+    inf = pen.info()
+    assert inf.energy == pytest.approx(pd.E, rel=1e-12)
+    Oc = pen.export(abi.EXPORT_O)
+    Gc = pen.export(abi.EXPORT_G)
+    assert np.all(Oc[:, P1:] == 0) and np.all(Gc[:, P1:] == 0)
+    assert _rel(Oc[:, :P1], pd.Oc) <= 1e-12
+    assert _rel(Gc[:, :P1], pd.Gpc) <= 1e-12
+    assert _rel(pen.export(abi.EXPORT_W), pd.w) <= 1e-12
+    assert _rel(pen.export(abi.EXPORT_LNPSI), pd.lnpsi) <= 1e-13
+    assert _rel(pen.export(abi.EXPORT_ELOC), pd.eloc) <= 1e-12
+    assert np.array_equal(pen.export(abi.EXPORT_ROWS), pd.rows)
+
+
+def test_build_parity_tiny(ctx, abi):
+    w = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, th, _, _ = w.inputs()
+    pen, pd = _build_both(ctx, abi, 6, 3, 3, 24, h, eri, th)
+    _check_build(abi, pen, pd)
+    pen.free()
+
+
+def test_build_parity_f2_full_size(ctx, abi):
+    """All 14,400 rows of the F2-shaped workload, element by element."""
+    w = synth.WORKLOADS["f2_10o14e"]
+    h, eri, th, _, _ = w.inputs()
+    pen, pd = _build_both(ctx, abi, 10, 7, 7, 40, h, eri, th)
+    _check_build(abi, pen, pd)
+    pen.free()
+
+
+def test_build_parity_mc_rows_licl_shape(ctx, abi):
+    """LiCl-shaped system (28 spin orbitals, Nh=56) on 1,000 Monte Carlo rows with multiplicities."""
+    h, eri = synth.integrals(14, 111)
+    th = synth.rbm_theta(14, 56, 111)
+    rows, cnt = _mc_rows(14, 7, 7, 1000, 111, h)
+    pen, pd = _build_both(ctx, abi, 14, 7, 7, 56, h, eri, th, rows, cnt)
+    _check_build(abi, pen, pd)
+    pen.free()
+
+
+@pytest.mark.parametrize("n,na,nb,nh", [(2, 1, 1, 2), (3, 3, 1, 4), (4, 0, 2, 3), (32, 1, 1, 4),
+                                        (5, 2, 3, 7)])
+def test_build_parity_edge_shapes(ctx, abi, n, na, nb, nh):
+    """Degenerate sectors: 4 determinants, a full spin shell, an empty spin, M = 64, odd P+1."""
+    h, eri = synth.integrals(n, 17)
+    th = synth.rbm_theta(n, nh, 17, sigma=0.2)
+    pen, pd = _build_both(ctx, abi, n, na, nb, nh, h, eri, th)
+    _check_build(abi, pen, pd)
+    pen.free()
+
+
+# ------------------------------------------------------------------ pencil
+def _check_products(abi, pen, pd, mode, nvec=3, tol=1e-10, prec=0):
+    S, Hp = lm.pencil_matrices(pd.Oc, pd.Gpc, pd.w)
+    Hs = lm.symmetrise(Hp, "half" if mode == abi.LM_SYM_HALF else "none")
+    P1 = S.shape[0]
+    rng = np.random.default_rng(7)
+    for _ in range(nvec):
+        v = rng.standard_normal(P1)
+        Hv = np.zeros(P1)
+        Sv = np.zeros(P1)
+        pen.apply(v, Hv, Sv, sym=mode, prec=prec)
+        assert _rel(Hv, Hs @ v) <= tol
+        assert _rel(Sv, S @ v) <= tol
+
+
+def test_pencil_products_tiny_and_f2(ctx, abi):
+    for name in ("tiny_6o6e", "f2_10o14e"):
+        w = synth.WORKLOADS[name]
+        h, eri, th, _, _ = w.inputs()
+        pen, pd = _build_both(ctx, abi, w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th)
+        _check_products(abi, pen, pd, abi.LM_SYM_NONE)
+        _check_products(abi, pen, pd, abi.LM_SYM_HALF)
+        pen.free()
+
+
+def test_pencil_products_mc_rows(ctx, abi):
+    h, eri = synth.integrals(14, 111)
+    th = synth.rbm_theta(14, 56, 111)
+    rows, cnt = _mc_rows(14, 7, 7, 1000, 111, h)
+    pen, pd = _build_both(ctx, abi, 14, 7, 7, 56, h, eri, th, rows, cnt)
+    _check_products(abi, pen, pd, abi.LM_SYM_HALF)
+    _check_products(abi, pen, pd, abi.LM_SYM_NONE)
+    pen.free()
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 2e-6), (2, 2e-2)])
+def test_pencil_products_low_precision(ctx, abi, prec, tol):
+    h, eri = synth.integrals(14, 111)
+    th = synth.rbm_theta(14, 56, 111)
+    rows, cnt = _mc_rows(14, 7, 7, 1000, 111, h)
+    pen, pd = _build_both(ctx, abi, 14, 7, 7, 56, h, eri, th, rows, cnt, prec=prec)
+    _check_products(abi, pen, pd, abi.LM_SYM_HALF, tol=tol, prec=prec)
+    _check_products(abi, pen, pd, abi.LM_SYM_HALF, tol=1e-10, prec=0)
+    pen.free()
+
+
+# ------------------------------------------------------------------ IRL
+def _irl_case(ctx, abi, w, theta=None, rows=None, counts=None, prec=0):
+    h, eri, th, _, _ = w.inputs()
+    if theta is not None:
+        th = theta
+    pen, pd = _build_both(ctx, abi, w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th, rows,
+                          counts, prec=prec)
+    ref = lm.lm_step(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th, rows, counts)
+    c = np.zeros(w.n_params + 1)
+    dth = np.zeros(w.n_params)
+    res = pen.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=500, prec=prec, c_out=c,
+                       dtheta_out=dth)
+    return pen, ref, res, c, dth
+
+
+def test_irl_tiny_paper_settings(ctx, abi):
+    """k=1, m=20, tol=1e-12 (the paper's settings) on the 6-orbital workload."""
+    w = synth.WORKLOADS["tiny_6o6e"]
+    pen, ref, res, c, dth = _irl_case(ctx, abi, w)
+    assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
+    assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-10)
+    assert _rel(dth, ref["dtheta"]) <= 1e-8
+    assert abs(c @ ref["c"]) == pytest.approx(1.0, abs=1e-10)
+    assert res.residual <= 1e-10
+    pen.free()
+
+
+def test_irl_tiny_larger_theta(ctx, abi):
+    """A spread-out spectrum (theta ~ N(0, 0.3)) that needs several restarts."""
+    w = synth.WORKLOADS["tiny_6o6e"]
+    th = synth.rbm_theta(6, 24, 9, sigma=0.3)
+    pen, ref, res, c, dth = _irl_case(ctx, abi, w, theta=th)
+    assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
+    assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-10)
+    assert _rel(dth, ref["dtheta"]) <= 1e-8
+    pen.free()
+
+
+def test_irl_f2_full_size(ctx, abi):
+    """F2-shaped: 14,400 determinants, P=860, m=30, k=10."""
+    w = synth.WORKLOADS["f2_10o14e"]
+    pen, ref, res, c, dth = _irl_case(ctx, abi, w)
+    assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
+    assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-10)
+    assert _rel(dth, ref["dtheta"]) <= 1e-8
+    assert res.lambda_gen_rq == pytest.approx(
+        float(ref["c"] @ (0.5 * (ref["Hp"] + ref["Hp"].T)) @ ref["c"] / (ref["c"] @ ref["S"] @ ref["c"])),
+        rel=1e-8)
+    pen.free()
+
+
+def test_irl_mc_rows_half(ctx, abi):
+    h, eri = synth.integrals(14, 111)
+    rows, cnt = _mc_rows(14, 7, 7, 2000, 111, h)
+    w = synth.Workload("mc", 14, 7, 7, 56, m=20, k=1)
+    pen, ref, res, c, dth = _irl_case(ctx, abi, w, rows=rows, counts=cnt)
+    assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
+    assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-10)
+    pen.free()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_irl_mixed_precision_refined_to_fp64(ctx, abi, prec):
+    """FP32 / BF16 storage with FP64 refinement: |lambda - lambda_FP64| <= 1e-9 Ha."""
+    h, eri = synth.integrals(14, 111)
+    rows, cnt = _mc_rows(14, 7, 7, 2000, 111, h)
+    w = synth.Workload("mc", 14, 7, 7, 56, m=20, k=1)
+    pen, ref, res, c, dth = _irl_case(ctx, abi, w, rows=rows, counts=cnt, prec=prec)
+    assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
+    assert abs(res.lambda_ - ref["lam"]) <= 1e-9
+    assert res.n_matvec_lowp > 0
+    pen.free()
+
+
+def test_two_lm_steps_follow_the_oracle(ctx, abi):
+    """theta <- theta + Delta theta twice; energies and eigenvalues track the oracle's own steps."""
+    w = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, th, _, _ = w.inputs()
+    sysd = ctx.system(6, 3, 3, 24, h, eri)
+    tg = th.copy()
+    to = th.copy()
+    pen = None
+    for step in range(2):
+        pen = ctx.build_OG(sysd, tg, pencil=pen)
+        res = pen.irl_step(m=20, k=1, tol=1e-12, theta_inout=tg)
+        ref = lm.lm_step(6, 3, 3, 24, h, eri, to)
+        assert res.energy == pytest.approx(ref["E"], rel=1e-10)
+        assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-8)
+        to = to + ref["dtheta"]
+        assert _rel(tg, to) <= 1e-7
+    pen.free()
+
+
+def test_determinism_bitwise(ctx, abi):
+    w = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, th, _, _ = w.inputs()
+    out = []
+    for _ in range(2):
+        sysd = ctx.system(6, 3, 3, 24, h, eri)
+        pen = ctx.build_OG(sysd, th)
+        c = np.zeros(w.n_params + 1)
+        res = pen.irl_step(m=20, k=1, c_out=c)
+        out.append((res.lambda_, c.copy(), pen.export(abi.EXPORT_G)))
+        pen.free()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+# ------------------------------------------------------------------ errors
+def test_error_paths(ctx, abi):
+    h, eri = synth.integrals(6, 1)
+    th = synth.rbm_theta(6, 4, 1)
+    sysd = ctx.system(6, 3, 3, 4, h, eri)
+    bad_rows = np.array([0b111111, 0b111000000111], dtype=np.uint64)  # first has 6 alpha electrons
+    with pytest.raises(abi.LMError) as e:
+        ctx.build_OG(sysd, th, rows=bad_rows)
+    assert e.value.code == abi.LM_ERR_ARG
+    big = ctx.system(33, 1, 1, 4, np.zeros((33, 33)), np.zeros(33 ** 4))
+    with pytest.raises(abi.LMError) as e:
+        ctx.build_OG(big, np.zeros(1000))
+    assert e.value.code == abi.LM_ERR_SIZE
+    pen = ctx.build_OG(sysd, th)
+    with pytest.raises(abi.LMError) as e:
+        pen.irl_step(m=65, k=1)
+    assert e.value.code == abi.LM_ERR_SIZE
+    with pytest.raises(abi.LMError) as e:
+        pen.irl_step(m=10, k=10)
+    assert e.value.code == abi.LM_ERR_SIZE
+    pen.free()
