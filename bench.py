@@ -243,13 +243,14 @@ def run_gpu(args, rank, world, local):
         out["kernels"] = kern
     # end to end through the C ABI with host buffers (copies inside the timed region)
     if not args.no_e2e:
-        h_p = torch.from_numpy(h).pin_memory().numpy()
-        eri_p = torch.from_numpy(eri).pin_memory().numpy()
-        th_p = torch.from_numpy(th0).pin_memory().numpy()
+        pinned = [torch.from_numpy(h).pin_memory(), torch.from_numpy(eri).pin_memory(),
+                  torch.from_numpy(th0).pin_memory(),
+                  torch.zeros(w.n_params, dtype=torch.float64).pin_memory(),
+                  None if rows is None else torch.from_numpy(rows.view(np.int64)).pin_memory(),
+                  None if counts is None else
+                  torch.from_numpy(counts.astype(np.float64)).pin_memory()]
+        h_p, eri_p, th_p, dth_p, rows_p, wts_p = [None if t is None else t.numpy() for t in pinned]
         th0_np = th0.copy()
-        dth_p = torch.zeros(w.n_params, dtype=torch.float64).pin_memory().numpy()
-        rows_p = None if rows is None else torch.from_numpy(rows.view(np.int64)).pin_memory().numpy()
-        wts_p = None if counts is None else torch.from_numpy(counts.astype(np.float64)).pin_memory().numpy()
         sysh = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h_p, eri_p)
         pen2 = None
         last = {}

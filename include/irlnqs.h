@@ -112,7 +112,8 @@ typedef struct {
 } irl_params;
 
 typedef struct {
-    double lambda;        /* lowest Ritz value of the SHEP (eq. standard_evp)     */
+    double lambda;        /* lowest eigenvalue of the SHEP (eq. standard_evp): the  */
+                          /* FP64 Rayleigh quotient of the refined Ritz vector      */
     double energy;        /* E(theta)                                             */
     double lambda_gen_rq; /* generalised Rayleigh quotient c^T H~' c / c^T S~ c   */
     double residual;      /* explicit FP64 ||H~' c - lambda c||, |c| = 1          */

@@ -146,7 +146,7 @@ struct IrlState {
     double h1[LM_MAXKRYLOV + 1];              // reduced CGS dots (pass 1)
     double h2[LM_MAXKRYLOV + 1];              // reduced CGS dots (pass 2)
     double lam, res, tnorm, tol_eff, bnorm;
-    double rq, rq_s, res_explicit, c0, yty;
+    double rq, rq_s, res_explicit, c0, yty, lam_ritz;
     int jend, broke, conv, err;
 };
 

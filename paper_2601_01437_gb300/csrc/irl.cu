@@ -51,145 +51,203 @@ __device__ __forceinline__ void cta_range(const LzArgs &a, int &e0, int &e1) {
 
 __device__ __forceinline__ bool lz_skip(const IrlState *st) { return st->broke != 0; }
 
-// dots[i] (i <= j) of V[:, i] with w over this CTA's entries, by warps
-__device__ void cta_dots(const LzArgs &a, int e0, int e1, int j, double *out) {
+constexpr int LE = 80;  // max entries per CTA: M+1 <= 65 plus the padding of the last row
+
+// Shared-memory working set of one Lanczos vector CTA.
+struct LzShared {
+    double V[(LM_MAXKRYLOV + 1) * LE];  // V[i][e - e0]
+    double w[LE];
+    double h[LM_MAXKRYLOV + 1];
+    double red[LT];
+};
+
+// Stage V[:, 0..j] and w over [e0, e1) into shared memory (one parallel round).
+__device__ void load_block(const LzArgs &a, LzShared &S, int e0, int e1, int j, bool with_w) {
+    const int E = e1 - e0;
+    for (int t = threadIdx.x; t < (j + 1) * E; t += LT) {
+        const int i = t / E, e = t % E;
+        S.V[i * LE + e] = a.V[(size_t)i * a.ldp + e0 + e];
+    }
+    if (with_w)
+        for (int e = threadIdx.x; e < E; e += LT) S.w[e] = a.w[e0 + e];
+}
+
+// dots d[i] = V[:, i] . w over this CTA's entries, i <= j. Warp q handles
+// i = q, q+8, ...; lane = entry; the warp's dots are reduced together.
+__device__ void block_dots(const LzShared &S, int E, int j, double *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i <= j; i += LT / 32) {
-        const double *vi = a.V + (size_t)i * a.ldp;
+    double acc[(LM_MAXKRYLOV + 8) / 8];
+#pragma unroll
+    for (int k = 0; k < (LM_MAXKRYLOV + 8) / 8; ++k) {
+        const int i = warp + 8 * k;
         double s = 0.0;
-        for (int e = e0 + lane; e < e1; e += 32) s = fma(vi[e], a.w[e], s);
-        s = warp_sum(s);
-        if (lane == 0) out[i] = s;
+        if (i <= j)
+            for (int e = lane; e < E; e += 32) s = fma(S.V[i * LE + e], S.w[e], s);
+        acc[k] = s;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < (LM_MAXKRYLOV + 8) / 8; ++k)
+            acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < (LM_MAXKRYLOV + 8) / 8; ++k) {
+            const int i = warp + 8 * k;
+            if (i <= j) out[i] = acc[k];
+        }
+}
+
+// h[i] = sum over CTAs of region[cta][i] (i <= j): 8 interleaved partial sums
+// per dot, then a fixed-order sum of the 8.
+__device__ void sum_dots(const LzArgs &a, LzShared &S, int region, int j) {
+    const double *d = a.dots + (size_t)region * a.nrow_grid * DLD;
+    for (int base = 0; base <= j; base += LT / 8) {
+        const int i = base + (threadIdx.x >> 3), part = threadIdx.x & 7;
+        double s = 0.0;
+        if (i <= j)
+            for (int b = part; b < a.nrow_grid; b += 8) s += d[(size_t)b * DLD + i];
+        S.red[threadIdx.x] = s;
+        __syncthreads();
+        if (part == 0 && i <= j) {
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q) t += S.red[threadIdx.x + q];
+            S.h[i] = t;
+        }
+        __syncthreads();
     }
 }
 
-// h[i] = sum over CTAs of dots[region][cta][i], fixed CTA order
-__device__ void sum_dots(const LzArgs &a, int region, int j, double *h) {
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+// w[e] -= sum_{i<=j} V[i][e] h[i] with the i-sum split over 8 threads per entry.
+__device__ void block_update(LzShared &S, int E, int j) {
+    const int e = threadIdx.x >> 3, part = threadIdx.x & 7;
+    for (int eb = 0; eb < E; eb += LT / 8) {
+        const int ee = eb + e;
         double s = 0.0;
-        const double *d = a.dots + (size_t)region * a.nrow_grid * DLD;
-        for (int b = 0; b < a.nrow_grid; ++b) s += d[(size_t)b * DLD + i];
-        h[i] = s;
+        if (ee < E)
+            for (int i = part; i <= j; i += 8) s = fma(S.V[i * LE + ee], S.h[i], s);
+        S.red[threadIdx.x] = s;
+        __syncthreads();
+        if (part == 0 && ee < E) {
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q) t += S.red[threadIdx.x + q];
+            S.w[ee] -= t;
+        }
+        __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(LT) k_lz_a(LzArgs a, int j) {
     if (lz_skip(a.st)) return;
+    __shared__ LzShared S;
     int e0, e1;
     cta_range(a, e0, e1);
-    __shared__ double s[LT / 32][72];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // w = sum_b part[b][e]: 8 warps split b, fixed-order combine
-    for (int base = e0; base < e1; base += 32) {
-        const int e = base + lane;
-        double acc = 0.0;
-        if (e < e1)
-            for (int b = warp; b < a.nparts; b += LT / 32) acc += a.part[(size_t)b * 2 * a.ldp + e];
-        s[warp][lane] = acc;
-        __syncthreads();
-        if (warp == 0 && e < e1) {
-            double t = 0.0;
-            for (int w = 0; w < LT / 32; ++w) t += s[w][lane];
-            a.w[e] = t;
+    const int E = e1 - e0;
+    load_block(a, S, e0, e1, j, false);
+    // w = sum_b part[b][e]: threads (entry, 1 of 8 slices of b), fixed-order combine
+    {
+        const int part = threadIdx.x & 7;
+        for (int eb = 0; eb < E; eb += LT / 8) {
+            const int ee = eb + (threadIdx.x >> 3);
+            double acc = 0.0;
+            if (ee < E)
+                for (int b = part; b < a.nparts; b += 8)
+                    acc += a.part[(size_t)b * 2 * a.ldp + e0 + ee];
+            S.red[threadIdx.x] = acc;
+            __syncthreads();
+            if (part == 0 && ee < E) {
+                double t = 0.0;
+                for (int q = 0; q < 8; ++q) t += S.red[threadIdx.x + q];
+                S.w[ee] = t;
+                a.w[e0 + ee] = t;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
-    cta_dots(a, e0, e1, j, a.dots + (size_t)blockIdx.x * DLD);
+    block_dots(S, E, j, a.dots + (size_t)blockIdx.x * DLD);
 }
 
 __global__ void __launch_bounds__(LT) k_lz_b(LzArgs a, int j) {
     if (lz_skip(a.st)) return;
+    __shared__ LzShared S;
     int e0, e1;
     cta_range(a, e0, e1);
-    __shared__ double h[LM_MAXKRYLOV + 1];
-    sum_dots(a, 0, j, h);
-    __syncthreads();
+    const int E = e1 - e0;
+    load_block(a, S, e0, e1, j, true);
+    sum_dots(a, S, 0, j);
     if (blockIdx.x == 0)
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) a.st->h1[i] = h[i];
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        double x = a.w[e];
-        for (int i = 0; i <= j; ++i) x = fma(-a.V[(size_t)i * a.ldp + e], h[i], x);
-        a.w[e] = x;
-    }
-    __syncthreads();
-    cta_dots(a, e0, e1, j, a.dots + ((size_t)a.nrow_grid + blockIdx.x) * DLD);
+        for (int i = threadIdx.x; i <= j; i += LT) a.st->h1[i] = S.h[i];
+    block_update(S, E, j);
+    for (int e = threadIdx.x; e < E; e += LT) a.w[e0 + e] = S.w[e];
+    block_dots(S, E, j, a.dots + ((size_t)a.nrow_grid + blockIdx.x) * DLD);
 }
 
 __global__ void __launch_bounds__(LT) k_lz_c(LzArgs a, int j) {
     if (lz_skip(a.st)) return;
+    __shared__ LzShared S;
+    __shared__ double coef[2];
     int e0, e1;
     cta_range(a, e0, e1);
-    __shared__ double h[LM_MAXKRYLOV + 1];
-    __shared__ double red[LT / 32][4];
-    __shared__ double coef[2];
-    sum_dots(a, 1, j, h);
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0 && j >= 0) a.st->alpha[j] = a.st->h1[j] + h[j];
-    if (blockIdx.x == 0)
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) a.st->h2[i] = h[i];
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        double x = a.w[e];
-        for (int i = 0; i <= j; ++i) x = fma(-a.V[(size_t)i * a.ldp + e], h[i], x);
-        a.w[e] = x;
+    const int E = e1 - e0;
+    load_block(a, S, e0, e1, j, true);
+    if (j >= 0) {
+        sum_dots(a, S, 1, j);
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.st->alpha[j] = a.st->h1[j] + S.h[j];
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i <= j; i += LT) a.st->h2[i] = S.h[i];
+        block_update(S, E, j);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (a.deflate) {
-        // grid row r = blockIdx.x: columns 1..n alpha, n+1..2n beta, column 0
+        // grid row r = blockIdx.x: entries 1..n alpha, n+1..2n beta, entry 0
         const int r = blockIdx.x, n = a.n_orb;
-        double sa = 0.0, sb = 0.0;
-        for (int c = 1 + threadIdx.x; c <= 2 * n; c += blockDim.x) {
-            double x = a.w[r * a.M1 + c];
-            if (c <= n) sa += x; else sb += x;
-        }
-        sa = warp_sum(sa);
-        sb = warp_sum(sb);
-        if (lane == 0) {
-            red[warp][0] = sa;
-            red[warp][1] = sb;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double A = 0.0, B = 0.0;
-            for (int w = 0; w < LT / 32; ++w) {
-                A += red[w][0];
-                B += red[w][1];
+        if (warp == 0) {
+            double sa = 0.0, sb = 0.0;
+            for (int c = 1 + lane; c <= 2 * n; c += 32) {
+                if (c <= n) sa += S.w[c]; else sb += S.w[c];
             }
-            if (r == 0) {
-                coef[0] = A / n;
-                coef[1] = B / n;
-            } else {
-                // least squares on span{1_alpha - Na e0, 1_beta - Nb e0}
-                const double w0 = a.w[r * a.M1];
-                const double na = a.na, nb = a.nb;
-                const double g11 = n + na * na, g22 = n + nb * nb, g12 = na * nb;
-                const double r1 = A - na * w0, r2 = B - nb * w0;
-                const double det = g11 * g22 - g12 * g12;
-                coef[0] = (g22 * r1 - g12 * r2) / det;
-                coef[1] = (g11 * r2 - g12 * r1) / det;
+            sa = warp_sum(sa);
+            sb = warp_sum(sb);
+            if (lane == 0) {
+                if (r == 0) {
+                    coef[0] = sa / n;
+                    coef[1] = sb / n;
+                } else {
+                    // least squares on span{1_alpha - Na e0, 1_beta - Nb e0}
+                    const double w0 = S.w[0];
+                    const double na = a.na, nb = a.nb;
+                    const double g11 = n + na * na, g22 = n + nb * nb, g12 = na * nb;
+                    const double r1 = sa - na * w0, r2 = sb - nb * w0;
+                    const double det = g11 * g22 - g12 * g12;
+                    coef[0] = (g22 * r1 - g12 * r2) / det;
+                    coef[1] = (g11 * r2 - g12 * r1) / det;
+                }
             }
         }
         __syncthreads();
-        for (int c = threadIdx.x; c <= 2 * n; c += blockDim.x) {
-            double &x = a.w[r * a.M1 + c];
+        for (int c = threadIdx.x; c <= 2 * n; c += LT) {
             if (c == 0) {
-                if (r > 0) x += coef[0] * a.na + coef[1] * a.nb;
+                if (r > 0) S.w[0] += coef[0] * a.na + coef[1] * a.nb;
             } else if (c <= n) {
-                x -= coef[0];
+                S.w[c] -= coef[0];
             } else {
-                x -= coef[1];
+                S.w[c] -= coef[1];
             }
         }
         __syncthreads();
     }
     double s2 = 0.0;
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) s2 = fma(a.w[e], a.w[e], s2);
+    for (int e = threadIdx.x; e < E; e += LT) {
+        a.w[e0 + e] = S.w[e];
+        s2 = fma(S.w[e], S.w[e], s2);
+    }
     s2 = warp_sum(s2);
-    if (lane == 0) red[warp][2] = s2;
+    if (lane == 0) S.red[warp] = s2;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < LT / 32; ++w) t += red[w][2];
+        for (int w = 0; w < LT / 32; ++w) t += S.red[w];
         a.dots[((size_t)2 * a.nrow_grid + blockIdx.x) * DLD] = t;
     }
 }
@@ -200,13 +258,22 @@ __global__ void __launch_bounds__(LT) k_lz_c(LzArgs a, int j) {
 // mode 2: restart residual (jout = k, stores beta_{k-1})
 __global__ void __launch_bounds__(LT) k_lz_d(LzArgs a, int j, int jout, int mode) {
     if (mode == 0 && lz_skip(a.st)) return;
+    __shared__ double red[LT];
     __shared__ double sb;
     __shared__ int sbrk;
-    if (threadIdx.x == 0) {
+    {
         double t = 0.0;
-        for (int b = 0; b < a.nrow_grid; ++b)
+        for (int b = threadIdx.x; b < a.nrow_grid; b += LT)
             t += a.dots[((size_t)2 * a.nrow_grid + b) * DLD];
-        const double beta = sqrt(t);
+        red[threadIdx.x] = t;
+        __syncthreads();
+        for (int h = LT / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        const double beta = sqrt(red[0]);
         int brk = 0;
         if (mode == 0) {
             double tn = fmax(a.st->tnorm, fmax(fabs(a.st->alpha[j]), beta));
@@ -306,7 +373,7 @@ __global__ void __launch_bounds__(TT) k_tri(TriArgs t) {
     __shared__ double Q[LM_MAXKRYLOV * LM_MAXKRYLOV];
     __shared__ double rc[LM_MAXKRYLOV], rs[LM_MAXKRYLOV];
     __shared__ int rp[LM_MAXKRYLOV];
-    __shared__ double sscale, u0last;
+    __shared__ double sscale;
     __shared__ int je_s, conv_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -363,27 +430,91 @@ __global__ void __launch_bounds__(TT) k_tri(TriArgs t) {
         double x = 0.5 * ((double)blo[i] + (double)bhi[i]);
         double pn, pn1, dpn, plo, pl1, dl;
         charpoly(as, b2s, je, lo, plo, pl1, dl);
-        for (int it = 0; it < 8; ++it) {
+        for (int it = 0; it < 12; ++it) {
             charpoly(as, b2s, je, x, pn, pn1, dpn);
             if (pn == 0.0) break;
+            const double step = dpn != 0.0 ? pn / dpn : 0.0;
+            // converged: accept an ulp-sized Newton step before any safeguarding
+            if (dpn != 0.0 && fabs(step) <= 4.0 * 2.220446049250313e-16 * fabs(x)) {
+                x -= step;
+                break;
+            }
             if ((pn > 0.0) == (plo > 0.0)) lo = x; else hi = x;
-            double xn = dpn != 0.0 ? x - pn / dpn : 0.5 * (lo + hi);
-            if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-            const double dx = fabs(xn - x);
+            double xn = dpn != 0.0 ? x - step : 0.5 * (lo + hi);
+            if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
             x = xn;
-            if (dx <= 2e-16 * fmax(fabs(x), 1e-3)) break;
         }
-        charpoly(as, b2s, je, x, pn, pn1, dpn);
         ritz[i] = x * sc;
-        if (i == 0) u0last = (dpn != 0.0) ? fabs(pn1 / dpn) : 1.0;
     }
     __syncthreads();
+    // (3) eigenvector of the lowest Ritz value by inverse iteration (FP64,
+    // tridiagonal elimination with partial pivoting, two sweeps); its last
+    // component gives the residual beta_m |u_m| of the Ritz pair.
+    __shared__ double us[LM_MAXKRYLOV];
     if (tid == 0) {
+        const double lam = ritz[0];
+        const double eps = 2.220446049250313e-16 * sc;
+        double y[LM_MAXKRYLOV], d[LM_MAXKRYLOV], du[LM_MAXKRYLOV], du2[LM_MAXKRYLOV],
+            dl[LM_MAXKRYLOV];
+        int piv[LM_MAXKRYLOV];
+        for (int i = 0; i < je; ++i) {
+            d[i] = a[i] - lam;
+            du[i] = i < je - 1 ? b[i] : 0.0;
+            dl[i] = i < je - 1 ? b[i] : 0.0;
+            du2[i] = 0.0;
+            y[i] = 1.0;
+        }
+        // LU with partial pivoting (the dgttrf layout)
+        for (int i = 0; i < je - 1; ++i) {
+            if (fabs(d[i]) >= fabs(dl[i])) {
+                piv[i] = 0;
+                if (d[i] == 0.0) d[i] = eps;
+                const double f = dl[i] / d[i];
+                dl[i] = f;
+                d[i + 1] -= f * du[i];
+            } else {
+                piv[i] = 1;
+                const double f = d[i] / dl[i];
+                d[i] = dl[i];
+                dl[i] = f;
+                const double tmp = du[i];
+                du[i] = d[i + 1];
+                d[i + 1] = tmp - f * d[i + 1];
+                if (i < je - 2) {
+                    du2[i] = du[i + 1];
+                    du[i + 1] = -f * du[i + 1];
+                }
+            }
+        }
+        if (d[je - 1] == 0.0) d[je - 1] = eps;
+        // pivot reciprocals once (independent divisions), so the solves are
+        // chains of multiply-adds only
+        for (int i = 0; i < je; ++i) d[i] = 1.0 / d[i];
+        for (int sweep = 0; sweep < 2; ++sweep) {
+            for (int i = 0; i < je - 1; ++i) {
+                if (piv[i] == 0) {
+                    y[i + 1] -= dl[i] * y[i];
+                } else {
+                    const double tmp = y[i];
+                    y[i] = y[i + 1];
+                    y[i + 1] = tmp - dl[i] * y[i];
+                }
+            }
+            y[je - 1] *= d[je - 1];
+            if (je > 1) y[je - 2] = (y[je - 2] - du[je - 2] * y[je - 1]) * d[je - 2];
+            for (int i = je - 3; i >= 0; --i)
+                y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) * d[i];
+            double nn = 0.0;
+            for (int i = 0; i < je; ++i) nn += y[i] * y[i];
+            nn = 1.0 / sqrt(nn);
+            for (int i = 0; i < je; ++i) y[i] *= nn;
+        }
+        for (int i = 0; i < je; ++i) us[i] = y[i];
         double tn = 0.0;
         for (int i = 0; i < je; ++i) tn = fmax(tn, fabs(ritz[i]));
         const double tol_eff = fmax(t.tol, t.rel * tn);
         const double bres = st->broke ? 0.0 : fabs(st->beta[je - 1]);
-        const double res = st->broke ? 0.0 : bres * sqrt(fmin(u0last, 1.0));
+        const double res = bres * fabs(y[je - 1]);
         st->lam = ritz[0];
         st->res = res;
         st->tol_eff = tol_eff;
@@ -392,69 +523,11 @@ __global__ void __launch_bounds__(TT) k_tri(TriArgs t) {
         st->conv = conv;
         conv_s = conv;
     }
-    for (int i = tid; i < je; i += TT) st->ritz[i] = ritz[i];
     __syncthreads();
+    for (int i = tid; i < je; i += TT) st->ritz[i] = ritz[i];
     if (conv_s || t.final_pass) {
-        // (3) eigenvector of the lowest Ritz value by inverse iteration (FP64,
-        // tridiagonal elimination with partial pivoting), two sweeps.
-        if (tid == 0) {
-            const double lam = ritz[0];
-            const double eps = 2.220446049250313e-16 * sc;
-            double y[LM_MAXKRYLOV], d[LM_MAXKRYLOV], du[LM_MAXKRYLOV], du2[LM_MAXKRYLOV],
-                dl[LM_MAXKRYLOV];
-            int piv[LM_MAXKRYLOV];
-            for (int i = 0; i < je; ++i) {
-                d[i] = a[i] - lam;
-                du[i] = i < je - 1 ? b[i] : 0.0;
-                dl[i] = i < je - 1 ? b[i] : 0.0;
-                du2[i] = 0.0;
-                y[i] = 1.0;
-            }
-            // LU with partial pivoting (LAPACK dgttrf layout)
-            for (int i = 0; i < je - 1; ++i) {
-                if (fabs(d[i]) >= fabs(dl[i])) {
-                    piv[i] = 0;
-                    if (d[i] == 0.0) d[i] = eps;
-                    const double f = dl[i] / d[i];
-                    dl[i] = f;
-                    d[i + 1] -= f * du[i];
-                } else {
-                    piv[i] = 1;
-                    const double f = d[i] / dl[i];
-                    d[i] = dl[i];
-                    dl[i] = f;
-                    const double tmp = du[i];
-                    du[i] = d[i + 1];
-                    d[i + 1] = tmp - f * d[i + 1];
-                    if (i < je - 2) {
-                        du2[i] = du[i + 1];
-                        du[i + 1] = -f * du[i + 1];
-                    }
-                }
-            }
-            if (d[je - 1] == 0.0) d[je - 1] = eps;
-            for (int sweep = 0; sweep < 2; ++sweep) {
-                for (int i = 0; i < je - 1; ++i) {
-                    if (piv[i] == 0) {
-                        y[i + 1] -= dl[i] * y[i];
-                    } else {
-                        const double tmp = y[i];
-                        y[i] = y[i + 1];
-                        y[i + 1] = tmp - dl[i] * y[i];
-                    }
-                }
-                y[je - 1] /= d[je - 1];
-                if (je > 1) y[je - 2] = (y[je - 2] - du[je - 2] * y[je - 1]) / d[je - 2];
-                for (int i = je - 3; i >= 0; --i)
-                    y[i] = (y[i] - du[i] * y[i + 1] - du2[i] * y[i + 2]) / d[i];
-                double nn = 0.0;
-                for (int i = 0; i < je; ++i) nn += y[i] * y[i];
-                nn = 1.0 / sqrt(nn);
-                for (int i = 0; i < je; ++i) y[i] *= nn;
-            }
-            for (int i = 0; i < je; ++i) st->u[i] = y[i];
-            st->jend = je;
-        }
+        for (int i = tid; i < je; i += TT) st->u[i] = us[i];
+        if (tid == 0) st->jend = je;
         return;
     }
     // (4) implicit restart: mu = m - k shifts (largest first), pipelined chase
@@ -472,11 +545,14 @@ __global__ void __launch_bounds__(TT) k_tri(TriArgs t) {
                     bx = a[0] - ritz[m - 1 - q];
                     bz = b[0];
                 }
-                double r = hypot(bx, bz);
-                double c = 1.0, s = 0.0;
-                if (r != 0.0) {
-                    c = bx / r;
-                    s = bz / r;
+                // Givens rotation from one reciprocal square root (r = |(x, z)|)
+                const double r2 = fma(bx, bx, bz * bz);
+                double r = 0.0, c = 1.0, s = 0.0;
+                if (r2 > 1e-300) {
+                    const double ri = rsqrt(r2);
+                    c = bx * ri;
+                    s = bz * ri;
+                    r = r2 * ri;
                 }
                 if (p > 0) b[p - 1] = r;
                 const double ap = a[p], aq = a[p + 1], bp = b[p];
@@ -600,7 +676,7 @@ __global__ void __launch_bounds__(1024) k_refine(double *y, const double *hy, co
     }
     __syncthreads();
     const double nrm = sqrt(sv[0]);
-    const double lam = st->lam;
+    const double lam = sv[1] / sv[0];  // explicit FP64 Rayleigh quotient of the Ritz vector
     const double sgn = sv[3] / nrm;
     double rr = 0.0;
     for (int e = tid; e < P1; e += blockDim.x) {
@@ -615,6 +691,8 @@ __global__ void __launch_bounds__(1024) k_refine(double *y, const double *hy, co
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][3];
         st->res_explicit = sqrt(t);
         st->rq = sv[1] / sv[0];
+        st->lam_ritz = st->lam;
+        st->lam = st->rq;
         st->rq_s = sv[1] / sv[2];
         st->c0 = fabs(y[0]) / nrm;
         st->yty = sv[0];

@@ -10,11 +10,11 @@
 // streams it through shared memory in tiles of R rows with the bulk-copy
 // (TMA) engine: one 1-D cp.async.bulk per matrix per tile (a tile of
 // consecutive rows of a row-major matrix is one contiguous range), completion
-// tracked by an mbarrier per pipeline stage. Thread t owns the columns
-// t, t+256, ...: it forms its share of every row dot, the dots are finished
-// with warp shuffles and a fixed-order cross-warp sum, and the rank-R update
-// of the CTA's y accumulators uses the same staged tile. Each CTA writes its
-// partial y; a second kernel sums the partials in CTA order (deterministic).
+// tracked by an mbarrier per pipeline stage. Each warp owns whole rows: the
+// row dot is a 5-step butterfly, and the update of the warp's register-
+// resident y uses the same staged row. y_S is a second, O-only pass. Each CTA
+// writes its partial y; a second kernel sums the partials in CTA order
+// (deterministic).
 #include <algorithm>
 
 #include "internal.cuh"
@@ -41,6 +41,8 @@ __device__ __forceinline__ float ld_s<__nv_bfloat16>(const __nv_bfloat16 *p) {
     return __bfloat162float(*p);
 }
 
+enum { MODE_H_NONE = 0, MODE_H_HALF = 1, MODE_S = 2 };
+
 template <typename T>
 struct PencilArgs {
     const T *O;
@@ -49,35 +51,44 @@ struct PencilArgs {
     int64_t n_rows;
     int ldp;
     const double *v;
-    double *part;   // [gridDim.x][2*ldp]
-    int half;       // sym HALF
-    int want_s;
+    double *out;    // [gridDim.x][out_ld]: this CTA's partial y
+    int out_ld;
     int stages;
+    int rows_per_tile;
     const int *skip;
     int *flags;
 };
 
-template <typename T, int NC, int R>
+// One warp per row: lane l owns columns l, l+32, ... of the row, so a row dot
+// is one 5-step butterfly and the rank-1 update of the warp's y accumulators
+// (registers) reuses the staged row. MODE_H_NONE: y += w (G.v) O;
+// MODE_H_HALF: y += w/2 ((G.v) O + (O.v) G); MODE_S: y += w (O.v) O (only O
+// is staged). At the end the 8 warps' accumulators are summed in warp order.
+template <typename T, int NJ, int MODE>
 __global__ void __launch_bounds__(PT) k_pencil(PencilArgs<T> a) {
     using AT = typename Acc<T>::type;
     extern __shared__ __align__(128) unsigned char smraw[];
     if (a.skip && *a.skip) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ldp = a.ldp;
+    const int ldp = a.ldp, R = a.rows_per_tile;
+    const int nmat = MODE == MODE_S ? 1 : 2;
     const size_t tile_elems = (size_t)R * ldp;
     T *stage_base = reinterpret_cast<T *>(smraw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smraw + (size_t)a.stages * 2 * tile_elems * sizeof(T));
-    AT *red = reinterpret_cast<AT *>(bars + a.stages);  // [PT/32][2R]
+    const size_t stage_bytes_all = (size_t)a.stages * nmat * tile_elems * sizeof(T);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smraw + stage_bytes_all);
+    AT *vs = reinterpret_cast<AT *>(bars + 8);  // v in the compute type, ldp entries
     __shared__ int s_ok;
 
     const int64_t r0 = a.n_rows * blockIdx.x / gridDim.x;
     const int64_t r1 = a.n_rows * (blockIdx.x + 1) / gridDim.x;
     const int ntiles = (int)((r1 - r0 + R - 1) / R);
+    const int nj = (ldp + 31) >> 5;
 
     if (tid == 0) {
         for (int s = 0; s < a.stages; ++s) mbar_init(&bars[s], 1);
         fence_barrier_init();
     }
+    for (int c = tid; c < ldp; c += PT) vs[c] = (AT)a.v[c];
     __syncthreads();
 
     auto issue = [&](int i) {
@@ -85,24 +96,18 @@ __global__ void __launch_bounds__(PT) k_pencil(PencilArgs<T> a) {
         const int64_t row = r0 + (int64_t)i * R;
         const int nr = (int)min((int64_t)R, r1 - row);
         const uint32_t bytes = (uint32_t)((size_t)nr * ldp * sizeof(T));
-        T *dO = stage_base + (size_t)s * 2 * tile_elems;
-        T *dG = dO + tile_elems;
-        mbar_arrive_expect_tx(&bars[s], 2 * bytes);
+        T *dO = stage_base + (size_t)s * nmat * tile_elems;
+        mbar_arrive_expect_tx(&bars[s], nmat * bytes);
         bulk_g2s(dO, a.O + row * ldp, bytes, &bars[s]);
-        bulk_g2s(dG, a.G + row * ldp, bytes, &bars[s]);
+        if (MODE != MODE_S) bulk_g2s(dO + tile_elems, a.G + row * ldp, bytes, &bars[s]);
     };
     if (tid == 0)
         for (int i = 0; i < min(a.stages, ntiles); ++i) issue(i);
 
-    AT vr[NC], yH[NC], yS[NC];
+    AT y[NJ];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-        const int c = tid + q * PT;
-        vr[q] = c < ldp ? (AT)a.v[c] : (AT)0;
-        yH[q] = 0;
-        yS[q] = 0;
-    }
-    const bool need_o_dot = a.half || a.want_s;
+    for (int j = 0; j < NJ; ++j) y[j] = 0;
+
     int consumed = 0;
     bool ok = true;
     for (int i = 0; i < ntiles; ++i) {
@@ -115,72 +120,54 @@ __global__ void __launch_bounds__(PT) k_pencil(PencilArgs<T> a) {
             break;
         }
         consumed = i + 1;
-        const int64_t row = r0 + (int64_t)i * R;
-        const int nr = (int)min((int64_t)R, r1 - row);
-        const T *tO = stage_base + (size_t)s * 2 * tile_elems;
+        const int64_t row0 = r0 + (int64_t)i * R;
+        const int nr = (int)min((int64_t)R, r1 - row0);
+        const T *tO = stage_base + (size_t)s * nmat * tile_elems;
         const T *tG = tO + tile_elems;
-        AT dG[R], dO[R];
+        for (int r = warp; r < nr; r += PT / 32) {
+            const T *ro = tO + (size_t)r * ldp;
+            const T *rg = tG + (size_t)r * ldp;
+            AT dg = 0, dov = 0;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            dG[r] = 0;
-            dO[r] = 0;
-        }
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            const int c = tid + q * PT;
-            if (c < ldp) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (r < nr) {
-                        dG[r] += ld_s(tG + (size_t)r * ldp + c) * vr[q];
-                        if (need_o_dot) dO[r] += ld_s(tO + (size_t)r * ldp + c) * vr[q];
+            for (int j = 0; j < NJ; ++j) {
+                if (j < nj) {
+                    const int c = lane + 32 * j;
+                    if (c < ldp) {
+                        if (MODE != MODE_S) dg += ld_s(rg + c) * vs[c];
+                        if (MODE != MODE_H_NONE) dov += ld_s(ro + c) * vs[c];
                     }
                 }
             }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            AT g = dG[r], o = dO[r];
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                g += __shfl_xor_sync(0xffffffffu, g, off);
-                o += __shfl_xor_sync(0xffffffffu, o, off);
+                if (MODE != MODE_S) dg += __shfl_xor_sync(0xffffffffu, dg, off);
+                if (MODE != MODE_H_NONE) dov += __shfl_xor_sync(0xffffffffu, dov, off);
             }
-            if (lane == 0) {
-                red[warp * 2 * R + r] = g;
-                red[warp * 2 * R + R + r] = o;
-            }
-        }
-        __syncthreads();
-        AT cg[R], co[R];
+            const AT wr = (AT)a.w[row0 + r];
+            if (MODE == MODE_H_NONE) {
+                const AT cg = wr * dg;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            AT g = 0, o = 0;
-            for (int w = 0; w < PT / 32; ++w) {
-                g += red[w * 2 * R + r];
-                o += red[w * 2 * R + R + r];
-            }
-            const AT wr = r < nr ? (AT)a.w[row + r] : (AT)0;
-            cg[r] = wr * g;
-            co[r] = wr * o;
-        }
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            const int c = tid + q * PT;
-            if (c < ldp) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (r < nr) {
-                        const AT ov = ld_s(tO + (size_t)r * ldp + c);
-                        if (a.half) {
-                            const AT gv = ld_s(tG + (size_t)r * ldp + c);
-                            yH[q] += (AT)0.5 * (cg[r] * ov + co[r] * gv);
-                        } else {
-                            yH[q] += cg[r] * ov;
-                        }
-                        if (a.want_s) yS[q] += co[r] * ov;
+                for (int j = 0; j < NJ; ++j)
+                    if (j < nj) {
+                        const int c = lane + 32 * j;
+                        if (c < ldp) y[j] += cg * ld_s(ro + c);
                     }
-                }
+            } else if (MODE == MODE_H_HALF) {
+                const AT cg = (AT)0.5 * wr * dg, co = (AT)0.5 * wr * dov;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j)
+                    if (j < nj) {
+                        const int c = lane + 32 * j;
+                        if (c < ldp) y[j] += cg * ld_s(ro + c) + co * ld_s(rg + c);
+                    }
+            } else {
+                const AT co = wr * dov;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j)
+                    if (j < nj) {
+                        const int c = lane + 32 * j;
+                        if (c < ldp) y[j] += co * ld_s(ro + c);
+                    }
             }
         }
         __syncthreads();
@@ -197,14 +184,21 @@ __global__ void __launch_bounds__(PT) k_pencil(PencilArgs<T> a) {
         __syncthreads();
         return;
     }
-    double *out = a.part + (size_t)blockIdx.x * 2 * ldp;
+    // Sum the 8 warps' accumulators in warp order (staging buffers are free now).
+    double *ys = reinterpret_cast<double *>(smraw);  // [8][ldp] FP64
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-        const int c = tid + q * PT;
-        if (c < ldp) {
-            out[c] = (double)yH[q];
-            out[ldp + c] = (double)yS[q];
+    for (int j = 0; j < NJ; ++j)
+        if (j < nj) {
+            const int c = lane + 32 * j;
+            if (c < ldp) ys[(size_t)warp * ldp + c] = (double)y[j];
         }
+    __syncthreads();
+    double *out = a.out + (size_t)blockIdx.x * a.out_ld;
+    for (int c = tid; c < ldp; c += PT) {
+        double t = 0.0;
+#pragma unroll
+        for (int w8 = 0; w8 < PT / 32; ++w8) t += ys[(size_t)w8 * ldp + c];
+        out[c] = t;
     }
 }
 
@@ -230,9 +224,23 @@ __global__ void k_reduce_partials(const double *part, int nparts, int ldp, doubl
     }
 }
 
-template <typename T, int NC, int R>
-int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, int half, int want_s,
-             const int *skip, int stages, size_t smem, cudaStream_t s) {
+template <typename T, int NJ, int MODE>
+int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out, const int *skip,
+             cudaStream_t s) {
+    const int nmat = MODE == MODE_S ? 1 : 2;
+    const size_t row_bytes = (size_t)nmat * p->ldp * sizeof(T);
+    // rows per tile: about 48 KB per pipeline stage, one row per warp when two
+    // such stages fit, fewer rows (idle warps) for very long FP64 rows
+    const size_t tail = 8 * sizeof(uint64_t) + (size_t)p->ldp * sizeof(typename Acc<T>::type) + 256;
+    const size_t budget = (size_t)p->ctx->smem_optin - tail - 2048;
+    int R = (int)std::min<size_t>(64, std::max<size_t>(1, 49152 / row_bytes));
+    if (R < PT / 32) R = (int)std::max<size_t>(1, std::min<size_t>(PT / 32, budget / (2 * row_bytes)));
+    const size_t stage_bytes = R * row_bytes;
+    int stages = (int)std::min<size_t>(4, budget / stage_bytes);
+    if (stages < 2)
+        return lm_fail(p->ctx, LM_ERR_SIZE, "pencil row of %d columns too long", p->ldp);
+    size_t smem = stages * stage_bytes + tail;
+    smem = std::max(smem, (size_t)(PT / 32) * p->ldp * sizeof(double) + 64);
     PencilArgs<T> a;
     a.O = O;
     a.G = G;
@@ -240,52 +248,42 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, int half, in
     a.n_rows = p->n_rows;
     a.ldp = p->ldp;
     a.v = v;
-    a.part = p->part;
-    a.half = half;
-    a.want_s = want_s;
+    a.out = out;
+    a.out_ld = 2 * p->ldp;
     a.stages = stages;
+    a.rows_per_tile = R;
     a.skip = skip;
     a.flags = p->ctx->d_flags;
-    cudaError_t e = cudaFuncSetAttribute(k_pencil<T, NC, R>,
+    cudaError_t e = cudaFuncSetAttribute(k_pencil<T, NJ, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return lm_cuda_check(p->ctx, e, "pencil smem attribute");
     lm_prof_begin(p->ctx, PROF_PENCIL, s);
-    k_pencil<T, NC, R><<<p->g_pencil, PT, smem, s>>>(a);
+    k_pencil<T, NJ, MODE><<<p->g_pencil, PT, smem, s>>>(a);
     lm_prof_end(p->ctx, PROF_PENCIL, s);
     lm_note_launch(p->ctx);
     p->ctx->pencil_rows += p->n_rows;
     return lm_cuda_check(p->ctx, cudaGetLastError(), "k_pencil");
 }
 
-template <typename T, int NC>
-int dispatch_r(lm_pencil *p, const T *O, const T *G, const double *v, int half, int want_s,
-               const int *skip, cudaStream_t s) {
-    // R rows per tile: about 48 KB of O+G per pipeline stage.
-    const size_t row_pair = 2 * (size_t)p->ldp * sizeof(T);
-    int R = (int)std::max<size_t>(1, 49152 / row_pair);
-    R = R >= 8 ? 8 : R >= 4 ? 4 : R >= 2 ? 2 : 1;
-    const size_t stage_bytes = R * row_pair;
-    const size_t extra = 64 * sizeof(uint64_t) + (PT / 32) * 2 * 8 * sizeof(double) + 256;
-    const size_t budget = (size_t)p->ctx->smem_optin - extra - 2048;
-    int stages = (int)std::min<size_t>(4, budget / stage_bytes);
-    if (stages < 2)
-        return lm_fail(p->ctx, LM_ERR_SIZE, "pencil row of %d columns too long", p->ldp);
-    const size_t smem = stages * stage_bytes + extra;
-    switch (R) {
-        case 8: return launch_t<T, NC, 8>(p, O, G, v, half, want_s, skip, stages, smem, s);
-        case 4: return launch_t<T, NC, 4>(p, O, G, v, half, want_s, skip, stages, smem, s);
-        case 2: return launch_t<T, NC, 2>(p, O, G, v, half, want_s, skip, stages, smem, s);
-        default: return launch_t<T, NC, 1>(p, O, G, v, half, want_s, skip, stages, smem, s);
-    }
+template <typename T, int NJ>
+int dispatch_mode(lm_pencil *p, const T *O, const T *G, const double *v, int half, int want_s,
+                  const int *skip, cudaStream_t s) {
+    int rc = half ? launch_t<T, NJ, MODE_H_HALF>(p, O, G, v, p->part, skip, s)
+                  : launch_t<T, NJ, MODE_H_NONE>(p, O, G, v, p->part, skip, s);
+    if (!rc && want_s) rc = launch_t<T, NJ, MODE_S>(p, O, G, v, p->part + p->ldp, skip, s);
+    return rc;
 }
 
 template <typename T>
 int dispatch_nc(lm_pencil *p, const T *O, const T *G, const double *v, int half, int want_s,
                 const int *skip, cudaStream_t s) {
-    const int nc = (p->ldp + PT - 1) / PT;
-    if (nc <= 2) return dispatch_r<T, 2>(p, O, G, v, half, want_s, skip, s);
-    if (nc <= 4) return dispatch_r<T, 4>(p, O, G, v, half, want_s, skip, s);
-    if (nc <= 8) return dispatch_r<T, 8>(p, O, G, v, half, want_s, skip, s);
+    const int nj = (p->ldp + 31) / 32;
+    if (nj <= 8) return dispatch_mode<T, 8>(p, O, G, v, half, want_s, skip, s);
+    if (nj <= 16) return dispatch_mode<T, 16>(p, O, G, v, half, want_s, skip, s);
+    if (nj <= 28) return dispatch_mode<T, 28>(p, O, G, v, half, want_s, skip, s);
+    if (nj <= 40) return dispatch_mode<T, 40>(p, O, G, v, half, want_s, skip, s);
+    if (nj <= 52) return dispatch_mode<T, 52>(p, O, G, v, half, want_s, skip, s);
+    if (nj <= 64) return dispatch_mode<T, 64>(p, O, G, v, half, want_s, skip, s);
     return lm_fail(p->ctx, LM_ERR_SIZE, "P+1 = %d above the supported 2048", p->P1);
 }
 
