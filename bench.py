@@ -35,7 +35,9 @@ METRIC = "LM steps/sec"
 UNIT = "LM steps/s"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-FP64_PEAK_TFLOPS = 1.20  # project probe: DFMA throughput on this machine's GB300 (FP64 ALU roofline)
+# ALU peaks measured by the project's probe on this machine's GB300 (FMA = 2 flops)
+FP64_PEAK_TFLOPS = 1.20
+FP32_PEAK_TFLOPS = 74.6
 
 
 def parse():
@@ -47,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="f2_10o14e")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--arith", default="df64", choices=["df64", "fp64"],
+                    help="row-build arithmetic (both FP64-accurate; df64 runs on the FP32 pipes)")
     return ap.parse_args()
 
 
@@ -55,6 +59,18 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(value, world, device=None):
+    """Max of a per-rank float over all ranks (identity at world size 1)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def peaks():
@@ -115,16 +131,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
-def algorithmic_units(w):
-    """Per-launch algorithmic work of the two dominant kernels (formulas in the design doc)."""
+def algorithmic_units(w, arith="df64"):
+    """Per-launch algorithmic work of the two dominant kernels (derivation in the design doc).
+
+    Row build: per connection x hidden unit (ratio, tanh) and per connection x
+    augmented row (accumulation into G), counted in the arithmetic the kernel
+    uses. df64: FP32 flops of the double-float formulation (add/mul 1, fma 2,
+    rcp 1): singles 90 + 43, doubles 110 + 65. fp64: FP64 flops (divide 1):
+    singles 9 + 4, doubles 13 + 6.
+    Pencil: O_c and G'_c read once, N_s (P+1) (b_O + b_G) + 8 N_s bytes.
+    """
     n, na, nb, nh = w.n_orb, w.n_alpha, w.n_beta, w.n_hidden
     va, vb = n - na, n - nb
     singles = na * va + nb * vb
     doubles = (na * (na - 1) // 2) * (va * (va - 1) // 2) + \
               (nb * (nb - 1) // 2) * (vb * (vb - 1) // 2) + na * va * nb * vb
-    # FP64 flops of the row build per determinant row:
-    #   singles: Nh*9 (ratio, tanh) + (Nh+1)*4 (accumulate); doubles: Nh*13 + (Nh+1)*6
-    flops_row = singles * (nh * 9 + (nh + 1) * 4) + doubles * (nh * 13 + (nh + 1) * 6)
+    c = {"df64": (90, 43, 110, 65), "fp64": (9, 4, 13, 6)}[arith]
+    flops_row = singles * (nh * c[0] + (nh + 1) * c[1]) + doubles * (nh * c[2] + (nh + 1) * c[3])
     build_flops = flops_row * w.n_rows
     P1 = (nh + 1) * (2 * n + 1)
     bytes_for = {"f64": 16, "f32": 8, "bf16": 4}
@@ -156,7 +179,8 @@ def run_gpu(args, rank, world, local):
     wts_d = None if counts is None else torch.from_numpy(counts.astype(np.float64)).to(dev)
     dth = torch.zeros(w.n_params, dtype=torch.float64, device=dev)
     ctx = abi.Context(local)
-    sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h_d, eri_d)
+    arith = abi.LM_ARITH_DF64 if args.arith == "df64" else abi.LM_ARITH_FP64
+    sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h_d, eri_d, arith=arith)
     state = {"pen": None, "res": None}
     torch.cuda.synchronize()
 
@@ -190,11 +214,7 @@ def run_gpu(args, rank, world, local):
         dist.barrier()
     st = ctx.stats()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     res = state["res"]
     out = {
         "metric": METRIC, "value": args.steps * world / (ms / 1e3), "unit": UNIT,
@@ -209,6 +229,8 @@ def run_gpu(args, rank, world, local):
             "l2": "inputs larger than L2: O_c+G'_c "
                   f"{w.n_rows * (w.n_params + 1) * 16 / 1e6:.0f} MB FP64 vs 129 MB L2",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "build_arith": ("double-float (FP32 pairs, 48-bit significand) row build; FP64 "
+                            "pencil, Lanczos and refinement") if args.arith == "df64" else "FP64",
         },
         "clocks": clk,
         "gpu_launches": int(st.launches),
@@ -217,17 +239,19 @@ def run_gpu(args, rank, world, local):
                       "residual": res.residual},
     }
     # roofline of the dominant kernel, live CUDA-event durations over the timed region
-    build_flops, pencil_bytes = algorithmic_units(w)
+    build_flops, pencil_bytes = algorithmic_units(w, args.arith)
     hbm, hbm_src = peaks()
     kern = {}
     if st.build_count:
         d = st.build_ms / st.build_count / 1e3
         ach = build_flops / d / 1e12
-        kern["build"] = {"kernel": "k_build_rows", "bound": "alu", "achieved": ach,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                         "traffic": None, "avg_ms": d * 1e3, "launches": int(st.build_count),
-                         "total_ms": st.build_ms,
-                         "peak_source": "FP64 DFMA throughput measured by the project probe"}
+        pk = FP32_PEAK_TFLOPS if args.arith == "df64" else FP64_PEAK_TFLOPS
+        kern["build"] = {"kernel": "k_build_rows_df" if args.arith == "df64" else "k_build_rows",
+                         "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                         "frac": ach / pk, "traffic": None, "avg_ms": d * 1e3,
+                         "launches": int(st.build_count), "total_ms": st.build_ms,
+                         "peak_source": ("FP32 FFMA" if args.arith == "df64" else "FP64 DFMA") +
+                         " throughput measured by the project probe (FMA = 2 flops)"}
     if st.pencil_count:
         d = st.pencil_ms / st.pencil_count / 1e3
         ach = pencil_bytes / d / 1e9
@@ -251,7 +275,7 @@ def run_gpu(args, rank, world, local):
                   torch.from_numpy(counts.astype(np.float64)).pin_memory()]
         h_p, eri_p, th_p, dth_p, rows_p, wts_p = [None if t is None else t.numpy() for t in pinned]
         th0_np = th0.copy()
-        sysh = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h_p, eri_p)
+        sysh = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h_p, eri_p, arith=arith)
         pen2 = None
         last = {}
 
@@ -274,11 +298,7 @@ def run_gpu(args, rank, world, local):
         for i in range(args.steps):
             e2e_step(args.warmup + i)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, world, dev)
         h2d = h.nbytes + eri.nbytes + th0.nbytes + (0 if rows is None else rows.nbytes) + \
             (0 if counts is None else counts.size * 8)
         d2h = 2 * th0.nbytes + 72

@@ -81,11 +81,18 @@ typedef struct lm_pencil lm_pencil;
  * H = sum_{pq,s} h_pq a+_ps a_qs + 1/2 sum_{pqrs,s,t} (pq|rs) a+_ps a+_rt a_st a_qs.
  * h: n_orb x n_orb real symmetric; eri: n_orb^4 chemist (pq|rs) with 8-fold
  * symmetry, index ((p*n+q)*n+r)*n+s. Both are read during lm_build_OG only. */
+/* Arithmetic of the row build (lm_build_OG). Both give FP64-level results:
+ * DF64 evaluates the per-connection work in double-float (pairs of FP32, a
+ * 48-bit significand, relative error ~2^-44 per operation) on the FP32 pipes;
+ * FP64 uses native FP64 throughout (GB300 runs FP64 at 1/62 of FP32). */
+typedef enum { LM_ARITH_DF64 = 0, LM_ARITH_FP64 = 1 } lm_arith;
+
 typedef struct {
     int n_orb, n_alpha, n_beta, n_hidden;
     const double *h;
     const double *eri;
-    double e_core; /* added to E and E_loc */
+    double e_core;    /* added to E and E_loc */
+    int build_arith;  /* lm_arith; 0 (DF64) by default */
 } lm_system;
 
 typedef struct {

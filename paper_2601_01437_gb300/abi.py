@@ -18,6 +18,7 @@ LM_OK, LM_ERR_ARG, LM_ERR_SIZE, LM_ERR_OOM, LM_ERR_CUDA, LM_ERR_TIMEOUT = 0, -1,
 IRL_OK, IRL_BREAKDOWN_INVARIANT, IRL_MAX_RESTARTS, LM_C0_TINY, LM_STATIONARY = 0, 1, 2, 3, 4
 LM_FP64, LM_FP32, LM_BF16 = 0, 1, 2
 LM_SYM_AUTO, LM_SYM_NONE, LM_SYM_HALF = 0, 1, 2
+LM_ARITH_DF64, LM_ARITH_FP64 = 0, 1
 EXPORT_O, EXPORT_G, EXPORT_LNPSI, EXPORT_ELOC, EXPORT_W, EXPORT_OBAR, EXPORT_ROWS = range(7)
 
 c_int, c_double, c_int64, c_uint64, c_vp = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
@@ -26,7 +27,7 @@ c_int, c_double, c_int64, c_uint64, c_vp = (ctypes.c_int, ctypes.c_double, ctype
 
 class lm_system(ctypes.Structure):
     _fields_ = [("n_orb", c_int), ("n_alpha", c_int), ("n_beta", c_int), ("n_hidden", c_int),
-                ("h", c_vp), ("eri", c_vp), ("e_core", c_double)]
+                ("h", c_vp), ("eri", c_vp), ("e_core", c_double), ("build_arith", c_int)]
 
 
 class lm_pencil_info(ctypes.Structure):
@@ -151,8 +152,8 @@ class Context:
         except Exception:
             pass
 
-    def system(self, n_orb, n_alpha, n_beta, n_hidden, h, eri, e_core=0.0):
-        s = lm_system(n_orb, n_alpha, n_beta, n_hidden, ptr(h), ptr(eri), e_core)
+    def system(self, n_orb, n_alpha, n_beta, n_hidden, h, eri, e_core=0.0, arith=LM_ARITH_DF64):
+        s = lm_system(n_orb, n_alpha, n_beta, n_hidden, ptr(h), ptr(eri), e_core, int(arith))
         s._keep = (h, eri)
         return s
 

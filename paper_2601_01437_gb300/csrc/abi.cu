@@ -83,7 +83,7 @@ void pencil_release(lm_pencil *p) {
     void *bufs[] = {p->rows, p->wt,   p->lnpsi, p->eloc, p->O,    p->G,   p->Olo,
                     p->Glo,  p->h,    p->eri,   p->theta, p->tabs, p->stats, p->part,
                     p->V,    p->wvec, p->yvec,  p->hy,   p->sy,   p->tvec, p->dots,
-                    p->st};
+                    p->st,   p->tdf};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->st_host) cudaFreeHost(p->st_host);
@@ -207,6 +207,9 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
         rc = rc ? rc : dalloc(ctx, &p->eri, (size_t)n * n * n * n);
         rc = rc ? rc : dalloc(ctx, &p->theta, L);
         rc = rc ? rc : dalloc(ctx, &p->tabs, (size_t)2 * nh * M + 2 * M + 8);
+        rc = rc ? rc
+                : dalloc(ctx, &p->tdf, (size_t)2 * nh * M + 2 * M + (size_t)n * n +
+                                           (size_t)n * n * n * n + 8);
         rc = rc ? rc : dalloc(ctx, &p->stats, 8 + L);
         rc = rc ? rc : dalloc(ctx, &p->part, (size_t)p->part_len);
         rc = rc ? rc : dalloc(ctx, &p->V, 2 * (LM_MAXKRYLOV + 1) * L);
@@ -230,6 +233,9 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
     p->given_weights = weights != nullptr;
     p->sym = enumerate ? LM_SYM_NONE : LM_SYM_HALF;
     p->e_core = sys->e_core;
+    if (sys->build_arith != LM_ARITH_DF64 && sys->build_arith != LM_ARITH_FP64)
+        return lm_fail(ctx, LM_ERR_ARG, "bad build_arith %d", sys->build_arith);
+    p->arith = sys->build_arith;
     int rc = 0;
     rc = rc ? rc : to_device(ctx, p->h, sys->h, sizeof(double) * n * n, s);
     rc = rc ? rc : to_device(ctx, p->eri, sys->eri, sizeof(double) * n * n * n * n, s);

@@ -8,6 +8,7 @@
 // 64-byte boundary for FP64 and on 16 bytes for the low-precision copies).
 #include <cstdarg>
 
+#include "df64.cuh"
 #include "internal.cuh"
 
 namespace {
@@ -438,6 +439,298 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_rows(BuildArgs A) {
     }
 }
 
+// ------------------------------------- K2-K6 in double-float arithmetic
+// tabs_df (float2 = df) = [exp(W) Nh x M | exp(-W) Nh x M | exp(a) M | exp(-a) M |
+//                          h n^2 | (pq|rs) n^4]
+__global__ void k_tables_df(const double *tabs, const double *h, const double *eri, int M, int nh,
+                            int n, float2 *out) {
+    const int n_exp = 2 * nh * M + 2 * M, n2 = n * n, n4 = n2 * n2;
+    const int tot = n_exp + n2 + n4;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+        double x = e < n_exp ? tabs[e] : (e < n_exp + n2 ? h[e - n_exp] : eri[e - n_exp - n2]);
+        const df d = df_from_double(x);
+        out[e] = make_float2(d.h, d.l);
+    }
+}
+
+__device__ __forceinline__ df ld_df(const float2 *p) {
+    const float2 v = *p;
+    return df_make(v.x, v.y);
+}
+__device__ __forceinline__ df ldg_df(const float2 *p) {
+    const float2 v = __ldg(p);
+    return df_make(v.x, v.y);
+}
+__device__ __forceinline__ void st_df(float2 *p, df a) { *p = make_float2(a.h, a.l); }
+
+struct BuildDfArgs {
+    SysView S;
+    int nh, M, M1, P1, ldp;
+    int ldF, ldS, nslice;
+    const double *theta;
+    const float2 *tdf;  // df tables (see k_tables_df)
+    const uint64_t *rows;
+    int64_t n_rows;
+    uint64_t amask, bmask;
+    double e_core;
+    double *lnpsi, *eloc, *O, *G;
+    int *flags;
+};
+
+constexpr int BDF_THREADS = 256;
+constexpr int BDF_TPC = 4;                        // threads per connection
+constexpr int BDF_K = BDF_THREADS / BDF_TPC;      // connections per batch
+
+// Slater-Condon <x'|H|x> (without sign) in double-float, integrals from tdf.
+__device__ __forceinline__ df exc_value_df(const SysView &S, const RowLists &L, const Exc &e,
+                                           const float2 *hd, const float2 *gd) {
+    const int n = S.n;
+    auto g4 = [&](int p, int q, int r, int s) {
+        return ldg_df(gd + (((size_t)p * n + q) * n + r) * n + s);
+    };
+    if (e.j < 0) {
+        const int sp = e.i >= n;
+        const int ip = e.i - sp * n, ap = e.a - sp * n;
+        df v = ldg_df(hd + ap * n + ip);
+        for (int t = 0; t < S.na; ++t) {
+            const int kp = L.oa[t];
+            v = df_add(v, g4(ap, ip, kp, kp));
+            if (sp == 0) v = df_sub(v, g4(ap, kp, kp, ip));
+        }
+        for (int t = 0; t < S.nb; ++t) {
+            const int kp = L.ob[t] - n;
+            v = df_add(v, g4(ap, ip, kp, kp));
+            if (sp == 1) v = df_sub(v, g4(ap, kp, kp, ip));
+        }
+        return v;
+    }
+    const int si = e.i >= n, sj = e.j >= n, sa = e.a >= n, sb = e.b >= n;
+    const int ip = e.i - si * n, jp = e.j - sj * n, ap = e.a - sa * n, bp = e.b - sb * n;
+    df v = df_make(0.f, 0.f);
+    if (sa == si && sb == sj) v = g4(ap, ip, bp, jp);
+    if (sa == sj && sb == si) v = df_sub(v, g4(ap, jp, bp, ip));
+    return v;
+}
+
+// Keep a running product m * 2^ex with m in [2^-60, 2^60].
+__device__ __forceinline__ void df_renorm(df &m, int &ex) {
+    const float a = fabsf(m.h);
+    if (a > 0x1p60f || a < 0x1p-60f) {
+        int k;
+        frexpf(m.h, &k);
+        m = df_ldexp(m, -k);
+        ex += k;
+    }
+}
+
+// Same computation as k_build_rows, with every per-connection and
+// per-(connection, hidden unit) operation in double-float arithmetic on the
+// FP32 pipes. Four threads share a connection, each taking every fourth
+// hidden unit; their partial products of cosh ratios are combined with
+// shuffles. FP64 remains for the per-row pre-activations, ln psi, the
+// diagonal element and the final conversion of each G entry.
+__global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    const int nh = A.nh, M = A.M, M1 = A.M1;
+    const int tid = threadIdx.x, lane = tid & 31;
+    int4 *sIdx = reinterpret_cast<int4 *>(smb);                 // [K]
+    RowLists *sL = reinterpret_cast<RowLists *>(sIdx + BDF_K);  // 1
+    float2 *sEW = reinterpret_cast<float2 *>(sL + 1);           // [nh][M]
+    float2 *sEWi = sEW + nh * M;                                // [nh][M]
+    float2 *sea = sEWi + nh * M;                                // [M]
+    float2 *seai = sea + M;                                     // [M]
+    float2 *sPQ = seai + M;                                     // [nh][2] (P, Q)
+    float2 *sTd = sPQ + 2 * nh;                                 // [nh] t as df
+    float2 *sF = sTd + nh;                                      // [K][ldF]
+    float2 *sC = sF + BDF_K * A.ldF;                            // [K]
+    float2 *sS = sC + BDF_K;                                    // [nslice][nh+1][ldS]
+    float2 *sA = sS + A.nslice * (nh + 1) * A.ldS;              // [nslice][nh+1]
+    float2 *sRed = sA + A.nslice * (nh + 1);                    // [BDF_THREADS/32]
+    double *sT = reinterpret_cast<double *>(sRed + BDF_THREADS / 32);  // [nh] t (FP64)
+    __shared__ double sDiag, sLn;
+    __shared__ int sBad;
+
+    const float2 *hd = A.tdf + 2 * nh * M + 2 * M;
+    const float2 *gd = hd + A.S.n * A.S.n;
+    for (int e = tid; e < 2 * nh * M + 2 * M; e += BDF_THREADS) sEW[e] = A.tdf[e];
+    __syncthreads();
+
+    const int nsl = A.nslice;
+    const int sc_r = tid % (nh + 1), sc_s = tid / (nh + 1);
+    const bool scatter_thread = sc_s < nsl;
+    const int kk = tid / BDF_TPC, sub = tid % BDF_TPC;
+
+    for (int64_t row = blockIdx.x; row < A.n_rows; row += gridDim.x) {
+        const uint64_t x = A.rows[row];
+        if (tid == 0) {
+            const int bad = (__popcll(x & A.amask) != A.S.na) ||
+                            (__popcll(x & A.bmask) != A.S.nb) || (x & ~(A.amask | A.bmask)) != 0;
+            sBad = bad;
+            if (bad) atomicOr(A.flags, FLAG_ROW_OUTSIDE_SECTOR);
+            make_lists(A.S, x, *sL);
+        }
+        __syncthreads();
+        if (sBad) {
+            __syncthreads();
+            continue;
+        }
+        for (int j = tid; j < nh; j += BDF_THREADS) {
+            double z = A.theta[(j + 1) * M1 - 1];
+            for (int p = 0; p < M; ++p)
+                if ((x >> p) & 1ull) z += A.theta[(j + 1) * M1 + p];
+            const double az = fabs(z);
+            const double e2 = exp(-2.0 * az);
+            const double inv = 1.0 / (1.0 + e2);
+            const double big = inv, small = e2 * inv;
+            const df P = df_from_double(z >= 0.0 ? big : small);   // e^{z} / (2 cosh z)
+            const df Q = df_from_double(z >= 0.0 ? small : big);   // e^{-z} / (2 cosh z)
+            sPQ[2 * j] = make_float2(P.h, P.l);
+            sPQ[2 * j + 1] = make_float2(Q.h, Q.l);
+            const double t = tanh(z);
+            sT[j] = t;
+            const df td = df_from_double(t);
+            sTd[j] = make_float2(td.h, td.l);
+        }
+        for (int e = tid; e < nsl * (nh + 1) * A.ldS; e += BDF_THREADS) sS[e] = make_float2(0.f, 0.f);
+        __syncthreads();
+        if (tid < 32) {
+            double lp = 0.0;
+            for (int j = tid; j < nh; j += 32) {
+                double zz = A.theta[(j + 1) * M1 - 1];
+                for (int p = 0; p < M; ++p)
+                    if ((x >> p) & 1ull) zz += A.theta[(j + 1) * M1 + p];
+                lp += fabs(zz) + log1p(exp(-2.0 * fabs(zz)));
+            }
+            for (int p = tid; p < M; p += 32)
+                if ((x >> p) & 1ull) lp += A.theta[p];
+            lp = warp_sum(lp);
+            if (tid == 0) sLn = lp;
+        } else if (tid < 64) {
+            const double d = diag_value_warp(A.S, *sL);
+            if (tid == 32) sDiag = d + A.e_core;
+        }
+        __syncthreads();
+
+        df el_part = df_make(0.f, 0.f);
+        df accA = df_make(0.f, 0.f);
+        const RowLists &L = *sL;
+        for (int k0 = 0; k0 < A.S.conn; k0 += BDF_K) {
+            const int k = k0 + kk;
+            const bool active = k < A.S.conn;
+            Exc e;
+            e.i = e.j = e.a = e.b = -1;
+            int sg = 1;
+            bool dbl = false;
+            df rp = df_make(1.f, 0.f);
+            int re = 0;
+            if (active) {
+                e = decode_exc(A.S, L, k);
+                (void)apply_exc(x, e, sg);
+                dbl = e.j >= 0;
+                float2 *Frow = sF + kk * A.ldF;
+                for (int j = sub; j < nh; j += BDF_TPC) {
+                    const float2 *ew = sEW + j * M;
+                    const float2 *ewi = sEWi + j * M;
+                    df ep = df_mul(ld_df(ew + e.a), ld_df(ewi + e.i));
+                    if (dbl) ep = df_mul(ep, df_mul(ld_df(ew + e.b), ld_df(ewi + e.j)));
+                    const df em = df_rcp(ep);
+                    const df t1 = df_mul(ep, ld_df(sPQ + 2 * j));
+                    const df u = df_mul(em, ld_df(sPQ + 2 * j + 1));
+                    const df q = df_add(t1, u);    // cosh(z+d)/cosh(z)
+                    const df nu = df_sub(t1, u);   // sinh(z+d)/cosh(z)
+                    rp = df_mul(rp, q);
+                    df_renorm(rp, re);
+                    st_df(Frow + j, df_div(nu, q));  // tanh(z+d)
+                }
+            }
+            // combine the partial products of the BDF_TPC lanes of a connection
+            // (all lanes take part; inactive ones carry 1 * 2^0)
+#pragma unroll
+            for (int off = 1; off < BDF_TPC; off <<= 1) {
+                const df o = df_make(__shfl_xor_sync(0xffffffffu, rp.h, off),
+                                     __shfl_xor_sync(0xffffffffu, rp.l, off));
+                const int oe = __shfl_xor_sync(0xffffffffu, re, off);
+                rp = df_mul(rp, o);
+                re += oe;
+                df_renorm(rp, re);
+            }
+            if (active && sub == 0) {
+                df hv = exc_value_df(A.S, L, e, hd, gd);
+                if (sg < 0) hv = df_neg(hv);
+                df ead = df_mul(ld_df(sea + e.a), ld_df(seai + e.i));
+                if (dbl) ead = df_mul(ead, df_mul(ld_df(sea + e.b), ld_df(seai + e.j)));
+                df c = df_mul(df_mul(hv, ead), rp);
+                c = df_ldexp(c, re);
+                st_df(sC + kk, c);
+                sIdx[kk] = make_int4(e.i, e.j, e.a, e.b);
+                el_part = df_add(el_part, c);
+            }
+            __syncthreads();
+            if (scatter_thread) {
+                const int kend = min(BDF_K, A.S.conn - k0);
+                float2 *Srow = sS + (sc_s * (nh + 1) + sc_r) * A.ldS;
+                for (int q = sc_s; q < kend; q += nsl) {
+                    df f = ld_df(sC + q);
+                    if (sc_r > 0) f = df_mul(f, ld_df(sF + q * A.ldF + sc_r - 1));
+                    const int4 ix = sIdx[q];
+                    accA = df_add(accA, f);
+                    st_df(Srow + ix.x, df_add(ld_df(Srow + ix.x), f));
+                    st_df(Srow + ix.z, df_add(ld_df(Srow + ix.z), f));
+                    if (ix.y >= 0) {
+                        st_df(Srow + ix.y, df_add(ld_df(Srow + ix.y), f));
+                        st_df(Srow + ix.w, df_add(ld_df(Srow + ix.w), f));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (scatter_thread) st_df(sA + sc_s * (nh + 1) + sc_r, accA);
+        // E_loc: per-warp df sums in lane order, then warps in order
+        {
+            df v = el_part;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const df o = df_make(__shfl_xor_sync(0xffffffffu, v.h, off),
+                                     __shfl_xor_sync(0xffffffffu, v.l, off));
+                v = df_add(v, o);
+            }
+            if (lane == 0) st_df(sRed + (tid >> 5), v);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            df el = df_from_double(sDiag);
+            for (int w = 0; w < BDF_THREADS / 32; ++w) el = df_add(el, ld_df(sRed + w));
+            A.eloc[row] = df_to_double(el);
+            A.lnpsi[row] = sLn;
+        }
+        // O row and G row
+        double *Orow = A.O + row * (int64_t)A.ldp;
+        double *Grow = A.G + row * (int64_t)A.ldp;
+        const df hdg = df_from_double(sDiag);
+        for (int e = tid; e < A.ldp; e += BDF_THREADS) {
+            double ov = 0.0, gv = 0.0;
+            if (e < A.P1) {
+                const int r = e / M1, c = e % M1;
+                const bool xc = (c == 0) || ((x >> (c - 1)) & 1ull);
+                ov = xc ? (r == 0 ? 1.0 : sT[r - 1]) : 0.0;
+                df at = (r == 0) ? hdg : df_mul(hdg, ld_df(sTd + r - 1));
+                for (int s2 = 0; s2 < nsl; ++s2) at = df_add(at, ld_df(sA + s2 * (nh + 1) + r));
+                if (c == 0) {
+                    gv = df_to_double(at);
+                } else {
+                    df sv = df_make(0.f, 0.f);
+                    for (int s2 = 0; s2 < nsl; ++s2)
+                        sv = df_add(sv, ld_df(sS + (s2 * (nh + 1) + r) * A.ldS + c - 1));
+                    gv = df_to_double(((x >> (c - 1)) & 1ull) ? df_sub(at, sv) : sv);
+                }
+            }
+            Orow[e] = ov;
+            Grow[e] = gv;
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------ K7: weights and statistics
 // Max of ln psi (for the |psi|^2 weights' shift): per-CTA partial maxima.
 __global__ void k_lnpsi_max_partial(const double *lnpsi, int64_t n, double *part) {
@@ -456,12 +749,10 @@ __global__ void k_lnpsi_max_partial(const double *lnpsi, int64_t n, double *part
     }
 }
 
-// Per-CTA partial sums over a contiguous row chunk: sum w, sum w E_loc,
-// sum w O[:, c]. w = exp(2 (ln psi - max)) (|psi|^2 up to a constant) or the
-// given weight. Unnormalised weights are stored in wt.
-__global__ void k_stats_partial(const double *O, const double *lnpsi, const double *eloc,
-                                const double *given, double *wt, int64_t n, int ldp,
-                                const double *max_part, int n_max_part, double *part) {
+// Unnormalised weights, one per row: w = exp(2 (ln psi - max)) (|psi|^2 up to a
+// constant) or the given weight.
+__global__ void k_weights(const double *lnpsi, const double *given, double *wt, int64_t n,
+                          const double *max_part, int n_max_part) {
     __shared__ double sMax;
     if (threadIdx.x == 0) {
         double m = -INFINITY;
@@ -470,23 +761,32 @@ __global__ void k_stats_partial(const double *O, const double *lnpsi, const doub
         sMax = m;
     }
     __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        wt[r] = given ? given[r] : exp(2.0 * (lnpsi[r] - sMax));
+}
+
+// Per-CTA partial sums over a contiguous row chunk: sum w, sum w E_loc,
+// sum w O[:, c].
+__global__ void k_stats_partial(const double *O, const double *eloc, const double *wt, int64_t n,
+                                int ldp, double *part) {
     const int64_t r0 = n * blockIdx.x / gridDim.x, r1 = n * (blockIdx.x + 1) / gridDim.x;
     double *out = part + (int64_t)blockIdx.x * (ldp + 2);
     for (int c = threadIdx.x; c < ldp; c += blockDim.x) {
-        double acc = 0.0;
-        for (int64_t r = r0; r < r1; ++r) {
-            double w = given ? given[r] : exp(2.0 * (lnpsi[r] - sMax));
-            acc = fma(w, O[r * ldp + c], acc);
+        double a0 = 0.0, a1 = 0.0;  // two interleaved chains
+        int64_t r = r0;
+        for (; r + 1 < r1; r += 2) {
+            a0 = fma(wt[r], O[r * ldp + c], a0);
+            a1 = fma(wt[r + 1], O[(r + 1) * ldp + c], a1);
         }
-        out[c] = acc;
+        if (r < r1) a0 = fma(wt[r], O[r * ldp + c], a0);
+        out[c] = a0 + a1;
     }
     if (threadIdx.x == 0) {
         double sw = 0.0, se = 0.0;
         for (int64_t r = r0; r < r1; ++r) {
-            double w = given ? given[r] : exp(2.0 * (lnpsi[r] - sMax));
-            wt[r] = w;
-            sw += w;
-            se = fma(w, eloc[r], se);
+            sw += wt[r];
+            se = fma(wt[r], eloc[r], se);
         }
         out[ldp] = sw;
         out[ldp + 1] = se;
@@ -634,27 +934,80 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     if (p->nh + 1 > BUILD_THREADS)
         return lm_fail(ctx, LM_ERR_SIZE, "n_hidden + 1 = %d exceeds %d", p->nh + 1,
                        BUILD_THREADS);
-    size_t smem = build_smem_bytes(p->nh, p->M, A.ldF, A.ldS, A.nslice);
-    if (smem > (size_t)ctx->smem_optin)
-        return lm_fail(ctx, LM_ERR_SIZE, "build kernel needs %zu B shared memory", smem);
-    cudaError_t e = cudaFuncSetAttribute(k_build_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return lm_cuda_check(ctx, e, "build smem attribute");
+    const size_t smem = build_smem_bytes(p->nh, p->M, A.ldF, A.ldS, A.nslice);
+    if (p->arith == LM_ARITH_FP64) {
+        if (smem > (size_t)ctx->smem_optin)
+            return lm_fail(ctx, LM_ERR_SIZE, "build kernel needs %zu B shared memory", smem);
+        cudaError_t e = cudaFuncSetAttribute(k_build_rows,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return lm_cuda_check(ctx, e, "build smem attribute");
+    }
 
     int tb = 256;
     k_tables<<<(p->nh * p->M + p->M + tb - 1) / tb, tb, 0, s>>>(p->theta, p->M, p->nh, p->tabs);
     lm_note_launch(ctx);
     if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_tables")) return rc;
 
-    int per_sm = std::max(1, (int)(200 * 1024 / smem));
-    per_sm = std::min(per_sm, 8);
-    int64_t grid = std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * per_sm);
-    if (grid < 1) grid = 1;
-    lm_prof_begin(ctx, PROF_BUILD, s);
-    k_build_rows<<<(unsigned)grid, BUILD_THREADS, smem, s>>>(A);
-    lm_prof_end(ctx, PROF_BUILD, s);
-    lm_note_launch(ctx);
-    if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_build_rows")) return rc;
+    if (p->arith == LM_ARITH_FP64) {
+        int per_sm = std::max(1, (int)(200 * 1024 / smem));
+        per_sm = std::min(per_sm, 8);
+        int64_t grid = std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * per_sm);
+        if (grid < 1) grid = 1;
+        lm_prof_begin(ctx, PROF_BUILD, s);
+        k_build_rows<<<(unsigned)grid, BUILD_THREADS, smem, s>>>(A);
+        lm_prof_end(ctx, PROF_BUILD, s);
+        lm_note_launch(ctx);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_build_rows")) return rc;
+    } else {
+        const int n = p->n;
+        const int ntab = 2 * p->nh * p->M + 2 * p->M + n * n + n * n * n * n;
+        k_tables_df<<<std::min(1024, (ntab + 255) / 256), 256, 0, s>>>(p->tabs, p->h, p->eri, p->M,
+                                                                       p->nh, n, p->tdf);
+        lm_note_launch(ctx);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_tables_df")) return rc;
+        BuildDfArgs B;
+        B.S = A.S;
+        B.nh = A.nh;
+        B.M = A.M;
+        B.M1 = A.M1;
+        B.P1 = A.P1;
+        B.ldp = A.ldp;
+        B.ldF = p->nh | 1;
+        B.ldS = p->M | 1;
+        B.nslice = std::max(1, BDF_THREADS / (p->nh + 1));
+        B.theta = p->theta;
+        B.tdf = p->tdf;
+        B.rows = p->rows;
+        B.n_rows = p->n_rows;
+        B.amask = A.amask;
+        B.bmask = A.bmask;
+        B.e_core = p->e_core;
+        B.lnpsi = p->lnpsi;
+        B.eloc = p->eloc;
+        B.O = p->O;
+        B.G = p->G;
+        B.flags = ctx->d_flags;
+        const size_t f2 = (size_t)2 * p->nh * p->M + 2 * p->M + 3 * p->nh +
+                          (size_t)BDF_K * B.ldF + BDF_K +
+                          (size_t)B.nslice * (p->nh + 1) * B.ldS + (size_t)B.nslice * (p->nh + 1) +
+                          BDF_THREADS / 32;
+        const size_t dsm = BDF_K * sizeof(int4) + sizeof(RowLists) + f2 * sizeof(float2) +
+                           (size_t)p->nh * sizeof(double) + 64;
+        if (dsm > (size_t)ctx->smem_optin)
+            return lm_fail(ctx, LM_ERR_SIZE, "df64 build kernel needs %zu B shared memory", dsm);
+        cudaError_t e2 = cudaFuncSetAttribute(k_build_rows_df,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+        if (e2 != cudaSuccess) return lm_cuda_check(ctx, e2, "df64 build smem attribute");
+        int per_sm = std::max(1, (int)(220 * 1024 / dsm));
+        per_sm = std::min(per_sm, 4);
+        int64_t grid = std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * per_sm);
+        if (grid < 1) grid = 1;
+        lm_prof_begin(ctx, PROF_BUILD, s);
+        k_build_rows_df<<<(unsigned)grid, BDF_THREADS, dsm, s>>>(B);
+        lm_prof_end(ctx, PROF_BUILD, s);
+        lm_note_launch(ctx);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_build_rows_df")) return rc;
+    }
 
     // weights, E, <O>
     const int nmax = std::max(1, std::min(ctx->sms, (int)((p->n_rows + 255) / 256)));
@@ -667,8 +1020,10 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     }
     const int nst = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_rows, ctx->sms * 2));
     double *spart = p->part + 256;
-    k_stats_partial<<<nst, 256, 0, s>>>(p->O, p->lnpsi, p->eloc, given, p->wt, p->n_rows, p->ldp,
-                                        maxpart, nmax, spart);
+    k_weights<<<(int)std::min<int64_t>((p->n_rows + 255) / 256, ctx->sms * 4), 256, 0, s>>>(
+        p->lnpsi, given, p->wt, p->n_rows, maxpart, nmax);
+    lm_note_launch(ctx);
+    k_stats_partial<<<nst, 256, 0, s>>>(p->O, p->eloc, p->wt, p->n_rows, p->ldp, spart);
     lm_note_launch(ctx);
     if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_stats_partial")) return rc;
     k_stats_final<<<(p->ldp + 255) / 256, 256, 0, s>>>(spart, nst, p->ldp, p->stats);

@@ -1,0 +1,87 @@
+// Double-float ("df64") arithmetic: a value is the unevaluated sum h + l of two
+// FP32 numbers with |l| <= ulp(h)/2, giving a 48-bit significand. Built from
+// error-free transformations: Dekker's FastTwoSum (Dekker 1971, "A
+// floating-point technique for extending the available precision"), Knuth's
+// TwoSum (TAOCP vol. 2, 4.2.2) and the FMA-based TwoProduct (Ogita, Rump &
+// Oishi 2005, "Accurate sum and dot product"). Division is one Newton
+// correction of an FP32 quotient (the double-single scheme of Bailey's DSFUN).
+//
+// On GB300 FP32 FMA throughput is 62x FP64's, so a df64 operation (5-12 FP32
+// instructions) costs a fraction of an FP64 one while keeping the relative
+// error near 2^-44. The __f*_rn intrinsics keep the compiler from fusing or
+// reassociating the error-free steps.
+#pragma once
+
+#include <cuda_runtime.h>
+
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df df_make(float h, float l) {
+    df r;
+    r.h = h;
+    r.l = l;
+    return r;
+}
+
+// s + e = a + b exactly, assuming |a| >= |b| or a == 0 (FastTwoSum)
+__device__ __forceinline__ df df_fts(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df_make(s, e);
+}
+
+// s + e = a + b exactly (TwoSum)
+__device__ __forceinline__ df df_ts(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df_make(s, e);
+}
+
+__device__ __forceinline__ df df_from_double(double x) {
+    const float h = __double2float_rn(x);
+    const float l = __double2float_rn(x - (double)h);
+    return df_make(h, l);
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ df df_neg(df a) { return df_make(-a.h, -a.l); }
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    const df s = df_ts(a.h, b.h);
+    const float e = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+    return df_fts(s.h, e);
+}
+
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);  // exact error of the product of the heads
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return df_fts(p, e);
+}
+
+// a / b: FP32 quotient q1, exact remainder a - b*q1 from TwoProduct, one correction
+__device__ __forceinline__ df df_div(df a, df b) {
+    const float rb = __frcp_rn(b.h);
+    const float q1 = __fmul_rn(a.h, rb);
+    const float p = __fmul_rn(b.h, q1);
+    const float pe = __fmaf_rn(b.h, q1, -p);
+    float r = __fsub_rn(a.h, p);
+    r = __fsub_rn(r, pe);
+    r = __fadd_rn(r, a.l);
+    r = __fmaf_rn(-b.l, q1, r);
+    const float q2 = __fmul_rn(r, rb);
+    return df_fts(q1, q2);
+}
+
+// 1 / b
+__device__ __forceinline__ df df_rcp(df b) { return df_div(df_make(1.0f, 0.0f), b); }
+
+// Multiply by 2^e exactly (as long as the result stays in the FP32 normal range)
+__device__ __forceinline__ df df_ldexp(df a, int e) { return df_make(ldexpf(a.h, e), ldexpf(a.l, e)); }

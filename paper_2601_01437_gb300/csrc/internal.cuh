@@ -165,6 +165,8 @@ struct lm_pencil {
     double *O, *G;      // N_s x ldp, centred in place
     void *Olo, *Glo;    // low-precision copies (float or bf16) or null
     double *h, *eri, *theta, *tabs;
+    float2 *tdf;        // double-float tables for the df64 build
+    int arith;          // lm_arith of the last build
     double *stats;      // [0] sum w, [1] E, [2] max lnpsi, [8..8+ldp) mean O
     double *part;       // reduction partials
     int64_t part_len;

@@ -81,8 +81,8 @@ def test_connections_bit_exact_sampled(ctx, n, na, nb, nrows):
 
 
 # ------------------------------------------------------------------ build
-def _build_both(ctx, abi, n, na, nb, nh, h, eri, theta, rows=None, counts=None, prec=0):
-    sysd = ctx.system(n, na, nb, nh, h, eri)
+def _build_both(ctx, abi, n, na, nb, nh, h, eri, theta, rows=None, counts=None, prec=0, arith=0):
+    sysd = ctx.system(n, na, nb, nh, h, eri, arith=arith)
     w = None if counts is None else counts.astype(np.float64)
     pen = ctx.build_OG(sysd, theta, rows=rows, weights=w, prec=prec)
     pd = lm.build_pencil(n, na, nb, nh, h, eri, theta, rows, counts)
@@ -104,40 +104,57 @@ def _check_build(abi, pen, pd):
     assert np.array_equal(pen.export(abi.EXPORT_ROWS), pd.rows)
 
 
-def test_build_parity_tiny(ctx, abi):
+ARITHS = pytest.mark.parametrize("arith", [0, 1], ids=["df64", "fp64"])
+
+
+@ARITHS
+def test_build_parity_tiny(ctx, abi, arith):
     w = synth.WORKLOADS["tiny_6o6e"]
     h, eri, th, _, _ = w.inputs()
-    pen, pd = _build_both(ctx, abi, 6, 3, 3, 24, h, eri, th)
+    pen, pd = _build_both(ctx, abi, 6, 3, 3, 24, h, eri, th, arith=arith)
     _check_build(abi, pen, pd)
     pen.free()
 
 
-def test_build_parity_f2_full_size(ctx, abi):
+@ARITHS
+def test_build_parity_f2_full_size(ctx, abi, arith):
     """All 14,400 rows of the F2-shaped workload, element by element."""
     w = synth.WORKLOADS["f2_10o14e"]
     h, eri, th, _, _ = w.inputs()
-    pen, pd = _build_both(ctx, abi, 10, 7, 7, 40, h, eri, th)
+    pen, pd = _build_both(ctx, abi, 10, 7, 7, 40, h, eri, th, arith=arith)
     _check_build(abi, pen, pd)
     pen.free()
 
 
-def test_build_parity_mc_rows_licl_shape(ctx, abi):
+@ARITHS
+def test_build_parity_mc_rows_licl_shape(ctx, abi, arith):
     """LiCl-shaped system (28 spin orbitals, Nh=56) on 1,000 Monte Carlo rows with multiplicities."""
     h, eri = synth.integrals(14, 111)
     th = synth.rbm_theta(14, 56, 111)
     rows, cnt = _mc_rows(14, 7, 7, 1000, 111, h)
-    pen, pd = _build_both(ctx, abi, 14, 7, 7, 56, h, eri, th, rows, cnt)
+    pen, pd = _build_both(ctx, abi, 14, 7, 7, 56, h, eri, th, rows, cnt, arith=arith)
     _check_build(abi, pen, pd)
     pen.free()
 
 
 @pytest.mark.parametrize("n,na,nb,nh", [(2, 1, 1, 2), (3, 3, 1, 4), (4, 0, 2, 3), (32, 1, 1, 4),
                                         (5, 2, 3, 7)])
-def test_build_parity_edge_shapes(ctx, abi, n, na, nb, nh):
+@ARITHS
+def test_build_parity_edge_shapes(ctx, abi, n, na, nb, nh, arith):
     """Degenerate sectors: 4 determinants, a full spin shell, an empty spin, M = 64, odd P+1."""
     h, eri = synth.integrals(n, 17)
     th = synth.rbm_theta(n, nh, 17, sigma=0.2)
-    pen, pd = _build_both(ctx, abi, n, na, nb, nh, h, eri, th)
+    pen, pd = _build_both(ctx, abi, n, na, nb, nh, h, eri, th, arith=arith)
+    _check_build(abi, pen, pd)
+    pen.free()
+
+
+@ARITHS
+def test_build_parity_large_theta(ctx, abi, arith):
+    """theta ~ N(0, 0.5): large pre-activations and cosh ratios far from 1."""
+    h, eri = synth.integrals(10, 23)
+    th = synth.rbm_theta(10, 40, 23, sigma=0.5)
+    pen, pd = _build_both(ctx, abi, 10, 7, 7, 40, h, eri, th, arith=arith)
     _check_build(abi, pen, pd)
     pen.free()
 
