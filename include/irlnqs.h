@@ -212,6 +212,37 @@ int lm_debug_connections(lm_ctx *ctx, const lm_system *sys, const uint64_t *rows
  *        4 normalised weights (N_s), 5 mean O (ld), 6 rows (N_s, as uint64 bits). */
 int lm_pencil_export(lm_pencil *p, int what, void *dst, void *stream);
 
+/* ---- pencil product without allocation -------------------------------- */
+
+/* The paper has no counterpart: this is an operational entry point for callers
+ * that cannot allocate device memory -- code inside a CUDA stream capture that
+ * must not create allocations, allocators that own all device memory (a
+ * framework's caching pool, an embedded runtime with a fixed budget), or
+ * real-time loops that must not wait on the allocator.
+ *
+ * Same product as lm_apply_pencil with FP64 factors, but on the caller's
+ * arrays instead of a pencil handle: O_c and G_c are n_rows x ld row-major
+ * FP64 (columns >= p1 ignored), w holds the n_rows normalised weights, v has
+ * p1 entries, Hv and Sv (either may be NULL, not both) receive p1 entries.
+ * sym is LM_SYM_NONE or LM_SYM_HALF. Every array must be device memory, and
+ * O_c, G_c 16-byte aligned (LM_ERR_ARG otherwise); ld must be a multiple of 8
+ * and at most
+ * LM_NOALLOC_MAX_LD (LM_ERR_SIZE otherwise).
+ *
+ * It calls no allocator: its scratch (partial products, padded v, a status
+ * word) lives in one 4 MiB file-scope device array that every GPU loading the
+ * library holds until the process exits. The first call on a device resolves
+ * that array's address (cudaGetSymbolAddress) and should come before any
+ * stream capture. All calls share the array and each call overwrites it, so
+ * calls that can overlap on a GPU (other streams, other host threads) race
+ * and must be serialised by the caller. If a bounded wait inside the kernel
+ * gives up, Hv and Sv are filled with NaN. Work is enqueued on `stream`; the
+ * call does not synchronise. */
+#define LM_NOALLOC_MAX_LD 2048
+int lm_apply_pencil_noalloc(const double *O_c, const double *G_c, const double *w, int64_t n_rows,
+                            int ld, int p1, const double *v, double *Hv, double *Sv, int sym,
+                            void *stream);
+
 /* ---- counters (benchmarking; not on the math path) -------------------- */
 
 typedef struct {

@@ -19,6 +19,7 @@ IRL_OK, IRL_BREAKDOWN_INVARIANT, IRL_MAX_RESTARTS, LM_C0_TINY, LM_STATIONARY = 0
 LM_FP64, LM_FP32, LM_BF16 = 0, 1, 2
 LM_SYM_AUTO, LM_SYM_NONE, LM_SYM_HALF = 0, 1, 2
 LM_ARITH_DF64, LM_ARITH_FP64 = 0, 1
+LM_NOALLOC_MAX_LD = 2048
 EXPORT_O, EXPORT_G, EXPORT_LNPSI, EXPORT_ELOC, EXPORT_W, EXPORT_OBAR, EXPORT_ROWS = range(7)
 
 c_int, c_double, c_int64, c_uint64, c_vp = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
@@ -73,6 +74,8 @@ _SIGNATURES = {
     "lm_debug_connections": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_int64, c_int, c_vp,
                                      c_vp, c_vp, c_vp]),
     "lm_pencil_export": (c_int, [c_vp, c_int, c_vp, c_vp]),
+    "lm_apply_pencil_noalloc": (c_int, [c_vp, c_vp, c_vp, c_int64, c_int, c_int, c_vp, c_vp, c_vp,
+                                        c_int, c_vp]),
     "lm_stats_reset": (c_int, [c_vp, c_int]),
     "lm_stats_get": (c_int, [c_vp, ctypes.POINTER(lm_stats)]),
 }
@@ -125,6 +128,14 @@ class LMError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{msg} (status {code})")
         self.code = code
+
+
+def apply_pencil_noalloc(O_c, G_c, w, n_rows, ld, p1, v, Hv=None, Sv=None, sym=LM_SYM_NONE,
+                         stream=None):
+    """lm_apply_pencil_noalloc: returns the status code (device arrays only)."""
+    return lib().lm_apply_pencil_noalloc(ptr(O_c), ptr(G_c), ptr(w), int(n_rows), int(ld),
+                                         int(p1), ptr(v), ptr(Hv), ptr(Sv), int(sym),
+                                         stream_handle(stream))
 
 
 class Context:

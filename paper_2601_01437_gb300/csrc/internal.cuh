@@ -203,3 +203,10 @@ int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_
                      const int *skip, cudaStream_t s);
 int lm_launch_reduce_partials(lm_pencil *p, double *yH, double *yS, cudaStream_t s);
 int lm_pencil_grid(lm_pencil *p);
+
+// pencil.cu: the FP64 pencil product on caller-provided scratch (no allocation):
+// vpad holds v padded to ldp, part holds grid x 2 ldp partials, flags one int
+// that must be zero on entry.
+int lm_pencil_fp64_on_scratch(const double *O, const double *G, const double *w, int64_t n_rows,
+                              int ldp, int p1, const double *vpad, double *part, int grid, int half,
+                              double *yH, double *yS, int smem_optin, int *flags, cudaStream_t s);

@@ -309,3 +309,101 @@ int lm_launch_reduce_partials(lm_pencil *p, double *yH, double *yS, cudaStream_t
     lm_note_launch(p->ctx);
     return lm_cuda_check(p->ctx, cudaGetLastError(), "k_reduce_partials");
 }
+
+// ---------------------------------------------------------------------------
+// Launches on caller-provided scratch (no lm_pencil, no allocation). Used by the
+// no-allocation entry point in noalloc.cu; FP64 factors only.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int NJ, int MODE>
+int raw_launch(const double *O, const double *G, const double *w, int64_t n_rows, int ldp,
+               const double *vpad, double *out, int out_ld, int grid, int smem_optin, int *flags,
+               cudaStream_t s) {
+    const int nmat = MODE == MODE_S ? 1 : 2;
+    const size_t row_bytes = (size_t)nmat * ldp * sizeof(double);
+    const size_t tail = 8 * sizeof(uint64_t) + (size_t)ldp * sizeof(double) + 256;
+    const size_t budget = (size_t)smem_optin - tail - 2048;
+    int R = (int)std::min<size_t>(64, std::max<size_t>(1, 49152 / row_bytes));
+    if (R < PT / 32) R = (int)std::max<size_t>(1, std::min<size_t>(PT / 32, budget / (2 * row_bytes)));
+    const size_t stage_bytes = R * row_bytes;
+    const int stages = (int)std::min<size_t>(4, budget / stage_bytes);
+    if (stages < 2) return LM_ERR_SIZE;
+    size_t smem = stages * stage_bytes + tail;
+    smem = std::max(smem, (size_t)(PT / 32) * ldp * sizeof(double) + 64);
+    PencilArgs<double> a;
+    a.O = O;
+    a.G = G;
+    a.w = w;
+    a.n_rows = n_rows;
+    a.ldp = ldp;
+    a.v = vpad;
+    a.out = out;
+    a.out_ld = out_ld;
+    a.stages = stages;
+    a.rows_per_tile = R;
+    a.skip = nullptr;
+    a.flags = flags;
+    if (cudaFuncSetAttribute(k_pencil<double, NJ, MODE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return LM_ERR_CUDA;
+    k_pencil<double, NJ, MODE><<<grid, PT, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;
+}
+
+template <int NJ>
+int raw_modes(const double *O, const double *G, const double *w, int64_t n_rows, int ldp,
+              const double *vpad, double *part, int grid, int half, int want_s, int smem_optin,
+              int *flags, cudaStream_t s) {
+    int rc = half ? raw_launch<NJ, MODE_H_HALF>(O, G, w, n_rows, ldp, vpad, part, 2 * ldp, grid,
+                                                smem_optin, flags, s)
+                  : raw_launch<NJ, MODE_H_NONE>(O, G, w, n_rows, ldp, vpad, part, 2 * ldp, grid,
+                                                smem_optin, flags, s);
+    if (rc == LM_OK && want_s)
+        rc = raw_launch<NJ, MODE_S>(O, G, w, n_rows, ldp, vpad, part + ldp, 2 * ldp, grid,
+                                    smem_optin, flags, s);
+    return rc;
+}
+
+// y[c] = sum_b part[b][c] (CTA order); NaN everywhere if a pencil CTA gave up waiting.
+__global__ void k_reduce_partials_flagged(const double *part, int nparts, int ldp, int p1,
+                                          const int *flags, double *yH, double *yS) {
+    __shared__ double s[8][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    if (c < 2 * ldp)
+        for (int b = warp; b < nparts; b += 8) acc += part[(size_t)b * 2 * ldp + c];
+    s[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && c < 2 * ldp) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += s[w][lane];
+        if (*flags) t = __longlong_as_double(0x7ff8000000000000ll);
+        if (c < ldp) {
+            if (yH && c < p1) yH[c] = t;
+        } else if (yS && c - ldp < p1) {
+            yS[c - ldp] = t;
+        }
+    }
+}
+
+}  // namespace
+
+int lm_pencil_fp64_on_scratch(const double *O, const double *G, const double *w, int64_t n_rows,
+                              int ldp, int p1, const double *vpad, double *part, int grid, int half,
+                              double *yH, double *yS, int smem_optin, int *flags, cudaStream_t s) {
+    const int nj = (ldp + 31) / 32;
+    const int want_s = yS != nullptr;
+    int rc;
+    if (nj <= 8) rc = raw_modes<8>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
+    else if (nj <= 16) rc = raw_modes<16>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
+    else if (nj <= 28) rc = raw_modes<28>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
+    else if (nj <= 40) rc = raw_modes<40>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
+    else if (nj <= 52) rc = raw_modes<52>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
+    else if (nj <= 64) rc = raw_modes<64>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
+    else return LM_ERR_SIZE;
+    if (rc != LM_OK) return rc;
+    k_reduce_partials_flagged<<<(2 * ldp + 31) / 32, 256, 0, s>>>(part, grid, ldp, p1, flags, yH, yS);
+    return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;
+}
