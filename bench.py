@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--workload", default="f2_10o14e")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pencil", default="df64", choices=["df64", "fp64"],
+                    help="storage of the FP64 workload's Lanczos pencil factors (both "
+                         "FP64-accurate; the final refinement always uses FP64)")
     ap.add_argument("--arith", default="df64", choices=["df64", "fp64"],
                     help="row-build arithmetic (both FP64-accurate; df64 runs on the FP32 pipes)")
     return ap.parse_args()
@@ -134,11 +137,11 @@ class ClockSampler:
 def algorithmic_units(w, arith="df64"):
     """Per-launch algorithmic work of the two dominant kernels (derivation in the design doc).
 
-    Row build: per connection x hidden unit (ratio, tanh) and per connection x
-    augmented row (accumulation into G), counted in the arithmetic the kernel
-    uses. df64: FP32 flops of the double-float formulation (add/mul 1, fma 2,
-    rcp 1): singles 90 + 43, doubles 110 + 65. fp64: FP64 flops (divide 1):
-    singles 9 + 4, doubles 13 + 6.
+    Row build: per connection x hidden unit (ratio factor, tanh) and per
+    connection x augmented row (accumulation into G), counted in the arithmetic
+    the kernel uses. df64: FP32 flops of the double-float formulation (add/mul
+    1, fma 2, rcp 1): singles 44 + 34, doubles 54 + 50. fp64: FP64 flops
+    (divide 1): singles 9 + 4, doubles 13 + 6.
     Pencil: O_c and G'_c read once, N_s (P+1) (b_O + b_G) + 8 N_s bytes.
     """
     n, na, nb, nh = w.n_orb, w.n_alpha, w.n_beta, w.n_hidden
@@ -146,7 +149,7 @@ def algorithmic_units(w, arith="df64"):
     singles = na * va + nb * vb
     doubles = (na * (na - 1) // 2) * (va * (va - 1) // 2) + \
               (nb * (nb - 1) // 2) * (vb * (vb - 1) // 2) + na * va * nb * vb
-    c = {"df64": (90, 43, 110, 65), "fp64": (9, 4, 13, 6)}[arith]
+    c = {"df64": (44, 34, 54, 50), "fp64": (9, 4, 13, 6)}[arith]
     flops_row = singles * (nh * c[0] + (nh + 1) * c[1]) + doubles * (nh * c[2] + (nh + 1) * c[3])
     build_flops = flops_row * w.n_rows
     P1 = (nh + 1) * (2 * n + 1)
@@ -168,7 +171,8 @@ def run_gpu(args, rank, world, local):
     if world > 1:
         w = synth.Workload(**{**w.__dict__, "seed": w.seed + rank})
     h, eri, th0, rows, counts = w.inputs()
-    prec = {"f64": abi.LM_FP64, "f32": abi.LM_FP32, "bf16": abi.LM_BF16}[w.precision]
+    prec = {"f64": abi.LM_DF64 if args.pencil == "df64" else abi.LM_FP64, "f32": abi.LM_FP32,
+            "bf16": abi.LM_BF16}[w.precision]
     dev = torch.device("cuda", local)
     s = torch.cuda.Stream(device=dev)
     h_d = torch.from_numpy(h).to(dev)
@@ -229,8 +233,11 @@ def run_gpu(args, rank, world, local):
             "l2": "inputs larger than L2: O_c+G'_c "
                   f"{w.n_rows * (w.n_params + 1) * 16 / 1e6:.0f} MB FP64 vs 129 MB L2",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "build_arith": ("double-float (FP32 pairs, 48-bit significand) row build; FP64 "
-                            "pencil, Lanczos and refinement") if args.arith == "df64" else "FP64",
+            "build_arith": ("double-float (FP32 pairs, 48-bit significand)"
+                            if args.arith == "df64" else "FP64"),
+            "pencil_storage": (("double-float factors" if args.pencil == "df64" else "FP64 factors")
+                               if w.precision == "f64" else w.precision) +
+                              "; FP64 Lanczos vectors, reorthogonalisation and refinement",
         },
         "clocks": clk,
         "gpu_launches": int(st.launches),
@@ -265,6 +272,25 @@ def run_gpu(args, rank, world, local):
                            if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
         out["roofline"]["kernel"] = kern[dom]["kernel"]
         out["kernels"] = kern
+    # mixed precision: the eigenvalue of each low-precision path against FP64 on one pencil
+    if w.precision in ("f32", "bf16"):
+        acc = {}
+        with torch.cuda.stream(s):
+            theta.copy_(th0_d)
+        pens = {}
+        for name, pr in (("fp32", abi.LM_FP32), ("bf16", abi.LM_BF16)):
+            pens[name] = ctx.build_OG(sysd, theta, rows=rows_d, weights=wts_d, n_rows=w.n_rows,
+                                      prec=pr, stream=s)
+        r64 = pens["fp32"].irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200, prec=abi.LM_FP64,
+                                    stream=s)
+        for name, pr in (("fp32", abi.LM_FP32), ("bf16", abi.LM_BF16)):
+            r = pens[name].irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200, prec=pr, stream=s)
+            acc[name] = {"abs_err_ha": abs(r.lambda_ - r64.lambda_), "lambda": r.lambda_,
+                         "n_matvec": r.n_matvec, "n_matvec_lowp": r.n_matvec_lowp,
+                         "residual": r.residual}
+            pens[name].free()
+        acc["fp64"] = {"lambda": r64.lambda_, "n_matvec": r64.n_matvec}
+        out["mixed_vs_fp64"] = acc
     # end to end through the C ABI with host buffers (copies inside the timed region)
     if not args.no_e2e:
         pinned = [torch.from_numpy(h).pin_memory(), torch.from_numpy(eri).pin_memory(),

@@ -65,7 +65,12 @@ enum {
     LM_STATIONARY = 4            /* lambda_min > -tol: theta is stationary    */
 };
 
-typedef enum { LM_FP64 = 0, LM_FP32 = 1, LM_BF16 = 2 } lm_precision;
+/* Storage of the pencil factors used by the Lanczos products. FP64 factors are
+ * always kept (exports, final refinement); the others are extra copies:
+ * FP32 / BF16 (FP32 accumulation, refined by FP64 restarts) and DF64
+ * (double-float FP32 pairs, 48-bit significand, products accurate to ~1e-14
+ * relative, computed on the FP32 pipes). */
+typedef enum { LM_FP64 = 0, LM_FP32 = 1, LM_BF16 = 2, LM_DF64 = 3 } lm_precision;
 
 /* symmetrisation of H~' inside the Lanczos operator */
 typedef enum {
@@ -150,8 +155,8 @@ const char *lm_last_error(const lm_ctx *ctx);
  *           n_rows = 0 to let the library size it).
  *   weights N_s non-negative sample weights (e.g. Monte Carlo multiplicities),
  *           normalised by their sum; NULL = |psi(x)|^2 / sum |psi|^2.
- *   prec    FP64 only, or FP64 plus an FP32 / BF16 copy of O_c and G'_c for
- *           low-precision Lanczos.
+ *   prec    FP64 only, or FP64 plus an FP32 / BF16 / DF64 copy of O_c and
+ *           G'_c for the Lanczos products.
  * Layout on the device: O_c, G'_c row-major N_s x ld FP64 (columns >= P+1 zero),
  *   O_c(x,0) = 1, G'_c(x,0) = E_loc(x) - E, and for k >= 1
  *   O_c(x,k) = O_k(x) - <O_k>, G'_c(x,k) = G_k(x) - <O_k> E_loc(x) - E O_c(x,k).

@@ -83,7 +83,7 @@ void pencil_release(lm_pencil *p) {
     void *bufs[] = {p->rows, p->wt,   p->lnpsi, p->eloc, p->O,    p->G,   p->Olo,
                     p->Glo,  p->h,    p->eri,   p->theta, p->tabs, p->stats, p->part,
                     p->V,    p->wvec, p->yvec,  p->hy,   p->sy,   p->tvec, p->dots,
-                    p->st,   p->tdf};
+                    p->st,   p->tdf,  p->wlo, p->bar};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->st_host) cudaFreeHost(p->st_host);
@@ -151,7 +151,7 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
     ctx->err[0] = 0;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return LM_ERR_CUDA;
     if (int rc = check_system(ctx, sys)) return rc;
-    if (prec != LM_FP64 && prec != LM_FP32 && prec != LM_BF16)
+    if (prec != LM_FP64 && prec != LM_FP32 && prec != LM_BF16 && prec != LM_DF64)
         return lm_fail(ctx, LM_ERR_ARG, "bad precision %d", (int)prec);
     cudaStream_t s = (cudaStream_t)stream;
     const int n = sys->n_orb, M = 2 * n, nh = sys->n_hidden;
@@ -194,12 +194,13 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
         int rc = 0;
         rc = rc ? rc : dalloc(ctx, &p->rows, nr);
         rc = rc ? rc : dalloc(ctx, &p->wt, nr);
+        rc = rc ? rc : dalloc(ctx, &p->wlo, nr);
         rc = rc ? rc : dalloc(ctx, &p->lnpsi, nr);
         rc = rc ? rc : dalloc(ctx, &p->eloc, nr);
         rc = rc ? rc : dalloc(ctx, &p->O, nr * L);
         rc = rc ? rc : dalloc(ctx, &p->G, nr * L);
         if (!rc && prec != LM_FP64) {
-            const size_t es = prec == LM_FP32 ? 4 : 2;
+            const size_t es = prec == LM_FP32 ? 4 : (prec == LM_DF64 ? 8 : 2);
             rc = lm_cuda_check(ctx, cudaMalloc(&p->Olo, nr * L * es), "cudaMalloc");
             rc = rc ? rc : lm_cuda_check(ctx, cudaMalloc(&p->Glo, nr * L * es), "cudaMalloc");
         }
@@ -220,6 +221,8 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
         rc = rc ? rc : dalloc(ctx, &p->tvec, L);
         rc = rc ? rc : dalloc(ctx, &p->dots, (size_t)3 * (nh + 1) * (LM_MAXKRYLOV + 8) + L + 64);
         rc = rc ? rc : dalloc(ctx, &p->st, 1);
+        rc = rc ? rc : dalloc(ctx, &p->bar, 64);
+        if (!rc) rc = lm_cuda_check(ctx, cudaMemsetAsync(p->bar, 0, 64 * sizeof(unsigned), s), "memset");
         if (!rc)
             rc = lm_cuda_check(ctx, cudaMallocHost(&p->st_host, sizeof(IrlState)), "cudaMallocHost");
         if (rc) {
@@ -265,7 +268,7 @@ extern "C" int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double
     if (!p || !v) return LM_ERR_ARG;
     lm_ctx *ctx = p->ctx;
     cudaSetDevice(ctx->device);
-    if (sym < 0 || sym > 2 || prec < 0 || prec > 2) return lm_fail(ctx, LM_ERR_ARG, "bad sym/prec");
+    if (sym < 0 || sym > 2 || prec < 0 || prec > 3) return lm_fail(ctx, LM_ERR_ARG, "bad sym/prec");
     cudaStream_t s = (cudaStream_t)stream;
     const int sy = sym == LM_SYM_AUTO ? p->sym : sym;
     // the kernels read ldp >= P+1 entries: stage v with zero padding

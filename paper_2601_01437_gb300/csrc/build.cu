@@ -440,14 +440,20 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_rows(BuildArgs A) {
 }
 
 // ------------------------------------- K2-K6 in double-float arithmetic
-// tabs_df (float2 = df) = [exp(W) Nh x M | exp(-W) Nh x M | exp(a) M | exp(-a) M |
-//                          h n^2 | (pq|rs) n^4]
-__global__ void k_tables_df(const double *tabs, const double *h, const double *eri, int M, int nh,
+// tdf (float2 = df) = [exp(2W) Nh x M | exp(-2W) Nh x M | h n^2 | (pq|rs) n^4]
+__global__ void k_tables_df(const double *theta, const double *h, const double *eri, int M, int nh,
                             int n, float2 *out) {
-    const int n_exp = 2 * nh * M + 2 * M, n2 = n * n, n4 = n2 * n2;
+    const int n_exp = 2 * nh * M, n2 = n * n, n4 = n2 * n2;
     const int tot = n_exp + n2 + n4;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
-        double x = e < n_exp ? tabs[e] : (e < n_exp + n2 ? h[e - n_exp] : eri[e - n_exp - n2]);
+        double x;
+        if (e < n_exp) {
+            const int f = e % (nh * M), j = f / M, p = f % M;
+            const double w = theta[(j + 1) * (M + 1) + p];
+            x = exp(e < nh * M ? 2.0 * w : -2.0 * w);
+        } else {
+            x = e < n_exp + n2 ? h[e - n_exp] : eri[e - n_exp - n2];
+        }
         const df d = df_from_double(x);
         out[e] = make_float2(d.h, d.l);
     }
@@ -466,7 +472,7 @@ __device__ __forceinline__ void st_df(float2 *p, df a) { *p = make_float2(a.h, a
 struct BuildDfArgs {
     SysView S;
     int nh, M, M1, P1, ldp;
-    int ldF, ldS, nslice;
+    int ldF, ldS, nslice, ns;  // ns = number of single excitations of a row
     const double *theta;
     const float2 *tdf;  // df tables (see k_tables_df)
     const uint64_t *rows;
@@ -523,37 +529,111 @@ __device__ __forceinline__ void df_renorm(df &m, int &ex) {
     }
 }
 
-// Same computation as k_build_rows, with every per-connection and
-// per-(connection, hidden unit) operation in double-float arithmetic on the
-// FP32 pipes. Four threads share a connection, each taking every fourth
-// hidden unit; their partial products of cosh ratios are combined with
-// shuffles. FP64 remains for the per-row pre-activations, ln psi, the
-// diagonal element and the final conversion of each G entry.
+// Lazy double-float accumulation acc += f (TwoSum of the heads, tails summed
+// unnormalised); df_fts(acc.h, acc.l) renormalises at the end.
+__device__ __forceinline__ void df_acc(df &acc, df f) {
+    const df s = df_ts(acc.h, f.h);
+    acc.h = s.h;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, f.l));
+}
+__device__ __forceinline__ df df_norm(df a) { return df_fts(a.h, a.l); }
+
+// Z +- 1 for Z > 0 in double-float
+__device__ __forceinline__ df df_add1(df z, float one) {
+    const df s = df_ts(z.h, one);
+    return df_fts(s.h, __fadd_rn(s.l, z.l));
+}
+
+// Single excitation s of a row (i -> a): alpha singles first, then beta.
+__device__ __forceinline__ void single_of(const SysView &S, const RowLists &L, int s, int &i,
+                                          int &a) {
+    if (s < S.ns_a) {
+        i = L.oa[s / S.nva];
+        a = L.va[s % S.nva];
+    } else {
+        s -= S.ns_a;
+        i = L.ob[s / S.nvb];
+        a = L.vb[s % S.nvb];
+    }
+}
+
+// Connection k as one or two single excitations s1 (, s2) (same order as decode_exc).
+__device__ __forceinline__ void singles_of_conn(const SysView &S, int k, int &s1, int &s2) {
+    s2 = -1;
+    if (k < S.ns_a) {
+        s1 = k;
+        return;
+    }
+    k -= S.ns_a;
+    if (k < S.ns_b) {
+        s1 = S.ns_a + k;
+        return;
+    }
+    k -= S.ns_b;
+    int lo, hi, vlo, vhi;
+    if (k < S.nd_aa) {
+        const int nvp = S.nva * (S.nva - 1) / 2;
+        unrank_pair(k / nvp, lo, hi);
+        unrank_pair(k % nvp, vlo, vhi);
+        s1 = lo * S.nva + vlo;
+        s2 = hi * S.nva + vhi;
+        return;
+    }
+    k -= S.nd_aa;
+    if (k < S.nd_bb) {
+        const int nvp = S.nvb * (S.nvb - 1) / 2;
+        unrank_pair(k / nvp, lo, hi);
+        unrank_pair(k % nvp, vlo, vhi);
+        s1 = S.ns_a + lo * S.nvb + vlo;
+        s2 = S.ns_a + hi * S.nvb + vhi;
+        return;
+    }
+    k -= S.nd_bb;
+    const int nbe = S.nb * S.nvb;
+    s1 = k / nbe;
+    s2 = S.ns_a + k % nbe;
+}
+
+// Same computation as k_build_rows, in double-float arithmetic on the FP32
+// pipes. For hidden unit j let sigma_j = -sign(z_j) (+1 if z_j < 0),
+// g_j = exp(2 sigma_j z_j) <= 1 and, for a connection moving orbitals with
+// shift d_j of the pre-activation, Z_j = g_j exp(2 sigma_j d_j). Then
+//   tanh(z_j + d_j) = sigma_j (Z_j - 1) / (Z_j + 1),
+//   prod_j cosh(z_j+d_j)/cosh(z_j) = exp(-sum_j sigma_j d_j) prod_j (1+Z_j) / prod_j (1+g_j).
+// Per row, every single excitation s (i -> a) gets B_s[j] = exp(2 sigma_j d_j),
+// A_s[j] = g_j B_s[j] and V_s = exp(a_a - a_i - sum_j sigma_j d_j); a double
+// (s1, s2) has Z_j = A_s1[j] B_s2[j] and factor V_s1 V_s2. So the work per
+// (connection, hidden unit) is one double-float product (doubles), Z +- 1, a
+// division and the running product. Four threads share a connection and
+// combine their partial products with shuffles.
 __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     extern __shared__ __align__(16) unsigned char smb[];
-    const int nh = A.nh, M = A.M, M1 = A.M1;
+    const int nh = A.nh, M = A.M, M1 = A.M1, NS = A.ns;
     const int tid = threadIdx.x, lane = tid & 31;
     int4 *sIdx = reinterpret_cast<int4 *>(smb);                 // [K]
-    RowLists *sL = reinterpret_cast<RowLists *>(sIdx + BDF_K);  // 1
-    float2 *sEW = reinterpret_cast<float2 *>(sL + 1);           // [nh][M]
-    float2 *sEWi = sEW + nh * M;                                // [nh][M]
-    float2 *sea = sEWi + nh * M;                                // [M]
-    float2 *seai = sea + M;                                     // [M]
-    float2 *sPQ = seai + M;                                     // [nh][2] (P, Q)
-    float2 *sTd = sPQ + 2 * nh;                                 // [nh] t as df
-    float2 *sF = sTd + nh;                                      // [K][ldF]
+    int2 *sSs = reinterpret_cast<int2 *>(sIdx + BDF_K);          // [K] single indices
+    RowLists *sL = reinterpret_cast<RowLists *>(sSs + BDF_K);   // 1
+    float2 *sA = reinterpret_cast<float2 *>(sL + 1);            // [NS][nh]  A_s[j]
+    float2 *sB = sA + NS * nh;                                  // [NS][nh]  B_s[j]
+    float2 *sV = sB + NS * nh;                                  // [NS]
+    float2 *sTd = sV + NS;                                      // [nh] t as df
+    float2 *sF = sTd + nh;                                      // [K][ldF]  tanh(z+d)
     float2 *sC = sF + BDF_K * A.ldF;                            // [K]
     float2 *sS = sC + BDF_K;                                    // [nslice][nh+1][ldS]
-    float2 *sA = sS + A.nslice * (nh + 1) * A.ldS;              // [nslice][nh+1]
-    float2 *sRed = sA + A.nslice * (nh + 1);                    // [BDF_THREADS/32]
-    double *sT = reinterpret_cast<double *>(sRed + BDF_THREADS / 32);  // [nh] t (FP64)
-    __shared__ double sDiag, sLn;
+    float2 *sAcc = sS + A.nslice * (nh + 1) * A.ldS;            // [nslice][nh+1]
+    float2 *sRed = sAcc + A.nslice * (nh + 1);                  // [BDF_THREADS/32]
+    double *sT = reinterpret_cast<double *>(sRed + BDF_THREADS / 32);  // [nh] t
+    double *sZ = sT + nh;                                              // [nh] z
+    double *sCs = sZ + nh;                                             // [M] sum_j sigma_j W_jp
+    float2 *sGd = reinterpret_cast<float2 *>(sCs + M);                 // [nh] g as df
+    float *sSig = reinterpret_cast<float *>(sGd + nh);                 // [nh] sigma
+    __shared__ double sDiag, sLn, sGinv;
     __shared__ int sBad;
 
-    const float2 *hd = A.tdf + 2 * nh * M + 2 * M;
-    const float2 *gd = hd + A.S.n * A.S.n;
-    for (int e = tid; e < 2 * nh * M + 2 * M; e += BDF_THREADS) sEW[e] = A.tdf[e];
-    __syncthreads();
+    const float2 *e2 = A.tdf;               // exp(2W) [nh][M]
+    const float2 *e2i = e2 + nh * M;        // exp(-2W) [nh][M]
+    const float2 *hd = e2 + 2 * nh * M;     // h [n][n]
+    const float2 *gd = hd + A.S.n * A.S.n;  // (pq|rs)
 
     const int nsl = A.nslice;
     const int sc_r = tid % (nh + 1), sc_s = tid / (nh + 1);
@@ -574,73 +654,97 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             __syncthreads();
             continue;
         }
+        // per hidden unit: z, tanh z, sigma, g (FP64 -> df)
         for (int j = tid; j < nh; j += BDF_THREADS) {
             double z = A.theta[(j + 1) * M1 - 1];
             for (int p = 0; p < M; ++p)
                 if ((x >> p) & 1ull) z += A.theta[(j + 1) * M1 + p];
-            const double az = fabs(z);
-            const double e2 = exp(-2.0 * az);
-            const double inv = 1.0 / (1.0 + e2);
-            const double big = inv, small = e2 * inv;
-            const df P = df_from_double(z >= 0.0 ? big : small);   // e^{z} / (2 cosh z)
-            const df Q = df_from_double(z >= 0.0 ? small : big);   // e^{-z} / (2 cosh z)
-            sPQ[2 * j] = make_float2(P.h, P.l);
-            sPQ[2 * j + 1] = make_float2(Q.h, Q.l);
+            sZ[j] = z;
             const double t = tanh(z);
             sT[j] = t;
             const df td = df_from_double(t);
             sTd[j] = make_float2(td.h, td.l);
+            sSig[j] = z < 0.0 ? 1.f : -1.f;
+            const df g = df_from_double(exp(-2.0 * fabs(z)));
+            sGd[j] = make_float2(g.h, g.l);
         }
         for (int e = tid; e < nsl * (nh + 1) * A.ldS; e += BDF_THREADS) sS[e] = make_float2(0.f, 0.f);
         __syncthreads();
         if (tid < 32) {
-            double lp = 0.0;
+            // ln psi = a.x + sum_j ln(2 cosh z_j); prod_j (1 + g_j) with g_j = e^{-2|z_j|}
+            double lp = 0.0, lg = 0.0;
             for (int j = tid; j < nh; j += 32) {
-                double zz = A.theta[(j + 1) * M1 - 1];
-                for (int p = 0; p < M; ++p)
-                    if ((x >> p) & 1ull) zz += A.theta[(j + 1) * M1 + p];
-                lp += fabs(zz) + log1p(exp(-2.0 * fabs(zz)));
+                const double az = fabs(sZ[j]);
+                const double g = exp(-2.0 * az);
+                lp += az + log1p(g);
+                lg += log1p(g);
             }
             for (int p = tid; p < M; p += 32)
                 if ((x >> p) & 1ull) lp += A.theta[p];
             lp = warp_sum(lp);
-            if (tid == 0) sLn = lp;
+            lg = warp_sum(lg);
+            if (tid == 0) {
+                sLn = lp;
+                sGinv = exp(-lg);
+            }
         } else if (tid < 64) {
             const double d = diag_value_warp(A.S, *sL);
             if (tid == 32) sDiag = d + A.e_core;
+        } else if (tid - 64 < M) {
+            const int p = tid - 64;
+            double cs = 0.0;
+            for (int j = 0; j < nh; ++j) {
+                const double w = A.theta[(j + 1) * M1 + p];
+                cs += sZ[j] < 0.0 ? w : -w;
+            }
+            sCs[p] = cs;
+        }
+        __syncthreads();
+        // per single excitation: V_s (FP64 exp), B_s[j], A_s[j] (df)
+        for (int e = tid; e < NS * nh; e += BDF_THREADS) {
+            const int s = e / nh, j = e % nh;
+            int i, a;
+            single_of(A.S, *sL, s, i, a);
+            const bool pos = sSig[j] > 0.f;
+            const df b = df_mul(ldg_df((pos ? e2 : e2i) + j * M + a),
+                                ldg_df((pos ? e2i : e2) + j * M + i));
+            st_df(sB + s * nh + j, b);
+            st_df(sA + s * nh + j, df_mul(ld_df(sGd + j), b));
+        }
+        for (int s = tid; s < NS; s += BDF_THREADS) {
+            int i, a;
+            single_of(A.S, *sL, s, i, a);
+            const double ex = (A.theta[a] - A.theta[i]) - (sCs[a] - sCs[i]);
+            const df v = df_from_double(exp(ex));
+            sV[s] = make_float2(v.h, v.l);
         }
         __syncthreads();
 
         df el_part = df_make(0.f, 0.f);
         df accA = df_make(0.f, 0.f);
         const RowLists &L = *sL;
+        const df ginv = df_from_double(sGinv);
         for (int k0 = 0; k0 < A.S.conn; k0 += BDF_K) {
             const int k = k0 + kk;
             const bool active = k < A.S.conn;
-            Exc e;
-            e.i = e.j = e.a = e.b = -1;
-            int sg = 1;
-            bool dbl = false;
+            int s1 = 0, s2 = -1;
             df rp = df_make(1.f, 0.f);
             int re = 0;
             if (active) {
-                e = decode_exc(A.S, L, k);
-                (void)apply_exc(x, e, sg);
-                dbl = e.j >= 0;
+                singles_of_conn(A.S, k, s1, s2);
                 float2 *Frow = sF + kk * A.ldF;
+                const float2 *a1 = sA + s1 * nh;
+                const float2 *b2 = sB + (s2 >= 0 ? s2 : 0) * nh;
                 for (int j = sub; j < nh; j += BDF_TPC) {
-                    const float2 *ew = sEW + j * M;
-                    const float2 *ewi = sEWi + j * M;
-                    df ep = df_mul(ld_df(ew + e.a), ld_df(ewi + e.i));
-                    if (dbl) ep = df_mul(ep, df_mul(ld_df(ew + e.b), ld_df(ewi + e.j)));
-                    const df em = df_rcp(ep);
-                    const df t1 = df_mul(ep, ld_df(sPQ + 2 * j));
-                    const df u = df_mul(em, ld_df(sPQ + 2 * j + 1));
-                    const df q = df_add(t1, u);    // cosh(z+d)/cosh(z)
-                    const df nu = df_sub(t1, u);   // sinh(z+d)/cosh(z)
-                    rp = df_mul(rp, q);
+                    df z = ld_df(a1 + j);
+                    if (s2 >= 0) z = df_mul(z, ld_df(b2 + j));
+                    const df zp = df_add1(z, 1.f);
+                    const df zm = df_add1(z, -1.f);
+                    df t = df_div(zm, zp);
+                    if (sSig[j] < 0.f) t = df_neg(t);
+                    st_df(Frow + j, t);  // tanh(z + d)
+                    rp = df_mul(rp, zp);
                     df_renorm(rp, re);
-                    st_df(Frow + j, df_div(nu, q));  // tanh(z+d)
                 }
             }
             // combine the partial products of the BDF_TPC lanes of a connection
@@ -655,15 +759,18 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 df_renorm(rp, re);
             }
             if (active && sub == 0) {
+                const Exc e = decode_exc(A.S, L, k);
+                int sg;
+                (void)apply_exc(x, e, sg);
                 df hv = exc_value_df(A.S, L, e, hd, gd);
                 if (sg < 0) hv = df_neg(hv);
-                df ead = df_mul(ld_df(sea + e.a), ld_df(seai + e.i));
-                if (dbl) ead = df_mul(ead, df_mul(ld_df(sea + e.b), ld_df(seai + e.j)));
-                df c = df_mul(df_mul(hv, ead), rp);
+                df f = df_mul(hv, ld_df(sV + s1));
+                if (s2 >= 0) f = df_mul(f, ld_df(sV + s2));
+                df c = df_mul(df_mul(f, ginv), rp);
                 c = df_ldexp(c, re);
                 st_df(sC + kk, c);
                 sIdx[kk] = make_int4(e.i, e.j, e.a, e.b);
-                el_part = df_add(el_part, c);
+                df_acc(el_part, c);
             }
             __syncthreads();
             if (scatter_thread) {
@@ -673,21 +780,22 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                     df f = ld_df(sC + q);
                     if (sc_r > 0) f = df_mul(f, ld_df(sF + q * A.ldF + sc_r - 1));
                     const int4 ix = sIdx[q];
-                    accA = df_add(accA, f);
-                    st_df(Srow + ix.x, df_add(ld_df(Srow + ix.x), f));
-                    st_df(Srow + ix.z, df_add(ld_df(Srow + ix.z), f));
+                    df_acc(accA, f);
+                    df t;
+                    t = ld_df(Srow + ix.x); df_acc(t, f); st_df(Srow + ix.x, t);
+                    t = ld_df(Srow + ix.z); df_acc(t, f); st_df(Srow + ix.z, t);
                     if (ix.y >= 0) {
-                        st_df(Srow + ix.y, df_add(ld_df(Srow + ix.y), f));
-                        st_df(Srow + ix.w, df_add(ld_df(Srow + ix.w), f));
+                        t = ld_df(Srow + ix.y); df_acc(t, f); st_df(Srow + ix.y, t);
+                        t = ld_df(Srow + ix.w); df_acc(t, f); st_df(Srow + ix.w, t);
                     }
                 }
             }
             __syncthreads();
         }
-        if (scatter_thread) st_df(sA + sc_s * (nh + 1) + sc_r, accA);
+        if (scatter_thread) st_df(sAcc + sc_s * (nh + 1) + sc_r, df_norm(accA));
         // E_loc: per-warp df sums in lane order, then warps in order
         {
-            df v = el_part;
+            df v = df_norm(el_part);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 const df o = df_make(__shfl_xor_sync(0xffffffffu, v.h, off),
@@ -714,13 +822,13 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 const bool xc = (c == 0) || ((x >> (c - 1)) & 1ull);
                 ov = xc ? (r == 0 ? 1.0 : sT[r - 1]) : 0.0;
                 df at = (r == 0) ? hdg : df_mul(hdg, ld_df(sTd + r - 1));
-                for (int s2 = 0; s2 < nsl; ++s2) at = df_add(at, ld_df(sA + s2 * (nh + 1) + r));
+                for (int s2 = 0; s2 < nsl; ++s2) at = df_add(at, ld_df(sAcc + s2 * (nh + 1) + r));
                 if (c == 0) {
                     gv = df_to_double(at);
                 } else {
                     df sv = df_make(0.f, 0.f);
                     for (int s2 = 0; s2 < nsl; ++s2)
-                        sv = df_add(sv, ld_df(sS + (s2 * (nh + 1) + r) * A.ldS + c - 1));
+                        sv = df_add(sv, df_norm(ld_df(sS + (s2 * (nh + 1) + r) * A.ldS + c - 1)));
                     gv = df_to_double(((x >> (c - 1)) & 1ull) ? df_sub(at, sv) : sv);
                 }
             }
@@ -817,6 +925,20 @@ __global__ void k_stats_final(const double *part, int nparts, int ldp, double *s
     }
 }
 
+template <typename TL>
+__device__ __forceinline__ TL to_low(double x) {
+    return (TL)x;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_low<__nv_bfloat16>(double x) {
+    return __double2bfloat16(x);
+}
+template <>
+__device__ __forceinline__ float2 to_low<float2>(double x) {
+    const df d = df_from_double(x);
+    return make_float2(d.h, d.l);
+}
+
 // Centre in place (FP64) and write the optional low-precision copies:
 //   O_c(x,0) = 1, G'_c(x,0) = E_loc - E,
 //   O_c(x,k) = O - <O_k>, G'_c(x,k) = G - <O_k> E_loc - E O_c(x,k),
@@ -824,7 +946,7 @@ __global__ void k_stats_final(const double *part, int nparts, int ldp, double *s
 template <typename TL>
 __global__ void k_centre(double *O, double *G, const double *eloc, double *wt,
                          const double *stats, int64_t n, int ldp, int P1, double e_core,
-                         TL *Olo, TL *Glo) {
+                         TL *Olo, TL *Glo, float2 *wlo) {
     const double E = stats[1];
     const double isw = 1.0 / stats[0];
     for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
@@ -848,11 +970,16 @@ __global__ void k_centre(double *O, double *G, const double *eloc, double *wt,
             Or[c] = oc;
             Gr[c] = gc;
             if (Olo) {
-                Olo[r * ldp + c] = (TL)oc;
-                Glo[r * ldp + c] = (TL)gc;
+                Olo[r * ldp + c] = to_low<TL>(oc);
+                Glo[r * ldp + c] = to_low<TL>(gc);
             }
         }
-        if (threadIdx.x == 0) wt[r] *= isw;
+        if (threadIdx.x == 0) {
+            const double wn = wt[r] * isw;
+            wt[r] = wn;
+            const df d = df_from_double(wn);
+            wlo[r] = make_float2(d.h, d.l);
+        }
     }
 }
 
@@ -960,8 +1087,8 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_build_rows")) return rc;
     } else {
         const int n = p->n;
-        const int ntab = 2 * p->nh * p->M + 2 * p->M + n * n + n * n * n * n;
-        k_tables_df<<<std::min(1024, (ntab + 255) / 256), 256, 0, s>>>(p->tabs, p->h, p->eri, p->M,
+        const int ntab = 2 * p->nh * p->M + n * n + n * n * n * n;
+        k_tables_df<<<std::min(1024, (ntab + 255) / 256), 256, 0, s>>>(p->theta, p->h, p->eri, p->M,
                                                                        p->nh, n, p->tdf);
         lm_note_launch(ctx);
         if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_tables_df")) return rc;
@@ -975,6 +1102,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         B.ldF = p->nh | 1;
         B.ldS = p->M | 1;
         B.nslice = std::max(1, BDF_THREADS / (p->nh + 1));
+        B.ns = A.S.ns_a + A.S.ns_b;
         B.theta = p->theta;
         B.tdf = p->tdf;
         B.rows = p->rows;
@@ -987,12 +1115,13 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         B.O = p->O;
         B.G = p->G;
         B.flags = ctx->d_flags;
-        const size_t f2 = (size_t)2 * p->nh * p->M + 2 * p->M + 3 * p->nh +
-                          (size_t)BDF_K * B.ldF + BDF_K +
-                          (size_t)B.nslice * (p->nh + 1) * B.ldS + (size_t)B.nslice * (p->nh + 1) +
+        const size_t nh_ = p->nh, M_ = p->M;
+        const size_t f2 = 2 * (size_t)B.ns * nh_ + B.ns + nh_ + (size_t)BDF_K * B.ldF + BDF_K +
+                          (size_t)B.nslice * (nh_ + 1) * B.ldS + (size_t)B.nslice * (nh_ + 1) +
                           BDF_THREADS / 32;
-        const size_t dsm = BDF_K * sizeof(int4) + sizeof(RowLists) + f2 * sizeof(float2) +
-                           (size_t)p->nh * sizeof(double) + 64;
+        const size_t dsm = BDF_K * (sizeof(int4) + sizeof(int2)) + sizeof(RowLists) +
+                           f2 * sizeof(float2) + (2 * nh_ + M_) * sizeof(double) +
+                           nh_ * (sizeof(float2) + sizeof(float)) + 64;
         if (dsm > (size_t)ctx->smem_optin)
             return lm_fail(ctx, LM_ERR_SIZE, "df64 build kernel needs %zu B shared memory", dsm);
         cudaError_t e2 = cudaFuncSetAttribute(k_build_rows_df,
@@ -1033,15 +1162,19 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     if (p->prec == LM_FP32)
         k_centre<float><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
                                               p->ldp, p->P1, p->e_core, (float *)p->Olo,
-                                              (float *)p->Glo);
+                                              (float *)p->Glo, p->wlo);
+    else if (p->prec == LM_DF64)
+        k_centre<float2><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
+                                               p->ldp, p->P1, p->e_core, (float2 *)p->Olo,
+                                               (float2 *)p->Glo, p->wlo);
     else if (p->prec == LM_BF16)
         k_centre<__nv_bfloat16><<<cgrid, 256, 0, s>>>(
             p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows, p->ldp, p->P1, p->e_core,
-            (__nv_bfloat16 *)p->Olo, (__nv_bfloat16 *)p->Glo);
+            (__nv_bfloat16 *)p->Olo, (__nv_bfloat16 *)p->Glo, p->wlo);
     else
         k_centre<double><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
                                                p->ldp, p->P1, p->e_core, (double *)nullptr,
-                                               (double *)nullptr);
+                                               (double *)nullptr, p->wlo);
     lm_note_launch(ctx);
     return lm_cuda_check(ctx, cudaGetLastError(), "k_centre");
 }

@@ -71,6 +71,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -162,6 +165,7 @@ struct lm_pencil {
     // device buffers (FP64 unless noted)
     uint64_t *rows;
     double *wt, *lnpsi, *eloc;
+    float2 *wlo;        // normalised weights as double-float
     double *O, *G;      // N_s x ldp, centred in place
     void *Olo, *Glo;    // low-precision copies (float or bf16) or null
     double *h, *eri, *theta, *tabs;
@@ -176,6 +180,7 @@ struct lm_pencil {
     double *wvec, *yvec, *hy, *sy, *tvec, *dots;
     IrlState *st;       // device
     IrlState *st_host;  // pinned mirror
+    unsigned *bar;      // grid-barrier words of the cooperative Lanczos kernel
     double E_host;
 };
 

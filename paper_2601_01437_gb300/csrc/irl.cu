@@ -42,6 +42,8 @@ struct LzArgs {
     int n_orb, na, nb;
     int deflate;
     IrlState *st;
+    unsigned *bar;      // [0] arrival count, [1] generation (cooperative kernel)
+    int *flags;
 };
 
 __device__ __forceinline__ void cta_range(const LzArgs &a, int &e0, int &e1) {
@@ -300,6 +302,168 @@ __global__ void __launch_bounds__(LT) k_lz_d(LzArgs a, int j, int jout, int mode
     const double inv = sb > 0.0 ? 1.0 / sb : 0.0;
     double *vout = a.V + (size_t)jout * a.ldp;
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) vout[e] = a.w[e] * inv;
+}
+
+// Grid-wide barrier for the cooperative Lanczos kernel (all CTAs co-resident by
+// the cooperative launch). The last CTA to arrive resets the count and bumps
+// the generation; the others poll it. The poll gives up after two seconds of
+// wall time, sets FLAG_TIMEOUT and lets the CTA continue, so it cannot hang.
+__device__ __forceinline__ void grid_barrier(unsigned *bar, int *flags) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (*gen == g) {
+                if (global_ns() - t0 > 2000000000ull) {
+                    atomicOr(flags, FLAG_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// One Lanczos step's vector work in a single cooperative launch: the bodies of
+// k_lz_a, k_lz_b, k_lz_c and k_lz_d (mode 0) separated by grid barriers.
+__global__ void __launch_bounds__(LT) k_lz_step(LzArgs a, int j) {
+    if (lz_skip(a.st)) return;  // uniform across the grid (written before launch)
+    __shared__ LzShared S;
+    __shared__ double coef[2];
+    __shared__ double sb;
+    __shared__ int sbrk;
+    int e0, e1;
+    cta_range(a, e0, e1);
+    const int E = e1 - e0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // (a) w = sum of the pencil partials; pass-1 dots
+    load_block(a, S, e0, e1, j, false);
+    {
+        const int part = threadIdx.x & 7;
+        for (int eb = 0; eb < E; eb += LT / 8) {
+            const int ee = eb + (threadIdx.x >> 3);
+            double acc = 0.0;
+            if (ee < E)
+                for (int b = part; b < a.nparts; b += 8)
+                    acc += a.part[(size_t)b * 2 * a.ldp + e0 + ee];
+            S.red[threadIdx.x] = acc;
+            __syncthreads();
+            if (part == 0 && ee < E) {
+                double t = 0.0;
+                for (int q = 0; q < 8; ++q) t += S.red[threadIdx.x + q];
+                S.w[ee] = t;
+            }
+            __syncthreads();
+        }
+    }
+    block_dots(S, E, j, a.dots + (size_t)blockIdx.x * DLD);
+    grid_barrier(a.bar, a.flags);
+    // (b) first projection; pass-2 dots
+    sum_dots(a, S, 0, j);
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= j; i += LT) a.st->h1[i] = S.h[i];
+    const double h1j = S.h[j];
+    block_update(S, E, j);
+    block_dots(S, E, j, a.dots + ((size_t)a.nrow_grid + blockIdx.x) * DLD);
+    grid_barrier(a.bar, a.flags);
+    // (c) second projection, alpha_j, null-space deflation, partial |w|^2
+    sum_dots(a, S, 1, j);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->alpha[j] = h1j + S.h[j];
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= j; i += LT) a.st->h2[i] = S.h[i];
+    block_update(S, E, j);
+    if (a.deflate) {
+        const int r = blockIdx.x, n = a.n_orb;
+        if (warp == 0) {
+            double sa = 0.0, sbe = 0.0;
+            for (int c = 1 + lane; c <= 2 * n; c += 32) {
+                if (c <= n) sa += S.w[c]; else sbe += S.w[c];
+            }
+            sa = warp_sum(sa);
+            sbe = warp_sum(sbe);
+            if (lane == 0) {
+                if (r == 0) {
+                    coef[0] = sa / n;
+                    coef[1] = sbe / n;
+                } else {
+                    const double w0 = S.w[0];
+                    const double na = a.na, nb = a.nb;
+                    const double g11 = n + na * na, g22 = n + nb * nb, g12 = na * nb;
+                    const double r1 = sa - na * w0, r2 = sbe - nb * w0;
+                    const double det = g11 * g22 - g12 * g12;
+                    coef[0] = (g22 * r1 - g12 * r2) / det;
+                    coef[1] = (g11 * r2 - g12 * r1) / det;
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c <= 2 * n; c += LT) {
+            if (c == 0) {
+                if (r > 0) S.w[0] += coef[0] * a.na + coef[1] * a.nb;
+            } else if (c <= n) {
+                S.w[c] -= coef[0];
+            } else {
+                S.w[c] -= coef[1];
+            }
+        }
+        __syncthreads();
+    }
+    {
+        double s2 = 0.0;
+        for (int e = threadIdx.x; e < E; e += LT) s2 = fma(S.w[e], S.w[e], s2);
+        s2 = warp_sum(s2);
+        if (lane == 0) S.red[warp] = s2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < LT / 32; ++w) t += S.red[w];
+            a.dots[((size_t)2 * a.nrow_grid + blockIdx.x) * DLD] = t;
+        }
+    }
+    grid_barrier(a.bar, a.flags);
+    // (d) beta_j = |w|, breakdown test, v_{j+1} = w / beta_j
+    {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < a.nrow_grid; b += LT)
+            t += a.dots[((size_t)2 * a.nrow_grid + b) * DLD];
+        S.red[threadIdx.x] = t;
+        __syncthreads();
+        for (int hh = LT / 2; hh > 0; hh >>= 1) {
+            if (threadIdx.x < hh) S.red[threadIdx.x] += S.red[threadIdx.x + hh];
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        const double beta = sqrt(S.red[0]);
+        const double alpha = h1j + S.h[j];
+        double tn = fmax(a.st->tnorm, fmax(fabs(alpha), beta));
+        if (j > 0) tn = fmax(tn, fabs(a.st->beta[j - 1]));
+        const int brk = beta <= 1e-14 * fmax(tn, 1e-300);
+        sb = beta;
+        sbrk = brk;
+    }
+    grid_barrier(a.bar, a.flags);  // every CTA has read tnorm / beta[j-1] before CTA 0 writes
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->beta[j] = sb;
+        a.st->tnorm = fmax(a.st->tnorm, fmax(fabs(h1j + S.h[j]), sb));
+        if (j > 0) a.st->tnorm = fmax(a.st->tnorm, fabs(a.st->beta[j - 1]));
+        if (sbrk) {
+            a.st->broke = 1;
+            a.st->jend = j + 1;
+        }
+    }
+    if (sbrk) return;
+    const double inv = sb > 0.0 ? 1.0 / sb : 0.0;
+    double *vout = a.V + (size_t)(j + 1) * a.ldp;
+    for (int e = threadIdx.x; e < E; e += LT) vout[e0 + e] = S.w[e] * inv;
 }
 
 // Random start vector: component e is 2u-1 with u the 53-bit uniform of
@@ -731,6 +895,7 @@ struct Run {
     LzArgs la;
     int m, k, sym, prec;
     int n_matvec, n_restart;
+    bool coop;  // one cooperative launch per Lanczos step
 };
 
 int lanczos_step(Run &R, int j) {
@@ -739,12 +904,19 @@ int lanczos_step(Run &R, int j) {
     const double *vj = p->V + (size_t)j * p->ldp;
     if (int rc = lm_launch_pencil(p, vj, R.sym, R.prec, 0, &p->st->broke, R.s)) return rc;
     const int g2 = R.la.nrow_grid;
+    R.n_matvec++;
+    if (R.coop) {
+        void *args[] = {(void *)&R.la, (void *)&j};
+        cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_lz_step, dim3(g2), dim3(LT),
+                                                    args, 0, R.s);
+        lm_note_launch(p->ctx);
+        return lm_cuda_check(p->ctx, e, "cooperative lanczos step");
+    }
     k_lz_a<<<g2, LT, 0, R.s>>>(R.la, j);
     k_lz_b<<<g2, LT, 0, R.s>>>(R.la, j);
     k_lz_c<<<g2, LT, 0, R.s>>>(R.la, j);
     k_lz_d<<<g2, LT, 0, R.s>>>(R.la, j, j + 1, 0);
     lm_note_launch(p->ctx, 4);
-    R.n_matvec++;
     return lm_cuda_check(p->ctx, cudaGetLastError(), "lanczos step");
 }
 
@@ -765,6 +937,7 @@ int run_irl(Run &R, double tol, double rel, int max_restarts, const double *v0_d
     lm_pencil *p = R.p;
     lm_ctx *ctx = p->ctx;
     cudaMemsetAsync(p->st, 0, sizeof(IrlState), R.s);
+    cudaMemsetAsync(p->bar, 0, 64 * sizeof(unsigned), R.s);
     k_init_start<<<(p->ldp + 255) / 256, 256, 0, R.s>>>(p->wvec, p->ldp, p->P1, seed, v0_dev);
     lm_note_launch(ctx);
     if (int rc = start_vector(R)) return rc;
@@ -822,7 +995,7 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
     if (prm->m > LM_MAXKRYLOV || prm->m < 2 || prm->k < 1 || prm->k >= prm->m || prm->m > p->P1)
         return lm_fail(ctx, LM_ERR_SIZE, "need 1 <= k < m <= min(64, P+1); got k=%d m=%d", prm->k,
                        prm->m);
-    if (prm->sym < 0 || prm->sym > 2 || prm->precision < 0 || prm->precision > 2)
+    if (prm->sym < 0 || prm->sym > 2 || prm->precision < 0 || prm->precision > 3)
         return lm_fail(ctx, LM_ERR_ARG, "bad sym or precision");
     Run R;
     R.p = p;
@@ -846,6 +1019,15 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
     R.la.nb = p->nb;
     R.la.deflate = prm->deflate_null;
     R.la.st = p->st;
+    R.la.bar = p->bar;
+    R.la.flags = ctx->d_flags;
+    {
+        // the cooperative step needs all nh+1 CTAs resident at once
+        int dev_coop = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&dev_coop, cudaDevAttrCooperativeLaunch, ctx->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lz_step, LT, 0);
+        R.coop = dev_coop && (int64_t)per_sm * ctx->sms >= R.la.nrow_grid;
+    }
 
     // optional start vector to the device
     const double *v0_dev = nullptr;
@@ -859,7 +1041,9 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
     }
     const int max_restarts = prm->max_restarts < 0 ? 0 : prm->max_restarts;
     int n_lowp = 0;
-    const bool lowp = prm->precision != LM_FP64 && p->Olo != nullptr;
+    const bool lowp = prm->precision != LM_FP64 && p->Olo != nullptr && p->prec != LM_DF64;
+    // double-float factors are accurate to ~1e-14: one phase at the FP64 tolerance
+    const bool dfp = prm->precision != LM_FP64 && p->Olo != nullptr && p->prec == LM_DF64;
     if (lowp) {
         // Low-precision phase: stop at the relative residual the storage format
         // supports, then continue the restarts with the FP64 operator from its
@@ -871,7 +1055,7 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
         cudaMemcpyAsync(p->hy, p->yvec, p->ldp * sizeof(double), cudaMemcpyDeviceToDevice, s);
         v0_dev = p->hy;
     }
-    R.prec = LM_FP64;
+    R.prec = dfp ? LM_DF64 : LM_FP64;
     if (int rc = run_irl(R, prm->tol, 50.0 * 2.220446049250313e-16, max_restarts, v0_dev,
                          prm->seed))
         return rc;

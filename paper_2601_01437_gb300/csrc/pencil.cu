@@ -17,29 +17,91 @@
 // (deterministic).
 #include <algorithm>
 
+#include "df64.cuh"
 #include "internal.cuh"
 
 namespace {
 
-constexpr int PT = 256;  // threads per pencil CTA
 
+
+// Arithmetic of the pencil per storage type: A is the accumulator / compute
+// type, madd(acc, a, b) forms acc += a b. FP64 storage computes in FP64;
+// FP32 and BF16 in FP32; float2 (double-float, h + l) storage computes with
+// error-free FP32 transformations and a lazily renormalised accumulator.
 template <typename T>
-struct Acc {
-    using type = float;
+struct PA;
+template <>
+struct PA<double> {
+    using A = double;
+    static __device__ __forceinline__ A zero() { return 0.0; }
+    static __device__ __forceinline__ A load(const double *p) { return *p; }
+    static __device__ __forceinline__ A from_double(double x) { return x; }
+    static __device__ __forceinline__ double to_double(A a) { return a; }
+    static __device__ __forceinline__ void madd(A &acc, A a, A b) { acc = fma(a, b, acc); }
+    static __device__ __forceinline__ A add(A a, A b) { return a + b; }
+    static __device__ __forceinline__ A mul(A a, A b) { return a * b; }
+    static __device__ __forceinline__ A shfl_xor(A a, int off) {
+        return __shfl_xor_sync(0xffffffffu, a, off);
+    }
+    static __device__ __forceinline__ A weight(const double *w, const float2 *, int64_t i) {
+        return w[i];
+    }
 };
 template <>
-struct Acc<double> {
-    using type = double;
+struct PA<float> {
+    using A = float;
+    static __device__ __forceinline__ A zero() { return 0.f; }
+    static __device__ __forceinline__ A load(const float *p) { return *p; }
+    static __device__ __forceinline__ A from_double(double x) { return (float)x; }
+    static __device__ __forceinline__ double to_double(A a) { return (double)a; }
+    static __device__ __forceinline__ void madd(A &acc, A a, A b) { acc = fmaf(a, b, acc); }
+    static __device__ __forceinline__ A add(A a, A b) { return a + b; }
+    static __device__ __forceinline__ A mul(A a, A b) { return a * b; }
+    static __device__ __forceinline__ A shfl_xor(A a, int off) {
+        return __shfl_xor_sync(0xffffffffu, a, off);
+    }
+    static __device__ __forceinline__ A weight(const double *, const float2 *wl, int64_t i) {
+        return wl[i].x;
+    }
 };
-
-template <typename T>
-__device__ __forceinline__ typename Acc<T>::type ld_s(const T *p) {
-    return (typename Acc<T>::type)(*p);
-}
 template <>
-__device__ __forceinline__ float ld_s<__nv_bfloat16>(const __nv_bfloat16 *p) {
-    return __bfloat162float(*p);
-}
+struct PA<__nv_bfloat16> : PA<float> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16 *p) {
+        return __bfloat162float(*p);
+    }
+};
+template <>
+struct PA<float2> {
+    using A = df;
+    static __device__ __forceinline__ A zero() { return df_make(0.f, 0.f); }
+    static __device__ __forceinline__ A load(const float2 *p) {
+        const float2 v = *p;
+        return df_make(v.x, v.y);
+    }
+    static __device__ __forceinline__ A from_double(double x) { return df_from_double(x); }
+    static __device__ __forceinline__ double to_double(A a) { return df_to_double(a); }
+    // acc += a b: exact head product by FMA, cross terms, head sum by TwoSum,
+    // everything else gathered in the (not yet renormalised) tail
+    static __device__ __forceinline__ void madd(A &acc, A a, A b) {
+        const float p = __fmul_rn(a.h, b.h);
+        float e = __fmaf_rn(a.h, b.h, -p);
+        e = __fmaf_rn(a.h, b.l, e);
+        e = __fmaf_rn(a.l, b.h, e);
+        const df s = df_ts(acc.h, p);
+        acc.h = s.h;
+        acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
+    }
+    static __device__ __forceinline__ A add(A a, A b) { return df_add(a, b); }
+    static __device__ __forceinline__ A mul(A a, A b) { return df_mul(a, b); }
+    static __device__ __forceinline__ A shfl_xor(A a, int off) {
+        return df_make(__shfl_xor_sync(0xffffffffu, a.h, off),
+                       __shfl_xor_sync(0xffffffffu, a.l, off));
+    }
+    static __device__ __forceinline__ A weight(const double *, const float2 *wl, int64_t i) {
+        const float2 v = wl[i];
+        return df_make(v.x, v.y);
+    }
+};
 
 enum { MODE_H_NONE = 0, MODE_H_HALF = 1, MODE_S = 2 };
 
@@ -48,6 +110,7 @@ struct PencilArgs {
     const T *O;
     const T *G;
     const double *w;
+    const float2 *wlo;  // the weights as double-float (FP32 / BF16 use .x)
     int64_t n_rows;
     int ldp;
     const double *v;
@@ -59,146 +122,169 @@ struct PencilArgs {
     int *flags;
 };
 
-// One warp per row: lane l owns columns l, l+32, ... of the row, so a row dot
-// is one 5-step butterfly and the rank-1 update of the warp's y accumulators
-// (registers) reuses the staged row. MODE_H_NONE: y += w (G.v) O;
+// Warp-specialised pipeline. Warp NCW (the last) is the producer: its lane 0
+// streams this CTA's rows, one row of O (and G) per pipeline stage, into a ring
+// of S stages with 1-D bulk copies, re-filling a stage as soon as its
+// consumer has released it (full / empty mbarrier pair per stage). Consumer
+// warp w takes rows w, w + NCW, ...: lane l owns columns l, l+32, ..., so a
+// row dot is one butterfly and the rank-1 update of the warp's register-
+// resident y reuses the staged row. MODE_H_NONE: y += w (G.v) O;
 // MODE_H_HALF: y += w/2 ((G.v) O + (O.v) G); MODE_S: y += w (O.v) O (only O
-// is staged). At the end the 8 warps' accumulators are summed in warp order.
-template <typename T, int NJ, int MODE>
-__global__ void __launch_bounds__(PT) k_pencil(PencilArgs<T> a) {
-    using AT = typename Acc<T>::type;
+// is staged). At the end the consumer warps' y are summed in warp order.
+// Every wait is bounded; a timeout sets FLAG_TIMEOUT and the CTA drains its
+// outstanding copies before exiting.
+// consumer warps: 16 for rows up to 896 columns, 8 (more registers each) beyond
+template <int NJ>
+struct Ncw {
+    static constexpr int value = NJ <= 28 ? 16 : 8;
+};
+
+template <typename T, int NJ, int MODE, int NCW = Ncw<NJ>::value>
+__global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
+    using P = PA<T>;
+    using AT = typename PA<T>::A;
     extern __shared__ __align__(128) unsigned char smraw[];
     if (a.skip && *a.skip) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ldp = a.ldp, R = a.rows_per_tile;
+    const int ldp = a.ldp, S = a.stages;
     const int nmat = MODE == MODE_S ? 1 : 2;
-    const size_t tile_elems = (size_t)R * ldp;
+    const size_t row_elems = (size_t)ldp;
     T *stage_base = reinterpret_cast<T *>(smraw);
-    const size_t stage_bytes_all = (size_t)a.stages * nmat * tile_elems * sizeof(T);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smraw + stage_bytes_all);
-    AT *vs = reinterpret_cast<AT *>(bars + 8);  // v in the compute type, ldp entries
-    __shared__ int s_ok;
+    const size_t stage_bytes_all = (size_t)S * nmat * row_elems * sizeof(T);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smraw + stage_bytes_all);
+    uint64_t *empty = full + S;
+    AT *vs = reinterpret_cast<AT *>(empty + S);  // v in the compute type, ldp entries
+    __shared__ int s_abort;
 
     const int64_t r0 = a.n_rows * blockIdx.x / gridDim.x;
     const int64_t r1 = a.n_rows * (blockIdx.x + 1) / gridDim.x;
-    const int ntiles = (int)((r1 - r0 + R - 1) / R);
+    const int nrows = (int)(r1 - r0);
     const int nj = (ldp + 31) >> 5;
 
     if (tid == 0) {
-        for (int s = 0; s < a.stages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        s_abort = 0;
         fence_barrier_init();
     }
-    for (int c = tid; c < ldp; c += PT) vs[c] = (AT)a.v[c];
+    for (int c = tid; c < ldp; c += blockDim.x) vs[c] = P::from_double(a.v[c]);
     __syncthreads();
-
-    auto issue = [&](int i) {
-        const int s = i % a.stages;
-        const int64_t row = r0 + (int64_t)i * R;
-        const int nr = (int)min((int64_t)R, r1 - row);
-        const uint32_t bytes = (uint32_t)((size_t)nr * ldp * sizeof(T));
-        T *dO = stage_base + (size_t)s * nmat * tile_elems;
-        mbar_arrive_expect_tx(&bars[s], nmat * bytes);
-        bulk_g2s(dO, a.O + row * ldp, bytes, &bars[s]);
-        if (MODE != MODE_S) bulk_g2s(dO + tile_elems, a.G + row * ldp, bytes, &bars[s]);
-    };
-    if (tid == 0)
-        for (int i = 0; i < min(a.stages, ntiles); ++i) issue(i);
 
     AT y[NJ];
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) y[j] = 0;
+    for (int j = 0; j < NJ; ++j) y[j] = P::zero();
 
-    int consumed = 0;
-    bool ok = true;
-    for (int i = 0; i < ntiles; ++i) {
-        const int s = i % a.stages;
-        const uint32_t par = (uint32_t)((i / a.stages) & 1);
-        if (tid == 0) s_ok = mbar_wait_bounded(&bars[s], par) ? 1 : 0;
-        __syncthreads();
-        if (!s_ok) {
-            ok = false;
-            break;
+    if (warp == NCW) {
+        // producer
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(row_elems * sizeof(T));
+            int issued = 0;
+            for (int i = 0; i < nrows; ++i) {
+                const int s = i % S;
+                if (i >= S && !mbar_wait_bounded(&empty[s], (uint32_t)(((i / S) - 1) & 1))) {
+                    atomicOr(a.flags, FLAG_TIMEOUT);
+                    atomicExch(&s_abort, 1);
+                    break;
+                }
+                if (*(volatile int *)&s_abort) break;
+                T *dst = stage_base + (size_t)s * nmat * row_elems;
+                mbar_arrive_expect_tx(&full[s], nmat * bytes);
+                bulk_g2s(dst, a.O + (r0 + i) * ldp, bytes, &full[s]);
+                if (MODE != MODE_S) bulk_g2s(dst + row_elems, a.G + (r0 + i) * ldp, bytes, &full[s]);
+                issued = i + 1;
+            }
+            // every issued copy lands before the CTA may exit (bounded)
+            for (int i = max(0, issued - S); i < issued; ++i)
+                (void)mbar_wait_bounded(&full[i % S], (uint32_t)((i / S) & 1));
         }
-        consumed = i + 1;
-        const int64_t row0 = r0 + (int64_t)i * R;
-        const int nr = (int)min((int64_t)R, r1 - row0);
-        const T *tO = stage_base + (size_t)s * nmat * tile_elems;
-        const T *tG = tO + tile_elems;
-        for (int r = warp; r < nr; r += PT / 32) {
-            const T *ro = tO + (size_t)r * ldp;
-            const T *rg = tG + (size_t)r * ldp;
-            AT dg = 0, dov = 0;
+    } else {
+        for (int i = warp; i < nrows; i += NCW) {
+            const int s = i % S;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(&full[s], (uint32_t)((i / S) & 1));
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok || *(volatile int *)&s_abort) {
+                if (lane == 0) {
+                    atomicOr(a.flags, FLAG_TIMEOUT);
+                    atomicExch(&s_abort, 1);
+                }
+                break;
+            }
+            const T *ro = stage_base + (size_t)s * nmat * row_elems;
+            const T *rg = ro + row_elems;
+            AT dg = P::zero(), dov = P::zero();
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
                 if (j < nj) {
                     const int c = lane + 32 * j;
                     if (c < ldp) {
-                        if (MODE != MODE_S) dg += ld_s(rg + c) * vs[c];
-                        if (MODE != MODE_H_NONE) dov += ld_s(ro + c) * vs[c];
+                        if (MODE != MODE_S) P::madd(dg, P::load(rg + c), vs[c]);
+                        if (MODE != MODE_H_NONE) P::madd(dov, P::load(ro + c), vs[c]);
                     }
                 }
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                if (MODE != MODE_S) dg += __shfl_xor_sync(0xffffffffu, dg, off);
-                if (MODE != MODE_H_NONE) dov += __shfl_xor_sync(0xffffffffu, dov, off);
+                if (MODE != MODE_S) dg = P::add(dg, P::shfl_xor(dg, off));
+                if (MODE != MODE_H_NONE) dov = P::add(dov, P::shfl_xor(dov, off));
             }
-            const AT wr = (AT)a.w[row0 + r];
+            const AT wr = P::weight(a.w, a.wlo, r0 + i);
             if (MODE == MODE_H_NONE) {
-                const AT cg = wr * dg;
+                const AT cg = P::mul(wr, dg);
 #pragma unroll
                 for (int j = 0; j < NJ; ++j)
                     if (j < nj) {
                         const int c = lane + 32 * j;
-                        if (c < ldp) y[j] += cg * ld_s(ro + c);
+                        if (c < ldp) P::madd(y[j], cg, P::load(ro + c));
                     }
             } else if (MODE == MODE_H_HALF) {
-                const AT cg = (AT)0.5 * wr * dg, co = (AT)0.5 * wr * dov;
+                const AT half = P::mul(wr, P::from_double(0.5));
+                const AT cg = P::mul(half, dg);
+                const AT co = P::mul(half, dov);
 #pragma unroll
                 for (int j = 0; j < NJ; ++j)
                     if (j < nj) {
                         const int c = lane + 32 * j;
-                        if (c < ldp) y[j] += cg * ld_s(ro + c) + co * ld_s(rg + c);
+                        if (c < ldp) {
+                            P::madd(y[j], cg, P::load(ro + c));
+                            P::madd(y[j], co, P::load(rg + c));
+                        }
                     }
             } else {
-                const AT co = wr * dov;
+                const AT co = P::mul(wr, dov);
 #pragma unroll
                 for (int j = 0; j < NJ; ++j)
                     if (j < nj) {
                         const int c = lane + 32 * j;
-                        if (c < ldp) y[j] += co * ld_s(ro + c);
+                        if (c < ldp) P::madd(y[j], co, P::load(ro + c));
                     }
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
         }
-        __syncthreads();
-        if (tid == 0 && i + a.stages < ntiles) issue(i + a.stages);
     }
-    if (!ok) {
-        // Drain the copies this CTA issued but did not consume before exiting.
-        if (tid == 0) {
-            atomicOr(a.flags, FLAG_TIMEOUT);
-            const int issued = min(ntiles, consumed + a.stages);
-            for (int i = consumed; i < issued; ++i)
-                (void)mbar_wait_bounded(&bars[i % a.stages], (uint32_t)((i / a.stages) & 1));
-        }
-        __syncthreads();
-        return;
-    }
-    // Sum the 8 warps' accumulators in warp order (staging buffers are free now).
-    double *ys = reinterpret_cast<double *>(smraw);  // [8][ldp] FP64
+    __syncthreads();
+    if (s_abort) return;
+    // Sum the consumer warps' accumulators in warp order, in the accumulator
+    // type (the ring is free now); one conversion to FP64 per column.
+    AT *ys = reinterpret_cast<AT *>(smraw);  // [NCW][ldp]
+    if (warp < NCW) {
 #pragma unroll
-    for (int j = 0; j < NJ; ++j)
-        if (j < nj) {
-            const int c = lane + 32 * j;
-            if (c < ldp) ys[(size_t)warp * ldp + c] = (double)y[j];
-        }
+        for (int j = 0; j < NJ; ++j)
+            if (j < nj) {
+                const int c = lane + 32 * j;
+                if (c < ldp) ys[(size_t)warp * ldp + c] = y[j];
+            }
+    }
     __syncthreads();
     double *out = a.out + (size_t)blockIdx.x * a.out_ld;
-    for (int c = tid; c < ldp; c += PT) {
-        double t = 0.0;
+    for (int c = tid; c < ldp; c += blockDim.x) {
+        AT t = ys[c];
 #pragma unroll
-        for (int w8 = 0; w8 < PT / 32; ++w8) t += ys[(size_t)w8 * ldp + c];
-        out[c] = t;
+        for (int w8 = 1; w8 < NCW; ++w8) t = P::add(t, ys[(size_t)w8 * ldp + c]);
+        out[c] = P::to_double(t);
     }
 }
 
@@ -229,22 +315,21 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
              cudaStream_t s) {
     const int nmat = MODE == MODE_S ? 1 : 2;
     const size_t row_bytes = (size_t)nmat * p->ldp * sizeof(T);
-    // rows per tile: about 48 KB per pipeline stage, one row per warp when two
-    // such stages fit, fewer rows (idle warps) for very long FP64 rows
-    const size_t tail = 8 * sizeof(uint64_t) + (size_t)p->ldp * sizeof(typename Acc<T>::type) + 256;
+    // ring of one-row stages filling the shared memory (at most 32 stages)
+    const size_t tail = (size_t)p->ldp * sizeof(typename PA<T>::A) + 256;
     const size_t budget = (size_t)p->ctx->smem_optin - tail - 2048;
-    int R = (int)std::min<size_t>(64, std::max<size_t>(1, 49152 / row_bytes));
-    if (R < PT / 32) R = (int)std::max<size_t>(1, std::min<size_t>(PT / 32, budget / (2 * row_bytes)));
-    const size_t stage_bytes = R * row_bytes;
-    int stages = (int)std::min<size_t>(4, budget / stage_bytes);
+    const int stages = (int)std::min<size_t>(32, budget / (row_bytes + 2 * sizeof(uint64_t)));
+    const int R = 1;
     if (stages < 2)
         return lm_fail(p->ctx, LM_ERR_SIZE, "pencil row of %d columns too long", p->ldp);
-    size_t smem = stages * stage_bytes + tail;
-    smem = std::max(smem, (size_t)(PT / 32) * p->ldp * sizeof(double) + 64);
+    size_t smem = stages * (row_bytes + 2 * sizeof(uint64_t)) + tail;
+    constexpr int NCW = Ncw<NJ>::value;
+    smem = std::max(smem, (size_t)NCW * p->ldp * sizeof(double) + 64);
     PencilArgs<T> a;
     a.O = O;
     a.G = G;
     a.w = p->wt;
+    a.wlo = p->wlo;
     a.n_rows = p->n_rows;
     a.ldp = p->ldp;
     a.v = v;
@@ -258,7 +343,7 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return lm_cuda_check(p->ctx, e, "pencil smem attribute");
     lm_prof_begin(p->ctx, PROF_PENCIL, s);
-    k_pencil<T, NJ, MODE><<<p->g_pencil, PT, smem, s>>>(a);
+    k_pencil<T, NJ, MODE><<<p->g_pencil, NCW * 32 + 32, smem, s>>>(a);
     lm_prof_end(p->ctx, PROF_PENCIL, s);
     lm_note_launch(p->ctx);
     p->ctx->pencil_rows += p->n_rows;
@@ -299,6 +384,9 @@ int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_
     if (p->prec == LM_FP32)
         return dispatch_nc<float>(p, (const float *)p->Olo, (const float *)p->Glo, v, half,
                                   want_s, skip, s);
+    if (p->prec == LM_DF64)
+        return dispatch_nc<float2>(p, (const float2 *)p->Olo, (const float2 *)p->Glo, v, half,
+                                   want_s, skip, s);
     return dispatch_nc<__nv_bfloat16>(p, (const __nv_bfloat16 *)p->Olo,
                                       (const __nv_bfloat16 *)p->Glo, v, half, want_s, skip, s);
 }
@@ -322,19 +410,19 @@ int raw_launch(const double *O, const double *G, const double *w, int64_t n_rows
                cudaStream_t s) {
     const int nmat = MODE == MODE_S ? 1 : 2;
     const size_t row_bytes = (size_t)nmat * ldp * sizeof(double);
-    const size_t tail = 8 * sizeof(uint64_t) + (size_t)ldp * sizeof(double) + 256;
+    const size_t tail = (size_t)ldp * sizeof(double) + 256;
     const size_t budget = (size_t)smem_optin - tail - 2048;
-    int R = (int)std::min<size_t>(64, std::max<size_t>(1, 49152 / row_bytes));
-    if (R < PT / 32) R = (int)std::max<size_t>(1, std::min<size_t>(PT / 32, budget / (2 * row_bytes)));
-    const size_t stage_bytes = R * row_bytes;
-    const int stages = (int)std::min<size_t>(4, budget / stage_bytes);
+    const int stages = (int)std::min<size_t>(32, budget / (row_bytes + 2 * sizeof(uint64_t)));
+    const int R = 1;
     if (stages < 2) return LM_ERR_SIZE;
-    size_t smem = stages * stage_bytes + tail;
-    smem = std::max(smem, (size_t)(PT / 32) * ldp * sizeof(double) + 64);
+    size_t smem = stages * (row_bytes + 2 * sizeof(uint64_t)) + tail;
+    constexpr int NCW = Ncw<NJ>::value;
+    smem = std::max(smem, (size_t)NCW * ldp * sizeof(double) + 64);
     PencilArgs<double> a;
     a.O = O;
     a.G = G;
     a.w = w;
+    a.wlo = nullptr;
     a.n_rows = n_rows;
     a.ldp = ldp;
     a.v = vpad;
@@ -347,7 +435,7 @@ int raw_launch(const double *O, const double *G, const double *w, int64_t n_rows
     if (cudaFuncSetAttribute(k_pencil<double, NJ, MODE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LM_ERR_CUDA;
-    k_pencil<double, NJ, MODE><<<grid, PT, smem, s>>>(a);
+    k_pencil<double, NJ, MODE><<<grid, NCW * 32 + 32, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;
 }
 

@@ -194,7 +194,7 @@ def test_pencil_products_mc_rows(ctx, abi):
     pen.free()
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 2e-6), (2, 2e-2)])
+@pytest.mark.parametrize("prec,tol", [(1, 2e-6), (2, 2e-2), (3, 1e-12)], ids=["fp32", "bf16", "df64"])
 def test_pencil_products_low_precision(ctx, abi, prec, tol):
     h, eri = synth.integrals(14, 111)
     th = synth.rbm_theta(14, 56, 111)
@@ -253,6 +253,26 @@ def test_irl_f2_full_size(ctx, abi):
     assert res.lambda_gen_rq == pytest.approx(
         float(ref["c"] @ (0.5 * (ref["Hp"] + ref["Hp"].T)) @ ref["c"] / (ref["c"] @ ref["S"] @ ref["c"])),
         rel=1e-8)
+    pen.free()
+
+
+def test_irl_f2_full_size_df64_pencil(ctx, abi):
+    """F2-shaped with double-float pencil factors in the Lanczos products."""
+    w = synth.WORKLOADS["f2_10o14e"]
+    pen, ref, res, c, dth = _irl_case(ctx, abi, w, prec=3)
+    assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
+    assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-10)
+    assert _rel(dth, ref["dtheta"]) <= 1e-8
+    assert res.residual <= 1e-10
+    pen.free()
+
+
+def test_pencil_products_f2_df64(ctx, abi):
+    w = synth.WORKLOADS["f2_10o14e"]
+    h, eri, th, _, _ = w.inputs()
+    pen, pd = _build_both(ctx, abi, 10, 7, 7, 40, h, eri, th, prec=3)
+    _check_products(abi, pen, pd, abi.LM_SYM_NONE, tol=1e-12, prec=3)
+    _check_products(abi, pen, pd, abi.LM_SYM_HALF, tol=1e-12, prec=3)
     pen.free()
 
 
