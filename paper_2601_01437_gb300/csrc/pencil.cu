@@ -126,13 +126,19 @@ struct PencilArgs {
 // streams this CTA's rows, one row of O (and G) per pipeline stage, into a ring
 // of S stages with 1-D bulk copies, re-filling a stage as soon as its
 // consumer has released it (full / empty mbarrier pair per stage). Consumer
-// warp w takes rows w, w + NCW, ...: lane l owns columns l, l+32, ..., so a
+// warp w takes rows w, w + C, ... (C consuming warps, below): lane l owns columns l, l+32, ..., so a
 // row dot is one butterfly and the rank-1 update of the warp's register-
 // resident y reuses the staged row. MODE_H_NONE: y += w (G.v) O;
 // MODE_H_HALF: y += w/2 ((G.v) O + (O.v) G); MODE_S: y += w (O.v) O (only O
 // is staged). At the end the consumer warps' y are summed in warp order.
 // Every wait is bounded; a timeout sets FLAG_TIMEOUT and the CTA drains its
 // outstanding copies before exiting.
+// Consumer warp w waits on full[i % S] with parity (i / S) & 1. That parity
+// names phase i / S unambiguously only while the stage's previous fill (row
+// i - S) has already landed, which holds when each warp's previous row i - C is
+// at or after i - S, i.e. when the number C of consuming warps is at most S.
+// So C = min(NCW, S); with fewer stages than warps the extra warps only join
+// the final sum with zero accumulators.
 // consumer warps: 16 for rows up to 896 columns, 8 (more registers each) beyond
 template <int NJ>
 struct Ncw {
@@ -147,6 +153,7 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
     if (a.skip && *a.skip) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ldp = a.ldp, S = a.stages;
+    const int ncons = min(NCW, S);  // consuming warps; see the parity note above
     const int nmat = MODE == MODE_S ? 1 : 2;
     const size_t row_elems = (size_t)ldp;
     T *stage_base = reinterpret_cast<T *>(smraw);
@@ -199,8 +206,8 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
             for (int i = max(0, issued - S); i < issued; ++i)
                 (void)mbar_wait_bounded(&full[i % S], (uint32_t)((i / S) & 1));
         }
-    } else {
-        for (int i = warp; i < nrows; i += NCW) {
+    } else if (warp < ncons) {
+        for (int i = warp; i < nrows; i += ncons) {
             const int s = i % S;
             bool ok = true;
             if (lane == 0) ok = mbar_wait_bounded(&full[s], (uint32_t)((i / S) & 1));

@@ -205,6 +205,23 @@ def test_pencil_products_low_precision(ctx, abi, prec, tol):
     pen.free()
 
 
+@pytest.mark.parametrize("n,na,nb,nh,mc", [(10, 2, 2, 41, 0), (14, 7, 7, 64, 600),
+                                           (32, 1, 1, 30, 0)],
+                         ids=["ldp888", "ldp1888", "ldp2016"])
+@pytest.mark.parametrize("prec", [0, 3], ids=["fp64", "df64"])
+def test_pencil_products_fewer_stages_than_warps(ctx, abi, n, na, nb, nh, mc, prec):
+    """Row widths whose shared-memory ring holds fewer stages than the kernel has
+    consumer warps (P+1 = 882, 1885, 2015 with 8-byte factors)."""
+    h, eri = synth.integrals(n, 31)
+    th = synth.rbm_theta(n, nh, 31, sigma=0.05)
+    rows, cnt = _mc_rows(n, na, nb, mc, 31, h) if mc else (None, None)
+    pen, pd = _build_both(ctx, abi, n, na, nb, nh, h, eri, th, rows, cnt, prec=prec)
+    tol = 1e-10 if prec == 0 else 1e-12
+    _check_products(abi, pen, pd, abi.LM_SYM_NONE, nvec=2, tol=tol, prec=prec)
+    _check_products(abi, pen, pd, abi.LM_SYM_HALF, nvec=2, tol=tol, prec=prec)
+    pen.free()
+
+
 # ------------------------------------------------------------------ IRL
 def _irl_case(ctx, abi, w, theta=None, rows=None, counts=None, prec=0):
     h, eri, th, _, _ = w.inputs()
