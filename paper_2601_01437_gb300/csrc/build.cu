@@ -627,7 +627,9 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     double *sCs = sZ + nh;                                             // [M] sum_j sigma_j W_jp
     float2 *sGd = reinterpret_cast<float2 *>(sCs + M);                 // [nh] g as df
     float *sSig = reinterpret_cast<float *>(sGd + nh);                 // [nh] sigma
+    int *sVe = reinterpret_cast<int *>(sSig + nh);                     // [NS] exponent of V_s
     __shared__ double sDiag, sLn, sGinv;
+    __shared__ int sGe;
     __shared__ int sBad;
 
     const float2 *e2 = A.tdf;               // exp(2W) [nh][M]
@@ -684,8 +686,13 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             lp = warp_sum(lp);
             lg = warp_sum(lg);
             if (tid == 0) {
+                // 1 / prod_j (1 + g_j) = sGinv * 2^sGe with sGinv in [0.5, 1): the
+                // product reaches 2^Nh, beyond the range whose double-float low
+                // word is still a normal FP32 number
                 sLn = lp;
-                sGinv = exp(-lg);
+                int ge = 0;
+                sGinv = frexp(exp(-lg), &ge);
+                sGe = ge;
             }
         } else if (tid < 64) {
             const double d = diag_value_warp(A.S, *sL);
@@ -715,8 +722,10 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             int i, a;
             single_of(A.S, *sL, s, i, a);
             const double ex = (A.theta[a] - A.theta[i]) - (sCs[a] - sCs[i]);
-            const df v = df_from_double(exp(ex));
+            int ve = 0;  // V_s = mantissa * 2^ve, mantissa in [0.5, 1)
+            const df v = df_from_double(frexp(exp(ex), &ve));
             sV[s] = make_float2(v.h, v.l);
+            sVe[s] = ve;
         }
         __syncthreads();
 
@@ -765,9 +774,13 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 df hv = exc_value_df(A.S, L, e, hd, gd);
                 if (sg < 0) hv = df_neg(hv);
                 df f = df_mul(hv, ld_df(sV + s1));
-                if (s2 >= 0) f = df_mul(f, ld_df(sV + s2));
+                int fe = re + sGe + sVe[s1];
+                if (s2 >= 0) {
+                    f = df_mul(f, ld_df(sV + s2));
+                    fe += sVe[s2];
+                }
                 df c = df_mul(df_mul(f, ginv), rp);
-                c = df_ldexp(c, re);
+                c = df_ldexp(c, fe);
                 st_df(sC + kk, c);
                 sIdx[kk] = make_int4(e.i, e.j, e.a, e.b);
                 df_acc(el_part, c);
@@ -1121,7 +1134,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
                           BDF_THREADS / 32;
         const size_t dsm = BDF_K * (sizeof(int4) + sizeof(int2)) + sizeof(RowLists) +
                            f2 * sizeof(float2) + (2 * nh_ + M_) * sizeof(double) +
-                           nh_ * (sizeof(float2) + sizeof(float)) + 64;
+                           nh_ * (sizeof(float2) + sizeof(float)) + B.ns * sizeof(int) + 64;
         if (dsm > (size_t)ctx->smem_optin)
             return lm_fail(ctx, LM_ERR_SIZE, "df64 build kernel needs %zu B shared memory", dsm);
         cudaError_t e2 = cudaFuncSetAttribute(k_build_rows_df,

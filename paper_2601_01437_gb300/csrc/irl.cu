@@ -24,6 +24,8 @@
 // f = beta_hat_k V_m Q[:, k] + beta_m Q[m-1, k-1] v_{m+1}.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -466,6 +468,261 @@ __global__ void __launch_bounds__(LT) k_lz_step(LzArgs a, int j) {
     for (int e = threadIdx.x; e < E; e += LT) vout[e0 + e] = S.w[e] * inv;
 }
 
+// ---------------------------------------------------------------- cluster step
+// One Lanczos step's vector work in a single thread-block cluster of C = 8 or
+// 16 CTAs (the whole grid). CTA q owns the parameter-grid rows
+// [q R / C, (q + 1) R / C) (R = Nh + 1), so the particle-number projection
+// stays inside a CTA. The three global reductions (pass-1 dots, pass-2 dots,
+// |w|^2) are exchanged through distributed shared memory between hardware
+// cluster barriers, and every CTA sums the C partials with the same fixed
+// tree, so all CTAs hold bit-identical dots and beta. No CTA spins on memory.
+constexpr int CT = 512;   // threads per cluster CTA
+constexpr int CE = 384;   // entries per CTA: P+1 <= 2048 gives <= 2048/8 + 65 + 31
+constexpr int CROWS = 16; // grid rows per CTA: Nh + 1 <= 128 over >= 8 CTAs
+constexpr int CW = CT / 32;
+constexpr int CNI = (LM_MAXKRYLOV + 1 + CW - 1) / CW;  // dots per warp
+
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+    cluster_arrive();
+    cluster_wait();
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_ncta() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// Generic address of the same shared variable in cluster CTA `rank`.
+__device__ __forceinline__ const double *peer_ptr(const double *local, uint32_t rank) {
+    uint64_t r;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"(local), "r"(rank));
+    return reinterpret_cast<const double *>(r);
+}
+
+struct LcShared {
+    double w[CE];  // (the V slice follows in dynamic shared memory)
+    double pd1[LM_MAXKRYLOV + 1];  // this CTA's pass-1 partial dots (read by peers)
+    double pd2[LM_MAXKRYLOV + 1];  // pass-2 partial dots (read by peers)
+    double pn[1];                  // partial |w|^2 (read by peers)
+    double h[LM_MAXKRYLOV + 1];    // reduced dots
+    double red[CT];
+    double coef[CROWS][2];
+};
+
+// sum over the C <= 16 cluster CTAs of x[rank] with one fixed pairwise tree
+__device__ __forceinline__ double cluster_tree_sum(const double *local, int C) {
+    double x[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) x[r] = r < C ? *peer_ptr(local, (uint32_t)r) : 0.0;
+#pragma unroll
+    for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+        for (int r = 0; r < h; ++r) x[r] += x[r + h];
+    return x[0];
+}
+
+// pd[i] = V[:, i] . w over this CTA's entries, i <= j, from the staged slice
+// Vs (leading dimension le): four threads per dot, each over every fourth
+// entry, combined by two shuffle levels.
+__device__ __forceinline__ void cluster_dots(const double *Vs, int le, const LcShared &S, int E,
+                                             int j, double *pd) {
+    const int i = threadIdx.x >> 2, part = threadIdx.x & 3;
+    double s0 = 0.0, s1 = 0.0;
+    if (i <= j) {
+        const double *vi = Vs + (size_t)i * le;
+        int e = part;
+        for (; e + 4 < E; e += 8) {
+            s0 = fma(vi[e], S.w[e], s0);
+            s1 = fma(vi[e + 4], S.w[e + 4], s1);
+        }
+        if (e < E) s0 = fma(vi[e], S.w[e], s0);
+    }
+    double t = s0 + s1;
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    if (part == 0 && i <= j) pd[i] = t;
+}
+
+// w[e] -= sum_{i<=j} Vs[i][e] h[i]: thread (g, e) sums i = g, g + ng, ...; the
+// ng group sums are combined in group order.
+__device__ __forceinline__ void cluster_update(const double *Vs, int le, LcShared &S, int E, int EP,
+                                               int ng, int j) {
+    const int tid = threadIdx.x;
+    const int g = tid / EP, e = tid % EP;
+    double s0 = 0.0, s1 = 0.0;
+    if (g < ng && e < E) {
+        int i = g;
+        for (; i + ng <= j; i += 2 * ng) {
+            s0 = fma(Vs[(size_t)i * le + e], S.h[i], s0);
+            s1 = fma(Vs[(size_t)(i + ng) * le + e], S.h[i + ng], s1);
+        }
+        if (i <= j) s0 = fma(Vs[(size_t)i * le + e], S.h[i], s0);
+    }
+    S.red[tid] = s0 + s1;
+    __syncthreads();
+    if (tid < E) {
+        double t = 0.0;
+        for (int q = 0; q < ng; ++q) t += S.red[q * EP + tid];
+        S.w[tid] -= t;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(CT, 1) k_lz_cluster(LzArgs a, int j) {
+    if (lz_skip(a.st)) return;  // uniform across the cluster (written before launch)
+    __shared__ LcShared S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int C = (int)cluster_ncta(), q = (int)cluster_rank();
+    const int R = a.nrow_grid;
+    const int rlo = q * R / C, rhi = (q + 1) * R / C;
+    const int e0 = rlo * a.M1;
+    const int E = (q == C - 1 ? a.ldp : rhi * a.M1) - e0;
+    const int EP = E > 0 ? (E + 31) & ~31 : 32;
+    const int ng = max(1, min(16, CT / EP));
+    // state that CTA 0 overwrites at the end, read before the first barrier
+    const double tn0 = a.st->tnorm;
+    const double bprev = j > 0 ? a.st->beta[j - 1] : 0.0;
+    // stage V[:, 0..j] over this CTA's entries (odd leading dimension: the four
+    // dot threads of a warp's different columns fall in different banks)
+    extern __shared__ double Vs[];
+    const int le = E | 1;
+    for (int t = tid; t < (j + 1) * E; t += CT) {
+        const int i = t / E, e = t - i * E;
+        Vs[(size_t)i * le + e] = a.V[(size_t)i * a.ldp + e0 + e];
+    }
+
+    // (a) w = sum over the pencil CTAs' partials, batches of 8 independent loads
+    {
+        const int g = tid / EP, e = tid % EP;
+        double acc = 0.0;
+        if (g < ng && e < E) {
+            const double *src = a.part + e0 + e;
+            const size_t stride = 2 * (size_t)a.ldp;
+            int b = g;
+            for (; b + 7 * ng < a.nparts; b += 8 * ng) {
+                double x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) x[u] = src[(size_t)(b + u * ng) * stride];
+                acc += ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+            }
+            for (; b < a.nparts; b += ng) acc += src[(size_t)b * stride];
+        }
+        S.red[tid] = acc;
+        __syncthreads();
+        if (tid < E) {
+            double t = 0.0;
+            for (int gg = 0; gg < ng; ++gg) t += S.red[gg * EP + tid];
+            S.w[tid] = t;
+        }
+        __syncthreads();
+    }
+    // (b) pass 1: h1 = V^T w, w -= V h1
+    cluster_dots(Vs, le, S, E, j, S.pd1);
+    cluster_sync();
+    for (int i = tid; i <= j; i += CT) S.h[i] = cluster_tree_sum(&S.pd1[i], C);
+    __syncthreads();
+    const double h1j = S.h[j];
+    if (q == 0)
+        for (int i = tid; i <= j; i += CT) a.st->h1[i] = S.h[i];
+    cluster_update(Vs, le, S, E, EP, ng, j);
+    // (c) pass 2: h2 = V^T w, w -= V h2; alpha_j = h1_j + h2_j
+    cluster_dots(Vs, le, S, E, j, S.pd2);
+    cluster_sync();  // also orders the reads of S.h above before it is overwritten
+    for (int i = tid; i <= j; i += CT) S.h[i] = cluster_tree_sum(&S.pd2[i], C);
+    __syncthreads();
+    const double alpha = h1j + S.h[j];
+    if (q == 0)
+        for (int i = tid; i <= j; i += CT) a.st->h2[i] = S.h[i];
+    cluster_update(Vs, le, S, E, EP, ng, j);
+    // (d) particle-number null space, per grid row (warp per row)
+    if (a.deflate) {
+        const int n = a.n_orb;
+        const int nr = rhi - rlo;
+        if (warp < nr) {
+            const int r = rlo + warp;
+            const double *wr = S.w + (size_t)warp * a.M1;
+            double sa = 0.0, sbe = 0.0;
+            for (int c = 1 + lane; c <= 2 * n; c += 32) {
+                if (c <= n) sa += wr[c]; else sbe += wr[c];
+            }
+            sa = warp_sum(sa);
+            sbe = warp_sum(sbe);
+            if (lane == 0) {
+                if (r == 0) {
+                    S.coef[warp][0] = sa / n;
+                    S.coef[warp][1] = sbe / n;
+                } else {
+                    // least squares on span{1_alpha - Na e0, 1_beta - Nb e0}
+                    const double w0 = wr[0];
+                    const double na = a.na, nb = a.nb;
+                    const double g11 = n + na * na, g22 = n + nb * nb, g12 = na * nb;
+                    const double r1 = sa - na * w0, r2 = sbe - nb * w0;
+                    const double det = g11 * g22 - g12 * g12;
+                    S.coef[warp][0] = (g22 * r1 - g12 * r2) / det;
+                    S.coef[warp][1] = (g11 * r2 - g12 * r1) / det;
+                }
+            }
+        }
+        __syncthreads();
+        for (int t = tid; t < nr * (2 * n + 1); t += CT) {
+            const int lr = t / (2 * n + 1), c = t % (2 * n + 1);
+            double *wr = S.w + (size_t)lr * a.M1;
+            if (c == 0) {
+                if (rlo + lr > 0) wr[0] += S.coef[lr][0] * a.na + S.coef[lr][1] * a.nb;
+            } else if (c <= n) {
+                wr[c] -= S.coef[lr][0];
+            } else {
+                wr[c] -= S.coef[lr][1];
+            }
+        }
+        __syncthreads();
+    }
+    // (e) beta_j = |w|, breakdown test, v_{j+1} = w / beta_j
+    {
+        double s2 = 0.0;
+        for (int e = tid; e < E; e += CT) s2 = fma(S.w[e], S.w[e], s2);
+        s2 = warp_sum(s2);
+        if (lane == 0) S.red[warp] = s2;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < CW; ++w) t += S.red[w];
+            S.pn[0] = t;
+        }
+    }
+    cluster_sync();
+    const double beta = sqrt(cluster_tree_sum(S.pn, C));
+    cluster_arrive();  // this CTA reads no peer memory after this point
+    double tn = fmax(tn0, fmax(fabs(alpha), beta));
+    if (j > 0) tn = fmax(tn, fabs(bprev));
+    const bool brk = beta <= 1e-14 * fmax(tn, 1e-300);
+    if (q == 0 && tid == 0) {
+        a.st->alpha[j] = alpha;
+        a.st->beta[j] = beta;
+        a.st->tnorm = tn;
+        if (brk) {
+            a.st->broke = 1;
+            a.st->jend = j + 1;
+        }
+    }
+    if (!brk) {
+        const double inv = 1.0 / beta;
+        double *vout = a.V + (size_t)(j + 1) * a.ldp + e0;
+        for (int e = tid; e < E; e += CT) vout[e] = S.w[e] * inv;
+    }
+    cluster_wait();  // no CTA exits while a peer may still read its shared memory
+}
+
 // Random start vector: component e is 2u-1 with u the 53-bit uniform of
 // SplitMix64 at counter e (state seed + (e+1) * golden gamma), zero padding.
 __device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t e) {
@@ -889,14 +1146,96 @@ __global__ void __launch_bounds__(1024) k_refine(double *y, const double *hy, co
 // =========================================================================
 namespace {
 
+// How a Lanczos step's vector work is launched.
+enum { LZ_SPLIT = 0, LZ_COOP = 1, LZ_CLUSTER = 2 };
+
 struct Run {
     lm_pencil *p;
     cudaStream_t s;
     LzArgs la;
     int m, k, sym, prec;
     int n_matvec, n_restart;
-    bool coop;  // one cooperative launch per Lanczos step
+    int lz_mode;   // LZ_*
+    int cluster;   // CTAs per cluster for LZ_CLUSTER
+    int cluster_emax;  // largest entry count of one cluster CTA
 };
+
+// Dynamic shared memory of k_lz_cluster for Lanczos step j: the V[:, 0..j]
+// slice with an odd leading dimension.
+size_t cluster_dyn_smem(int j1, int emax) { return (size_t)j1 * (emax | 1) * sizeof(double); }
+
+// Largest entry count and grid-row count of one CTA when R grid rows of M1
+// entries (ldp in all) are split over C CTAs the way k_lz_cluster splits them.
+void cluster_extent(int R, int M1, int ldp, int C, int &emax, int &rmax) {
+    emax = 0;
+    rmax = 0;
+    for (int q = 0; q < C; ++q) {
+        const int rlo = q * R / C, rhi = (q + 1) * R / C;
+        const int e = (q == C - 1 ? ldp : rhi * M1) - rlo * M1;
+        emax = std::max(emax, e);
+        rmax = std::max(rmax, rhi - rlo);
+    }
+}
+
+// Pick the Lanczos launch: one cluster of 16 (else 8) CTAs when the device can
+// place it and the split fits the kernel's shared arrays, else the cooperative
+// kernel, else four ordinary launches. IRLNQS_LANCZOS=cluster|coop|split
+// restricts the choice (for tests); a mode the device cannot run is skipped.
+void choose_lanczos(Run &R, lm_ctx *ctx) {
+    const char *env = getenv("IRLNQS_LANCZOS");
+    const bool any = !env || !*env;
+    R.lz_mode = LZ_SPLIT;
+    R.cluster = 0;
+    if (any || !strcmp(env, "cluster")) {
+        for (int C : {16, 8}) {
+            int emax = 0, rmax = 0;
+            cluster_extent(R.la.nrow_grid, R.la.M1, R.la.ldp, C, emax, rmax);
+            if (emax > CE || rmax > CROWS) continue;
+            const size_t dyn = cluster_dyn_smem(R.m, emax);
+            if (dyn + sizeof(LcShared) > (size_t)ctx->smem_optin) continue;
+            if (cudaFuncSetAttribute(k_lz_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dyn) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (C > 8 && cudaFuncSetAttribute(k_lz_cluster,
+                                              cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                              1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(C);
+            cfg.blockDim = dim3(CT);
+            cfg.dynamicSmemBytes = dyn;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, k_lz_cluster, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (nclusters >= 1) {
+                R.lz_mode = LZ_CLUSTER;
+                R.cluster = C;
+                R.cluster_emax = emax;
+                return;
+            }
+        }
+    }
+    if (any || !strcmp(env, "coop")) {
+        // the cooperative step needs all nh+1 CTAs resident at once
+        int dev_coop = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&dev_coop, cudaDevAttrCooperativeLaunch, ctx->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lz_step, LT, 0);
+        if (dev_coop && (int64_t)per_sm * ctx->sms >= R.la.nrow_grid) R.lz_mode = LZ_COOP;
+    }
+}
 
 int lanczos_step(Run &R, int j) {
     lm_pencil *p = R.p;
@@ -905,7 +1244,24 @@ int lanczos_step(Run &R, int j) {
     if (int rc = lm_launch_pencil(p, vj, R.sym, R.prec, 0, &p->st->broke, R.s)) return rc;
     const int g2 = R.la.nrow_grid;
     R.n_matvec++;
-    if (R.coop) {
+    if (R.lz_mode == LZ_CLUSTER) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = R.cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(R.cluster);
+        cfg.blockDim = dim3(CT);
+        cfg.dynamicSmemBytes = cluster_dyn_smem(j + 1, R.cluster_emax);
+        cfg.stream = R.s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_lz_cluster, R.la, j);
+        lm_note_launch(p->ctx);
+        return lm_cuda_check(p->ctx, e, "cluster lanczos step");
+    }
+    if (R.lz_mode == LZ_COOP) {
         void *args[] = {(void *)&R.la, (void *)&j};
         cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_lz_step, dim3(g2), dim3(LT),
                                                     args, 0, R.s);
@@ -1021,13 +1377,7 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
     R.la.st = p->st;
     R.la.bar = p->bar;
     R.la.flags = ctx->d_flags;
-    {
-        // the cooperative step needs all nh+1 CTAs resident at once
-        int dev_coop = 0, per_sm = 0;
-        cudaDeviceGetAttribute(&dev_coop, cudaDevAttrCooperativeLaunch, ctx->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lz_step, LT, 0);
-        R.coop = dev_coop && (int64_t)per_sm * ctx->sms >= R.la.nrow_grid;
-    }
+    choose_lanczos(R, ctx);
 
     // optional start vector to the device
     const double *v0_dev = nullptr;

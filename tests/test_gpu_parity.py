@@ -137,13 +137,17 @@ def test_build_parity_mc_rows_licl_shape(ctx, abi, arith):
     pen.free()
 
 
-@pytest.mark.parametrize("n,na,nb,nh", [(2, 1, 1, 2), (3, 3, 1, 4), (4, 0, 2, 3), (32, 1, 1, 4),
-                                        (5, 2, 3, 7)])
+@pytest.mark.parametrize("n,na,nb,nh,sigma", [(2, 1, 1, 2, 0.2), (3, 3, 1, 4, 0.2),
+                                              (4, 0, 2, 3, 0.2), (32, 1, 1, 4, 0.2),
+                                              (5, 2, 3, 7, 0.2), (6, 3, 3, 127, 0.02),
+                                              (6, 3, 3, 127, 0.5)])
 @ARITHS
-def test_build_parity_edge_shapes(ctx, abi, n, na, nb, nh, arith):
-    """Degenerate sectors: 4 determinants, a full spin shell, an empty spin, M = 64, odd P+1."""
+def test_build_parity_edge_shapes(ctx, abi, n, na, nb, nh, sigma, arith):
+    """Degenerate sectors: 4 determinants, a full spin shell, an empty spin, M = 64,
+    odd P+1; the largest hidden layer (Nh = 127), where prod_j (1 + e^{-2|z_j|})
+    reaches 2^127 for small theta and the cosh ratios span e^{+-70} for large theta."""
     h, eri = synth.integrals(n, 17)
-    th = synth.rbm_theta(n, nh, 17, sigma=0.2)
+    th = synth.rbm_theta(n, nh, 17, sigma=sigma)
     pen, pd = _build_both(ctx, abi, n, na, nb, nh, h, eri, th, arith=arith)
     _check_build(abi, pen, pd)
     pen.free()
@@ -300,6 +304,36 @@ def test_irl_mc_rows_half(ctx, abi):
     pen, ref, res, c, dth = _irl_case(ctx, abi, w, rows=rows, counts=cnt)
     assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
     assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-10)
+    pen.free()
+
+
+LZ_CASES = {
+    # exact 6-orbital sector, 25 grid rows of 13 entries
+    "tiny": (synth.Workload("tiny", 6, 3, 3, 24, m=20, k=1), None),
+    # 3 grid rows of 9 entries: fewer rows than cluster CTAs
+    "few_rows": (synth.Workload("few", 4, 2, 2, 2, seed=5, m=12, k=3), 0.2),
+    # LiCl-shaped, 57 grid rows of 29 entries on Monte Carlo rows
+    "mc_licl": (synth.Workload("mc", 14, 7, 7, 56, exact=False, n_samples=1500, m=20, k=1),
+                None),
+    # Nh + 1 = 128 grid rows (the largest hidden layer), 6-orbital sector
+    "wide_grid": (synth.Workload("wide", 6, 3, 3, 127, seed=3, m=24, k=4), 0.02),
+}
+
+
+@pytest.mark.parametrize("case", list(LZ_CASES))
+@pytest.mark.parametrize("mode", ["cluster", "coop", "split"])
+def test_irl_lanczos_launch_modes(ctx, abi, monkeypatch, mode, case):
+    """The three launch forms of a Lanczos step (one thread-block cluster, one
+    cooperative grid, four kernels) against the FP64 oracle."""
+    monkeypatch.setenv("IRLNQS_LANCZOS", mode)
+    w, sigma = LZ_CASES[case]
+    h, eri, th, rows, cnt = w.inputs()
+    if sigma is not None:
+        th = synth.rbm_theta(w.n_orb, w.n_hidden, w.seed, sigma=sigma)
+    pen, ref, res, c, dth = _irl_case(ctx, abi, w, theta=th, rows=rows, counts=cnt)
+    assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
+    assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-10)
+    assert _rel(dth, ref["dtheta"]) <= 1e-8
     pen.free()
 
 
