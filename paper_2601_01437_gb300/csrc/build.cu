@@ -613,10 +613,12 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     int4 *sIdx = reinterpret_cast<int4 *>(smb);                 // [K]
     int2 *sSs = reinterpret_cast<int2 *>(sIdx + BDF_K);          // [K] single indices
     RowLists *sL = reinterpret_cast<RowLists *>(sSs + BDF_K);   // 1
-    float2 *sA = reinterpret_cast<float2 *>(sL + 1);            // [NS][nh]  A_s[j]
-    float2 *sB = sA + NS * nh;                                  // [NS][nh]  B_s[j]
-    float2 *sV = sB + NS * nh;                                  // [NS]
-    float2 *sTd = sV + NS;                                      // [nh] t as df
+    const int ldA = nh | 1;  // odd row stride: the connections of a warp hit distinct banks
+    float2 *sA = reinterpret_cast<float2 *>(sL + 1);            // [NS][ldA]  A_s[j]
+    float2 *sB = sA + NS * ldA;                                 // [NS][ldA]  B_s[j]
+    float2 *sV = sB + NS * ldA;                                 // [NS]
+    float2 *sHs = sV + NS;                                      // [NS] singles' <x'|H|x>
+    float2 *sTd = sHs + NS;                                     // [nh] t as df
     float2 *sF = sTd + nh;                                      // [K][ldF]  tanh(z+d)
     float2 *sC = sF + BDF_K * A.ldF;                            // [K]
     float2 *sS = sC + BDF_K;                                    // [nslice][nh+1][ldS]
@@ -624,8 +626,9 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     float2 *sRed = sAcc + A.nslice * (nh + 1);                  // [BDF_THREADS/32]
     double *sT = reinterpret_cast<double *>(sRed + BDF_THREADS / 32);  // [nh] t
     double *sZ = sT + nh;                                              // [nh] z
-    double *sCs = sZ + nh;                                             // [M] sum_j sigma_j W_jp
-    float2 *sGd = reinterpret_cast<float2 *>(sCs + M);                 // [nh] g as df
+    double *sL1 = sZ + nh;                                             // [nh] ln(1 + g_j)
+    double *sCs = sL1 + nh;                                            // [2][M] sum_j sigma_j W_jp
+    float2 *sGd = reinterpret_cast<float2 *>(sCs + 2 * M);             // [nh] g as df
     float *sSig = reinterpret_cast<float *>(sGd + nh);                 // [nh] sigma
     int *sVe = reinterpret_cast<int *>(sSig + nh);                     // [NS] exponent of V_s
     __shared__ double sDiag, sLn, sGinv;
@@ -656,30 +659,62 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             __syncthreads();
             continue;
         }
-        // per hidden unit: z, tanh z, sigma, g (FP64 -> df)
+        // per hidden unit (FP64): z_j from the occupied lists; with
+        // em = expm1(-2|z|): g = e^{-2|z|} = 1 + em, tanh z = sign(z) (-em) / (2 + em)
+        // (no cancellation for small |z|), l1 = log1p(g) = ln(1 + g)
         for (int j = tid; j < nh; j += BDF_THREADS) {
-            double z = A.theta[(j + 1) * M1 - 1];
-            for (int p = 0; p < M; ++p)
-                if ((x >> p) & 1ull) z += A.theta[(j + 1) * M1 + p];
+            const double *wj = A.theta + (size_t)(j + 1) * M1;
+            double za = wj[-1], zb = 0.0;
+            for (int t = 0; t < A.S.na; ++t) za += wj[sL->oa[t]];
+            for (int t = 0; t < A.S.nb; ++t) zb += wj[sL->ob[t]];
+            const double z = za + zb;
             sZ[j] = z;
-            const double t = tanh(z);
+            const double em = expm1(-2.0 * fabs(z));
+            const double g = 1.0 + em;
+            const double t = copysign(-em / (2.0 + em), z);
             sT[j] = t;
+            sL1[j] = log1p(g);
             const df td = df_from_double(t);
             sTd[j] = make_float2(td.h, td.l);
             sSig[j] = z < 0.0 ? 1.f : -1.f;
-            const df g = df_from_double(exp(-2.0 * fabs(z)));
-            sGd[j] = make_float2(g.h, g.l);
+            const df gd = df_from_double(g);
+            sGd[j] = make_float2(gd.h, gd.l);
+        }
+        {
+            // <x'|H|x> of every single excitation (without sign), one warp per
+            // single: lanes over the occupied orbitals, then a fixed-order
+            // butterfly; warps that hold no hidden unit above do this
+            const int w0 = (nh + 31) >> 5, warp = tid >> 5;
+            for (int sgl = warp - w0; warp >= w0 && sgl < NS; sgl += BDF_THREADS / 32 - w0) {
+                int i, a;
+                single_of(A.S, *sL, sgl, i, a);
+                const int n = A.S.n, sp = i >= n;
+                const int ip = i - sp * n, ap = a - sp * n;
+                df v = df_make(0.f, 0.f);
+                for (int t = lane; t < A.S.na + A.S.nb; t += 32) {
+                    const bool ta = t < A.S.na;
+                    const int kp = ta ? sL->oa[t] : sL->ob[t - A.S.na] - n;
+                    const float2 *gk = gd + ((size_t)ap * n + ip) * n * n;
+                    v = df_add(v, ldg_df(gk + (size_t)kp * n + kp));
+                    if ((ta ? 0 : 1) == sp)
+                        v = df_sub(v, ldg_df(gd + (((size_t)ap * n + kp) * n + kp) * n + ip));
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    v = df_add(v, df_make(__shfl_xor_sync(0xffffffffu, v.h, off),
+                                          __shfl_xor_sync(0xffffffffu, v.l, off)));
+                if (lane == 0) st_df(sHs + sgl, df_add(ldg_df(hd + ap * n + ip), v));
+            }
         }
         for (int e = tid; e < nsl * (nh + 1) * A.ldS; e += BDF_THREADS) sS[e] = make_float2(0.f, 0.f);
         __syncthreads();
         if (tid < 32) {
-            // ln psi = a.x + sum_j ln(2 cosh z_j); prod_j (1 + g_j) with g_j = e^{-2|z_j|}
+            // ln psi = a.x + sum_j (|z_j| + ln(1 + g_j)) (the ln 2 of each cosh cancels
+            // in every ratio and is dropped); prod_j (1 + g_j) = exp(sum_j l1_j)
             double lp = 0.0, lg = 0.0;
             for (int j = tid; j < nh; j += 32) {
-                const double az = fabs(sZ[j]);
-                const double g = exp(-2.0 * az);
-                lp += az + log1p(g);
-                lg += log1p(g);
+                lp += fabs(sZ[j]) + sL1[j];
+                lg += sL1[j];
             }
             for (int p = tid; p < M; p += 32)
                 if ((x >> p) & 1ull) lp += A.theta[p];
@@ -697,14 +732,22 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
         } else if (tid < 64) {
             const double d = diag_value_warp(A.S, *sL);
             if (tid == 32) sDiag = d + A.e_core;
-        } else if (tid - 64 < M) {
-            const int p = tid - 64;
-            double cs = 0.0;
-            for (int j = 0; j < nh; ++j) {
-                const double w = A.theta[(j + 1) * M1 + p];
-                cs += sZ[j] < 0.0 ? w : -w;
+        } else if (tid - 64 < 2 * M) {
+            // sum_j sigma_j W_jp in two interleaved halves (combined where used)
+            const int p = (tid - 64) % M, half = (tid - 64) / M;
+            double c0 = 0.0, c1 = 0.0;
+            int j = half;
+            for (; j + 2 < nh; j += 4) {
+                const double w0 = A.theta[(size_t)(j + 1) * M1 + p];
+                const double w1 = A.theta[(size_t)(j + 3) * M1 + p];
+                c0 += sZ[j] < 0.0 ? w0 : -w0;
+                c1 += sZ[j + 2] < 0.0 ? w1 : -w1;
             }
-            sCs[p] = cs;
+            if (j < nh) {
+                const double w0 = A.theta[(size_t)(j + 1) * M1 + p];
+                c0 += sZ[j] < 0.0 ? w0 : -w0;
+            }
+            sCs[half * M + p] = c0 + c1;
         }
         __syncthreads();
         // per single excitation: V_s (FP64 exp), B_s[j], A_s[j] (df)
@@ -715,13 +758,14 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             const bool pos = sSig[j] > 0.f;
             const df b = df_mul(ldg_df((pos ? e2 : e2i) + j * M + a),
                                 ldg_df((pos ? e2i : e2) + j * M + i));
-            st_df(sB + s * nh + j, b);
-            st_df(sA + s * nh + j, df_mul(ld_df(sGd + j), b));
+            st_df(sB + s * ldA + j, b);
+            st_df(sA + s * ldA + j, df_mul(ld_df(sGd + j), b));
         }
         for (int s = tid; s < NS; s += BDF_THREADS) {
             int i, a;
             single_of(A.S, *sL, s, i, a);
-            const double ex = (A.theta[a] - A.theta[i]) - (sCs[a] - sCs[i]);
+            const double csa = sCs[a] + sCs[M + a], csi = sCs[i] + sCs[M + i];
+            const double ex = (A.theta[a] - A.theta[i]) - (csa - csi);
             int ve = 0;  // V_s = mantissa * 2^ve, mantissa in [0.5, 1)
             const df v = df_from_double(frexp(exp(ex), &ve));
             sV[s] = make_float2(v.h, v.l);
@@ -739,21 +783,36 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             int s1 = 0, s2 = -1;
             df rp = df_make(1.f, 0.f);
             int re = 0;
+            // the connection's <x'|H|x> (lane 0): singles from the row's table,
+            // doubles' integrals fetched here so their latency hides behind the
+            // hidden-unit loop
+            Exc e;
+            int sg = 1;
+            df hv = df_make(0.f, 0.f);
+            if (active && sub == 0) {
+                e = decode_exc(A.S, L, k);
+                (void)apply_exc(x, e, sg);
+                if (e.j < 0) hv = ld_df(sHs + k);
+                else hv = exc_value_df(A.S, L, e, hd, gd);
+            }
             if (active) {
                 singles_of_conn(A.S, k, s1, s2);
                 float2 *Frow = sF + kk * A.ldF;
-                const float2 *a1 = sA + s1 * nh;
-                const float2 *b2 = sB + (s2 >= 0 ? s2 : 0) * nh;
+                const float2 *a1 = sA + s1 * ldA;
+                const float2 *b2 = sB + (s2 >= 0 ? s2 : 0) * ldA;
+                // Z_j = A_s1[j] (B_s2[j]); u = 1 / (1 + Z); tanh(z + d) = sigma (1 - 2u);
+                // the running product of (1 + Z_j) stays >= 1 and is rescaled past 2^60
+#pragma unroll 2
                 for (int j = sub; j < nh; j += BDF_TPC) {
                     df z = ld_df(a1 + j);
                     if (s2 >= 0) z = df_mul(z, ld_df(b2 + j));
                     const df zp = df_add1(z, 1.f);
-                    const df zm = df_add1(z, -1.f);
-                    df t = df_div(zm, zp);
+                    const df u = df_rcp_ge1(zp);
+                    df t = df_one_minus(df_make(2.f * u.h, 2.f * u.l));
                     if (sSig[j] < 0.f) t = df_neg(t);
                     st_df(Frow + j, t);  // tanh(z + d)
                     rp = df_mul(rp, zp);
-                    df_renorm(rp, re);
+                    if (rp.h > 0x1p60f) df_renorm(rp, re);
                 }
             }
             // combine the partial products of the BDF_TPC lanes of a connection
@@ -768,10 +827,6 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 df_renorm(rp, re);
             }
             if (active && sub == 0) {
-                const Exc e = decode_exc(A.S, L, k);
-                int sg;
-                (void)apply_exc(x, e, sg);
-                df hv = exc_value_df(A.S, L, e, hd, gd);
                 if (sg < 0) hv = df_neg(hv);
                 df f = df_mul(hv, ld_df(sV + s1));
                 int fe = re + sGe + sVe[s1];
@@ -794,12 +849,23 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                     if (sc_r > 0) f = df_mul(f, ld_df(sF + q * A.ldF + sc_r - 1));
                     const int4 ix = sIdx[q];
                     df_acc(accA, f);
-                    df t;
-                    t = ld_df(Srow + ix.x); df_acc(t, f); st_df(Srow + ix.x, t);
-                    t = ld_df(Srow + ix.z); df_acc(t, f); st_df(Srow + ix.z, t);
+                    // the orbitals a connection moves are distinct: load all, add, store
+                    df t0 = ld_df(Srow + ix.x), t1 = ld_df(Srow + ix.z);
                     if (ix.y >= 0) {
-                        t = ld_df(Srow + ix.y); df_acc(t, f); st_df(Srow + ix.y, t);
-                        t = ld_df(Srow + ix.w); df_acc(t, f); st_df(Srow + ix.w, t);
+                        df t2 = ld_df(Srow + ix.y), t3 = ld_df(Srow + ix.w);
+                        df_acc(t0, f);
+                        df_acc(t1, f);
+                        df_acc(t2, f);
+                        df_acc(t3, f);
+                        st_df(Srow + ix.x, t0);
+                        st_df(Srow + ix.z, t1);
+                        st_df(Srow + ix.y, t2);
+                        st_df(Srow + ix.w, t3);
+                    } else {
+                        df_acc(t0, f);
+                        df_acc(t1, f);
+                        st_df(Srow + ix.x, t0);
+                        st_df(Srow + ix.z, t1);
                     }
                 }
             }
@@ -1129,11 +1195,11 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         B.G = p->G;
         B.flags = ctx->d_flags;
         const size_t nh_ = p->nh, M_ = p->M;
-        const size_t f2 = 2 * (size_t)B.ns * nh_ + B.ns + nh_ + (size_t)BDF_K * B.ldF + BDF_K +
+        const size_t f2 = 2 * (size_t)B.ns * (nh_ | 1) + 2 * B.ns + nh_ + (size_t)BDF_K * B.ldF + BDF_K +
                           (size_t)B.nslice * (nh_ + 1) * B.ldS + (size_t)B.nslice * (nh_ + 1) +
                           BDF_THREADS / 32;
         const size_t dsm = BDF_K * (sizeof(int4) + sizeof(int2)) + sizeof(RowLists) +
-                           f2 * sizeof(float2) + (2 * nh_ + M_) * sizeof(double) +
+                           f2 * sizeof(float2) + (3 * nh_ + 2 * M_) * sizeof(double) +
                            nh_ * (sizeof(float2) + sizeof(float)) + B.ns * sizeof(int) + 64;
         if (dsm > (size_t)ctx->smem_optin)
             return lm_fail(ctx, LM_ERR_SIZE, "df64 build kernel needs %zu B shared memory", dsm);

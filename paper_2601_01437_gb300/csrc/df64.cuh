@@ -83,5 +83,27 @@ __device__ __forceinline__ df df_div(df a, df b) {
 // 1 / b
 __device__ __forceinline__ df df_rcp(df b) { return df_div(df_make(1.0f, 0.0f), b); }
 
+// 1 / b for b.h >= 1: the hardware's approximate FP32 reciprocal, one FP32
+// Newton step (relative error ~2^-24), then the double-float correction
+// q = r0 + r0 (1 - b r0) with the remainder 1 - b r0 formed exactly, which
+// squares the FP32 error (~2^-47 relative).
+__device__ __forceinline__ df df_rcp_ge1(df b) {
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(b.h));
+    r0 = __fmaf_rn(r0, __fmaf_rn(-b.h, r0, 1.0f), r0);
+    const float p = __fmul_rn(b.h, r0);
+    const float pe = __fmaf_rn(b.h, r0, -p);  // b.h r0 = p + pe exactly
+    float r = __fsub_rn(1.0f, p);             // exact: p is within 2^-22 of 1
+    r = __fsub_rn(r, pe);
+    r = __fmaf_rn(-b.l, r0, r);
+    return df_fts(r0, __fmul_rn(r, r0));
+}
+
+// 1 - a for 0 <= a <= 2 (TwoSum of 1 and -a.h, then the tail)
+__device__ __forceinline__ df df_one_minus(df a) {
+    const df s = df_ts(1.0f, -a.h);
+    return df_ts(s.h, __fsub_rn(s.l, a.l));
+}
+
 // Multiply by 2^e exactly (as long as the result stays in the FP32 normal range)
 __device__ __forceinline__ df df_ldexp(df a, int e) { return df_make(ldexpf(a.h, e), ldexpf(a.l, e)); }

@@ -480,7 +480,6 @@ constexpr int CT = 512;   // threads per cluster CTA
 constexpr int CE = 384;   // entries per CTA: P+1 <= 2048 gives <= 2048/8 + 65 + 31
 constexpr int CROWS = 16; // grid rows per CTA: Nh + 1 <= 128 over >= 8 CTAs
 constexpr int CW = CT / 32;
-constexpr int CNI = (LM_MAXKRYLOV + 1 + CW - 1) / CW;  // dots per warp
 
 __device__ __forceinline__ void cluster_arrive() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
