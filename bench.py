@@ -266,8 +266,15 @@ def run_gpu(args, rank, world, local):
                           "unit": "GB/s", "frac": ach / hbm, "traffic": None,
                           "avg_ms": d * 1e3, "launches": int(st.pencil_count),
                           "total_ms": st.pencil_ms, "peak_source": f"{hbm_src} hbm_gbs"}
+    # the remaining step kernels (live event timings, no roofline: latency bound)
+    for key, name, ms, cnt in (("lanczos", "k_lz_cluster", st.lanczos_ms, st.lanczos_count),
+                               ("prep", "k_weights..k_centre", st.prep_ms, st.prep_count),
+                               ("tri", "k_tri", st.tri_ms, st.tri_count)):
+        if cnt:
+            kern[key] = {"kernel": name, "avg_ms": ms / cnt, "launches": int(cnt),
+                         "total_ms": ms}
     if kern:
-        dom = max(kern, key=lambda k: kern[k]["total_ms"])
+        dom = max((k for k in kern if "frac" in kern[k]), key=lambda k: kern[k]["total_ms"])
         out["roofline"] = {k: v for k, v in kern[dom].items()
                            if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
         out["roofline"]["kernel"] = kern[dom]["kernel"]

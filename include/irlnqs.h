@@ -257,11 +257,19 @@ typedef struct {
     double pencil_ms;      /* summed device time of the pencil kernel launches    */
     int64_t pencil_count;
     int64_t pencil_rows;   /* rows streamed by those pencil launches               */
+    double lanczos_ms;     /* Lanczos step vector kernels (one interval per step)  */
+    int64_t lanczos_count;
+    double prep_ms;        /* weights, statistics and centring after a build       */
+    int64_t prep_count;
+    double tri_ms;         /* tridiagonal eigen-solve / shift kernel (per cycle)   */
+    int64_t tri_count;
 } lm_stats;
 
-/* Reset the counters; profile = 1 also brackets every row-build and pencil
- * launch with CUDA events (recorded on the launch stream) until the next
- * reset. lm_stats_get synchronises the device before reading the events. */
+/* Reset the counters; profile = 1 also brackets every row-build, pencil,
+ * Lanczos-step, preparation and tridiagonal launch (or launch sequence) with
+ * CUDA events recorded on the launch stream, until the next reset (at most
+ * 2048 intervals per class are timed). lm_stats_get synchronises the device
+ * before reading the events. */
 int lm_stats_reset(lm_ctx *ctx, int profile);
 int lm_stats_get(lm_ctx *ctx, lm_stats *out);
 

@@ -53,7 +53,9 @@ class irl_result(ctypes.Structure):
 
 class lm_stats(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("build_ms", c_double), ("build_count", c_int64),
-                ("pencil_ms", c_double), ("pencil_count", c_int64), ("pencil_rows", c_int64)]
+                ("pencil_ms", c_double), ("pencil_count", c_int64), ("pencil_rows", c_int64),
+                ("lanczos_ms", c_double), ("lanczos_count", c_int64), ("prep_ms", c_double),
+                ("prep_count", c_int64), ("tri_ms", c_double), ("tri_count", c_int64)]
 
 
 _lib = None

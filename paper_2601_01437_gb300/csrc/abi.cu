@@ -134,7 +134,7 @@ extern "C" int lm_destroy(lm_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaFree(ctx->d_flags);
     if (ctx->ev_ready)
-        for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < LM_PROF_CLASSES; ++c)
             for (int i = 0; i < LM_PROF_EVENTS; ++i)
                 for (int k = 0; k < 2; ++k) cudaEventDestroy(ctx->ev[c][i][k]);
     delete ctx;
@@ -400,7 +400,7 @@ extern "C" int lm_stats_reset(lm_ctx *ctx, int profile) {
     if (!ctx) return LM_ERR_ARG;
     cudaSetDevice(ctx->device);
     if (profile && !ctx->ev_ready) {
-        for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < LM_PROF_CLASSES; ++c)
             for (int i = 0; i < LM_PROF_EVENTS; ++i)
                 for (int k = 0; k < 2; ++k)
                     if (cudaEventCreate(&ctx->ev[c][i][k]) != cudaSuccess)
@@ -410,7 +410,7 @@ extern "C" int lm_stats_reset(lm_ctx *ctx, int profile) {
     ctx->profile = profile;
     ctx->launches = 0;
     ctx->pencil_rows = 0;
-    for (int c = 0; c < 2; ++c) ctx->ev_used[c] = ctx->ev_count[c] = 0;
+    for (int c = 0; c < LM_PROF_CLASSES; ++c) ctx->ev_used[c] = ctx->ev_count[c] = 0;
     return LM_OK;
 }
 
@@ -418,8 +418,8 @@ extern "C" int lm_stats_get(lm_ctx *ctx, lm_stats *out) {
     if (!ctx || !out) return LM_ERR_ARG;
     cudaSetDevice(ctx->device);
     if (int rc = lm_cuda_check(ctx, cudaDeviceSynchronize(), "lm_stats_get")) return rc;
-    double ms[2] = {0.0, 0.0};
-    for (int c = 0; c < 2; ++c)
+    double ms[LM_PROF_CLASSES] = {0.0};
+    for (int c = 0; c < LM_PROF_CLASSES; ++c)
         for (int64_t i = 0; i < ctx->ev_used[c]; ++i) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, ctx->ev[c][i][0], ctx->ev[c][i][1]) == cudaSuccess) ms[c] += t;
@@ -430,5 +430,12 @@ extern "C" int lm_stats_get(lm_ctx *ctx, lm_stats *out) {
     out->pencil_ms = ms[PROF_PENCIL];
     out->pencil_count = ctx->profile ? ctx->ev_used[PROF_PENCIL] : ctx->ev_count[PROF_PENCIL];
     out->pencil_rows = ctx->pencil_rows;
+    auto count = [&](int c) { return ctx->profile ? ctx->ev_used[c] : ctx->ev_count[c]; };
+    out->lanczos_ms = ms[PROF_LANCZOS];
+    out->lanczos_count = count(PROF_LANCZOS);
+    out->prep_ms = ms[PROF_PREP];
+    out->prep_count = count(PROF_PREP);
+    out->tri_ms = ms[PROF_TRI];
+    out->tri_count = count(PROF_TRI);
     return LM_OK;
 }

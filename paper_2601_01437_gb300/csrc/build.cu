@@ -980,27 +980,59 @@ __global__ void k_stats_partial(const double *O, const double *eloc, const doubl
     }
 }
 
-// stats[0] = sum w, stats[1] = E, stats[8 + c] = <O_c>
-__global__ void k_stats_final(const double *part, int nparts, int ldp, double *stats) {
-    __shared__ double sw;
-    if (threadIdx.x == 0) {
+// stats[0] = sum w, stats[1] = E, stats[8 + c] = <O_c>. CTA b covers columns
+// [32 b, 32 b + 32): warp q sums the partials q, q + 8, ... of its lane's
+// column, then the 8 warp sums are added in warp order. Every CTA forms sum w
+// itself (the same fixed order), so no second pass is needed.
+__global__ void __launch_bounds__(256) k_stats_final(const double *part, int nparts, int ldp,
+                                                      double *stats) {
+    __shared__ double red[8][33];
+    __shared__ double s_sw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t ld2 = ldp + 2;
+    {
         double a = 0.0, b = 0.0;
-        for (int p = 0; p < nparts; ++p) {
-            a += part[(int64_t)p * (ldp + 2) + ldp];
-            b += part[(int64_t)p * (ldp + 2) + ldp + 1];
+        for (int q = threadIdx.x; q < nparts; q += 256) {
+            a += part[q * ld2 + ldp];
+            b += part[q * ld2 + ldp + 1];
         }
-        sw = a;
-        if (blockIdx.x == 0) {
-            stats[0] = a;
-            stats[1] = b / a;
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (lane == 0) {
+            red[warp][0] = a;
+            red[warp][1] = b;
         }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double ta = 0.0, tb = 0.0;
+            for (int w = 0; w < 8; ++w) {
+                ta += red[w][0];
+                tb += red[w][1];
+            }
+            s_sw = ta;
+            if (blockIdx.x == 0) {
+                stats[0] = ta;
+                stats[1] = tb / ta;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * 32 + lane;
+    double a0 = 0.0, a1 = 0.0;
     if (c < ldp) {
-        double a = 0.0;
-        for (int p = 0; p < nparts; ++p) a += part[(int64_t)p * (ldp + 2) + c];
-        stats[8 + c] = a / sw;
+        int q = warp;
+        for (; q + 8 < nparts; q += 16) {
+            a0 += part[q * ld2 + c];
+            a1 += part[(q + 8) * ld2 + c];
+        }
+        if (q < nparts) a0 += part[q * ld2 + c];
+    }
+    red[warp][lane] = a0 + a1;
+    __syncthreads();
+    if (warp == 0 && c < ldp) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w][lane];
+        stats[8 + c] = t / s_sw;
     }
 }
 
@@ -1014,7 +1046,7 @@ __device__ __forceinline__ __nv_bfloat16 to_low<__nv_bfloat16>(double x) {
 }
 template <>
 __device__ __forceinline__ float2 to_low<float2>(double x) {
-    const df d = df_from_double(x);
+    const df d = df_split_bits(x);  // integer split: the centring kernel is FP64-pipe bound
     return make_float2(d.h, d.l);
 }
 
@@ -1221,6 +1253,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     const int nmax = std::max(1, std::min(ctx->sms, (int)((p->n_rows + 255) / 256)));
     double *maxpart = p->part;  // reuse the partials buffer (nmax doubles first)
     double *given = p->given_weights ? p->wt : nullptr;
+    lm_prof_begin(ctx, PROF_PREP, s);
     if (!given) {
         k_lnpsi_max_partial<<<nmax, 256, 0, s>>>(p->lnpsi, p->n_rows, maxpart);
         lm_note_launch(ctx);
@@ -1234,7 +1267,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     k_stats_partial<<<nst, 256, 0, s>>>(p->O, p->eloc, p->wt, p->n_rows, p->ldp, spart);
     lm_note_launch(ctx);
     if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_stats_partial")) return rc;
-    k_stats_final<<<(p->ldp + 255) / 256, 256, 0, s>>>(spart, nst, p->ldp, p->stats);
+    k_stats_final<<<(p->ldp + 31) / 32, 256, 0, s>>>(spart, nst, p->ldp, p->stats);
     lm_note_launch(ctx);
     if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_stats_final")) return rc;
     int cgrid = (int)std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * 16);
@@ -1254,6 +1287,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         k_centre<double><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
                                                p->ldp, p->P1, p->e_core, (double *)nullptr,
                                                (double *)nullptr, p->wlo);
+    lm_prof_end(ctx, PROF_PREP, s);
     lm_note_launch(ctx);
     return lm_cuda_check(ctx, cudaGetLastError(), "k_centre");
 }

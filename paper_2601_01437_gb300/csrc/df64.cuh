@@ -83,6 +83,37 @@ __device__ __forceinline__ df df_div(df a, df b) {
 // 1 / b
 __device__ __forceinline__ df df_rcp(df b) { return df_div(df_make(1.0f, 0.0f), b); }
 
+// a * b + c (TwoProduct of the heads, TwoSum with c's head, tails summed)
+__device__ __forceinline__ df df_fma(df a, df b, df c) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    const df s = df_ts(p, c.h);
+    return df_fts(s.h, __fadd_rn(s.l, __fadd_rn(e, c.l)));
+}
+
+// Double-float split of an FP64 value by integer operations (no FP64
+// instruction on the common path): the head is the value rounded to 24
+// significant bits (the carry of the rounding increment runs into the
+// exponent field), the tail is the remaining 29 fraction bits minus the
+// rounding increment, converted once and scaled by 2^(e - 52). Exact head,
+// tail within 2^-24 of itself: |x - h - l| <= 2^-48 |x|. Values outside
+// [2^-70, 2^100] (zero included) take the FP64 route.
+__device__ __forceinline__ df df_split_bits(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+    const int ex = (int)((hi >> 20) & 0x7ffu);
+    if (ex < 1023 - 70 || ex > 1023 + 100) return df_from_double(x);
+    const unsigned sign = hi & 0x80000000u;
+    const unsigned up = (lo >> 28) & 1u;  // first dropped bit: round the head up
+    const unsigned hb = (((unsigned)(ex - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)) + up;
+    const int rt = (int)(lo & 0x1fffffffu) - (int)(up << 29);  // tail in units of 2^(ex - 1075)
+    const float scale = __uint_as_float((unsigned)(ex - 948) << 23);  // 2^(ex - 1075)
+    const float l = __int2float_rn(rt) * scale;
+    return df_make(__uint_as_float(sign | hb), sign ? -l : l);
+}
+
 // 1 / b for b.h >= 1: the hardware's approximate FP32 reciprocal, one FP32
 // Newton step (relative error ~2^-24), then the double-float correction
 // q = r0 + r0 (1 - b r0) with the remainder 1 - b r0 formed exactly, which
@@ -97,6 +128,18 @@ __device__ __forceinline__ df df_rcp_ge1(df b) {
     r = __fsub_rn(r, pe);
     r = __fmaf_rn(-b.l, r0, r);
     return df_fts(r0, __fmul_rn(r, r0));
+}
+
+// 1 / sqrt(s) for s > 0: the approximate FP32 reciprocal square root y0, then
+// one Newton step y0 + y0 (1 - s y0^2) / 2 with s y0^2 formed in double-float
+// (y0^2 exactly by TwoProduct), which squares y0's error (~2^-46 relative).
+__device__ __forceinline__ df df_rsqrt(df s) {
+    float y0;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(s.h));
+    const float q = __fmul_rn(y0, y0);
+    const df t = df_mul(s, df_make(q, __fmaf_rn(y0, y0, -q)));  // s y0^2, close to 1
+    const float r = __fsub_rn(__fsub_rn(1.0f, t.h), t.l);       // 1 - t.h is exact
+    return df_fts(y0, __fmul_rn(__fmul_rn(0.5f, y0), r));
 }
 
 // 1 - a for 0 <= a <= 2 (TwoSum of 1 and -a.h, then the tail)

@@ -104,7 +104,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // ---------------------------------------------------------------------------
 // Handles
 // ---------------------------------------------------------------------------
-#define LM_PROF_EVENTS 4096
+#define LM_PROF_EVENTS 2048
+#define LM_PROF_CLASSES 5
 
 struct lm_ctx {
     int device;
@@ -115,14 +116,14 @@ struct lm_ctx {
     // counters
     int64_t launches;
     int profile;
-    cudaEvent_t ev[2][LM_PROF_EVENTS][2];  // [class][pair][start/end]
+    cudaEvent_t ev[LM_PROF_CLASSES][LM_PROF_EVENTS][2];  // [class][pair][start/end]
     int ev_ready;
-    int64_t ev_used[2];
-    int64_t ev_count[2];
+    int64_t ev_used[LM_PROF_CLASSES];
+    int64_t ev_count[LM_PROF_CLASSES];
     int64_t pencil_rows;
 };
 
-enum { PROF_BUILD = 0, PROF_PENCIL = 1 };
+enum { PROF_BUILD = 0, PROF_PENCIL = 1, PROF_LANCZOS = 2, PROF_PREP = 3, PROF_TRI = 4 };
 
 inline void lm_note_launch(lm_ctx *ctx, int n = 1) { ctx->launches += n; }
 // Event pair around one launch of a profiled kernel class (no-op unless profiling).
@@ -203,9 +204,10 @@ int lm_launch_connections(lm_ctx *ctx, int n, int na, int nb, const double *h,
 
 // pencil.cu
 // partial products of the pencil over row blocks; y_H into part[b][0..ldp),
-// y_S into part[b][ldp..2ldp)
+// y_S into part[b][ldp..2ldp); FP64 values, or double-float pairs in the same
+// 8-byte slots when out_df is set
 int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_s,
-                     const int *skip, cudaStream_t s);
+                     const int *skip, cudaStream_t s, int out_df = 0);
 int lm_launch_reduce_partials(lm_pencil *p, double *yH, double *yS, cudaStream_t s);
 int lm_pencil_grid(lm_pencil *p);
 

@@ -27,6 +27,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "df64.cuh"
 #include "internal.cuh"
 
 namespace {
@@ -46,6 +47,9 @@ struct LzArgs {
     IrlState *st;
     unsigned *bar;      // [0] arrival count, [1] generation (cooperative kernel)
     int *flags;
+    // particle-number projection constants as double-float pairs (cluster
+    // kernel): 1/n and the inverse Gram matrix [[g22, -g12], [-g12, g11]] / det
+    float2 inv_n, gi11, gi12, gi22;
 };
 
 __device__ __forceinline__ void cta_range(const LzArgs &a, int &e0, int &e1) {
@@ -476,6 +480,13 @@ __global__ void __launch_bounds__(LT) k_lz_step(LzArgs a, int j) {
 // |w|^2) are exchanged through distributed shared memory between hardware
 // cluster barriers, and every CTA sums the C partials with the same fixed
 // tree, so all CTAs hold bit-identical dots and beta. No CTA spins on memory.
+//
+// The vector arithmetic runs in double-float on the FP32 pipes (GB300 issues
+// one FP64 warp instruction per ~16 cycles per SM, which made the FP64 form
+// of this latency-bound step slow): the pencil writes its partials as
+// double-float pairs, the V slice is split into pairs by integer operations,
+// and FP64 remains only for the stored basis vector and the scalars (alpha,
+// beta, its square root and reciprocal, the projection coefficients).
 constexpr int CT = 512;   // threads per cluster CTA
 constexpr int CE = 384;   // entries per CTA: P+1 <= 2048 gives <= 2048/8 + 65 + 31
 constexpr int CROWS = 16; // grid rows per CTA: Nh + 1 <= 128 over >= 8 CTAs
@@ -502,77 +513,86 @@ __device__ __forceinline__ uint32_t cluster_ncta() {
     return r;
 }
 // Generic address of the same shared variable in cluster CTA `rank`.
-__device__ __forceinline__ const double *peer_ptr(const double *local, uint32_t rank) {
+__device__ __forceinline__ const float2 *peer_ptr(const float2 *local, uint32_t rank) {
     uint64_t r;
     asm volatile("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"(local), "r"(rank));
-    return reinterpret_cast<const double *>(r);
+    return reinterpret_cast<const float2 *>(r);
+}
+__device__ __forceinline__ df ldf(const float2 *p) {
+    const float2 v = *p;
+    return df_make(v.x, v.y);
+}
+__device__ __forceinline__ void stf(float2 *p, df a) { *p = make_float2(a.h, a.l); }
+__device__ __forceinline__ df shfl_df(df a, int off) {
+    return df_make(__shfl_xor_sync(0xffffffffu, a.h, off), __shfl_xor_sync(0xffffffffu, a.l, off));
 }
 
 struct LcShared {
-    double w[CE];  // (the V slice follows in dynamic shared memory)
-    double pd1[LM_MAXKRYLOV + 1];  // this CTA's pass-1 partial dots (read by peers)
-    double pd2[LM_MAXKRYLOV + 1];  // pass-2 partial dots (read by peers)
-    double pn[1];                  // partial |w|^2 (read by peers)
-    double h[LM_MAXKRYLOV + 1];    // reduced dots
-    double red[CT];
-    double coef[CROWS][2];
+    float2 w[CE];                  // (the V slice follows in dynamic shared memory)
+    float2 pd1[LM_MAXKRYLOV + 1];  // this CTA's pass-1 partial dots (read by peers)
+    float2 pd2[LM_MAXKRYLOV + 1];  // pass-2 partial dots (read by peers)
+    float2 pn[1];                  // partial |w|^2 (read by peers)
+    float2 h[LM_MAXKRYLOV + 1];    // reduced dots
+    float2 h1s[LM_MAXKRYLOV + 1];  // reduced pass-1 dots kept for the state (CTA 0)
+    float2 red[CT];
+    float2 coef[CROWS][2];
 };
 
 // sum over the C <= 16 cluster CTAs of x[rank] with one fixed pairwise tree
-__device__ __forceinline__ double cluster_tree_sum(const double *local, int C) {
-    double x[16];
+__device__ __forceinline__ df cluster_tree_sum(const float2 *local, int C) {
+    df x[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) x[r] = r < C ? *peer_ptr(local, (uint32_t)r) : 0.0;
+    for (int r = 0; r < 16; ++r) x[r] = r < C ? ldf(peer_ptr(local, (uint32_t)r)) : df_make(0.f, 0.f);
 #pragma unroll
     for (int h = 8; h > 0; h >>= 1)
 #pragma unroll
-        for (int r = 0; r < h; ++r) x[r] += x[r + h];
+        for (int r = 0; r < h; ++r) x[r] = df_add(x[r], x[r + h]);
     return x[0];
 }
 
 // pd[i] = V[:, i] . w over this CTA's entries, i <= j, from the staged slice
 // Vs (leading dimension le): four threads per dot, each over every fourth
 // entry, combined by two shuffle levels.
-__device__ __forceinline__ void cluster_dots(const double *Vs, int le, const LcShared &S, int E,
-                                             int j, double *pd) {
+__device__ __forceinline__ void cluster_dots(const float2 *Vs, int le, const LcShared &S, int E,
+                                             int j, float2 *pd) {
     const int i = threadIdx.x >> 2, part = threadIdx.x & 3;
-    double s0 = 0.0, s1 = 0.0;
+    df s0 = df_make(0.f, 0.f), s1 = df_make(0.f, 0.f);
     if (i <= j) {
-        const double *vi = Vs + (size_t)i * le;
+        const float2 *vi = Vs + (size_t)i * le;
         int e = part;
         for (; e + 4 < E; e += 8) {
-            s0 = fma(vi[e], S.w[e], s0);
-            s1 = fma(vi[e + 4], S.w[e + 4], s1);
+            s0 = df_fma(ldf(vi + e), ldf(S.w + e), s0);
+            s1 = df_fma(ldf(vi + e + 4), ldf(S.w + e + 4), s1);
         }
-        if (e < E) s0 = fma(vi[e], S.w[e], s0);
+        if (e < E) s0 = df_fma(ldf(vi + e), ldf(S.w + e), s0);
     }
-    double t = s0 + s1;
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
-    t += __shfl_xor_sync(0xffffffffu, t, 2);
-    if (part == 0 && i <= j) pd[i] = t;
+    df t = df_add(s0, s1);
+    t = df_add(t, shfl_df(t, 1));
+    t = df_add(t, shfl_df(t, 2));
+    if (part == 0 && i <= j) stf(pd + i, t);
 }
 
 // w[e] -= sum_{i<=j} Vs[i][e] h[i]: thread (g, e) sums i = g, g + ng, ...; the
 // ng group sums are combined in group order.
-__device__ __forceinline__ void cluster_update(const double *Vs, int le, LcShared &S, int E, int EP,
+__device__ __forceinline__ void cluster_update(const float2 *Vs, int le, LcShared &S, int E, int EP,
                                                int ng, int j) {
     const int tid = threadIdx.x;
     const int g = tid / EP, e = tid % EP;
-    double s0 = 0.0, s1 = 0.0;
+    df s0 = df_make(0.f, 0.f), s1 = df_make(0.f, 0.f);
     if (g < ng && e < E) {
         int i = g;
         for (; i + ng <= j; i += 2 * ng) {
-            s0 = fma(Vs[(size_t)i * le + e], S.h[i], s0);
-            s1 = fma(Vs[(size_t)(i + ng) * le + e], S.h[i + ng], s1);
+            s0 = df_fma(ldf(Vs + (size_t)i * le + e), ldf(S.h + i), s0);
+            s1 = df_fma(ldf(Vs + (size_t)(i + ng) * le + e), ldf(S.h + i + ng), s1);
         }
-        if (i <= j) s0 = fma(Vs[(size_t)i * le + e], S.h[i], s0);
+        if (i <= j) s0 = df_fma(ldf(Vs + (size_t)i * le + e), ldf(S.h + i), s0);
     }
-    S.red[tid] = s0 + s1;
+    stf(S.red + tid, df_add(s0, s1));
     __syncthreads();
     if (tid < E) {
-        double t = 0.0;
-        for (int q = 0; q < ng; ++q) t += S.red[q * EP + tid];
-        S.w[tid] -= t;
+        df t = df_make(0.f, 0.f);
+        for (int q = 0; q < ng; ++q) t = df_add(t, ldf(S.red + q * EP + tid));
+        stf(S.w + tid, df_sub(ldf(S.w + tid), t));
     }
     __syncthreads();
 }
@@ -591,133 +611,167 @@ __global__ void __launch_bounds__(CT, 1) k_lz_cluster(LzArgs a, int j) {
     // state that CTA 0 overwrites at the end, read before the first barrier
     const double tn0 = a.st->tnorm;
     const double bprev = j > 0 ? a.st->beta[j - 1] : 0.0;
-    // stage V[:, 0..j] over this CTA's entries (odd leading dimension: the four
-    // dot threads of a warp's different columns fall in different banks)
-    extern __shared__ double Vs[];
+    const float tn0f = (float)tn0, bprevf = (float)fabs(bprev);
+    // stage V[:, 0..j] over this CTA's entries as double-float pairs (odd
+    // leading dimension: the four dot threads of different columns in a warp
+    // fall in different banks)
+    extern __shared__ float2 Vs[];
     const int le = E | 1;
     for (int t = tid; t < (j + 1) * E; t += CT) {
         const int i = t / E, e = t - i * E;
-        Vs[(size_t)i * le + e] = a.V[(size_t)i * a.ldp + e0 + e];
+        stf(Vs + (size_t)i * le + e, df_split_bits(a.V[(size_t)i * a.ldp + e0 + e]));
     }
 
-    // (a) w = sum over the pencil CTAs' partials, batches of 8 independent loads
+    // (a) w = sum over the pencil CTAs' double-float partials: batches of 8
+    // independent loads summed pairwise, batches in order, groups in order
     {
+        const float2 *part = reinterpret_cast<const float2 *>(a.part);
         const int g = tid / EP, e = tid % EP;
-        double acc = 0.0;
+        df acc = df_make(0.f, 0.f);
         if (g < ng && e < E) {
-            const double *src = a.part + e0 + e;
+            const float2 *src = part + e0 + e;
             const size_t stride = 2 * (size_t)a.ldp;
-            int b = g;
-            for (; b + 7 * ng < a.nparts; b += 8 * ng) {
-                double x[8];
+            // 16 loads in flight per round (zeros past the end), summed pairwise
+            for (int b = g; b < a.nparts; b += 16 * ng) {
+                df x[16];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) x[u] = src[(size_t)(b + u * ng) * stride];
-                acc += ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+                for (int u = 0; u < 16; ++u) {
+                    const int bb = b + u * ng;
+                    x[u] = bb < a.nparts ? ldf(src + (size_t)bb * stride) : df_make(0.f, 0.f);
+                }
+#pragma unroll
+                for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+                    for (int u = 0; u < h; ++u) x[u] = df_add(x[u], x[u + h]);
+                acc = df_add(acc, x[0]);
             }
-            for (; b < a.nparts; b += ng) acc += src[(size_t)b * stride];
         }
-        S.red[tid] = acc;
+        stf(S.red + tid, acc);
         __syncthreads();
         if (tid < E) {
-            double t = 0.0;
-            for (int gg = 0; gg < ng; ++gg) t += S.red[gg * EP + tid];
-            S.w[tid] = t;
+            df t = df_make(0.f, 0.f);
+            for (int gg = 0; gg < ng; ++gg) t = df_add(t, ldf(S.red + gg * EP + tid));
+            stf(S.w + tid, t);
         }
         __syncthreads();
     }
     // (b) pass 1: h1 = V^T w, w -= V h1
     cluster_dots(Vs, le, S, E, j, S.pd1);
     cluster_sync();
-    for (int i = tid; i <= j; i += CT) S.h[i] = cluster_tree_sum(&S.pd1[i], C);
+    for (int i = tid; i <= j; i += CT) stf(S.h + i, cluster_tree_sum(S.pd1 + i, C));
     __syncthreads();
-    const double h1j = S.h[j];
-    if (q == 0)
-        for (int i = tid; i <= j; i += CT) a.st->h1[i] = S.h[i];
+    const df h1j = ldf(S.h + j);
+    if (q == 0 && tid <= j) stf(S.h1s + tid, ldf(S.h + tid));  // kept for the state
     cluster_update(Vs, le, S, E, EP, ng, j);
     // (c) pass 2: h2 = V^T w, w -= V h2; alpha_j = h1_j + h2_j
     cluster_dots(Vs, le, S, E, j, S.pd2);
     cluster_sync();  // also orders the reads of S.h above before it is overwritten
-    for (int i = tid; i <= j; i += CT) S.h[i] = cluster_tree_sum(&S.pd2[i], C);
+    for (int i = tid; i <= j; i += CT) stf(S.h + i, cluster_tree_sum(S.pd2 + i, C));
     __syncthreads();
-    const double alpha = h1j + S.h[j];
-    if (q == 0)
-        for (int i = tid; i <= j; i += CT) a.st->h2[i] = S.h[i];
+    const df alpha = df_add(h1j, ldf(S.h + j));
     cluster_update(Vs, le, S, E, EP, ng, j);
-    // (d) particle-number null space, per grid row (warp per row)
+    // (d) particle-number null space, per grid row (warp per row); the row sums
+    // in double-float, the 2 x 2 solve in FP64 by one lane
     if (a.deflate) {
         const int n = a.n_orb;
         const int nr = rhi - rlo;
         if (warp < nr) {
             const int r = rlo + warp;
-            const double *wr = S.w + (size_t)warp * a.M1;
-            double sa = 0.0, sbe = 0.0;
+            const float2 *wr = S.w + (size_t)warp * a.M1;
+            df sa = df_make(0.f, 0.f), sbe = df_make(0.f, 0.f);
             for (int c = 1 + lane; c <= 2 * n; c += 32) {
-                if (c <= n) sa += wr[c]; else sbe += wr[c];
+                if (c <= n) sa = df_add(sa, ldf(wr + c));
+                else sbe = df_add(sbe, ldf(wr + c));
             }
-            sa = warp_sum(sa);
-            sbe = warp_sum(sbe);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                sa = df_add(sa, shfl_df(sa, off));
+                sbe = df_add(sbe, shfl_df(sbe, off));
+            }
             if (lane == 0) {
+                df c0, c1;
                 if (r == 0) {
-                    S.coef[warp][0] = sa / n;
-                    S.coef[warp][1] = sbe / n;
+                    c0 = df_mul(sa, ldf(&a.inv_n));
+                    c1 = df_mul(sbe, ldf(&a.inv_n));
                 } else {
                     // least squares on span{1_alpha - Na e0, 1_beta - Nb e0}
-                    const double w0 = wr[0];
-                    const double na = a.na, nb = a.nb;
-                    const double g11 = n + na * na, g22 = n + nb * nb, g12 = na * nb;
-                    const double r1 = sa - na * w0, r2 = sbe - nb * w0;
-                    const double det = g11 * g22 - g12 * g12;
-                    S.coef[warp][0] = (g22 * r1 - g12 * r2) / det;
-                    S.coef[warp][1] = (g11 * r2 - g12 * r1) / det;
+                    const df w0 = ldf(wr);
+                    const float na = (float)a.na, nb = (float)a.nb;  // exact
+                    const df r1 = df_sub(sa, df_mul(df_make(na, 0.f), w0));
+                    const df r2 = df_sub(sbe, df_mul(df_make(nb, 0.f), w0));
+                    c0 = df_add(df_mul(ldf(&a.gi11), r1), df_mul(ldf(&a.gi12), r2));
+                    c1 = df_add(df_mul(ldf(&a.gi12), r1), df_mul(ldf(&a.gi22), r2));
                 }
+                stf(&S.coef[warp][0], c0);
+                stf(&S.coef[warp][1], c1);
+                // entry 0 of a hidden row moves by Na c0 + Nb c1
+                stf(&S.red[warp], df_add(df_mul(df_make((float)a.na, 0.f), c0),
+                                         df_mul(df_make((float)a.nb, 0.f), c1)));
             }
         }
         __syncthreads();
         for (int t = tid; t < nr * (2 * n + 1); t += CT) {
             const int lr = t / (2 * n + 1), c = t % (2 * n + 1);
-            double *wr = S.w + (size_t)lr * a.M1;
+            float2 *wr = S.w + (size_t)lr * a.M1;
             if (c == 0) {
-                if (rlo + lr > 0) wr[0] += S.coef[lr][0] * a.na + S.coef[lr][1] * a.nb;
-            } else if (c <= n) {
-                wr[c] -= S.coef[lr][0];
+                if (rlo + lr > 0) stf(wr, df_add(ldf(wr), ldf(&S.red[lr])));
             } else {
-                wr[c] -= S.coef[lr][1];
+                stf(wr + c, df_sub(ldf(wr + c), ldf(&S.coef[lr][c <= n ? 0 : 1])));
             }
         }
         __syncthreads();
     }
-    // (e) beta_j = |w|, breakdown test, v_{j+1} = w / beta_j
+    // (e) beta_j = |w| (df: s = |w|^2, y = 1/sqrt(s), beta = s y), breakdown
+    // test, v_{j+1} = w y
     {
-        double s2 = 0.0;
-        for (int e = tid; e < E; e += CT) s2 = fma(S.w[e], S.w[e], s2);
-        s2 = warp_sum(s2);
-        if (lane == 0) S.red[warp] = s2;
+        df s2 = df_make(0.f, 0.f);
+        if (warp * 32 < E) {
+            for (int e = tid; e < E; e += CT) {
+                const df we = ldf(S.w + e);
+                s2 = df_fma(we, we, s2);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s2 = df_add(s2, shfl_df(s2, off));
+        }
+        __syncthreads();  // the projection's use of S.red is over
+        if (lane == 0) stf(S.red + warp, s2);
         __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < CW; ++w) t += S.red[w];
-            S.pn[0] = t;
+        if (warp == 0) {
+            df t = lane < CW ? ldf(S.red + lane) : df_make(0.f, 0.f);
+#pragma unroll
+            for (int off = CW / 2; off > 0; off >>= 1) t = df_add(t, shfl_df(t, off));
+            if (lane == 0) stf(S.pn, t);
         }
     }
     cluster_sync();
-    const double beta = sqrt(cluster_tree_sum(S.pn, C));
+    const df ss = cluster_tree_sum(S.pn, C);
     cluster_arrive();  // this CTA reads no peer memory after this point
-    double tn = fmax(tn0, fmax(fabs(alpha), beta));
-    if (j > 0) tn = fmax(tn, fabs(bprev));
-    const bool brk = beta <= 1e-14 * fmax(tn, 1e-300);
-    if (q == 0 && tid == 0) {
-        a.st->alpha[j] = alpha;
-        a.st->beta[j] = beta;
-        a.st->tnorm = tn;
-        if (brk) {
-            a.st->broke = 1;
-            a.st->jend = j + 1;
-        }
-    }
+    const df y = ss.h > 0.f ? df_rsqrt(ss) : df_make(0.f, 0.f);
+    const df beta = df_mul(ss, y);
+    // the same decision in every CTA (FP32 threshold on identical values)
+    const float tnf = fmaxf(fmaxf(tn0f, fabsf(alpha.h)), fmaxf(beta.h, bprevf));
+    const bool brk = !(beta.h > 1e-14f * fmaxf(tnf, 1e-30f));
     if (!brk) {
-        const double inv = 1.0 / beta;
         double *vout = a.V + (size_t)(j + 1) * a.ldp + e0;
-        for (int e = tid; e < E; e += CT) vout[e] = S.w[e] * inv;
+        for (int e = tid; e < E; e += CT) vout[e] = df_to_double(df_mul(ldf(S.w + e), y));
+    }
+    if (q == 0) {
+        if (tid <= j) {
+            a.st->h1[tid] = df_to_double(ldf(S.h1s + tid));
+            a.st->h2[tid] = df_to_double(ldf(S.h + tid));
+        }
+        if (tid == 0) {
+            const double al = df_to_double(alpha), be = df_to_double(beta);
+            double tn = fmax(tn0, fmax(fabs(al), be));
+            if (j > 0) tn = fmax(tn, fabs(bprev));
+            a.st->alpha[j] = al;
+            a.st->beta[j] = be;
+            a.st->tnorm = tn;
+            if (brk) {
+                a.st->broke = 1;
+                a.st->jend = j + 1;
+            }
+        }
     }
     cluster_wait();  // no CTA exits while a peer may still read its shared memory
 }
@@ -1236,13 +1290,26 @@ void choose_lanczos(Run &R, lm_ctx *ctx) {
     }
 }
 
+int lanczos_vectors(Run &R, int j);
+
 int lanczos_step(Run &R, int j) {
     lm_pencil *p = R.p;
     R.la.V = p->V;
     const double *vj = p->V + (size_t)j * p->ldp;
-    if (int rc = lm_launch_pencil(p, vj, R.sym, R.prec, 0, &p->st->broke, R.s)) return rc;
-    const int g2 = R.la.nrow_grid;
+    if (int rc = lm_launch_pencil(p, vj, R.sym, R.prec, 0, &p->st->broke, R.s,
+                                  R.lz_mode == LZ_CLUSTER))
+        return rc;
     R.n_matvec++;
+    lm_prof_begin(p->ctx, PROF_LANCZOS, R.s);
+    const int rc = lanczos_vectors(R, j);
+    lm_prof_end(p->ctx, PROF_LANCZOS, R.s);
+    return rc;
+}
+
+// The vector work of Lanczos step j (after its pencil product).
+int lanczos_vectors(Run &R, int j) {
+    lm_pencil *p = R.p;
+    const int g2 = R.la.nrow_grid;
     if (R.lz_mode == LZ_CLUSTER) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
@@ -1307,7 +1374,9 @@ int run_irl(Run &R, double tol, double rel, int max_restarts, const double *v0_d
         ta.final_pass = cycle >= max_restarts;
         ta.tol = tol;
         ta.rel = rel;
+        lm_prof_begin(ctx, PROF_TRI, R.s);
         k_tri<<<1, TT, 0, R.s>>>(ta);
+        lm_prof_end(ctx, PROF_TRI, R.s);
         lm_note_launch(ctx);
         if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_tri")) return rc;
         cudaError_t e = cudaMemcpyAsync(p->st_host, p->st, sizeof(IrlState),
@@ -1376,6 +1445,20 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
     R.la.st = p->st;
     R.la.bar = p->bar;
     R.la.flags = ctx->d_flags;
+    {
+        // projection constants (see k_lz_cluster) as double-float pairs
+        const double n = p->n, na = p->na, nb = p->nb;
+        const double g11 = n + na * na, g22 = n + nb * nb, g12 = na * nb;
+        const double det = g11 * g22 - g12 * g12;
+        auto pair = [](double x) {
+            const float h = (float)x;
+            return make_float2(h, (float)(x - (double)h));
+        };
+        R.la.inv_n = pair(1.0 / n);
+        R.la.gi11 = pair(g22 / det);
+        R.la.gi12 = pair(-g12 / det);
+        R.la.gi22 = pair(g11 / det);
+    }
     choose_lanczos(R, ctx);
 
     // optional start vector to the device

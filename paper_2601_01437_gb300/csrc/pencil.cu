@@ -37,6 +37,10 @@ struct PA<double> {
     static __device__ __forceinline__ A load(const double *p) { return *p; }
     static __device__ __forceinline__ A from_double(double x) { return x; }
     static __device__ __forceinline__ double to_double(A a) { return a; }
+    static __device__ __forceinline__ float2 to_df(A a) {
+        const df d = df_split_bits(a);
+        return make_float2(d.h, d.l);
+    }
     static __device__ __forceinline__ void madd(A &acc, A a, A b) { acc = fma(a, b, acc); }
     static __device__ __forceinline__ A add(A a, A b) { return a + b; }
     static __device__ __forceinline__ A mul(A a, A b) { return a * b; }
@@ -54,6 +58,7 @@ struct PA<float> {
     static __device__ __forceinline__ A load(const float *p) { return *p; }
     static __device__ __forceinline__ A from_double(double x) { return (float)x; }
     static __device__ __forceinline__ double to_double(A a) { return (double)a; }
+    static __device__ __forceinline__ float2 to_df(A a) { return make_float2(a, 0.f); }
     static __device__ __forceinline__ void madd(A &acc, A a, A b) { acc = fmaf(a, b, acc); }
     static __device__ __forceinline__ A add(A a, A b) { return a + b; }
     static __device__ __forceinline__ A mul(A a, A b) { return a * b; }
@@ -80,6 +85,7 @@ struct PA<float2> {
     }
     static __device__ __forceinline__ A from_double(double x) { return df_from_double(x); }
     static __device__ __forceinline__ double to_double(A a) { return df_to_double(a); }
+    static __device__ __forceinline__ float2 to_df(A a) { return make_float2(a.h, a.l); }
     // acc += a b: exact head product by FMA, cross terms, head sum by TwoSum,
     // everything else gathered in the (not yet renormalised) tail
     static __device__ __forceinline__ void madd(A &acc, A a, A b) {
@@ -120,6 +126,7 @@ struct PencilArgs {
     int rows_per_tile;
     const int *skip;
     int *flags;
+    int out_df;     // partials as double-float pairs (same 8-byte slots) instead of FP64
 };
 
 // Warp-specialised pipeline. Warp NCW (the last) is the producer: its lane 0
@@ -291,7 +298,8 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
         AT t = ys[c];
 #pragma unroll
         for (int w8 = 1; w8 < NCW; ++w8) t = P::add(t, ys[(size_t)w8 * ldp + c]);
-        out[c] = P::to_double(t);
+        if (a.out_df) reinterpret_cast<float2 *>(out)[c] = P::to_df(t);
+        else out[c] = P::to_double(t);
     }
 }
 
@@ -319,7 +327,7 @@ __global__ void k_reduce_partials(const double *part, int nparts, int ldp, doubl
 
 template <typename T, int NJ, int MODE>
 int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out, const int *skip,
-             cudaStream_t s) {
+             int out_df, cudaStream_t s) {
     const int nmat = MODE == MODE_S ? 1 : 2;
     const size_t row_bytes = (size_t)nmat * p->ldp * sizeof(T);
     // ring of one-row stages filling the shared memory (at most 32 stages)
@@ -346,6 +354,7 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
     a.rows_per_tile = R;
     a.skip = skip;
     a.flags = p->ctx->d_flags;
+    a.out_df = out_df;
     cudaError_t e = cudaFuncSetAttribute(k_pencil<T, NJ, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return lm_cuda_check(p->ctx, e, "pencil smem attribute");
@@ -359,23 +368,24 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
 
 template <typename T, int NJ>
 int dispatch_mode(lm_pencil *p, const T *O, const T *G, const double *v, int half, int want_s,
-                  const int *skip, cudaStream_t s) {
-    int rc = half ? launch_t<T, NJ, MODE_H_HALF>(p, O, G, v, p->part, skip, s)
-                  : launch_t<T, NJ, MODE_H_NONE>(p, O, G, v, p->part, skip, s);
-    if (!rc && want_s) rc = launch_t<T, NJ, MODE_S>(p, O, G, v, p->part + p->ldp, skip, s);
+                  const int *skip, int out_df, cudaStream_t s) {
+    int rc = half ? launch_t<T, NJ, MODE_H_HALF>(p, O, G, v, p->part, skip, out_df, s)
+                  : launch_t<T, NJ, MODE_H_NONE>(p, O, G, v, p->part, skip, out_df, s);
+    if (!rc && want_s)
+        rc = launch_t<T, NJ, MODE_S>(p, O, G, v, p->part + p->ldp, skip, out_df, s);
     return rc;
 }
 
 template <typename T>
 int dispatch_nc(lm_pencil *p, const T *O, const T *G, const double *v, int half, int want_s,
-                const int *skip, cudaStream_t s) {
+                const int *skip, int out_df, cudaStream_t s) {
     const int nj = (p->ldp + 31) / 32;
-    if (nj <= 8) return dispatch_mode<T, 8>(p, O, G, v, half, want_s, skip, s);
-    if (nj <= 16) return dispatch_mode<T, 16>(p, O, G, v, half, want_s, skip, s);
-    if (nj <= 28) return dispatch_mode<T, 28>(p, O, G, v, half, want_s, skip, s);
-    if (nj <= 40) return dispatch_mode<T, 40>(p, O, G, v, half, want_s, skip, s);
-    if (nj <= 52) return dispatch_mode<T, 52>(p, O, G, v, half, want_s, skip, s);
-    if (nj <= 64) return dispatch_mode<T, 64>(p, O, G, v, half, want_s, skip, s);
+    if (nj <= 8) return dispatch_mode<T, 8>(p, O, G, v, half, want_s, skip, out_df, s);
+    if (nj <= 16) return dispatch_mode<T, 16>(p, O, G, v, half, want_s, skip, out_df, s);
+    if (nj <= 28) return dispatch_mode<T, 28>(p, O, G, v, half, want_s, skip, out_df, s);
+    if (nj <= 40) return dispatch_mode<T, 40>(p, O, G, v, half, want_s, skip, out_df, s);
+    if (nj <= 52) return dispatch_mode<T, 52>(p, O, G, v, half, want_s, skip, out_df, s);
+    if (nj <= 64) return dispatch_mode<T, 64>(p, O, G, v, half, want_s, skip, out_df, s);
     return lm_fail(p->ctx, LM_ERR_SIZE, "P+1 = %d above the supported 2048", p->P1);
 }
 
@@ -384,18 +394,19 @@ int dispatch_nc(lm_pencil *p, const T *O, const T *G, const double *v, int half,
 int lm_pencil_grid(lm_pencil *p) { return p->ctx->sms; }
 
 int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_s,
-                     const int *skip, cudaStream_t s) {
+                     const int *skip, cudaStream_t s, int out_df) {
     const int half = (sym == LM_SYM_HALF);
     if (prec == LM_FP64 || p->prec == LM_FP64 || p->Olo == nullptr)
-        return dispatch_nc<double>(p, p->O, p->G, v, half, want_s, skip, s);
+        return dispatch_nc<double>(p, p->O, p->G, v, half, want_s, skip, out_df, s);
     if (p->prec == LM_FP32)
         return dispatch_nc<float>(p, (const float *)p->Olo, (const float *)p->Glo, v, half,
-                                  want_s, skip, s);
+                                  want_s, skip, out_df, s);
     if (p->prec == LM_DF64)
         return dispatch_nc<float2>(p, (const float2 *)p->Olo, (const float2 *)p->Glo, v, half,
-                                   want_s, skip, s);
+                                   want_s, skip, out_df, s);
     return dispatch_nc<__nv_bfloat16>(p, (const __nv_bfloat16 *)p->Olo,
-                                      (const __nv_bfloat16 *)p->Glo, v, half, want_s, skip, s);
+                                      (const __nv_bfloat16 *)p->Glo, v, half, want_s, skip,
+                                      out_df, s);
 }
 
 int lm_launch_reduce_partials(lm_pencil *p, double *yH, double *yS, cudaStream_t s) {
@@ -439,6 +450,7 @@ int raw_launch(const double *O, const double *G, const double *w, int64_t n_rows
     a.rows_per_tile = R;
     a.skip = nullptr;
     a.flags = flags;
+    a.out_df = 0;
     if (cudaFuncSetAttribute(k_pencil<double, NJ, MODE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LM_ERR_CUDA;

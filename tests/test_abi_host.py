@@ -43,6 +43,7 @@ def test_struct_layouts_match_c(lib, tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(lm_system), sizeof(lm_pencil_info), sizeof(irl_params), sizeof(irl_result));
   printf("%zu %zu %zu %zu %zu\\n", offsetof(irl_params, seed), offsetof(irl_params, v0), offsetof(irl_result, status), offsetof(lm_pencil_info, energy), offsetof(lm_system, build_arith));
+  printf("%zu %zu\\n", sizeof(lm_stats), offsetof(lm_stats, tri_count));
   return 0; }
 """)
     exe = tmp_path / "layout"
@@ -52,7 +53,8 @@ int main(void) {
     want = [ctypes.sizeof(lib.lm_system), ctypes.sizeof(lib.lm_pencil_info),
             ctypes.sizeof(lib.irl_params), ctypes.sizeof(lib.irl_result),
             lib.irl_params.seed.offset, lib.irl_params.v0.offset, lib.irl_result.status.offset,
-            lib.lm_pencil_info.energy.offset, lib.lm_system.build_arith.offset]
+            lib.lm_pencil_info.energy.offset, lib.lm_system.build_arith.offset,
+            ctypes.sizeof(lib.lm_stats), lib.lm_stats.tri_count.offset]
     assert [int(x) for x in out] == want
 
 
