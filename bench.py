@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="f2_10o14e")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-pencil-c2", action="store_true",
+                    help="skip the pencil-matvec HBM measurement on the LiCl-shaped MC pencil")
     ap.add_argument("--pencil", default="df64", choices=["df64", "fp64"],
                     help="storage of the FP64 workload's Lanczos pencil factors (both "
                          "FP64-accurate; the final refinement always uses FP64)")
@@ -339,7 +341,51 @@ def run_gpu(args, rank, world, local):
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         pen2.free()
     state["pen"].free()
+    if not args.no_pencil_c2 and rank == 0 and world == 1:
+        out["pencil_c2"] = pencil_c2(abi, ctx, s, dev, hbm, hbm_src)
     ctx.close()
+    return out
+
+
+def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10):
+    """Pencil-matvec HBM bandwidth on the LiCl-shaped Monte Carlo pencil (262,144 rows,
+    P+1 = 1,653: O_c and G'_c far larger than L2), per storage precision: the
+    symmetrised product y_H = (O_c^T W G'_c v + G'_c^T W O_c v)/2 of the IRL inner
+    loop, which reads each matrix once. Live CUDA-event durations of k_pencil."""
+    import torch
+    w = synth.WORKLOADS["licl_14o14e_mc"]
+    h, eri, th, rows, counts = w.inputs()
+    sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, torch.from_numpy(h).to(dev),
+                      torch.from_numpy(eri).to(dev))
+    rows_d = torch.from_numpy(rows.view(np.int64)).to(dev)
+    wts_d = torch.from_numpy(counts.astype(np.float64)).to(dev)
+    th_d = torch.from_numpy(th).to(dev)
+    p1 = w.n_params + 1
+    g = torch.Generator(device="cpu").manual_seed(5)
+    v = torch.randn(p1, dtype=torch.float64, generator=g).to(dev)
+    hv = torch.empty_like(v)
+    out = {}
+    for name, pr, b in (("fp32", abi.LM_FP32, 4), ("bf16", abi.LM_BF16, 2),
+                        ("df64", abi.LM_DF64, 8)):
+        pen = ctx.build_OG(sysd, th_d, rows=rows_d, weights=wts_d, n_rows=w.n_rows, prec=pr,
+                           stream=s)
+        cases = [(name, pr, b)] + ([("fp64", abi.LM_FP64, 8)] if name == "fp32" else [])
+        for nm, pp, bb in cases:
+            for _ in range(3):
+                pen.apply(v, hv, None, sym=abi.LM_SYM_HALF, prec=pp, stream=s)
+            torch.cuda.synchronize()
+            ctx.stats_reset(profile=True)
+            for _ in range(reps):
+                pen.apply(v, hv, None, sym=abi.LM_SYM_HALF, prec=pp, stream=s)
+            st = ctx.stats()
+            d = st.pencil_ms / st.pencil_count / 1e3
+            nbytes = w.n_rows * p1 * 2 * bb + 8 * w.n_rows
+            out[nm] = {"avg_ms": d * 1e3, "achieved": nbytes / d / 1e9, "unit": "GB/s",
+                       "peak": hbm, "frac": nbytes / d / 1e9 / hbm, "bytes": nbytes,
+                       "launches": int(st.pencil_count)}
+        pen.free()
+    out["workload"] = (f"{w.name}: {w.n_rows} MC rows x P+1 = {p1}, symmetrised H~' product, "
+                       f"peak = {hbm_src} hbm_gbs")
     return out
 
 

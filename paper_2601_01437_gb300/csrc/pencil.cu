@@ -50,6 +50,17 @@ struct PA<double> {
     static __device__ __forceinline__ A weight(const double *w, const float2 *, int64_t i) {
         return w[i];
     }
+    // 16-byte vector loads: two stored values / two compute values
+    static __device__ __forceinline__ void load_vec(const double *p, A *o) {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+    static __device__ __forceinline__ void load_avec(const A *p, A *o) { load_vec(p, o); }
+    static __device__ __forceinline__ void store_avec(A *p, const A *o) {
+        *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+    }
+    static __device__ __forceinline__ void renorm(A &) {}
 };
 template <>
 struct PA<float> {
@@ -68,11 +79,42 @@ struct PA<float> {
     static __device__ __forceinline__ A weight(const double *, const float2 *wl, int64_t i) {
         return wl[i].x;
     }
+    // 16-byte vector loads: four stored values / compute values four at a time
+    static __device__ __forceinline__ void load_vec(const float *p, A *o) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+    static __device__ __forceinline__ void load_avec(const A *p, A *o) { load_vec(p, o); }
+    static __device__ __forceinline__ void store_avec(A *p, const A *o) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    static __device__ __forceinline__ void renorm(A &) {}
 };
 template <>
 struct PA<__nv_bfloat16> : PA<float> {
     static __device__ __forceinline__ float load(const __nv_bfloat16 *p) {
         return __bfloat162float(*p);
+    }
+    // eight stored values in one 16-byte load; compute values in two float4
+    static __device__ __forceinline__ void load_vec(const __nv_bfloat16 *p, A *o) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p);
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {  // bf16 -> fp32 is a 16-bit shift
+            o[2 * k] = __uint_as_float(w[k] << 16);
+            o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
+    static __device__ __forceinline__ void load_avec(const A *p, A *o) {
+        PA<float>::load_vec(p, o);
+        PA<float>::load_vec(p + 4, o + 4);
+    }
+    static __device__ __forceinline__ void store_avec(A *p, const A *o) {
+        PA<float>::store_avec(p, o);
+        PA<float>::store_avec(p + 4, o + 4);
     }
 };
 template <>
@@ -107,6 +149,19 @@ struct PA<float2> {
         const float2 v = wl[i];
         return df_make(v.x, v.y);
     }
+    static __device__ __forceinline__ void load_vec(const float2 *p, A *o) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        o[0] = df_make(v.x, v.y);
+        o[1] = df_make(v.z, v.w);
+    }
+    static __device__ __forceinline__ void load_avec(const A *p, A *o) {
+        load_vec(reinterpret_cast<const float2 *>(p), o);
+    }
+    static __device__ __forceinline__ void store_avec(A *p, const A *o) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
+    }
+    // fold the lazily accumulated tail back into the head
+    static __device__ __forceinline__ void renorm(A &a) { a = df_fts(a.h, a.l); }
 };
 
 enum { MODE_H_NONE = 0, MODE_H_HALF = 1, MODE_S = 2 };
@@ -128,6 +183,85 @@ struct PencilArgs {
     int *flags;
     int out_df;     // partials as double-float pairs (same 8-byte slots) instead of FP64
 };
+
+// Columns per lane per 16-byte shared-memory access (8 BF16, 4 FP32, 2 FP64 or
+// double-float), and the number of 32 x VEC column chunks covering NJ x 32.
+template <typename T>
+struct VEC {
+    static constexpr int value = 16 / (int)sizeof(T);
+};
+template <typename T, int NJ>
+struct NCV {
+    static constexpr int value = (NJ + VEC<T>::value - 1) / VEC<T>::value;
+};
+
+// One staged row: lane l owns columns k * 32 VEC + l VEC + [0, VEC) of chunk k
+// (ldp is a multiple of 32, so a chunk's last lanes are the only partial
+// ones, and they hold whole vectors or nothing). Row dot(s) by one butterfly,
+// then the rank-1 update of the register-resident y:
+// MODE_H_NONE: y += w (G.v) O; MODE_H_HALF: y += w/2 ((G.v) O + (O.v) G);
+// MODE_S: y += w (O.v) O.
+template <typename T, int NJ, int MODE>
+__device__ __forceinline__ void consume_row(const T *ro, const T *rg, const typename PA<T>::A *vs,
+                                            int ldp, int lane, typename PA<T>::A wr,
+                                            typename PA<T>::A (&y)[NCV<T, NJ>::value][VEC<T>::value]) {
+    using P = PA<T>;
+    using AT = typename PA<T>::A;
+    constexpr int W = VEC<T>::value, NC = NCV<T, NJ>::value;
+    AT dg = P::zero(), dov = P::zero();
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int c0 = k * 32 * W + lane * W;
+        if (c0 < ldp) {
+            AT vv[W], x[W];
+            P::load_avec(vs + c0, vv);
+            if (MODE != MODE_S) {
+                P::load_vec(rg + c0, x);
+#pragma unroll
+                for (int v = 0; v < W; ++v) P::madd(dg, x[v], vv[v]);
+            }
+            if (MODE != MODE_H_NONE) {
+                P::load_vec(ro + c0, x);
+#pragma unroll
+                for (int v = 0; v < W; ++v) P::madd(dov, x[v], vv[v]);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        if (MODE != MODE_S) dg = P::add(dg, P::shfl_xor(dg, off));
+        if (MODE != MODE_H_NONE) dov = P::add(dov, P::shfl_xor(dov, off));
+    }
+    AT cg, co;
+    if (MODE == MODE_H_HALF) {
+        const AT half = P::mul(wr, P::from_double(0.5));
+        cg = P::mul(half, dg);
+        co = P::mul(half, dov);
+    } else {
+        cg = P::mul(wr, dg);
+        co = P::mul(wr, dov);
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int c0 = k * 32 * W + lane * W;
+        if (c0 < ldp) {
+            AT x[W];
+            P::load_vec(ro + c0, x);
+            if (MODE == MODE_S) {
+#pragma unroll
+                for (int v = 0; v < W; ++v) P::madd(y[k][v], co, x[v]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < W; ++v) P::madd(y[k][v], cg, x[v]);
+                if (MODE == MODE_H_HALF) {
+                    P::load_vec(rg + c0, x);
+#pragma unroll
+                    for (int v = 0; v < W; ++v) P::madd(y[k][v], co, x[v]);
+                }
+            }
+        }
+    }
+}
 
 // Warp-specialised pipeline. Warp NCW (the last) is the producer: its lane 0
 // streams this CTA's rows, one row of O (and G) per pipeline stage, into a ring
@@ -159,12 +293,13 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
     extern __shared__ __align__(128) unsigned char smraw[];
     if (a.skip && *a.skip) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ldp = a.ldp, S = a.stages;
+    const int ldp = a.ldp, S = a.stages, R = a.rows_per_tile;
     const int ncons = min(NCW, S);  // consuming warps; see the parity note above
     const int nmat = MODE == MODE_S ? 1 : 2;
     const size_t row_elems = (size_t)ldp;
+    const size_t tile_elems = (size_t)R * row_elems;  // one matrix's rows of a stage
     T *stage_base = reinterpret_cast<T *>(smraw);
-    const size_t stage_bytes_all = (size_t)S * nmat * row_elems * sizeof(T);
+    const size_t stage_bytes_all = (size_t)S * nmat * tile_elems * sizeof(T);
     uint64_t *full = reinterpret_cast<uint64_t *>(smraw + stage_bytes_all);
     uint64_t *empty = full + S;
     AT *vs = reinterpret_cast<AT *>(empty + S);  // v in the compute type, ldp entries
@@ -173,7 +308,7 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
     const int64_t r0 = a.n_rows * blockIdx.x / gridDim.x;
     const int64_t r1 = a.n_rows * (blockIdx.x + 1) / gridDim.x;
     const int nrows = (int)(r1 - r0);
-    const int nj = (ldp + 31) >> 5;
+    const int ntiles = (nrows + R - 1) / R;
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
@@ -186,16 +321,17 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
     for (int c = tid; c < ldp; c += blockDim.x) vs[c] = P::from_double(a.v[c]);
     __syncthreads();
 
-    AT y[NJ];
+    AT y[NCV<T, NJ>::value][VEC<T>::value];
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) y[j] = P::zero();
+    for (int k = 0; k < NCV<T, NJ>::value; ++k)
+#pragma unroll
+        for (int v = 0; v < VEC<T>::value; ++v) y[k][v] = P::zero();
 
     if (warp == NCW) {
         // producer
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)(row_elems * sizeof(T));
             int issued = 0;
-            for (int i = 0; i < nrows; ++i) {
+            for (int i = 0; i < ntiles; ++i) {
                 const int s = i % S;
                 if (i >= S && !mbar_wait_bounded(&empty[s], (uint32_t)(((i / S) - 1) & 1))) {
                     atomicOr(a.flags, FLAG_TIMEOUT);
@@ -203,10 +339,14 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
                     break;
                 }
                 if (*(volatile int *)&s_abort) break;
-                T *dst = stage_base + (size_t)s * nmat * row_elems;
+                // the tile's rows are consecutive in O and in G: one copy per matrix
+                const int nr = min(R, nrows - i * R);
+                const uint32_t bytes = (uint32_t)(nr * row_elems * sizeof(T));
+                const int64_t row = r0 + (int64_t)i * R;
+                T *dst = stage_base + (size_t)s * nmat * tile_elems;
                 mbar_arrive_expect_tx(&full[s], nmat * bytes);
-                bulk_g2s(dst, a.O + (r0 + i) * ldp, bytes, &full[s]);
-                if (MODE != MODE_S) bulk_g2s(dst + row_elems, a.G + (r0 + i) * ldp, bytes, &full[s]);
+                bulk_g2s(dst, a.O + row * ldp, bytes, &full[s]);
+                if (MODE != MODE_S) bulk_g2s(dst + tile_elems, a.G + row * ldp, bytes, &full[s]);
                 issued = i + 1;
             }
             // every issued copy lands before the CTA may exit (bounded)
@@ -214,7 +354,7 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
                 (void)mbar_wait_bounded(&full[i % S], (uint32_t)((i / S) & 1));
         }
     } else if (warp < ncons) {
-        for (int i = warp; i < nrows; i += ncons) {
+        for (int i = warp; i < ntiles; i += ncons) {
             const int s = i % S;
             bool ok = true;
             if (lane == 0) ok = mbar_wait_bounded(&full[s], (uint32_t)((i / S) & 1));
@@ -226,55 +366,17 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
                 }
                 break;
             }
-            const T *ro = stage_base + (size_t)s * nmat * row_elems;
-            const T *rg = ro + row_elems;
-            AT dg = P::zero(), dov = P::zero();
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                if (j < nj) {
-                    const int c = lane + 32 * j;
-                    if (c < ldp) {
-                        if (MODE != MODE_S) P::madd(dg, P::load(rg + c), vs[c]);
-                        if (MODE != MODE_H_NONE) P::madd(dov, P::load(ro + c), vs[c]);
-                    }
-                }
+            const int nr = min(R, nrows - i * R);
+            for (int rr = 0; rr < nr; ++rr) {
+                const T *ro = stage_base + (size_t)s * nmat * tile_elems + (size_t)rr * row_elems;
+                consume_row<T, NJ, MODE>(ro, ro + tile_elems, vs, ldp, lane,
+                                         P::weight(a.w, a.wlo, r0 + (int64_t)i * R + rr), y);
             }
+            if ((i / ncons) % 16 == 15)  // fold lazily accumulated tails now and then
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                if (MODE != MODE_S) dg = P::add(dg, P::shfl_xor(dg, off));
-                if (MODE != MODE_H_NONE) dov = P::add(dov, P::shfl_xor(dov, off));
-            }
-            const AT wr = P::weight(a.w, a.wlo, r0 + i);
-            if (MODE == MODE_H_NONE) {
-                const AT cg = P::mul(wr, dg);
+                for (int k = 0; k < NCV<T, NJ>::value; ++k)
 #pragma unroll
-                for (int j = 0; j < NJ; ++j)
-                    if (j < nj) {
-                        const int c = lane + 32 * j;
-                        if (c < ldp) P::madd(y[j], cg, P::load(ro + c));
-                    }
-            } else if (MODE == MODE_H_HALF) {
-                const AT half = P::mul(wr, P::from_double(0.5));
-                const AT cg = P::mul(half, dg);
-                const AT co = P::mul(half, dov);
-#pragma unroll
-                for (int j = 0; j < NJ; ++j)
-                    if (j < nj) {
-                        const int c = lane + 32 * j;
-                        if (c < ldp) {
-                            P::madd(y[j], cg, P::load(ro + c));
-                            P::madd(y[j], co, P::load(rg + c));
-                        }
-                    }
-            } else {
-                const AT co = P::mul(wr, dov);
-#pragma unroll
-                for (int j = 0; j < NJ; ++j)
-                    if (j < nj) {
-                        const int c = lane + 32 * j;
-                        if (c < ldp) P::madd(y[j], co, P::load(ro + c));
-                    }
-            }
+                    for (int v = 0; v < VEC<T>::value; ++v) P::renorm(y[k][v]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
@@ -285,12 +387,12 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
     // type (the ring is free now); one conversion to FP64 per column.
     AT *ys = reinterpret_cast<AT *>(smraw);  // [NCW][ldp]
     if (warp < NCW) {
+        constexpr int W = VEC<T>::value;
 #pragma unroll
-        for (int j = 0; j < NJ; ++j)
-            if (j < nj) {
-                const int c = lane + 32 * j;
-                if (c < ldp) ys[(size_t)warp * ldp + c] = y[j];
-            }
+        for (int k = 0; k < NCV<T, NJ>::value; ++k) {
+            const int c0 = k * 32 * W + lane * W;
+            if (c0 < ldp) P::store_avec(ys + (size_t)warp * ldp + c0, y[k]);
+        }
     }
     __syncthreads();
     double *out = a.out + (size_t)blockIdx.x * a.out_ld;
@@ -330,14 +432,18 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
              int out_df, cudaStream_t s) {
     const int nmat = MODE == MODE_S ? 1 : 2;
     const size_t row_bytes = (size_t)nmat * p->ldp * sizeof(T);
-    // ring of one-row stages filling the shared memory (at most 32 stages)
+    // ring of stages filling the shared memory (at most 32). A stage holds R
+    // consecutive rows, R chosen so that a stage carries about 16 KB: short rows
+    // (BF16, FP32, small P) would otherwise leave the one producer lane issuing
+    // copies and barrier operations faster than HBM delivers the rows.
+    const int R = (int)std::max<size_t>(1, std::min<size_t>(8, 16384 / row_bytes));
+    const size_t tile_bytes = (size_t)R * row_bytes;
     const size_t tail = (size_t)p->ldp * sizeof(typename PA<T>::A) + 256;
     const size_t budget = (size_t)p->ctx->smem_optin - tail - 2048;
-    const int stages = (int)std::min<size_t>(32, budget / (row_bytes + 2 * sizeof(uint64_t)));
-    const int R = 1;
+    const int stages = (int)std::min<size_t>(32, budget / (tile_bytes + 2 * sizeof(uint64_t)));
     if (stages < 2)
         return lm_fail(p->ctx, LM_ERR_SIZE, "pencil row of %d columns too long", p->ldp);
-    size_t smem = stages * (row_bytes + 2 * sizeof(uint64_t)) + tail;
+    size_t smem = stages * (tile_bytes + 2 * sizeof(uint64_t)) + tail;
     constexpr int NCW = Ncw<NJ>::value;
     smem = std::max(smem, (size_t)NCW * p->ldp * sizeof(double) + 64);
     PencilArgs<T> a;
