@@ -107,6 +107,7 @@ typedef struct {
     int precision;        /* lm_precision of the low-precision copy (FP64: none) */
     int sym;              /* resolved lm_sym */
     double energy;        /* E(theta) = sum_x w(x) E_loc(x), including e_core */
+    int grid;             /* CTAs of each pencil-product launch (lm_pencil_set_grid) */
 } lm_pencil_info;
 
 /* IRL settings (Algorithm 1; the paper uses k = 1, m = 20, tol = 1e-12). */
@@ -196,6 +197,14 @@ int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, double *c_out
 int lm_pencil_info_get(lm_pencil *p, lm_pencil_info *out);
 int lm_pencil_free(lm_pencil *p);
 
+/* Number of CTAs each pencil-product launch of p uses (default: one per SM),
+ * 1 <= ctas <= SM count (LM_ERR_ARG otherwise). The products sum the CTAs'
+ * partial vectors in a fixed order, so results depend on this number (in the
+ * last bits) and on nothing else about the launch or what runs beside it: an
+ * instance run alone with the grid a batch chose reproduces the batch result
+ * exactly. */
+int lm_pencil_set_grid(lm_pencil *p, int ctas);
+
 /* ---- inspection (tests and tools; not on the timed path) -------------- */
 
 /* Enumerate the (n_alpha, n_beta) sector in ascending order into out
@@ -247,6 +256,84 @@ int lm_pencil_export(lm_pencil *p, int what, void *dst, void *stream);
 int lm_apply_pencil_noalloc(const double *O_c, const double *G_c, const double *w, int64_t n_rows,
                             int ld, int p1, const double *v, double *Hv, double *Sv, int sym,
                             void *stream);
+
+/* ---- batched LM steps (many independent systems on one GPU) ----------- */
+
+/* One instance of a batch: one LM step (build of O_c/G'_c, IRL for the lowest
+ * Ritz pair, FP64 refinement, update) of an independent system. Pointers may
+ * be host or device memory; theta_inout (nullable) is advanced in place by
+ * dtheta, dtheta_out (nullable) receives it. */
+typedef struct {
+    lm_system sys;
+    const double *theta;       /* P parameters */
+    const uint64_t *rows;      /* NULL: exact sector enumeration; else n_rows samples */
+    const double *weights;     /* NULL: |psi|^2 weights; else one weight per row */
+    int64_t n_rows;            /* sample count (ignored for exact enumeration) */
+    int precision;             /* lm_precision of the stored O/G copies */
+    irl_params irl;
+    double *dtheta_out;
+    double *theta_inout;
+} lm_batch_item;
+
+typedef struct lm_batch lm_batch;
+
+/* A batch engine over n_streams CUDA streams (1..64). It keeps one pencil per
+ * item index across lm_batch_run calls (device-resident O/G and Lanczos
+ * bases; rebuilt in place when the shape is unchanged). autotune = 1 picks,
+ * for every new pencil shape, the pencil-product grid that minimises SM time
+ * per product (CTAs x duration, timed alone once); autotune = 0 keeps one CTA
+ * per SM. */
+int lm_batch_create(lm_ctx *ctx, int n_streams, int autotune, lm_batch **out);
+
+/* Run one LM step of every item concurrently (instance i on stream i mod
+ * n_streams; no instance waits for another except for GPU resources) and
+ * return when all have finished. results[i] is instance i's irl_result;
+ * grid_out (nullable, n entries) receives the pencil grid each instance used.
+ * Each instance's arithmetic is exactly that of irl_step on the same inputs
+ * and grid. Errors: the first failing instance's code (LM_ERR_*); the
+ * others' results are still written. */
+int lm_batch_run(lm_batch *b, int n, const lm_batch_item *items, irl_result *results,
+                 int *grid_out);
+int lm_batch_free(lm_batch *b);
+
+/* ---- serving: a request loop with continuous admission ---------------- */
+
+typedef struct lm_server lm_server;
+
+typedef struct {
+    int64_t ticket;       /* as returned by lm_server_submit */
+    int system_id;
+    int status;           /* LM_OK or LM_ERR_* */
+    int grid;             /* pencil-product CTAs the request used (lm_pencil_set_grid) */
+    irl_result result;
+    double t_submit_ms;   /* host steady-clock times of the request */
+    double t_admit_ms;
+    double t_done_ms;
+} lm_response;
+
+/* A server over n_streams streams (at most that many requests in flight)
+ * that admits work only while the estimated device footprint of the resident
+ * systems stays within hbm_budget_bytes (idle systems are evicted, least
+ * recently used first, to make room). */
+int lm_server_create(lm_ctx *ctx, size_t hbm_budget_bytes, int n_streams, int autotune,
+                     lm_server **out);
+/* Register a system: its integrals, rows and weights are copied into the
+ * server (host memory); its pencil is created on first admission and stays
+ * resident across requests. Returns its id in *system_id. */
+int lm_server_add_system(lm_server *srv, const lm_system *sys, const uint64_t *rows,
+                         const double *weights, int64_t n_rows, int precision, int *system_id);
+/* Queue one LM-step request: theta (host, P entries, copied now), the IRL
+ * settings; dtheta_out (host, P, nullable) is written when the request
+ * completes. Requests for one system run one at a time, in order. */
+int lm_server_submit(lm_server *srv, int system_id, const double *theta,
+                     const irl_params *prm, double *dtheta_out, int64_t *ticket);
+/* Advance all in-flight work without blocking: admit queued requests that
+ * fit, move every in-flight request whose device work has completed to its
+ * next stage, and return up to cap finished responses (*n_out of them). */
+int lm_server_poll(lm_server *srv, lm_response *out, int cap, int *n_out);
+/* Requests submitted but not yet returned by lm_server_poll. */
+int lm_server_pending(lm_server *srv, int *n);
+int lm_server_free(lm_server *srv);
 
 /* ---- counters (benchmarking; not on the math path) -------------------- */
 

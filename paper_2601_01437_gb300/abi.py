@@ -33,7 +33,7 @@ class lm_system(ctypes.Structure):
 
 class lm_pencil_info(ctypes.Structure):
     _fields_ = [("n_rows", c_int64), ("n_params", c_int), ("ld", c_int), ("precision", c_int),
-                ("sym", c_int), ("energy", c_double)]
+                ("sym", c_int), ("energy", c_double), ("grid", c_int)]
 
 
 class irl_params(ctypes.Structure):
@@ -49,6 +49,18 @@ class irl_result(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class lm_batch_item(ctypes.Structure):
+    _fields_ = [("sys", lm_system), ("theta", c_vp), ("rows", c_vp), ("weights", c_vp),
+                ("n_rows", c_int64), ("precision", c_int), ("irl", irl_params),
+                ("dtheta_out", c_vp), ("theta_inout", c_vp)]
+
+
+class lm_response(ctypes.Structure):
+    _fields_ = [("ticket", c_int64), ("system_id", c_int), ("status", c_int), ("grid", c_int),
+                ("result", irl_result), ("t_submit_ms", c_double), ("t_admit_ms", c_double),
+                ("t_done_ms", c_double)]
 
 
 class lm_stats(ctypes.Structure):
@@ -78,6 +90,18 @@ _SIGNATURES = {
     "lm_pencil_export": (c_int, [c_vp, c_int, c_vp, c_vp]),
     "lm_apply_pencil_noalloc": (c_int, [c_vp, c_vp, c_vp, c_int64, c_int, c_int, c_vp, c_vp, c_vp,
                                         c_int, c_vp]),
+    "lm_pencil_set_grid": (c_int, [c_vp, c_int]),
+    "lm_batch_create": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_vp)]),
+    "lm_batch_run": (c_int, [c_vp, c_int, c_vp, c_vp, c_vp]),
+    "lm_batch_free": (c_int, [c_vp]),
+    "lm_server_create": (c_int, [c_vp, ctypes.c_size_t, c_int, c_int, ctypes.POINTER(c_vp)]),
+    "lm_server_add_system": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_vp, c_int64, c_int,
+                                     ctypes.POINTER(c_int)]),
+    "lm_server_submit": (c_int, [c_vp, c_int, c_vp, ctypes.POINTER(irl_params), c_vp,
+                                 ctypes.POINTER(c_int64)]),
+    "lm_server_poll": (c_int, [c_vp, c_vp, c_int, ctypes.POINTER(c_int)]),
+    "lm_server_pending": (c_int, [c_vp, ctypes.POINTER(c_int)]),
+    "lm_server_free": (c_int, [c_vp]),
     "lm_stats_reset": (c_int, [c_vp, c_int]),
     "lm_stats_get": (c_int, [c_vp, ctypes.POINTER(lm_stats)]),
 }
@@ -256,7 +280,97 @@ class Pencil:
         self.ctx.check(lib().lm_pencil_export(self.handle, int(what), ptr(out), None), "export")
         return out
 
+    def set_grid(self, ctas):
+        self.ctx.check(lib().lm_pencil_set_grid(self.handle, int(ctas)), "lm_pencil_set_grid")
+
     def free(self):
         if self.handle:
             lib().lm_pencil_free(self.handle)
+            self.handle = None
+
+
+def irl_settings(m=20, k=1, tol=1e-12, max_restarts=200, seed=111, sym=LM_SYM_AUTO,
+                 prec=LM_FP64, deflate_null=1):
+    return irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null), None)
+
+
+class Batch:
+    """lm_batch_create / lm_batch_run / lm_batch_free."""
+
+    def __init__(self, ctx: Context, n_streams=16, autotune=True):
+        h = c_vp()
+        ctx.check(lib().lm_batch_create(ctx.handle, int(n_streams), int(autotune),
+                                        ctypes.byref(h)), "lm_batch_create")
+        self.ctx, self.handle = ctx, h.value
+
+    def run(self, items):
+        """items: list of dicts with sys, theta, rows, weights, n_rows, precision, irl
+        (an irl_params), dtheta_out, theta_inout. Returns (results, grids)."""
+        n = len(items)
+        arr = (lm_batch_item * n)()
+        keep = []
+        for i, it in enumerate(items):
+            rows = it.get("rows")
+            arr[i].sys = it["sys"]
+            arr[i].theta = ptr(it["theta"])
+            arr[i].rows = ptr(rows)
+            arr[i].weights = ptr(it.get("weights"))
+            arr[i].n_rows = int(it.get("n_rows", 0 if rows is None else rows.shape[0]))
+            arr[i].precision = int(it.get("precision", LM_FP32))
+            arr[i].irl = it["irl"]
+            arr[i].dtheta_out = ptr(it.get("dtheta_out"))
+            arr[i].theta_inout = ptr(it.get("theta_inout"))
+            keep.append(it)
+        res = (irl_result * n)()
+        grids = (c_int * n)()
+        rc = lib().lm_batch_run(self.handle, n, ctypes.cast(arr, c_vp), ctypes.cast(res, c_vp),
+                                ctypes.cast(grids, c_vp))
+        self.ctx.check(rc, "lm_batch_run")
+        return list(res), list(grids)
+
+    def free(self):
+        if self.handle:
+            lib().lm_batch_free(self.handle)
+            self.handle = None
+
+
+class Server:
+    """lm_server_*: submit LM-step requests, poll for finished responses."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes, n_streams=16, autotune=True):
+        h = c_vp()
+        ctx.check(lib().lm_server_create(ctx.handle, int(hbm_budget_bytes), int(n_streams),
+                                         int(autotune), ctypes.byref(h)), "lm_server_create")
+        self.ctx, self.handle = ctx, h.value
+
+    def add_system(self, sys, rows=None, weights=None, precision=LM_FP32):
+        sid = c_int()
+        n = 0 if rows is None else int(rows.shape[0])
+        self.ctx.check(lib().lm_server_add_system(self.handle, ctypes.byref(sys), ptr(rows),
+                                                  ptr(weights), n, int(precision),
+                                                  ctypes.byref(sid)), "lm_server_add_system")
+        return sid.value
+
+    def submit(self, system_id, theta, irl, dtheta_out=None):
+        t = c_int64()
+        self.ctx.check(lib().lm_server_submit(self.handle, int(system_id), ptr(theta),
+                                              ctypes.byref(irl), ptr(dtheta_out),
+                                              ctypes.byref(t)), "lm_server_submit")
+        return t.value
+
+    def poll(self, cap=64):
+        buf = (lm_response * cap)()
+        n = c_int()
+        self.ctx.check(lib().lm_server_poll(self.handle, ctypes.cast(buf, c_vp), cap,
+                                            ctypes.byref(n)), "lm_server_poll")
+        return [buf[i] for i in range(n.value)]
+
+    def pending(self):
+        n = c_int()
+        self.ctx.check(lib().lm_server_pending(self.handle, ctypes.byref(n)), "pending")
+        return n.value
+
+    def free(self):
+        if self.handle:
+            lib().lm_server_free(self.handle)
             self.handle = None

@@ -86,7 +86,7 @@ void pencil_release(lm_pencil *p) {
                     p->st,   p->tdf,  p->wlo, p->bar};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    if (p->st_host) cudaFreeHost(p->st_host);
+    if (p->hs) cudaFreeHost(p->hs);
     delete p;
 }
 
@@ -144,9 +144,9 @@ extern "C" int lm_destroy(lm_ctx *ctx) {
 extern "C" const char *lm_last_error(const lm_ctx *ctx) { return ctx ? ctx->err : "null context"; }
 
 // ---------------------------------------------------------------- build
-extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *theta,
-                           const uint64_t *rows, const double *weights, int64_t n_rows,
-                           lm_precision prec, void *stream, lm_pencil **inout) {
+int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
+                     const uint64_t *rows, const double *weights, int64_t n_rows,
+                     lm_precision prec, void *stream, lm_pencil **inout) {
     if (!ctx || !inout || !theta) return lm_fail(ctx, LM_ERR_ARG, "null argument");
     ctx->err[0] = 0;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return LM_ERR_CUDA;
@@ -224,7 +224,12 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
         rc = rc ? rc : dalloc(ctx, &p->bar, 64);
         if (!rc) rc = lm_cuda_check(ctx, cudaMemsetAsync(p->bar, 0, 64 * sizeof(unsigned), s), "memset");
         if (!rc)
-            rc = lm_cuda_check(ctx, cudaMallocHost(&p->st_host, sizeof(IrlState)), "cudaMallocHost");
+            rc = lm_cuda_check(ctx, cudaMallocHost(&p->hs, sizeof(PencilHost)), "cudaMallocHost");
+        if (!rc) {
+            p->st_host = &p->hs->st;
+            p->d_flags = &p->st->flags;
+            rc = lm_cuda_check(ctx, cudaMemsetAsync(p->st, 0, sizeof(IrlState), s), "memset");
+        }
         if (rc) {
             pencil_release(p);
             return rc;
@@ -251,16 +256,33 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
         return rc;
     }
     if (weights && (rc = to_device(ctx, p->wt, weights, sizeof(double) * n_rows, s))) return rc;
+    if ((rc = lm_cuda_check(ctx, cudaMemsetAsync(p->d_flags, 0, sizeof(int), s), "memset")))
+        return rc;
     if ((rc = lm_launch_build(p, s))) return rc;
-    int flags = 0;
-    double E = 0.0;
-    cudaError_t e = cudaMemcpyAsync(&E, p->stats + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if ((rc = lm_cuda_check(ctx, e, "energy read-back"))) return rc;
-    if ((rc = lm_read_flags(ctx, s, &flags))) return rc;
-    p->E_host = E;
-    if (flags & FLAG_ROW_OUTSIDE_SECTOR)
-        return lm_fail(ctx, LM_ERR_ARG, "a row lies outside the (N_alpha, N_beta) sector");
+    cudaError_t e = cudaMemcpyAsync(&p->hs->E, p->stats + 1, sizeof(double),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&p->hs->flags, p->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    return lm_cuda_check(ctx, e, "energy read-back");
+}
+
+int lm_build_finish(lm_pencil *p) {
+    p->E_host = p->hs->E;
+    if (p->hs->flags & FLAG_ROW_OUTSIDE_SECTOR)
+        return lm_fail(p->ctx, LM_ERR_ARG, "a row lies outside the (N_alpha, N_beta) sector");
+    if (p->hs->flags & FLAG_TIMEOUT)
+        return lm_fail(p->ctx, LM_ERR_TIMEOUT, "a bounded wait of the build timed out");
     return LM_OK;
+}
+
+extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *theta,
+                           const uint64_t *rows, const double *weights, int64_t n_rows,
+                           lm_precision prec, void *stream, lm_pencil **inout) {
+    if (int rc = lm_build_enqueue(ctx, sys, theta, rows, weights, n_rows, prec, stream, inout))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = lm_cuda_check(ctx, cudaStreamSynchronize(s), "build")) return rc;
+    return lm_build_finish(*inout);
 }
 
 extern "C" int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double *Sv, int sym,
@@ -296,8 +318,31 @@ extern "C" int lm_pencil_info_get(lm_pencil *p, lm_pencil_info *out) {
     out->precision = p->prec;
     out->sym = p->sym;
     out->energy = p->E_host;
+    out->grid = p->g_pencil;
     return LM_OK;
 }
+
+extern "C" int lm_pencil_set_grid(lm_pencil *p, int ctas) {
+    if (!p) return LM_ERR_ARG;
+    if (ctas < 1 || ctas > p->ctx->sms)
+        return lm_fail(p->ctx, LM_ERR_ARG, "pencil grid %d outside 1..%d", ctas, p->ctx->sms);
+    p->g_pencil = ctas;  // the partials buffer holds one vector pair per SM
+    return LM_OK;
+}
+
+// Device bytes a pencil of this shape holds (the server's admission estimate).
+size_t lm_pencil_footprint(lm_ctx *ctx, int n, int nh, int64_t n_rows, int prec) {
+    const size_t M = 2 * n, P1 = (nh + 1) * (M + 1), L = (P1 + 7) / 8 * 8, nr = n_rows;
+    const size_t es = prec == LM_FP64 ? 0 : (prec == LM_FP32 ? 4 : (prec == LM_DF64 ? 8 : 2));
+    size_t b = nr * L * (16 + 2 * es);              // O, G and the low-precision copies
+    b += nr * (8 * 5 + 8);                         // rows, weights (x2), ln psi, E_loc
+    b += (size_t)n * n * n * n * 16 + 2 * 4 * nh * M * 8;  // integrals and tables
+    b += (size_t)ctx->sms * 2 * L * 8;             // partial products
+    b += 2 * (LM_MAXKRYLOV + 1) * L * 8 + 16 * L * 8 + (1 << 20);  // bases, vectors, state
+    return b;
+}
+
+void lm_pencil_release(lm_pencil *p) { pencil_release(p); }
 
 extern "C" int lm_pencil_free(lm_pencil *p) {
     if (!p) return LM_ERR_ARG;

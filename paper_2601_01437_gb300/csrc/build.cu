@@ -1168,7 +1168,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     A.eloc = p->eloc;
     A.O = p->O;
     A.G = p->G;
-    A.flags = ctx->d_flags;
+    A.flags = p->d_flags;
     if (p->nh + 1 > BUILD_THREADS)
         return lm_fail(ctx, LM_ERR_SIZE, "n_hidden + 1 = %d exceeds %d", p->nh + 1,
                        BUILD_THREADS);
@@ -1225,7 +1225,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         B.eloc = p->eloc;
         B.O = p->O;
         B.G = p->G;
-        B.flags = ctx->d_flags;
+        B.flags = p->d_flags;
         const size_t nh_ = p->nh, M_ = p->M;
         const size_t f2 = 2 * (size_t)B.ns * (nh_ | 1) + 2 * B.ns + nh_ + (size_t)BDF_K * B.ldF + BDF_K +
                           (size_t)B.nslice * (nh_ + 1) * B.ldS + (size_t)B.nslice * (nh_ + 1) +

@@ -152,6 +152,15 @@ struct IrlState {
     double lam, res, tnorm, tol_eff, bnorm;
     double rq, rq_s, res_explicit, c0, yty, lam_ritz;
     int jend, broke, conv, err;
+    int flags;  // this pencil's device error flags (FLAG_*), cleared at each IRL start
+};
+
+// Pinned host scratch of a pencil: the IRL state read-back, and the energy and
+// flags of the last build.
+struct PencilHost {
+    IrlState st;
+    double E;
+    int flags;
 };
 
 struct lm_pencil {
@@ -180,7 +189,9 @@ struct lm_pencil {
     double *V;          // ldp x (LM_MAXKRYLOV + 1), column-major
     double *wvec, *yvec, *hy, *sy, *tvec, *dots;
     IrlState *st;       // device
-    IrlState *st_host;  // pinned mirror
+    IrlState *st_host;  // pinned mirror (inside hs)
+    PencilHost *hs;     // pinned host scratch
+    int *d_flags;       // &st->flags: error flags of this pencil's kernels
     unsigned *bar;      // grid-barrier words of the cooperative Lanczos kernel
     double E_host;
 };
@@ -192,6 +203,27 @@ int lm_fail(lm_ctx *ctx, int code, const char *fmt, ...);
 int lm_cuda_check(lm_ctx *ctx, cudaError_t e, const char *what);
 bool lm_is_device_ptr(const void *p);
 int lm_read_flags(lm_ctx *ctx, cudaStream_t s, int *flags);
+// lm_build_OG in two halves: enqueue the build (and the read-back of E and the
+// flags into pinned memory) on `stream`; after that work has completed,
+// lm_build_finish checks the flags and publishes E.
+int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
+                     const uint64_t *rows, const double *weights, int64_t n_rows,
+                     lm_precision prec, void *stream, lm_pencil **inout);
+int lm_build_finish(lm_pencil *p);
+size_t lm_pencil_footprint(lm_ctx *ctx, int n, int nh, int64_t n_rows, int prec);
+void lm_pencil_release(lm_pencil *p);  // frees without a device-wide synchronisation
+
+// Resumable IRL (irl.cu): the host side of irl_step as a state machine.
+// irl_job_advance enqueues the next stretch of device work on the job's stream
+// and records the job's event; call it again once that event has completed
+// (the first call starts the job). *done = 1 when the result is final.
+struct IrlJob;
+int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *dtheta_out,
+                   double *theta_inout, cudaStream_t s, IrlJob **out);
+int irl_job_advance(IrlJob *job, int *done);
+cudaEvent_t irl_job_event(const IrlJob *job);
+void irl_job_result(const IrlJob *job, irl_result *out);
+void irl_job_free(IrlJob *job);
 
 // build.cu
 int lm_launch_enumerate(lm_ctx *ctx, int n, int na, int nb, uint64_t *out, int64_t count,

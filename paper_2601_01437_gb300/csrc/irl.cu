@@ -1246,8 +1246,11 @@ void choose_lanczos(Run &R, lm_ctx *ctx) {
             if (emax > CE || rmax > CROWS) continue;
             const size_t dyn = cluster_dyn_smem(R.m, emax);
             if (dyn + sizeof(LcShared) > (size_t)ctx->smem_optin) continue;
+            // the attribute is the kernel's, shared by every pencil whose jobs
+            // may be in flight at once (batches, the server): set the device's
+            // limit, which every launch's own size stays under
             if (cudaFuncSetAttribute(k_lz_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)dyn) != cudaSuccess) {
+                                     ctx->smem_optin - (int)sizeof(LcShared)) != cudaSuccess) {
                 cudaGetLastError();
                 continue;
             }
@@ -1354,74 +1357,149 @@ int start_vector(Run &R) {
     return lm_cuda_check(p->ctx, cudaGetLastError(), "start vector");
 }
 
-int run_irl(Run &R, double tol, double rel, int max_restarts, const double *v0_dev,
-            uint64_t seed) {
-    lm_pencil *p = R.p;
-    lm_ctx *ctx = p->ctx;
+}  // namespace
+
+// ---------------------------------------------------------------- job
+// The host side of one IRL solve as a resumable state machine. Each call of
+// advance() enqueues the next stretch of device work on the job's stream and
+// records the job's event after it:
+//   start of a phase: reset the state, start vector, first Lanczos cycle,
+//     tridiagonal solve and the state read-back;
+//   after a cycle: either an implicit restart and the next cycle, or the Ritz
+//     vector; a low-precision phase then hands its Ritz vector to the FP64 /
+//     double-float phase as start vector;
+//   refinement: explicit FP64 products, Rayleigh quotients and the update.
+// irl_step drives one job synchronously; the batch and server engines poll
+// many jobs on many streams. The kernel sequence of a job does not depend on
+// what else runs on the device, so its result does not either.
+enum { JOB_INIT = 0, JOB_CYCLE = 1, JOB_REFINE = 2, JOB_DONE = 3 };
+
+struct IrlJob {
+    Run R;
+    lm_pencil *p;
+    cudaStream_t s;
+    irl_params prm;
+    int state;
+    bool lowp, dfp, in_lowp;
+    int n_lowp, cycle, max_restarts;
+    double rel;
+    const double *v0_dev;
+    double *c_out, *dtheta_out, *theta_inout, *dth_tmp;
+    bool c_dev, d_dev, t_dev;
+    cudaEvent_t ev;
+};
+
+namespace {
+
+int job_check(IrlJob *J, const char *what) {
+    return lm_cuda_check(J->p->ctx, cudaGetLastError(), what);
+}
+
+// state read-back (IRL state and flags) on the job's stream, then the event
+int job_readback(IrlJob *J) {
+    lm_pencil *p = J->p;
+    cudaError_t e = cudaMemcpyAsync(p->st_host, p->st, sizeof(IrlState), cudaMemcpyDeviceToHost,
+                                    J->s);
+    if (e == cudaSuccess) e = cudaEventRecord(J->ev, J->s);
+    return lm_cuda_check(p->ctx, e, "IRL state read-back");
+}
+
+// Lanczos steps j0 .. m-1 and the tridiagonal work of one cycle
+int job_cycle(IrlJob *J, int j0) {
+    Run &R = J->R;
+    lm_pencil *p = J->p;
+    for (int j = j0; j < R.m; ++j)
+        if (int rc = lanczos_step(R, j)) return rc;
+    TriArgs ta;
+    ta.st = p->st;
+    ta.m = R.m;
+    ta.k = R.k;
+    ta.final_pass = J->cycle >= J->max_restarts;
+    ta.tol = J->prm.tol;
+    ta.rel = J->rel;
+    lm_prof_begin(p->ctx, PROF_TRI, R.s);
+    k_tri<<<1, TT, 0, R.s>>>(ta);
+    lm_prof_end(p->ctx, PROF_TRI, R.s);
+    lm_note_launch(p->ctx);
+    if (int rc = job_check(J, "k_tri")) return rc;
+    return job_readback(J);
+}
+
+// a phase: reset, start vector from v0 (or the seeded random vector), cycle 0
+int job_phase_start(IrlJob *J) {
+    Run &R = J->R;
+    lm_pencil *p = J->p;
+    if (J->in_lowp) {
+        R.prec = p->prec;
+        J->rel = p->prec == LM_FP32 ? 1e-6 : 1e-3;  // the storage format's resolution
+    } else {
+        R.prec = J->dfp ? LM_DF64 : LM_FP64;
+        J->rel = 50.0 * 2.220446049250313e-16;
+    }
+    J->cycle = 0;
     cudaMemsetAsync(p->st, 0, sizeof(IrlState), R.s);
     cudaMemsetAsync(p->bar, 0, 64 * sizeof(unsigned), R.s);
-    k_init_start<<<(p->ldp + 255) / 256, 256, 0, R.s>>>(p->wvec, p->ldp, p->P1, seed, v0_dev);
-    lm_note_launch(ctx);
+    k_init_start<<<(p->ldp + 255) / 256, 256, 0, R.s>>>(p->wvec, p->ldp, p->P1, J->prm.seed,
+                                                         J->v0_dev);
+    lm_note_launch(p->ctx);
+    if (int rc = job_check(J, "k_init_start")) return rc;
     if (int rc = start_vector(R)) return rc;
-    int j0 = 0;
-    for (int cycle = 0;; ++cycle) {
-        for (int j = j0; j < R.m; ++j)
-            if (int rc = lanczos_step(R, j)) return rc;
-        TriArgs ta;
-        ta.st = p->st;
-        ta.m = R.m;
-        ta.k = R.k;
-        ta.final_pass = cycle >= max_restarts;
-        ta.tol = tol;
-        ta.rel = rel;
-        lm_prof_begin(ctx, PROF_TRI, R.s);
-        k_tri<<<1, TT, 0, R.s>>>(ta);
-        lm_prof_end(ctx, PROF_TRI, R.s);
-        lm_note_launch(ctx);
-        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_tri")) return rc;
-        cudaError_t e = cudaMemcpyAsync(p->st_host, p->st, sizeof(IrlState),
-                                        cudaMemcpyDeviceToHost, R.s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(R.s);
-        if (int rc = lm_cuda_check(ctx, e, "IRL state read-back")) return rc;
-        int flags = 0;
-        if (int rc = lm_read_flags(ctx, R.s, &flags)) return rc;
-        if (flags & FLAG_TIMEOUT) return lm_fail(ctx, LM_ERR_TIMEOUT, "pencil pipeline wait timed out");
-        const IrlState &h = *p->st_host;
-        if (h.conv || h.broke || cycle >= max_restarts) break;
-        // implicit restart
-        double *Vnew = p->V + (size_t)(LM_MAXKRYLOV + 1) * p->ldp;
-        k_restart<<<R.la.nrow_grid, LT, 0, R.s>>>(R.la, Vnew, R.m, R.k);
-        lm_note_launch(ctx);
-        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_restart")) return rc;
-        // swap halves: the kept vectors now live in Vnew
-        cudaMemcpyAsync(p->V, Vnew, (size_t)R.k * p->ldp * sizeof(double),
-                        cudaMemcpyDeviceToDevice, R.s);
-        R.la.V = p->V;
-        k_lz_d<<<R.la.nrow_grid, LT, 0, R.s>>>(R.la, 0, R.k, 2);
-        lm_note_launch(ctx);
-        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "restart normalise")) return rc;
-        R.n_restart++;
-        j0 = R.k;
-    }
-    k_ritz_vector<<<(p->ldp + 255) / 256, 256, 0, R.s>>>(p->V, p->st, p->ldp, p->yvec);
+    return job_cycle(J, 0);
+}
+
+// explicit FP64 refinement: H~' y and S~ y in one pass, Rayleigh quotients,
+// residual, update; outputs to the caller's buffers; then the event
+int job_refine(IrlJob *J) {
+    Run &R = J->R;
+    lm_pencil *p = J->p;
+    lm_ctx *ctx = p->ctx;
+    cudaStream_t s = J->s;
+    if (int rc = lm_launch_pencil(p, p->yvec, R.sym, LM_FP64, 1, nullptr, s)) return rc;
+    if (int rc = lm_launch_reduce_partials(p, p->hy, p->sy, s)) return rc;
+    R.n_matvec++;
+    if (J->theta_inout && !J->t_dev)
+        cudaMemcpyAsync(p->tvec, J->theta_inout, (p->P1 - 1) * sizeof(double),
+                        cudaMemcpyHostToDevice, s);
+    int *status_dev = reinterpret_cast<int *>(&p->st->err);
+    k_refine<<<1, 1024, 0, s>>>(p->yvec, p->hy, p->sy, p->st, p->ldp, p->P1,
+                                J->c_dev ? J->c_out : nullptr,
+                                J->d_dev ? J->dtheta_out : J->dth_tmp,
+                                J->theta_inout ? (J->t_dev ? J->theta_inout : p->tvec) : nullptr,
+                                J->prm.tol, status_dev);
     lm_note_launch(ctx);
-    return lm_cuda_check(ctx, cudaGetLastError(), "k_ritz_vector");
+    if (int rc = job_check(J, "k_refine")) return rc;
+    if (J->c_out && !J->c_dev)
+        cudaMemcpyAsync(J->c_out, p->yvec, p->P1 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (J->dtheta_out && !J->d_dev)
+        cudaMemcpyAsync(J->dtheta_out, J->dth_tmp, (p->P1 - 1) * sizeof(double),
+                        cudaMemcpyDeviceToHost, s);
+    if (J->theta_inout && !J->t_dev)
+        cudaMemcpyAsync(J->theta_inout, p->tvec, (p->P1 - 1) * sizeof(double),
+                        cudaMemcpyDeviceToHost, s);
+    return job_readback(J);
 }
 
 }  // namespace
 
-extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, double *c_out,
-                        double *dtheta_out, double *theta_inout, void *stream) {
+int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *dtheta_out,
+                   double *theta_inout, cudaStream_t s, IrlJob **out) {
     if (!p || !prm || !out) return LM_ERR_ARG;
     lm_ctx *ctx = p->ctx;
-    cudaSetDevice(ctx->device);
-    cudaStream_t s = (cudaStream_t)stream;
     if (prm->m > LM_MAXKRYLOV || prm->m < 2 || prm->k < 1 || prm->k >= prm->m || prm->m > p->P1)
         return lm_fail(ctx, LM_ERR_SIZE, "need 1 <= k < m <= min(64, P+1); got k=%d m=%d", prm->k,
                        prm->m);
     if (prm->sym < 0 || prm->sym > 2 || prm->precision < 0 || prm->precision > 3)
         return lm_fail(ctx, LM_ERR_ARG, "bad sym or precision");
-    Run R;
+    IrlJob *J = new IrlJob();
+    J->p = p;
+    J->s = s;
+    J->prm = *prm;
+    J->state = JOB_INIT;
+    if (cudaEventCreateWithFlags(&J->ev, cudaEventDisableTiming) != cudaSuccess) {
+        delete J;
+        return lm_fail(ctx, LM_ERR_CUDA, "cudaEventCreate");
+    }
+    Run &R = J->R;
     R.p = p;
     R.s = s;
     R.m = prm->m;
@@ -1444,7 +1522,7 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
     R.la.deflate = prm->deflate_null;
     R.la.st = p->st;
     R.la.bar = p->bar;
-    R.la.flags = ctx->d_flags;
+    R.la.flags = p->d_flags;
     {
         // projection constants (see k_lz_cluster) as double-float pairs
         const double n = p->n, na = p->na, nb = p->nb;
@@ -1460,76 +1538,122 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
         R.la.gi22 = pair(g11 / det);
     }
     choose_lanczos(R, ctx);
-
-    // optional start vector to the device
-    const double *v0_dev = nullptr;
+    J->max_restarts = prm->max_restarts < 0 ? 0 : prm->max_restarts;
+    J->lowp = prm->precision != LM_FP64 && p->Olo != nullptr && p->prec != LM_DF64;
+    // double-float factors are accurate to ~1e-14: one phase at the FP64 tolerance
+    J->dfp = prm->precision != LM_FP64 && p->Olo != nullptr && p->prec == LM_DF64;
+    J->in_lowp = J->lowp;
+    J->n_lowp = 0;
+    J->v0_dev = nullptr;
+    J->c_out = c_out;
+    J->dtheta_out = dtheta_out;
+    J->theta_inout = theta_inout;
+    J->c_dev = c_out && lm_is_device_ptr(c_out);
+    J->d_dev = dtheta_out && lm_is_device_ptr(dtheta_out);
+    J->t_dev = theta_inout && lm_is_device_ptr(theta_inout);
+    J->dth_tmp = p->dots + (size_t)3 * (p->nh + 1) * DLD;  // scratch >= ldp
     if (prm->v0) {
         if (lm_is_device_ptr(prm->v0)) {
-            v0_dev = prm->v0;
+            J->v0_dev = prm->v0;
         } else {
             cudaMemcpyAsync(p->yvec, prm->v0, p->P1 * sizeof(double), cudaMemcpyHostToDevice, s);
-            v0_dev = p->yvec;
+            J->v0_dev = p->yvec;
         }
     }
-    const int max_restarts = prm->max_restarts < 0 ? 0 : prm->max_restarts;
-    int n_lowp = 0;
-    const bool lowp = prm->precision != LM_FP64 && p->Olo != nullptr && p->prec != LM_DF64;
-    // double-float factors are accurate to ~1e-14: one phase at the FP64 tolerance
-    const bool dfp = prm->precision != LM_FP64 && p->Olo != nullptr && p->prec == LM_DF64;
-    if (lowp) {
-        // Low-precision phase: stop at the relative residual the storage format
-        // supports, then continue the restarts with the FP64 operator from its
-        // Ritz vector until the requested tolerance.
-        R.prec = p->prec;
-        const double rel = p->prec == LM_FP32 ? 1e-6 : 1e-3;
-        if (int rc = run_irl(R, prm->tol, rel, max_restarts, v0_dev, prm->seed)) return rc;
-        n_lowp = R.n_matvec;
-        cudaMemcpyAsync(p->hy, p->yvec, p->ldp * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        v0_dev = p->hy;
-    }
-    R.prec = dfp ? LM_DF64 : LM_FP64;
-    if (int rc = run_irl(R, prm->tol, 50.0 * 2.220446049250313e-16, max_restarts, v0_dev,
-                         prm->seed))
-        return rc;
+    *out = J;
+    return LM_OK;
+}
 
-    // explicit FP64 refinement: H~' y and S~ y in one pass
-    if (int rc = lm_launch_pencil(p, p->yvec, R.sym, LM_FP64, 1, nullptr, s)) return rc;
-    if (int rc = lm_launch_reduce_partials(p, p->hy, p->sy, s)) return rc;
-    R.n_matvec++;
-    const bool c_dev = c_out && lm_is_device_ptr(c_out);
-    const bool d_dev = dtheta_out && lm_is_device_ptr(dtheta_out);
-    const bool t_dev = theta_inout && lm_is_device_ptr(theta_inout);
-    double *dth_tmp = p->dots + (size_t)3 * (p->nh + 1) * DLD;  // scratch >= ldp
-    if (theta_inout && !t_dev)
-        cudaMemcpyAsync(p->tvec, theta_inout, (p->P1 - 1) * sizeof(double),
-                        cudaMemcpyHostToDevice, s);
-    int *status_dev = reinterpret_cast<int *>(&p->st->err);
-    k_refine<<<1, 1024, 0, s>>>(p->yvec, p->hy, p->sy, p->st, p->ldp, p->P1,
-                                c_dev ? c_out : nullptr, d_dev ? dtheta_out : dth_tmp,
-                                theta_inout ? (t_dev ? theta_inout : p->tvec) : nullptr, prm->tol,
-                                status_dev);
-    lm_note_launch(ctx);
-    if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_refine")) return rc;
-    cudaMemcpyAsync(p->st_host, p->st, sizeof(IrlState), cudaMemcpyDeviceToHost, s);
-    if (c_out && !c_dev)
-        cudaMemcpyAsync(c_out, p->yvec, p->P1 * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (dtheta_out && !d_dev)
-        cudaMemcpyAsync(dtheta_out, dth_tmp, (p->P1 - 1) * sizeof(double), cudaMemcpyDeviceToHost,
-                        s);
-    if (theta_inout && !t_dev)
-        cudaMemcpyAsync(theta_inout, p->tvec, (p->P1 - 1) * sizeof(double),
-                        cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (int rc = lm_cuda_check(ctx, e, "irl_step")) return rc;
-    const IrlState &h = *p->st_host;
+int irl_job_advance(IrlJob *J, int *done) {
+    *done = 0;
+    lm_pencil *p = J->p;
+    lm_ctx *ctx = p->ctx;
+    Run &R = J->R;
+    if (J->state == JOB_INIT) {
+        J->state = JOB_CYCLE;
+        return job_phase_start(J);
+    }
+    if (J->state == JOB_CYCLE) {
+        const IrlState &h = *p->st_host;
+        if (h.flags & FLAG_TIMEOUT)
+            return lm_fail(ctx, LM_ERR_TIMEOUT, "pencil pipeline wait timed out");
+        if (!(h.conv || h.broke || J->cycle >= J->max_restarts)) {
+            // implicit restart, then the next cycle from j = k
+            double *Vnew = p->V + (size_t)(LM_MAXKRYLOV + 1) * p->ldp;
+            k_restart<<<R.la.nrow_grid, LT, 0, R.s>>>(R.la, Vnew, R.m, R.k);
+            lm_note_launch(ctx);
+            if (int rc = job_check(J, "k_restart")) return rc;
+            // swap halves: the kept vectors now live in Vnew
+            cudaMemcpyAsync(p->V, Vnew, (size_t)R.k * p->ldp * sizeof(double),
+                            cudaMemcpyDeviceToDevice, R.s);
+            R.la.V = p->V;
+            k_lz_d<<<R.la.nrow_grid, LT, 0, R.s>>>(R.la, 0, R.k, 2);
+            lm_note_launch(ctx);
+            if (int rc = job_check(J, "restart normalise")) return rc;
+            R.n_restart++;
+            J->cycle++;
+            return job_cycle(J, R.k);
+        }
+        k_ritz_vector<<<(p->ldp + 255) / 256, 256, 0, R.s>>>(p->V, p->st, p->ldp, p->yvec);
+        lm_note_launch(ctx);
+        if (int rc = job_check(J, "k_ritz_vector")) return rc;
+        if (J->in_lowp) {
+            // the low-precision Ritz vector starts the FP64 phase
+            J->n_lowp = R.n_matvec;
+            cudaMemcpyAsync(p->hy, p->yvec, p->ldp * sizeof(double), cudaMemcpyDeviceToDevice,
+                            R.s);
+            J->v0_dev = p->hy;
+            J->in_lowp = false;
+            return job_phase_start(J);
+        }
+        J->state = JOB_REFINE;
+        return job_refine(J);
+    }
+    if (J->state == JOB_REFINE) {
+        J->state = JOB_DONE;
+        *done = 1;
+        return LM_OK;
+    }
+    *done = 1;
+    return LM_OK;
+}
+
+cudaEvent_t irl_job_event(const IrlJob *J) { return J->ev; }
+
+void irl_job_result(const IrlJob *J, irl_result *out) {
+    const IrlState &h = *J->p->st_host;
     out->lambda = h.lam;
-    out->energy = p->E_host;
+    out->energy = J->p->E_host;
     out->lambda_gen_rq = h.rq_s;
     out->residual = h.res_explicit;
     out->c0 = h.c0;
     out->status = h.err;
-    out->n_matvec = R.n_matvec;
-    out->n_restart = R.n_restart;
-    out->n_matvec_lowp = n_lowp;
-    return LM_OK;
+    out->n_matvec = J->R.n_matvec;
+    out->n_restart = J->R.n_restart;
+    out->n_matvec_lowp = J->n_lowp;
+}
+
+void irl_job_free(IrlJob *J) {
+    if (!J) return;
+    cudaEventDestroy(J->ev);
+    delete J;
+}
+
+extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, double *c_out,
+                        double *dtheta_out, double *theta_inout, void *stream) {
+    if (!p || !prm || !out) return LM_ERR_ARG;
+    lm_ctx *ctx = p->ctx;
+    cudaSetDevice(ctx->device);
+    IrlJob *J = nullptr;
+    if (int rc = irl_job_create(p, prm, c_out, dtheta_out, theta_inout, (cudaStream_t)stream, &J))
+        return rc;
+    int done = 0, rc = LM_OK;
+    while (!rc && !done) {
+        rc = irl_job_advance(J, &done);
+        if (!rc && !done)
+            rc = lm_cuda_check(ctx, cudaEventSynchronize(J->ev), "irl_step");
+    }
+    if (!rc) irl_job_result(J, out);
+    irl_job_free(J);
+    return rc;
 }

@@ -196,8 +196,8 @@ struct NCV {
 };
 
 // One staged row: lane l owns columns k * 32 VEC + l VEC + [0, VEC) of chunk k
-// (ldp is a multiple of 32, so a chunk's last lanes are the only partial
-// ones, and they hold whole vectors or nothing). Row dot(s) by one butterfly,
+// (ldp is a multiple of 8 and so of VEC: in the last, partial chunk a lane
+// holds a whole vector or nothing). Row dot(s) by one butterfly,
 // then the rank-1 update of the register-resident y:
 // MODE_H_NONE: y += w (G.v) O; MODE_H_HALF: y += w/2 ((G.v) O + (O.v) G);
 // MODE_S: y += w (O.v) O.
@@ -459,7 +459,7 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
     a.stages = stages;
     a.rows_per_tile = R;
     a.skip = skip;
-    a.flags = p->ctx->d_flags;
+    a.flags = p->d_flags;
     a.out_df = out_df;
     cudaError_t e = cudaFuncSetAttribute(k_pencil<T, NJ, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

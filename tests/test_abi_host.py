@@ -44,6 +44,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(lm_system), sizeof(lm_pencil_info), sizeof(irl_params), sizeof(irl_result));
   printf("%zu %zu %zu %zu %zu\\n", offsetof(irl_params, seed), offsetof(irl_params, v0), offsetof(irl_result, status), offsetof(lm_pencil_info, energy), offsetof(lm_system, build_arith));
   printf("%zu %zu\\n", sizeof(lm_stats), offsetof(lm_stats, tri_count));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(lm_batch_item), offsetof(lm_batch_item, irl), offsetof(lm_batch_item, theta_inout), sizeof(lm_response), offsetof(lm_response, t_done_ms));
+  printf("%zu %zu\\n", sizeof(lm_pencil_info), offsetof(lm_pencil_info, grid));
   return 0; }
 """)
     exe = tmp_path / "layout"
@@ -54,7 +56,11 @@ int main(void) {
             ctypes.sizeof(lib.irl_params), ctypes.sizeof(lib.irl_result),
             lib.irl_params.seed.offset, lib.irl_params.v0.offset, lib.irl_result.status.offset,
             lib.lm_pencil_info.energy.offset, lib.lm_system.build_arith.offset,
-            ctypes.sizeof(lib.lm_stats), lib.lm_stats.tri_count.offset]
+            ctypes.sizeof(lib.lm_stats), lib.lm_stats.tri_count.offset,
+            ctypes.sizeof(lib.lm_batch_item), lib.lm_batch_item.irl.offset,
+            lib.lm_batch_item.theta_inout.offset, ctypes.sizeof(lib.lm_response),
+            lib.lm_response.t_done_ms.offset,
+            ctypes.sizeof(lib.lm_pencil_info), lib.lm_pencil_info.grid.offset]
     assert [int(x) for x in out] == want
 
 
