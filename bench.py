@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-pencil-c2", action="store_true",
                     help="skip the pencil-matvec HBM measurement on the LiCl-shaped MC pencil")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance batch")
+    ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving run")
+    ap.add_argument("--serve-seconds", type=float, default=1.0,
+                    help="length of the Poisson arrival stream of the serving run")
     ap.add_argument("--pencil", default="df64", choices=["df64", "fp64"],
                     help="storage of the FP64 workload's Lanczos pencil factors (both "
                          "FP64-accurate; the final refinement always uses FP64)")
@@ -343,6 +347,10 @@ def run_gpu(args, rank, world, local):
     state["pen"].free()
     if not args.no_pencil_c2 and rank == 0 and world == 1:
         out["pencil_c2"] = pencil_c2(abi, ctx, s, dev, hbm, hbm_src)
+    if not args.no_batched and rank == 0 and world == 1:
+        out["batched_c3"] = batched_c3(abi, ctx)
+    if not args.no_serving and rank == 0 and world == 1:
+        out["serving_c4"] = serving_c4(abi, ctx, seconds=args.serve_seconds)
     ctx.close()
     return out
 
@@ -387,6 +395,172 @@ def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10):
     out["workload"] = (f"{w.name}: {w.n_rows} MC rows x P+1 = {p1}, symmetrised H~' product, "
                        f"peak = {hbm_src} hbm_gbs")
     return out
+
+
+def batched_c3(abi, ctx, steps=3, warmup=1, n_streams=16):
+    """64 uneven independent instances (8-10 orbitals, 6-14 electrons, 784-14,400
+    determinants, Nh 16-40), one LM step each per batch call: FP32 O/G copies,
+    FP64 continuation and refinement, autotuned pencil grids, 16 streams. Against
+    the same instances solved one after another in plain FP64 (FP64 O/G)."""
+    import torch
+    inst = synth.batched_instances(64)
+    data = []
+    for w in inst:
+        h, eri, th, _, _ = w.inputs()
+        data.append((w, h, eri, th))
+
+    def items(prec, thetas, dths):
+        out = []
+        for (w, h, eri, _), th, d in zip(data, thetas, dths):
+            out.append({"sys": ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri),
+                        "theta": th, "theta_inout": th, "dtheta_out": d, "precision": prec,
+                        "irl": abi.irl_settings(m=w.m, k=w.k, tol=w.tol, prec=prec)})
+        return out
+
+    b = abi.Batch(ctx, n_streams=n_streams, autotune=True)
+    thetas = [d[3].copy() for d in data]
+    dths = [np.zeros(d[0].n_params) for d in data]
+    for _ in range(warmup):
+        res, grids = b.run(items(abi.LM_FP32, thetas, dths))
+    thetas = [d[3].copy() for d in data]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        res, grids = b.run(items(abi.LM_FP32, thetas, dths))
+    el = time.perf_counter() - t0
+    b.free()
+    # mixed vs FP64 on the same (first-step) parameters
+    th0 = [d[3].copy() for d in data]
+    b32 = abi.Batch(ctx, n_streams=n_streams, autotune=True)
+    r32, _ = b32.run(items(abi.LM_FP32, [t.copy() for t in th0], [np.zeros_like(x) for x in dths]))
+    b32.free()
+    # the plain per-instance path: each instance alone (its own resident pencil,
+    # created in an untimed first pass), FP64 O/G, one after another
+    pens, r64 = [], []
+    for w, h, eri, th in data:
+        sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri)
+        pen = ctx.build_OG(sysd, th.copy(), prec=abi.LM_FP64)
+        r64.append(pen.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200, prec=abi.LM_FP64))
+        pens.append((sysd, pen))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for (w, h, eri, th), (sysd, pen) in zip(data, pens):
+        ctx.build_OG(sysd, th, prec=abi.LM_FP64, pencil=pen)
+        pen.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200, prec=abi.LM_FP64)
+    el64 = time.perf_counter() - t1
+    for _, pen in pens:
+        pen.free()
+    err = max(abs(a.lambda_ - c.lambda_) for a, c in zip(r32, r64))
+    sizes = [w.n_det for w, _, _, _ in data]
+    return {"workload": f"batched_64: 64 instances, {min(sizes)}-{max(sizes)} determinants, "
+                        f"P+1 {min(w.n_params for w, *_ in data) + 1}-"
+                        f"{max(w.n_params for w, *_ in data) + 1}, m=20 k=1, FP32 O/G with FP64 "
+                        f"refinement, {n_streams} streams, autotuned pencil grids",
+            "value": 64 * steps / el, "unit": "LM steps/s", "steps": steps, "warmup": warmup,
+            "ms_per_batch": el / steps * 1e3,
+            "fp64_sequential": {"value": 64 / el64, "unit": "LM steps/s",
+                                "path": "each instance alone, FP64 O/G, one stream"},
+            "speedup_vs_fp64_sequential": (64 * steps / el) / (64 / el64),
+            "max_abs_lambda_err_vs_fp64_ha": err,
+            "grids": sorted(set(int(g) for g in grids))}
+
+
+def serving_c4(abi, ctx, seconds=1.0, rate=200.0, n_streams=16, seed=111):
+    """Poisson LM-step requests at `rate` per second for `seconds`, 60/30/10 % of
+    c0-, c1- and c2-sized systems (6, 3 and 1 systems), continuous admission under a
+    150 GB budget; latency from submit to result. Against the same requests solved
+    one after another in plain FP64 (a bounded sample)."""
+    classes = []
+    for name, count in (("tiny_6o6e", 6), ("f2_10o14e", 3), ("licl_14o14e_mc", 1)):
+        base = synth.WORKLOADS[name]
+        members = []
+        for k in range(count):
+            w = synth.Workload(**{**base.__dict__, "seed": base.seed + k})
+            h, eri, th, rows, cnt = w.inputs()
+            members.append((w, h, eri, th, rows, None if cnt is None else cnt.astype(np.float64)))
+        classes.append(members)
+    srv = abi.Server(ctx, hbm_budget_bytes=150 << 30, n_streams=n_streams, autotune=True)
+    sids = []
+    for members in classes:
+        ids = []
+        for (w, h, eri, th, rows, wts) in members:
+            ids.append(srv.add_system(ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri),
+                                      rows=rows, weights=wts, precision=abi.LM_FP32))
+        sids.append(ids)
+    # warm every system once (pencil creation, grid tuning) before the stream starts
+    for c, members in enumerate(classes):
+        for k, (w, *_rest) in enumerate(members):
+            srv.submit(sids[c][k], members[k][3], abi.irl_settings(m=w.m, k=w.k, tol=w.tol,
+                                                                   prec=abi.LM_FP32))
+    warm = 0
+    while warm < sum(len(m) for m in classes):
+        warm += len(srv.poll())
+    times, cls = synth.poisson_arrivals(rate, seconds, seed)
+    rr = [0, 0, 0]
+    reqs = []
+    for c in cls:
+        k = rr[c] % len(classes[c])
+        rr[c] += 1
+        reqs.append((c, k))
+    outs = {}
+    done = []
+    t0 = time.perf_counter()
+    i = 0
+    while len(done) < len(reqs):
+        now = time.perf_counter() - t0
+        while i < len(reqs) and times[i] <= now:
+            c, k = reqs[i]
+            w = classes[c][k][0]
+            out = np.zeros(w.n_params)
+            t = srv.submit(sids[c][k], classes[c][k][3],
+                           abi.irl_settings(m=w.m, k=w.k, tol=w.tol, prec=abi.LM_FP32), out)
+            outs[t] = (c, out)
+            i += 1
+        got = srv.poll()
+        done += got
+        if not got:
+            time.sleep(0.0002)
+    wall = time.perf_counter() - t0
+    srv.free()
+    lat = np.array([r.t_done_ms - r.t_submit_ms for r in done])
+    by_cls = {}
+    for r in done:
+        by_cls.setdefault(outs[r.ticket][0], []).append(r.t_done_ms - r.t_submit_ms)
+    bad = sum(1 for r in done if r.status != abi.LM_OK)
+    # plain FP64 sequential baseline on a bounded sample in the same class mix
+    sample = reqs[:40]
+    pens = {}
+    for c, k in sorted(set(sample)):  # one resident FP64 pencil per system, built untimed
+        w, h, eri, th, rows, wts = classes[c][k]
+        sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri)
+        pens[c, k] = (sysd, ctx.build_OG(sysd, th, rows=rows, weights=wts, n_rows=w.n_rows,
+                                         prec=abi.LM_FP64))
+    t1 = time.perf_counter()
+    for c, k in sample:
+        w, h, eri, th, rows, wts = classes[c][k]
+        sysd, pen = pens[c, k]
+        ctx.build_OG(sysd, th, rows=rows, weights=wts, n_rows=w.n_rows, prec=abi.LM_FP64,
+                     pencil=pen)
+        pen.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200, prec=abi.LM_FP64)
+    seq = len(sample) / (time.perf_counter() - t1)
+    for _, pen in pens.values():
+        pen.free()
+    names = ["c0 tiny_6o6e", "c1 f2_10o14e", "c2 licl_14o14e_mc"]
+    return {"workload": f"serving: Poisson {rate:g} req/s for {seconds:g} s "
+                        f"({len(reqs)} requests), mix 60/30/10 % of c0/c1/c2 sizes over 6/3/1 "
+                        f"systems, FP32 O/G with FP64 refinement, {n_streams} streams, "
+                        "150 GB budget",
+            "completed": len(done), "errors": bad,
+            "throughput": len(done) / wall, "unit": "LM steps/s",
+            "offered_rate": len(reqs) / seconds,
+            "utilisation": (len(reqs) / seconds) / (len(done) / wall),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99)),
+                           "by_class_p50": {names[c]: float(np.percentile(v, 50))
+                                            for c, v in sorted(by_cls.items())}},
+            "fp64_sequential": {"value": seq, "unit": "LM steps/s",
+                                "sample": f"first {len(sample)} requests of the stream, "
+                                          "each built and solved alone with FP64 O/G"}}
 
 
 # ------------------------------------------------------------------ oracle (CPU)

@@ -275,11 +275,16 @@ __device__ __forceinline__ void consume_row(const T *ro, const T *rg, const type
 // Every wait is bounded; a timeout sets FLAG_TIMEOUT and the CTA drains its
 // outstanding copies before exiting.
 // Consumer warp w waits on full[i % S] with parity (i / S) & 1. That parity
-// names phase i / S unambiguously only while the stage's previous fill (row
-// i - S) has already landed, which holds when each warp's previous row i - C is
-// at or after i - S, i.e. when the number C of consuming warps is at most S.
-// So C = min(NCW, S); with fewer stages than warps the extra warps only join
-// the final sum with zero accumulators.
+// names phase i / S unambiguously only if the stage's previous fill (tile
+// i - S) has already landed when the warp starts to wait. Bulk copies may land
+// in any order, so "an earlier tile has landed" does not follow from a later
+// one having landed: it holds only for tiles the same warp has itself waited
+// for. With C consuming warps taking tiles w, w + C, ..., tile i - S is one of
+// warp w's own earlier tiles exactly when S is a multiple of C. So C =
+// min(NCW, S) and the launch rounds S down to a multiple of C (with fewer
+// stages than warps the extra warps only join the final sum with zero
+// accumulators). The producer's waits on `empty` need no such condition: it
+// refills a stage only after its own wait on that stage's previous release.
 // consumer warps: 16 for rows up to 896 columns, 8 (more registers each) beyond
 template <int NJ>
 struct Ncw {
@@ -294,7 +299,7 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
     if (a.skip && *a.skip) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ldp = a.ldp, S = a.stages, R = a.rows_per_tile;
-    const int ncons = min(NCW, S);  // consuming warps; see the parity note above
+    const int ncons = min(NCW, S);  // consuming warps (S is a multiple); see the note above
     const int nmat = MODE == MODE_S ? 1 : 2;
     const size_t row_elems = (size_t)ldp;
     const size_t tile_elems = (size_t)R * row_elems;  // one matrix's rows of a stage
@@ -440,11 +445,12 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
     const size_t tile_bytes = (size_t)R * row_bytes;
     const size_t tail = (size_t)p->ldp * sizeof(typename PA<T>::A) + 256;
     const size_t budget = (size_t)p->ctx->smem_optin - tail - 2048;
-    const int stages = (int)std::min<size_t>(32, budget / (tile_bytes + 2 * sizeof(uint64_t)));
+    constexpr int NCW = Ncw<NJ>::value;
+    int stages = (int)std::min<size_t>(32, budget / (tile_bytes + 2 * sizeof(uint64_t)));
     if (stages < 2)
         return lm_fail(p->ctx, LM_ERR_SIZE, "pencil row of %d columns too long", p->ldp);
+    stages -= stages % std::min(NCW, stages);  // a multiple of the consuming warps
     size_t smem = stages * (tile_bytes + 2 * sizeof(uint64_t)) + tail;
-    constexpr int NCW = Ncw<NJ>::value;
     smem = std::max(smem, (size_t)NCW * p->ldp * sizeof(double) + 64);
     PencilArgs<T> a;
     a.O = O;
@@ -536,11 +542,12 @@ int raw_launch(const double *O, const double *G, const double *w, int64_t n_rows
     const size_t row_bytes = (size_t)nmat * ldp * sizeof(double);
     const size_t tail = (size_t)ldp * sizeof(double) + 256;
     const size_t budget = (size_t)smem_optin - tail - 2048;
-    const int stages = (int)std::min<size_t>(32, budget / (row_bytes + 2 * sizeof(uint64_t)));
+    constexpr int NCW = Ncw<NJ>::value;
+    int stages = (int)std::min<size_t>(32, budget / (row_bytes + 2 * sizeof(uint64_t)));
     const int R = 1;
     if (stages < 2) return LM_ERR_SIZE;
+    stages -= stages % std::min(NCW, stages);  // a multiple of the consuming warps
     size_t smem = stages * (row_bytes + 2 * sizeof(uint64_t)) + tail;
-    constexpr int NCW = Ncw<NJ>::value;
     smem = std::max(smem, (size_t)NCW * ldp * sizeof(double) + 64);
     PencilArgs<double> a;
     a.O = O;

@@ -226,6 +226,20 @@ def test_pencil_products_fewer_stages_than_warps(ctx, abi, n, na, nb, nh, mc, pr
     pen.free()
 
 
+@pytest.mark.parametrize("n,na,nb,nh", [(10, 7, 7, 35), (10, 3, 3, 36)], ids=["ldp760", "ldp784"])
+def test_pencil_products_stage_count_multiple(ctx, abi, n, na, nb, nh):
+    """FP32 rows of 760 / 784 columns: two rows per pipeline stage, and a shared-memory
+    ring that holds 18 stages for 16 consumer warps unless the launch rounds it to a
+    multiple of them (bulk copies land in any order). Repeated products must all match."""
+    h, eri = synth.integrals(n, 41)
+    th = synth.rbm_theta(n, nh, 41, sigma=0.05)
+    pen, pd = _build_both(ctx, abi, n, na, nb, nh, h, eri, th, prec=abi.LM_FP32)
+    for _ in range(3):
+        _check_products(abi, pen, pd, abi.LM_SYM_NONE, nvec=2, tol=2e-6, prec=abi.LM_FP32)
+        _check_products(abi, pen, pd, abi.LM_SYM_HALF, nvec=1, tol=2e-6, prec=abi.LM_FP32)
+    pen.free()
+
+
 # ------------------------------------------------------------------ IRL
 def _irl_case(ctx, abi, w, theta=None, rows=None, counts=None, prec=0):
     h, eri, th, _, _ = w.inputs()
