@@ -25,6 +25,32 @@ int lm_cuda_check(lm_ctx *ctx, cudaError_t e, const char *what) {
     return lm_fail(ctx, LM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+bool lm_is_pageable(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeUnregistered;
+}
+
+double *lm_stage_irl(lm_pencil *p, int which) {
+    return reinterpret_cast<double *>(p->hstage + p->st_out) + (size_t)which * p->ldp;
+}
+
+int lm_stage_h2d(lm_pencil *p, void *dst, const void *src, size_t n, size_t off, cudaStream_t s) {
+    if (n == 0) return LM_OK;
+    cudaMemcpyKind kind = cudaMemcpyHostToDevice;
+    if (lm_is_device_ptr(src)) {
+        kind = cudaMemcpyDeviceToDevice;
+    } else if (lm_is_pageable(src)) {
+        std::memcpy(p->hstage + off, src, n);
+        src = p->hstage + off;
+    }
+    return lm_cuda_check(p->ctx, cudaMemcpyAsync(dst, src, n, kind, s), "input copy");
+}
+
 bool lm_is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes at;
@@ -87,6 +113,7 @@ void pencil_release(lm_pencil *p) {
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->hs) cudaFreeHost(p->hs);
+    if (p->hstage) cudaFreeHost(p->hstage);
     delete p;
 }
 
@@ -226,6 +253,14 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
         if (!rc)
             rc = lm_cuda_check(ctx, cudaMallocHost(&p->hs, sizeof(PencilHost)), "cudaMallocHost");
         if (!rc) {
+            const size_t in_fixed = 8 * ((size_t)n * n + (size_t)n * n * n * n + L);
+            p->st_in_rows = (in_fixed + 255) / 256 * 256;
+            p->st_in_w = p->st_in_rows + (8 * nr + 255) / 256 * 256;
+            p->st_out = p->st_in_w + (8 * nr + 255) / 256 * 256;
+            rc = lm_cuda_check(ctx, cudaMallocHost(&p->hstage, p->st_out + 4 * 8 * L + 256),
+                               "cudaMallocHost");
+        }
+        if (!rc) {
             p->st_host = &p->hs->st;
             p->d_flags = &p->st->flags;
             rc = lm_cuda_check(ctx, cudaMemsetAsync(p->st, 0, sizeof(IrlState), s), "memset");
@@ -245,17 +280,22 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
         return lm_fail(ctx, LM_ERR_ARG, "bad build_arith %d", sys->build_arith);
     p->arith = sys->build_arith;
     int rc = 0;
-    rc = rc ? rc : to_device(ctx, p->h, sys->h, sizeof(double) * n * n, s);
-    rc = rc ? rc : to_device(ctx, p->eri, sys->eri, sizeof(double) * n * n * n * n, s);
-    rc = rc ? rc : to_device(ctx, p->theta, theta, sizeof(double) * (P1 - 1), s);
+    const size_t nn = (size_t)n * n;
+    rc = rc ? rc : lm_stage_h2d(p, p->h, sys->h, sizeof(double) * nn, 0, s);
+    rc = rc ? rc : lm_stage_h2d(p, p->eri, sys->eri, sizeof(double) * nn * nn, 8 * nn, s);
+    rc = rc ? rc : lm_stage_h2d(p, p->theta, theta, sizeof(double) * (P1 - 1),
+                                8 * (nn + nn * nn), s);
     if (rc) return rc;
     if (enumerate) {
         if ((rc = lm_launch_enumerate(ctx, n, sys->n_alpha, sys->n_beta, p->rows, n_rows, s)))
             return rc;
-    } else if ((rc = to_device(ctx, p->rows, rows, sizeof(uint64_t) * n_rows, s))) {
+    } else if ((rc = lm_stage_h2d(p, p->rows, rows, sizeof(uint64_t) * n_rows, p->st_in_rows,
+                                  s))) {
         return rc;
     }
-    if (weights && (rc = to_device(ctx, p->wt, weights, sizeof(double) * n_rows, s))) return rc;
+    if (weights &&
+        (rc = lm_stage_h2d(p, p->wt, weights, sizeof(double) * n_rows, p->st_in_w, s)))
+        return rc;
     if ((rc = lm_cuda_check(ctx, cudaMemsetAsync(p->d_flags, 0, sizeof(int), s), "memset")))
         return rc;
     if ((rc = lm_launch_build(p, s))) return rc;

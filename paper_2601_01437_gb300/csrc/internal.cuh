@@ -191,6 +191,13 @@ struct lm_pencil {
     IrlState *st;       // device
     IrlState *st_host;  // pinned mirror (inside hs)
     PencilHost *hs;     // pinned host scratch
+    // Pinned staging of caller host arrays: a copy from or to pageable host
+    // memory synchronises its stream (to) or the host (from), which would
+    // serialise concurrent instances. Inputs are copied here on the host and
+    // sent asynchronously; host outputs land here and are copied out when the
+    // job completes. Layout: LM_STAGE_* offsets below.
+    unsigned char *hstage;
+    size_t st_in_rows, st_in_w, st_out;  // byte offsets of rows, weights, IRL region
     int *d_flags;       // &st->flags: error flags of this pencil's kernels
     unsigned *bar;      // grid-barrier words of the cooperative Lanczos kernel
     double E_host;
@@ -211,6 +218,15 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
                      lm_precision prec, void *stream, lm_pencil **inout);
 int lm_build_finish(lm_pencil *p);
 size_t lm_pencil_footprint(lm_ctx *ctx, int n, int nh, int64_t n_rows, int prec);
+// Staging regions: h at 0, eri after it, theta after that (ldp doubles), rows
+// at st_in_rows, weights at st_in_w; the IRL region at st_out holds four ldp
+// vectors: theta_inout, c, dtheta, v0.
+enum { LM_STAGE_TIO = 0, LM_STAGE_C = 1, LM_STAGE_DTH = 2, LM_STAGE_V0 = 3 };
+double *lm_stage_irl(lm_pencil *p, int which);
+// Copy n bytes of a caller array (device, pinned or pageable host) to device
+// memory on stream s; pageable sources go through the pencil's staging at off.
+int lm_stage_h2d(lm_pencil *p, void *dst, const void *src, size_t n, size_t off, cudaStream_t s);
+bool lm_is_pageable(const void *ptr);
 void lm_pencil_release(lm_pencil *p);  // frees without a device-wide synchronisation
 
 // Resumable IRL (irl.cu): the host side of irl_step as a state machine.

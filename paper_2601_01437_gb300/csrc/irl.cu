@@ -1246,11 +1246,8 @@ void choose_lanczos(Run &R, lm_ctx *ctx) {
             if (emax > CE || rmax > CROWS) continue;
             const size_t dyn = cluster_dyn_smem(R.m, emax);
             if (dyn + sizeof(LcShared) > (size_t)ctx->smem_optin) continue;
-            // the attribute is the kernel's, shared by every pencil whose jobs
-            // may be in flight at once (batches, the server): set the device's
-            // limit, which every launch's own size stays under
             if (cudaFuncSetAttribute(k_lz_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     ctx->smem_optin - (int)sizeof(LcShared)) != cudaSuccess) {
+                                     (int)dyn) != cudaSuccess) {
                 cudaGetLastError();
                 continue;
             }
@@ -1324,6 +1321,13 @@ int lanczos_vectors(Run &R, int j) {
         cfg.blockDim = dim3(CT);
         cfg.dynamicSmemBytes = cluster_dyn_smem(j + 1, R.cluster_emax);
         cfg.stream = R.s;
+        // The limit is an attribute of the kernel, shared by every pencil whose
+        // jobs may be in flight at once (batches, the server): set it to this
+        // launch's size right before the launch (all launches come from one
+        // host thread).
+        if (cudaFuncSetAttribute(k_lz_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cfg.dynamicSmemBytes) != cudaSuccess)
+            return lm_cuda_check(p->ctx, cudaGetLastError(), "cluster smem attribute");
         cfg.attrs = at;
         cfg.numAttrs = 1;
         cudaError_t e = cudaLaunchKernelEx(&cfg, k_lz_cluster, R.la, j);
@@ -1457,9 +1461,11 @@ int job_refine(IrlJob *J) {
     if (int rc = lm_launch_pencil(p, p->yvec, R.sym, LM_FP64, 1, nullptr, s)) return rc;
     if (int rc = lm_launch_reduce_partials(p, p->hy, p->sy, s)) return rc;
     R.n_matvec++;
+    const size_t stage_vec = (size_t)8 * p->ldp;
     if (J->theta_inout && !J->t_dev)
-        cudaMemcpyAsync(p->tvec, J->theta_inout, (p->P1 - 1) * sizeof(double),
-                        cudaMemcpyHostToDevice, s);
+        if (int rc = lm_stage_h2d(p, p->tvec, J->theta_inout, (p->P1 - 1) * sizeof(double),
+                                  p->st_out + LM_STAGE_TIO * stage_vec, s))
+            return rc;
     int *status_dev = reinterpret_cast<int *>(&p->st->err);
     k_refine<<<1, 1024, 0, s>>>(p->yvec, p->hy, p->sy, p->st, p->ldp, p->P1,
                                 J->c_dev ? J->c_out : nullptr,
@@ -1468,13 +1474,15 @@ int job_refine(IrlJob *J) {
                                 J->prm.tol, status_dev);
     lm_note_launch(ctx);
     if (int rc = job_check(J, "k_refine")) return rc;
+    // host outputs land in the pinned staging; irl_job_advance copies them out
     if (J->c_out && !J->c_dev)
-        cudaMemcpyAsync(J->c_out, p->yvec, p->P1 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(lm_stage_irl(p, LM_STAGE_C), p->yvec, p->P1 * sizeof(double),
+                        cudaMemcpyDeviceToHost, s);
     if (J->dtheta_out && !J->d_dev)
-        cudaMemcpyAsync(J->dtheta_out, J->dth_tmp, (p->P1 - 1) * sizeof(double),
+        cudaMemcpyAsync(lm_stage_irl(p, LM_STAGE_DTH), J->dth_tmp, (p->P1 - 1) * sizeof(double),
                         cudaMemcpyDeviceToHost, s);
     if (J->theta_inout && !J->t_dev)
-        cudaMemcpyAsync(J->theta_inout, p->tvec, (p->P1 - 1) * sizeof(double),
+        cudaMemcpyAsync(lm_stage_irl(p, LM_STAGE_TIO), p->tvec, (p->P1 - 1) * sizeof(double),
                         cudaMemcpyDeviceToHost, s);
     return job_readback(J);
 }
@@ -1556,7 +1564,11 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
         if (lm_is_device_ptr(prm->v0)) {
             J->v0_dev = prm->v0;
         } else {
-            cudaMemcpyAsync(p->yvec, prm->v0, p->P1 * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (int rc = lm_stage_h2d(p, p->yvec, prm->v0, p->P1 * sizeof(double),
+                                      p->st_out + LM_STAGE_V0 * (size_t)8 * p->ldp, s)) {
+                irl_job_free(J);
+                return rc;
+            }
             J->v0_dev = p->yvec;
         }
     }
@@ -1611,6 +1623,14 @@ int irl_job_advance(IrlJob *J, int *done) {
     }
     if (J->state == JOB_REFINE) {
         J->state = JOB_DONE;
+        if (J->c_out && !J->c_dev)
+            std::memcpy(J->c_out, lm_stage_irl(p, LM_STAGE_C), p->P1 * sizeof(double));
+        if (J->dtheta_out && !J->d_dev)
+            std::memcpy(J->dtheta_out, lm_stage_irl(p, LM_STAGE_DTH),
+                        (p->P1 - 1) * sizeof(double));
+        if (J->theta_inout && !J->t_dev)
+            std::memcpy(J->theta_inout, lm_stage_irl(p, LM_STAGE_TIO),
+                        (p->P1 - 1) * sizeof(double));
         *done = 1;
         return LM_OK;
     }
