@@ -473,6 +473,7 @@ struct BuildDfArgs {
     SysView S;
     int nh, M, M1, P1, ldp;
     int ldF, ldS, nslice, ns;  // ns = number of single excitations of a row
+    int fuseB;  // keep only the B table; A_s[j] = g_j B_s[j] formed on the fly
     const double *theta;
     const float2 *tdf;  // df tables (see k_tables_df)
     const uint64_t *rows;
@@ -614,8 +615,8 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     int2 *sSs = reinterpret_cast<int2 *>(sIdx + BDF_K);          // [K] single indices
     RowLists *sL = reinterpret_cast<RowLists *>(sSs + BDF_K);   // 1
     const int ldA = nh | 1;  // odd row stride: the connections of a warp hit distinct banks
-    float2 *sA = reinterpret_cast<float2 *>(sL + 1);            // [NS][ldA]  A_s[j]
-    float2 *sB = sA + NS * ldA;                                 // [NS][ldA]  B_s[j]
+    float2 *sA = reinterpret_cast<float2 *>(sL + 1);            // [NS][ldA]  A_s[j] (unless fuseB)
+    float2 *sB = sA + (A.fuseB ? 0 : NS * ldA);                 // [NS][ldA]  B_s[j]
     float2 *sV = sB + NS * ldA;                                 // [NS]
     float2 *sHs = sV + NS;                                      // [NS] singles' <x'|H|x>
     float2 *sTd = sHs + NS;                                     // [nh] t as df
@@ -759,7 +760,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             const df b = df_mul(ldg_df((pos ? e2 : e2i) + j * M + a),
                                 ldg_df((pos ? e2i : e2) + j * M + i));
             st_df(sB + s * ldA + j, b);
-            st_df(sA + s * ldA + j, df_mul(ld_df(sGd + j), b));
+            if (!A.fuseB) st_df(sA + s * ldA + j, df_mul(ld_df(sGd + j), b));
         }
         for (int s = tid; s < NS; s += BDF_THREADS) {
             int i, a;
@@ -804,7 +805,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 // the running product of (1 + Z_j) stays >= 1 and is rescaled past 2^60
 #pragma unroll 2
                 for (int j = sub; j < nh; j += BDF_TPC) {
-                    df z = ld_df(a1 + j);
+                    df z = A.fuseB ? df_mul(ld_df(sGd + j), ld_df(sB + s1 * ldA + j)) : ld_df(a1 + j);
                     if (s2 >= 0) z = df_mul(z, ld_df(b2 + j));
                     const df zp = df_add1(z, 1.f);
                     const df u = df_rcp_ge1(zp);
@@ -1214,6 +1215,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         B.ldS = p->M | 1;
         B.nslice = std::max(1, BDF_THREADS / (p->nh + 1));
         B.ns = A.S.ns_a + A.S.ns_b;
+        B.fuseB = 0;
         B.theta = p->theta;
         B.tdf = p->tdf;
         B.rows = p->rows;
@@ -1227,18 +1229,36 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         B.G = p->G;
         B.flags = p->d_flags;
         const size_t nh_ = p->nh, M_ = p->M;
-        const size_t f2 = 2 * (size_t)B.ns * (nh_ | 1) + 2 * B.ns + nh_ + (size_t)BDF_K * B.ldF + BDF_K +
-                          (size_t)B.nslice * (nh_ + 1) * B.ldS + (size_t)B.nslice * (nh_ + 1) +
-                          BDF_THREADS / 32;
-        const size_t dsm = BDF_K * (sizeof(int4) + sizeof(int2)) + sizeof(RowLists) +
-                           f2 * sizeof(float2) + (3 * nh_ + 2 * M_) * sizeof(double) +
-                           nh_ * (sizeof(float2) + sizeof(float)) + B.ns * sizeof(int) + 64;
+        auto smem_of = [&](int fuse, int nsl) {
+            const size_t f2 = (size_t)(fuse ? 1 : 2) * B.ns * (nh_ | 1) + 2 * B.ns + nh_ +
+                              (size_t)BDF_K * B.ldF + BDF_K + (size_t)nsl * (nh_ + 1) * B.ldS +
+                              (size_t)nsl * (nh_ + 1) + BDF_THREADS / 32;
+            return BDF_K * (sizeof(int4) + sizeof(int2)) + sizeof(RowLists) +
+                   f2 * sizeof(float2) + (3 * nh_ + 2 * M_) * sizeof(double) +
+                   nh_ * (sizeof(float2) + sizeof(float)) + B.ns * sizeof(int) + 64;
+        };
+        // Large systems (many single excitations) would hold one CTA per SM:
+        // dropping the A table (one more double-float product per connection
+        // and hidden unit) and halving the scatter slices can fit a second.
+        // Take the first variant that reaches the most CTAs per SM.
+        auto per_sm_of = [&](size_t bytes) { return (int)(233472 / (bytes + 1024)); };
+        {
+            const int v_nsl[3] = {B.nslice, B.nslice, std::max(1, B.nslice / 2)};
+            const int v_fuse[3] = {0, 1, 1};
+            int best = 0;
+            for (int v = 1; v < 3; ++v)
+                if (per_sm_of(smem_of(v_fuse[v], v_nsl[v])) > per_sm_of(smem_of(v_fuse[best], v_nsl[best])))
+                    best = v;
+            B.fuseB = v_fuse[best];
+            B.nslice = v_nsl[best];
+        }
+        const size_t dsm = smem_of(B.fuseB, B.nslice);
         if (dsm > (size_t)ctx->smem_optin)
             return lm_fail(ctx, LM_ERR_SIZE, "df64 build kernel needs %zu B shared memory", dsm);
         cudaError_t e2 = cudaFuncSetAttribute(k_build_rows_df,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
         if (e2 != cudaSuccess) return lm_cuda_check(ctx, e2, "df64 build smem attribute");
-        int per_sm = std::max(1, (int)(220 * 1024 / dsm));
+        int per_sm = std::max(1, per_sm_of(dsm));
         per_sm = std::min(per_sm, 4);
         int64_t grid = std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * per_sm);
         if (grid < 1) grid = 1;
