@@ -1261,6 +1261,10 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         int per_sm = std::max(1, per_sm_of(dsm));
         per_sm = std::min(per_sm, 4);
         int64_t grid = std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * per_sm);
+        // Many rows per resident CTA: one CTA per row instead, so that the
+        // hardware can schedule other streams' kernels (e.g. small systems of a
+        // server) as rows finish, rather than after the whole build
+        if (p->n_rows > 64 * grid) grid = std::min<int64_t>(p->n_rows, 0x7fffffff);
         if (grid < 1) grid = 1;
         lm_prof_begin(ctx, PROF_BUILD, s);
         k_build_rows_df<<<(unsigned)grid, BDF_THREADS, dsm, s>>>(B);

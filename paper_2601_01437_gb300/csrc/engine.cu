@@ -255,6 +255,10 @@ struct Req {
 struct lm_server {
     lm_ctx *ctx;
     cudaStream_t tune = nullptr;  // grid tuning runs alone on this stream
+    // streams [0, n_high) have the device's highest priority and serve small
+    // systems, the rest the lowest priority and large ones (when both pools
+    // have free streams; otherwise any free stream)
+    int n_high = 0;
     size_t budget, resident = 0;
     int autotune;
     std::vector<cudaStream_t> streams;
@@ -280,9 +284,13 @@ extern "C" int lm_server_create(lm_ctx *ctx, size_t hbm_budget_bytes, int n_stre
         delete v;
         return lm_fail(ctx, LM_ERR_CUDA, "cudaStreamCreate");
     }
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    v->n_high = std::max(1, n_streams / 2);
     for (int i = 0; i < n_streams; ++i) {
         cudaStream_t s;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, i < v->n_high ? hi : lo) !=
+            cudaSuccess) {
             for (cudaStream_t t : v->streams) cudaStreamDestroy(t);
             cudaStreamDestroy(v->tune);
             delete v;
@@ -475,15 +483,21 @@ extern "C" int lm_server_poll(lm_server *v, lm_response *out, int cap, int *n_ou
     // admit queued requests, oldest first, that have an idle system, a free
     // stream and room in the budget (later requests may pass a blocked one)
     for (auto it = v->queued.begin(); it != v->queued.end();) {
-        int stream = -1;
-        for (int k = 0; k < (int)v->streams.size(); ++k)
-            if (!v->stream_busy[k]) {
-                stream = k;
-                break;
-            }
-        if (stream < 0) break;
         Req *q = *it;
         SysRec &r = v->systems[q->sys_id];
+        // small systems (under 64 MB of O/G) prefer the high-priority pool
+        const bool small = r.footprint < ((size_t)64 << 20);
+        int stream = -1;
+        const int ns = (int)v->streams.size();
+        for (int pass = 0; pass < 2 && stream < 0; ++pass)
+            for (int k = 0; k < ns; ++k) {
+                const bool high = k < v->n_high;
+                if (!v->stream_busy[k] && (pass == 1 || high == small)) {
+                    stream = k;
+                    break;
+                }
+            }
+        if (stream < 0) break;
         if (r.busy || (!r.p && !server_make_room(v, r.footprint))) {
             ++it;
             continue;
