@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving run")
     ap.add_argument("--serve-seconds", type=float, default=1.0,
                     help="length of the Poisson arrival stream of the serving run")
+    ap.add_argument("--c2-rows", type=int, default=262144,
+                    help="rows of the LiCl-shaped pencil used for the c2 pencil measurement")
+    ap.add_argument("--pencil-only", action="store_true",
+                    help="only the c2 pencil measurement (profiling runs)")
     ap.add_argument("--pencil", default="df64", choices=["df64", "fp64"],
                     help="storage of the FP64 workload's Lanczos pencil factors (both "
                          "FP64-accurate; the final refinement always uses FP64)")
@@ -355,13 +359,15 @@ def run_gpu(args, rank, world, local):
     return out
 
 
-def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10):
+def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10, n_rows=262144, precs=None):
     """Pencil-matvec HBM bandwidth on the LiCl-shaped Monte Carlo pencil (262,144 rows,
     P+1 = 1,653: O_c and G'_c far larger than L2), per storage precision: the
     symmetrised product y_H = (O_c^T W G'_c v + G'_c^T W O_c v)/2 of the IRL inner
     loop, which reads each matrix once. Live CUDA-event durations of k_pencil."""
     import torch
     w = synth.WORKLOADS["licl_14o14e_mc"]
+    if n_rows != w.n_samples:
+        w = synth.Workload(**{**w.__dict__, "n_samples": n_rows})
     h, eri, th, rows, counts = w.inputs()
     sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, torch.from_numpy(h).to(dev),
                       torch.from_numpy(eri).to(dev))
@@ -375,6 +381,8 @@ def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10):
     out = {}
     for name, pr, b in (("fp32", abi.LM_FP32, 4), ("bf16", abi.LM_BF16, 2),
                         ("df64", abi.LM_DF64, 8)):
+        if precs is not None and name not in precs:
+            continue
         pen = ctx.build_OG(sysd, th_d, rows=rows_d, weights=wts_d, n_rows=w.n_rows, prec=pr,
                            stream=s)
         cases = [(name, pr, b)] + ([("fp64", abi.LM_FP64, 8)] if name == "fp32" else [])
@@ -612,6 +620,20 @@ def main():
                 "e2e": {"value": sps, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
+        return
+    if args.pencil_only:
+        import torch
+        import __graft_entry__ as entry
+        entry.build()
+        from paper_2601_01437_gb300 import abi
+        torch.cuda.set_device(local)
+        ctx = abi.Context(local)
+        dev = torch.device("cuda", local)
+        hbm, hbm_src = peaks()
+        print(json.dumps({"pencil_c2": pencil_c2(abi, ctx, torch.cuda.Stream(device=dev), dev, hbm,
+                                                 hbm_src, reps=3, n_rows=args.c2_rows,
+                                                 precs=("fp32",))}), flush=True)
+        ctx.close()
         return
     out = run_gpu(args, rank, world, local)
     if rank == 0:
