@@ -144,6 +144,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
+# DRAM bytes (read + write) per launch from the ncu captures summarised in
+# profiles/ (k_build_rows_df_f2_10o14e.md, k_pencil_df64_f2_10o14e.md,
+# k_pencil_fp32_licl_mc.md, the last scaled from 65,536 to 262,144 rows). They
+# describe the kernels as committed with them; set an entry to None when its
+# kernel changes until it is captured again.
+NCU_TRAFFIC = {("k_build_rows_df", "f2_10o14e"): 138.34e6,
+               ("k_pencil", "f2_10o14e"): 204.0e6,
+               ("k_pencil_fp32", "licl_14o14e_mc"): 3.488e9}
+
+
 def algorithmic_units(w, arith="df64"):
     """Per-launch algorithmic work of the two dominant kernels (derivation in the design doc).
 
@@ -263,9 +273,12 @@ def run_gpu(args, rank, world, local):
         d = st.build_ms / st.build_count / 1e3
         ach = build_flops / d / 1e12
         pk = FP32_PEAK_TFLOPS if args.arith == "df64" else FP64_PEAK_TFLOPS
-        kern["build"] = {"kernel": "k_build_rows_df" if args.arith == "df64" else "k_build_rows",
+        kname = "k_build_rows_df" if args.arith == "df64" else "k_build_rows"
+        kern["build"] = {"kernel": kname,
                          "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                         "frac": ach / pk, "traffic": None, "avg_ms": d * 1e3,
+                         "frac": ach / pk,
+                         "traffic": NCU_TRAFFIC.get((kname, w.name)) if args.arith == "df64" else None,
+                         "avg_ms": d * 1e3,
                          "launches": int(st.build_count), "total_ms": st.build_ms,
                          "peak_source": ("FP32 FFMA" if args.arith == "df64" else "FP64 DFMA") +
                          " throughput measured by the project probe (FMA = 2 flops)"}
@@ -273,7 +286,9 @@ def run_gpu(args, rank, world, local):
         d = st.pencil_ms / st.pencil_count / 1e3
         ach = pencil_bytes / d / 1e9
         kern["pencil"] = {"kernel": "k_pencil", "bound": "hbm", "achieved": ach, "peak": hbm,
-                          "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                          "unit": "GB/s", "frac": ach / hbm,
+                          "traffic": NCU_TRAFFIC.get(("k_pencil", w.name))
+                          if args.pencil == "df64" and w.precision == "f64" else None,
                           "avg_ms": d * 1e3, "launches": int(st.pencil_count),
                           "total_ms": st.pencil_ms, "peak_source": f"{hbm_src} hbm_gbs"}
     # the remaining step kernels (live event timings, no roofline: latency bound)
@@ -398,7 +413,9 @@ def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10, n_rows=262144, precs=None
             nbytes = w.n_rows * p1 * 2 * bb + 8 * w.n_rows
             out[nm] = {"avg_ms": d * 1e3, "achieved": nbytes / d / 1e9, "unit": "GB/s",
                        "peak": hbm, "frac": nbytes / d / 1e9 / hbm, "bytes": nbytes,
-                       "launches": int(st.pencil_count)}
+                       "launches": int(st.pencil_count),
+                       "traffic": (NCU_TRAFFIC[("k_pencil_fp32", "licl_14o14e_mc")]
+                                   if nm == "fp32" and n_rows == 262144 else None)}
         pen.free()
     out["workload"] = (f"{w.name}: {w.n_rows} MC rows x P+1 = {p1}, symmetrised H~' product, "
                        f"peak = {hbm_src} hbm_gbs")
