@@ -1439,6 +1439,14 @@ int job_phase_start(IrlJob *J) {
     } else {
         R.prec = J->dfp ? LM_DF64 : LM_FP64;
         J->rel = 50.0 * 2.220446049250313e-16;
+        // The FP64 continuation of a low-precision phase starts from a Ritz
+        // vector already accurate to the storage's resolution: short cycles
+        // (Krylov dimension 8, at least k + 2) reach the tolerance in one or
+        // two of them instead of a full m-step cycle.
+        if (J->lowp) {
+            R.m = std::min(J->prm.m, std::max(8, J->prm.k + 2));
+            choose_lanczos(R, p->ctx);
+        }
     }
     J->cycle = 0;
     cudaMemsetAsync(p->st, 0, sizeof(IrlState), R.s);

@@ -198,7 +198,9 @@ def test_pencil_products_mc_rows(ctx, abi):
     pen.free()
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 2e-6), (2, 2e-2), (3, 1e-12)], ids=["fp32", "bf16", "df64"])
+# double-float factors are the FP64-accurate storage (48-bit significand), held to
+# the FP64 path's bar on pencil products (1e-10 relative)
+@pytest.mark.parametrize("prec,tol", [(1, 2e-6), (2, 2e-2), (3, 1e-10)], ids=["fp32", "bf16", "df64"])
 def test_pencil_products_low_precision(ctx, abi, prec, tol):
     h, eri = synth.integrals(14, 111)
     th = synth.rbm_theta(14, 56, 111)
