@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving run")
     ap.add_argument("--serve-seconds", type=float, default=1.0,
                     help="length of the Poisson arrival stream of the serving run")
+    ap.add_argument("--serve-streams", type=int, default=16,
+                    help="requests in flight at once in the serving run")
     ap.add_argument("--c2-rows", type=int, default=262144,
                     help="rows of the LiCl-shaped pencil used for the c2 pencil measurement")
     ap.add_argument("--pencil-only", action="store_true",
@@ -369,7 +371,8 @@ def run_gpu(args, rank, world, local):
     if not args.no_batched and rank == 0 and world == 1:
         out["batched_c3"] = batched_c3(abi, ctx)
     if not args.no_serving and rank == 0 and world == 1:
-        out["serving_c4"] = serving_c4(abi, ctx, seconds=args.serve_seconds)
+        out["serving_c4"] = serving_c4(abi, ctx, seconds=args.serve_seconds,
+                                       n_streams=args.serve_streams)
     ctx.close()
     return out
 
@@ -548,9 +551,10 @@ def serving_c4(abi, ctx, seconds=1.0, rate=200.0, n_streams=16, seed=111):
     wall = time.perf_counter() - t0
     srv.free()
     lat = np.array([r.t_done_ms - r.t_submit_ms for r in done])
-    by_cls = {}
+    by_cls, svc_cls = {}, {}
     for r in done:
         by_cls.setdefault(outs[r.ticket][0], []).append(r.t_done_ms - r.t_submit_ms)
+        svc_cls.setdefault(outs[r.ticket][0], []).append(r.t_done_ms - r.t_admit_ms)
     bad = sum(1 for r in done if r.status != abi.LM_OK)
     # plain FP64 sequential baseline for the same request list: each class's solo
     # service time (build + IRL with FP64 O/G on a resident pencil, mean of a few
@@ -583,7 +587,9 @@ def serving_c4(abi, ctx, seconds=1.0, rate=200.0, n_streams=16, seed=111):
             "latency_ms": {"p50": float(np.percentile(lat, 50)),
                            "p99": float(np.percentile(lat, 99)),
                            "by_class_p50": {names[c]: float(np.percentile(v, 50))
-                                            for c, v in sorted(by_cls.items())}},
+                                            for c, v in sorted(by_cls.items())},
+                           "service_by_class_p50": {names[c]: float(np.percentile(v, 50))
+                                                    for c, v in sorted(svc_cls.items())}},
             "fp64_sequential": {"value": seq, "unit": "LM steps/s",
                                 "service_ms": {names[c]: t * 1e3 for c, t in per_cls.items()},
                                 "sample": "the same request list solved one after another "
