@@ -339,7 +339,7 @@ extern "C" int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double
     if (int rc = to_device(ctx, p->tvec, v, p->P1 * sizeof(double), s)) return rc;
     const double *vd = p->tvec;
     if (int rc = lm_launch_pencil(p, vd, sy, prec, Sv != nullptr, nullptr, s)) return rc;
-    if (int rc = lm_launch_reduce_partials(p, p->hy, p->sy, s)) return rc;
+    if (int rc = lm_launch_reduce_partials(p, prec, p->hy, p->sy, s)) return rc;
     bool h1 = false, h2 = false;
     if (Hv)
         if (int rc = from_device(ctx, Hv, p->hy, p->P1 * sizeof(double), s, h1)) return rc;

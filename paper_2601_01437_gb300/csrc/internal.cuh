@@ -184,7 +184,8 @@ struct lm_pencil {
     double *stats;      // [0] sum w, [1] E, [2] max lnpsi, [8..8+ldp) mean O
     double *part;       // reduction partials
     int64_t part_len;
-    int g_pencil;       // CTAs of the pencil kernel
+    int g_pencil;       // CTAs of a product on the stored factors (tunable); an FP64
+                        // product of a low-precision pencil always runs on every SM
     // IRL workspace
     double *V;          // ldp x (LM_MAXKRYLOV + 1), column-major
     double *wvec, *yvec, *hy, *sy, *tvec, *dots;
@@ -256,7 +257,9 @@ int lm_launch_connections(lm_ctx *ctx, int n, int na, int nb, const double *h,
 // 8-byte slots when out_df is set
 int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_s,
                      const int *skip, cudaStream_t s, int out_df = 0);
-int lm_launch_reduce_partials(lm_pencil *p, double *yH, double *yS, cudaStream_t s);
+int lm_launch_reduce_partials(lm_pencil *p, int prec, double *yH, double *yS, cudaStream_t s);
+// CTAs (= partial vector pairs) of a product of precision prec on pencil p
+int lm_pencil_ctas(const lm_pencil *p, int prec);
 int lm_pencil_grid(lm_pencil *p);
 
 // pencil.cu: the FP64 pencil product on caller-provided scratch (no allocation):

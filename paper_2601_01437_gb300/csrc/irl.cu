@@ -1448,6 +1448,7 @@ int job_phase_start(IrlJob *J) {
             choose_lanczos(R, p->ctx);
         }
     }
+    R.la.nparts = lm_pencil_ctas(p, R.prec);
     J->cycle = 0;
     cudaMemsetAsync(p->st, 0, sizeof(IrlState), R.s);
     cudaMemsetAsync(p->bar, 0, 64 * sizeof(unsigned), R.s);
@@ -1467,7 +1468,7 @@ int job_refine(IrlJob *J) {
     lm_ctx *ctx = p->ctx;
     cudaStream_t s = J->s;
     if (int rc = lm_launch_pencil(p, p->yvec, R.sym, LM_FP64, 1, nullptr, s)) return rc;
-    if (int rc = lm_launch_reduce_partials(p, p->hy, p->sy, s)) return rc;
+    if (int rc = lm_launch_reduce_partials(p, LM_FP64, p->hy, p->sy, s)) return rc;
     R.n_matvec++;
     const size_t stage_vec = (size_t)8 * p->ldp;
     if (J->theta_inout && !J->t_dev)
@@ -1526,7 +1527,6 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
     R.la.V = p->V;
     R.la.w = p->wvec;
     R.la.part = p->part;
-    R.la.nparts = p->g_pencil;
     R.la.dots = p->dots;
     R.la.ldp = p->ldp;
     R.la.M1 = p->M1;

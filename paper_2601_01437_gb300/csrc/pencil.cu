@@ -16,6 +16,7 @@
 // writes its partial y; a second kernel sums the partials in CTA order
 // (deterministic).
 #include <algorithm>
+#include <type_traits>
 
 #include "df64.cuh"
 #include "internal.cuh"
@@ -471,7 +472,8 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return lm_cuda_check(p->ctx, e, "pencil smem attribute");
     lm_prof_begin(p->ctx, PROF_PENCIL, s);
-    k_pencil<T, NJ, MODE><<<p->g_pencil, NCW * 32 + 32, smem, s>>>(a);
+    const int grid = lm_pencil_ctas(p, std::is_same<T, double>::value ? (int)LM_FP64 : p->prec);
+    k_pencil<T, NJ, MODE><<<grid, NCW * 32 + 32, smem, s>>>(a);
     lm_prof_end(p->ctx, PROF_PENCIL, s);
     lm_note_launch(p->ctx);
     p->ctx->pencil_rows += p->n_rows;
@@ -505,6 +507,15 @@ int dispatch_nc(lm_pencil *p, const T *O, const T *G, const double *v, int half,
 
 int lm_pencil_grid(lm_pencil *p) { return p->ctx->sms; }
 
+// A product on FP64 factors is bound by the FP64 pipe, not by HBM: its SM time
+// hardly depends on the grid, so the FP64 copies of a low-precision pencil (the
+// continuation and refinement of a mixed-precision step) always take every SM,
+// whatever grid the low-precision products were tuned to.
+int lm_pencil_ctas(const lm_pencil *p, int prec) {
+    const bool fp64 = prec == LM_FP64 || p->Olo == nullptr;
+    return fp64 && p->prec != LM_FP64 ? p->ctx->sms : p->g_pencil;
+}
+
 int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_s,
                      const int *skip, cudaStream_t s, int out_df) {
     const int half = (sym == LM_SYM_HALF);
@@ -521,9 +532,9 @@ int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_
                                       out_df, s);
 }
 
-int lm_launch_reduce_partials(lm_pencil *p, double *yH, double *yS, cudaStream_t s) {
+int lm_launch_reduce_partials(lm_pencil *p, int prec, double *yH, double *yS, cudaStream_t s) {
     const int blocks = (2 * p->ldp + 31) / 32;
-    k_reduce_partials<<<blocks, 256, 0, s>>>(p->part, p->g_pencil, p->ldp, yH, yS);
+    k_reduce_partials<<<blocks, 256, 0, s>>>(p->part, lm_pencil_ctas(p, prec), p->ldp, yH, yS);
     lm_note_launch(p->ctx);
     return lm_cuda_check(p->ctx, cudaGetLastError(), "k_reduce_partials");
 }
