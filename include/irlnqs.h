@@ -280,9 +280,12 @@ typedef struct lm_batch lm_batch;
 /* A batch engine over n_streams CUDA streams (1..64). It keeps one pencil per
  * item index across lm_batch_run calls (device-resident O/G and Lanczos
  * bases; rebuilt in place when the shape is unchanged). autotune = 1 picks,
- * for every new pencil shape, the pencil-product grid that minimises SM time
- * per product (CTAs x duration, timed alone once); autotune = 0 keeps one CTA
- * per SM. */
+ * for every new pencil shape, the grid of the products on its stored factors
+ * that costs the least shared capacity: with t the duration of a product timed
+ * alone once, cost = max(t x CTAs / SMs, bytes streamed / HBM streaming rate);
+ * among grids within 3 % of the least cost the fastest is kept. autotune = 0
+ * keeps one CTA per SM. FP64 products of a low-precision pencil always use
+ * one CTA per SM. */
 int lm_batch_create(lm_ctx *ctx, int n_streams, int autotune, lm_batch **out);
 
 /* Run one LM step of every item concurrently (instance i on stream i mod

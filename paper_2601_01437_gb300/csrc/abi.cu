@@ -146,6 +146,14 @@ extern "C" int lm_create(lm_ctx **out, int device) {
     c->device = device;
     c->err[0] = 0;
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    {
+        // streaming rate: 85 % of the interface's peak (double data rate x bus
+        // width), about what a copy kernel sustains on HBM3e
+        int khz = 0, bits = 0;
+        cudaDeviceGetAttribute(&khz, cudaDevAttrMemoryClockRate, device);
+        cudaDeviceGetAttribute(&bits, cudaDevAttrGlobalMemoryBusWidth, device);
+        c->hbm_bytes_per_ms = 0.85 * 2.0 * (double)khz * (bits / 8);
+    }
     cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_flags, 0, sizeof(int)) != cudaSuccess) {

@@ -10,9 +10,14 @@
 //
 // The pencil-product grid of every new pencil shape can be autotuned: each
 // candidate grid (one CTA per SM, 1/2, 1/4, 1/8 of that) is timed alone on the
-// built pencil and the one with the least SM time per product (CTAs x
-// duration) is kept: under concurrency the SMs a product does not occupy go
-// to other instances, so SM time, not latency, is what a batch pays.
+// built pencil. Under concurrency a product holds two shared resources for its
+// duration t: a share g/SMs of the SMs and a share of the HBM bandwidth, at
+// least (bytes streamed / streaming rate) / t. Its cost is the larger share
+// times t, max(t g / SMs, bytes / rate); the grid of least cost is kept, and
+// among grids within 3 % of it the fastest. A product that streams from HBM
+// costs about the same on any grid (fewer SMs only stretch it), so it keeps a
+// large grid and its latency; a small, cache-resident one moves to a small
+// grid and leaves the other SMs to other instances.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -33,7 +38,7 @@ double now_ms() {
 
 using GridKey = std::tuple<int, int64_t, int, int>;  // ldp, rows, storage, symmetrisation
 
-// Pick (once per shape) the pencil grid with the least SM time per product.
+// Pick (once per shape) the pencil grid of least cost (rule above).
 int autotune_grid(lm_pencil *p, cudaStream_t s, std::map<GridKey, int> &cache) {
     lm_ctx *ctx = p->ctx;
     const GridKey key{p->ldp, p->n_rows, p->prec, p->sym};
@@ -49,8 +54,12 @@ int autotune_grid(lm_pencil *p, cudaStream_t s, std::map<GridKey, int> &cache) {
     cudaMemsetAsync(p->tvec, 0, p->ldp * sizeof(double), s);
     const int prof = ctx->profile;
     ctx->profile = 0;  // keep the tuning launches out of the counters
-    int best = ctx->sms;
-    double best_cost = 0.0;
+    // bytes one product streams: both factors and the weights
+    const int esize = p->prec == LM_FP32 ? 4 : p->prec == LM_BF16 ? 2 : 8;
+    const double bytes = (double)p->n_rows * ((double)p->ldp * esize * 2 + 8);
+    const double hbm_ms = ctx->hbm_bytes_per_ms > 0 ? bytes / ctx->hbm_bytes_per_ms : 0.0;
+    int grid[4], n = 0;
+    double t[4], cost[4];
     int rc = LM_OK;
     for (int div : {1, 2, 4, 8}) {
         const int g = ctx->sms / div;
@@ -64,15 +73,23 @@ int autotune_grid(lm_pencil *p, cudaStream_t s, std::map<GridKey, int> &cache) {
         if (rc) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double cost = (double)ms * g;
-        if (div == 1 || cost < best_cost) {
-            best_cost = cost;
-            best = g;
-        }
+        grid[n] = g;
+        t[n] = ms / 3.0;
+        cost[n] = std::max(t[n] * g / ctx->sms, hbm_ms);
+        ++n;
     }
     ctx->profile = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    int best = ctx->sms;
+    if (n > 0) {
+        double least = cost[0];
+        for (int i = 1; i < n; ++i) least = std::min(least, cost[i]);
+        int b = -1;
+        for (int i = 0; i < n; ++i)
+            if (cost[i] <= 1.03 * least && (b < 0 || t[i] < t[b])) b = i;
+        best = grid[b];
+    }
     p->g_pencil = best;
     if (!rc) cache[key] = best;
     return rc;

@@ -111,6 +111,7 @@ struct lm_ctx {
     int device;
     int sms;
     int smem_optin;
+    double hbm_bytes_per_ms;  // streaming rate assumed by grid tuning (0: unknown)
     int *d_flags;        // device error flags
     char err[512];
     // counters
