@@ -599,14 +599,17 @@ __device__ __forceinline__ void singles_of_conn(const SysView &S, int k, int &s1
 // pipes. For hidden unit j let sigma_j = -sign(z_j) (+1 if z_j < 0),
 // g_j = exp(2 sigma_j z_j) <= 1 and, for a connection moving orbitals with
 // shift d_j of the pre-activation, Z_j = g_j exp(2 sigma_j d_j). Then
-//   tanh(z_j + d_j) = sigma_j (Z_j - 1) / (Z_j + 1),
+//   tanh(z_j + d_j) = sigma_j (1 - 2 u_j),  u_j = 1 / (1 + Z_j),
 //   prod_j cosh(z_j+d_j)/cosh(z_j) = exp(-sum_j sigma_j d_j) prod_j (1+Z_j) / prod_j (1+g_j).
 // Per row, every single excitation s (i -> a) gets B_s[j] = exp(2 sigma_j d_j),
 // A_s[j] = g_j B_s[j] and V_s = exp(a_a - a_i - sum_j sigma_j d_j); a double
 // (s1, s2) has Z_j = A_s1[j] B_s2[j] and factor V_s1 V_s2. So the work per
 // (connection, hidden unit) is one double-float product (doubles), Z +- 1, a
 // division and the running product. Four threads share a connection and
-// combine their partial products with shuffles.
+// combine their partial products with shuffles. The G sums are accumulated
+// from c u_j rather than c tanh(z_j + d_j): over any connection set Q,
+// sum_Q c tanh = sigma_j (sum_Q c - 2 sum_Q c u_j), and sum_Q c is the hidden
+// row 0 of the same sums, so the conversion happens once per output element.
 __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     extern __shared__ __align__(16) unsigned char smb[];
     const int nh = A.nh, M = A.M, M1 = A.M1, NS = A.ns;
@@ -625,7 +628,8 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     float2 *sS = sC + BDF_K;                                    // [nslice][nh+1][ldS]
     float2 *sAcc = sS + A.nslice * (nh + 1) * A.ldS;            // [nslice][nh+1]
     float2 *sRed = sAcc + A.nslice * (nh + 1);                  // [BDF_THREADS/32]
-    double *sT = reinterpret_cast<double *>(sRed + BDF_THREADS / 32);  // [nh] t
+    float2 *sAf = sRed + BDF_THREADS / 32;                      // [nh+1] sums over all connections
+    double *sT = reinterpret_cast<double *>(sAf + (nh + 1));    // [nh] t
     double *sZ = sT + nh;                                              // [nh] z
     double *sL1 = sZ + nh;                                             // [nh] ln(1 + g_j)
     double *sCs = sL1 + nh;                                            // [2][M] sum_j sigma_j W_jp
@@ -801,17 +805,14 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 float2 *Frow = sF + kk * A.ldF;
                 const float2 *a1 = sA + s1 * ldA;
                 const float2 *b2 = sB + (s2 >= 0 ? s2 : 0) * ldA;
-                // Z_j = A_s1[j] (B_s2[j]); u = 1 / (1 + Z); tanh(z + d) = sigma (1 - 2u);
-                // the running product of (1 + Z_j) stays >= 1 and is rescaled past 2^60
+                // Z_j = A_s1[j] (B_s2[j]); u = 1 / (1 + Z); the running product of
+                // (1 + Z_j) stays >= 1 and is rescaled past 2^60
 #pragma unroll 2
                 for (int j = sub; j < nh; j += BDF_TPC) {
                     df z = A.fuseB ? df_mul(ld_df(sGd + j), ld_df(sB + s1 * ldA + j)) : ld_df(a1 + j);
                     if (s2 >= 0) z = df_mul(z, ld_df(b2 + j));
                     const df zp = df_add1(z, 1.f);
-                    const df u = df_rcp_ge1(zp);
-                    df t = df_one_minus(df_make(2.f * u.h, 2.f * u.l));
-                    if (sSig[j] < 0.f) t = df_neg(t);
-                    st_df(Frow + j, t);  // tanh(z + d)
+                    st_df(Frow + j, df_rcp_ge1(zp));  // u_j
                     rp = df_mul(rp, zp);
                     if (rp.h > 0x1p60f) df_renorm(rp, re);
                 }
@@ -849,7 +850,6 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                     df f = ld_df(sC + q);
                     if (sc_r > 0) f = df_mul(f, ld_df(sF + q * A.ldF + sc_r - 1));
                     const int4 ix = sIdx[q];
-                    df_acc(accA, f);
                     // the orbitals a connection moves are distinct: load all, add, store
                     df t0 = ld_df(Srow + ix.x), t1 = ld_df(Srow + ix.z);
                     if (ix.y >= 0) {
@@ -863,6 +863,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                         st_df(Srow + ix.y, t2);
                         st_df(Srow + ix.w, t3);
                     } else {
+                        df_acc(accA, f);  // singles only (see below)
                         df_acc(t0, f);
                         df_acc(t1, f);
                         st_df(Srow + ix.x, t0);
@@ -891,24 +892,46 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             A.eloc[row] = df_to_double(el);
             A.lnpsi[row] = sLn;
         }
-        // O row and G row
+        // The sum over all connections: a single removes one occupied orbital and
+        // a double two, so sum_all = (sum over occupied p of S[p] + sum_singles) / 2.
+        for (int r = tid; r <= nh; r += BDF_THREADS) {
+            df a = df_make(0.f, 0.f);
+            for (int s2 = 0; s2 < nsl; ++s2) {
+                const float2 *Srow = sS + (s2 * (nh + 1) + r) * A.ldS;
+                a = df_add(a, ld_df(sAcc + s2 * (nh + 1) + r));
+                for (int t = 0; t < A.S.na; ++t) a = df_add(a, df_norm(ld_df(Srow + sL->oa[t])));
+                for (int t = 0; t < A.S.nb; ++t) a = df_add(a, df_norm(ld_df(Srow + sL->ob[t])));
+            }
+            st_df(sAf + r, df_make(0.5f * a.h, 0.5f * a.l));
+        }
+        __syncthreads();
+        // O row and G row; sums of c u_j become sums of c tanh(z_j + d_j)
         double *Orow = A.O + row * (int64_t)A.ldp;
         double *Grow = A.G + row * (int64_t)A.ldp;
         const df hdg = df_from_double(sDiag);
+        auto to_tanh = [&](df s0, df su, int r) {
+            const df t = df_sub(s0, df_make(2.f * su.h, 2.f * su.l));
+            return sSig[r - 1] < 0.f ? df_neg(t) : t;
+        };
         for (int e = tid; e < A.ldp; e += BDF_THREADS) {
             double ov = 0.0, gv = 0.0;
             if (e < A.P1) {
                 const int r = e / M1, c = e % M1;
                 const bool xc = (c == 0) || ((x >> (c - 1)) & 1ull);
                 ov = xc ? (r == 0 ? 1.0 : sT[r - 1]) : 0.0;
+                df a = ld_df(sAf + r);
+                if (r > 0) a = to_tanh(ld_df(sAf), a, r);
                 df at = (r == 0) ? hdg : df_mul(hdg, ld_df(sTd + r - 1));
-                for (int s2 = 0; s2 < nsl; ++s2) at = df_add(at, ld_df(sAcc + s2 * (nh + 1) + r));
+                at = df_add(at, a);
                 if (c == 0) {
                     gv = df_to_double(at);
                 } else {
-                    df sv = df_make(0.f, 0.f);
-                    for (int s2 = 0; s2 < nsl; ++s2)
+                    df sv = df_make(0.f, 0.f), s0 = df_make(0.f, 0.f);
+                    for (int s2 = 0; s2 < nsl; ++s2) {
                         sv = df_add(sv, df_norm(ld_df(sS + (s2 * (nh + 1) + r) * A.ldS + c - 1)));
+                        s0 = df_add(s0, df_norm(ld_df(sS + (s2 * (nh + 1)) * A.ldS + c - 1)));
+                    }
+                    if (r > 0) sv = to_tanh(s0, sv, r);
                     gv = df_to_double(((x >> (c - 1)) & 1ull) ? df_sub(at, sv) : sv);
                 }
             }
@@ -1232,7 +1255,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         auto smem_of = [&](int fuse, int nsl) {
             const size_t f2 = (size_t)(fuse ? 1 : 2) * B.ns * (nh_ | 1) + 2 * B.ns + nh_ +
                               (size_t)BDF_K * B.ldF + BDF_K + (size_t)nsl * (nh_ + 1) * B.ldS +
-                              (size_t)nsl * (nh_ + 1) + BDF_THREADS / 32;
+                              (size_t)nsl * (nh_ + 1) + BDF_THREADS / 32 + nh_ + 1;
             return BDF_K * (sizeof(int4) + sizeof(int2)) + sizeof(RowLists) +
                    f2 * sizeof(float2) + (3 * nh_ + 2 * M_) * sizeof(double) +
                    nh_ * (sizeof(float2) + sizeof(float)) + B.ns * sizeof(int) + 64;
