@@ -828,6 +828,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 re += oe;
                 df_renorm(rp, re);
             }
+            df c = df_make(0.f, 0.f);
             if (active && sub == 0) {
                 if (sg < 0) hv = df_neg(hv);
                 df f = df_mul(hv, ld_df(sV + s1));
@@ -836,19 +837,27 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                     f = df_mul(f, ld_df(sV + s2));
                     fe += sVe[s2];
                 }
-                df c = df_mul(df_mul(f, ginv), rp);
-                c = df_ldexp(c, fe);
+                c = df_ldexp(df_mul(df_mul(f, ginv), rp), fe);
                 st_df(sC + kk, c);
                 sIdx[kk] = make_int4(e.i, e.j, e.a, e.b);
                 df_acc(el_part, c);
+            }
+            // the row of the connection becomes c u_j, here where every thread
+            // works, rather than in the scatter below
+            c.h = __shfl_sync(0xffffffffu, c.h, lane & ~(BDF_TPC - 1));
+            c.l = __shfl_sync(0xffffffffu, c.l, lane & ~(BDF_TPC - 1));
+            if (active) {
+                float2 *Frow = sF + kk * A.ldF;
+                for (int j = sub; j < nh; j += BDF_TPC) st_df(Frow + j, df_mul(c, ld_df(Frow + j)));
             }
             __syncthreads();
             if (scatter_thread) {
                 const int kend = min(BDF_K, A.S.conn - k0);
                 float2 *Srow = sS + (sc_s * (nh + 1) + sc_r) * A.ldS;
+                const float2 *Fcol = sc_r > 0 ? sF + sc_r - 1 : sC;
+                const int ldq = sc_r > 0 ? A.ldF : 1;
                 for (int q = sc_s; q < kend; q += nsl) {
-                    df f = ld_df(sC + q);
-                    if (sc_r > 0) f = df_mul(f, ld_df(sF + q * A.ldF + sc_r - 1));
+                    const df f = ld_df(Fcol + q * ldq);
                     const int4 ix = sIdx[q];
                     // the orbitals a connection moves are distinct: load all, add, store
                     df t0 = ld_df(Srow + ix.x), t1 = ld_df(Srow + ix.z);
