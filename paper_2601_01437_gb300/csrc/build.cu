@@ -7,6 +7,7 @@
 // row-major, padded to ldp columns (a multiple of 8, so every row starts on a
 // 64-byte boundary for FP64 and on 16 bytes for the low-precision copies).
 #include <cstdarg>
+#include <cstdlib>
 
 #include "df64.cuh"
 #include "internal.cuh"
@@ -614,9 +615,8 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     extern __shared__ __align__(16) unsigned char smb[];
     const int nh = A.nh, M = A.M, M1 = A.M1, NS = A.ns;
     const int tid = threadIdx.x, lane = tid & 31;
-    int4 *sIdx = reinterpret_cast<int4 *>(smb);                 // [K]
-    int2 *sSs = reinterpret_cast<int2 *>(sIdx + BDF_K);          // [K] single indices
-    RowLists *sL = reinterpret_cast<RowLists *>(sSs + BDF_K);   // 1
+    int4 *sIdx = reinterpret_cast<int4 *>(smb);                 // [K] moved orbitals i, j, a, b
+    RowLists *sL = reinterpret_cast<RowLists *>(sIdx + BDF_K);  // 1
     const int ldA = nh | 1;  // odd row stride: the connections of a warp hit distinct banks
     float2 *sA = reinterpret_cast<float2 *>(sL + 1);            // [NS][ldA]  A_s[j] (unless fuseB)
     float2 *sB = sA + (A.fuseB ? 0 : NS * ldA);                 // [NS][ldA]  B_s[j]
@@ -1265,24 +1265,41 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
             const size_t f2 = (size_t)(fuse ? 1 : 2) * B.ns * (nh_ | 1) + 2 * B.ns + nh_ +
                               (size_t)BDF_K * B.ldF + BDF_K + (size_t)nsl * (nh_ + 1) * B.ldS +
                               (size_t)nsl * (nh_ + 1) + BDF_THREADS / 32 + nh_ + 1;
-            return BDF_K * (sizeof(int4) + sizeof(int2)) + sizeof(RowLists) +
+            return BDF_K * sizeof(int4) + sizeof(RowLists) +
                    f2 * sizeof(float2) + (3 * nh_ + 2 * M_) * sizeof(double) +
                    nh_ * (sizeof(float2) + sizeof(float)) + B.ns * sizeof(int) + 64;
         };
-        // Large systems (many single excitations) would hold one CTA per SM:
-        // dropping the A table (one more double-float product per connection
-        // and hidden unit) and halving the scatter slices can fit a second.
-        // Take the first variant that reaches the most CTAs per SM.
-        auto per_sm_of = [&](size_t bytes) { return (int)(233472 / (bytes + 1024)); };
+        // Pick the layout with the most CTAs per SM up to three (enough to hide
+        // the phases' barriers behind each other), then the A table kept
+        // (dropping it costs one more double-float product per connection and
+        // hidden unit), then the most scatter slices. Per CTA the SM also holds
+        // 1 KB of reserved and a few bytes of static shared memory. Measured on
+        // the F2-shaped rows: 3 slices with the A table at 3 CTAs/SM 3.22 ms,
+        // 2 slices without it at 4 CTAs/SM 3.28 ms; LiCl-shaped: 2 slices
+        // without it at 2 CTAs/SM 406 ms, 3 or 4 slices at 1 CTA/SM 570-620 ms.
+        auto per_sm_of = [&](size_t bytes) { return (int)(233472 / (bytes + 1024 + 64)); };
         {
-            const int v_nsl[3] = {B.nslice, B.nslice, std::max(1, B.nslice / 2)};
-            const int v_fuse[3] = {0, 1, 1};
-            int best = 0;
-            for (int v = 1; v < 3; ++v)
-                if (per_sm_of(smem_of(v_fuse[v], v_nsl[v])) > per_sm_of(smem_of(v_fuse[best], v_nsl[best])))
-                    best = v;
-            B.fuseB = v_fuse[best];
-            B.nslice = v_nsl[best];
+            int best_fuse = 1, best_nsl = 1, best_key = -1;
+            for (int nsl = 1; nsl <= B.nslice; ++nsl)
+                for (int fuse = 0; fuse <= 1; ++fuse) {
+                    const int sm = std::min(3, per_sm_of(smem_of(fuse, nsl)));
+                    const int key = (sm * 2 + (1 - fuse)) * 256 + nsl;
+                    if (key > best_key) {
+                        best_key = key;
+                        best_fuse = fuse;
+                        best_nsl = nsl;
+                    }
+                }
+            // IRLNQS_BUILD_LAYOUT="slices:fuse" overrides the choice (tuning runs)
+            const char *env = getenv("IRLNQS_BUILD_LAYOUT");
+            int e_nsl = 0, e_fuse = 0;
+            if (env && sscanf(env, "%d:%d", &e_nsl, &e_fuse) == 2 && e_nsl >= 1 &&
+                e_nsl <= B.nslice && (e_fuse == 0 || e_fuse == 1)) {
+                best_nsl = e_nsl;
+                best_fuse = e_fuse;
+            }
+            B.fuseB = best_fuse;
+            B.nslice = best_nsl;
         }
         const size_t dsm = smem_of(B.fuseB, B.nslice);
         if (dsm > (size_t)ctx->smem_optin)
