@@ -151,7 +151,7 @@ class ClockSampler:
 # k_pencil_fp32_licl_mc.md, the last scaled from 65,536 to 262,144 rows). They
 # describe the kernels as committed with them; set an entry to None when its
 # kernel changes until it is captured again.
-NCU_TRAFFIC = {("k_build_rows_df", "f2_10o14e"): 138.34e6,
+NCU_TRAFFIC = {("k_build_rows_df", "f2_10o14e"): 138.43e6,
                ("k_pencil", "f2_10o14e"): 204.0e6,
                ("k_pencil_fp32", "licl_14o14e_mc"): 3.488e9}
 
@@ -162,8 +162,11 @@ def algorithmic_units(w, arith="df64"):
     Row build: per connection x hidden unit (ratio factor, tanh) and per
     connection x augmented row (accumulation into G), counted in the arithmetic
     the kernel uses. df64: FP32 flops of the double-float formulation (add/mul
-    1, fma 2, rcp 1): singles 44 + 34, doubles 54 + 50. fp64: FP64 flops
-    (divide 1): singles 9 + 4, doubles 13 + 6.
+    1, fma 2, rcp 1; df product 10, 1 + Z 10, reciprocal 16, lazy sum 8): per
+    hidden unit 1 + Z, 1/(1 + Z), the running product and the scaling by c
+    (doubles also Z = A B), per augmented row one lazy sum per moved orbital
+    (singles also the all-connection sum): singles 46 + 24, doubles 56 + 32.
+    fp64: FP64 flops (divide 1): singles 9 + 4, doubles 13 + 6.
     Pencil: O_c and G'_c read once, N_s (P+1) (b_O + b_G) + 8 N_s bytes.
     """
     n, na, nb, nh = w.n_orb, w.n_alpha, w.n_beta, w.n_hidden
@@ -171,7 +174,7 @@ def algorithmic_units(w, arith="df64"):
     singles = na * va + nb * vb
     doubles = (na * (na - 1) // 2) * (va * (va - 1) // 2) + \
               (nb * (nb - 1) // 2) * (vb * (vb - 1) // 2) + na * va * nb * vb
-    c = {"df64": (44, 34, 54, 50), "fp64": (9, 4, 13, 6)}[arith]
+    c = {"df64": (46, 24, 56, 32), "fp64": (9, 4, 13, 6)}[arith]
     flops_row = singles * (nh * c[0] + (nh + 1) * c[1]) + doubles * (nh * c[2] + (nh + 1) * c[3])
     build_flops = flops_row * w.n_rows
     P1 = (nh + 1) * (2 * n + 1)
