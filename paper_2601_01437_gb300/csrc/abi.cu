@@ -280,6 +280,7 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
         cudaMemsetAsync(p->V, 0, 2 * (LM_MAXKRYLOV + 1) * L * sizeof(double), s);
         *inout = p;
     }
+    const bool have_sector = p->enumerated;  // a pencil rebuilt in place keeps its rows
     p->enumerated = enumerate;
     p->given_weights = weights != nullptr;
     p->sym = enumerate ? LM_SYM_NONE : LM_SYM_HALF;
@@ -295,7 +296,8 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
                                 8 * (nn + nn * nn), s);
     if (rc) return rc;
     if (enumerate) {
-        if ((rc = lm_launch_enumerate(ctx, n, sys->n_alpha, sys->n_beta, p->rows, n_rows, s)))
+        if (!have_sector &&
+            (rc = lm_launch_enumerate(ctx, n, sys->n_alpha, sys->n_beta, p->rows, n_rows, s)))
             return rc;
     } else if ((rc = lm_stage_h2d(p, p->rows, rows, sizeof(uint64_t) * n_rows, p->st_in_rows,
                                   s))) {

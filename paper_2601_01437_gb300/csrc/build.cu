@@ -990,17 +990,34 @@ __global__ void k_weights(const double *lnpsi, const double *given, double *wt, 
 // sum w O[:, c].
 __global__ void k_stats_partial(const double *O, const double *eloc, const double *wt, int64_t n,
                                 int ldp, double *part) {
+    // column pairs (ldp is a multiple of 8, rows start 64-byte aligned); four
+    // independent row chains per thread keep enough loads in flight to stream O
     const int64_t r0 = n * blockIdx.x / gridDim.x, r1 = n * (blockIdx.x + 1) / gridDim.x;
     double *out = part + (int64_t)blockIdx.x * (ldp + 2);
-    for (int c = threadIdx.x; c < ldp; c += blockDim.x) {
-        double a0 = 0.0, a1 = 0.0;  // two interleaved chains
+    for (int c = 2 * threadIdx.x; c < ldp; c += 2 * blockDim.x) {
+        double2 a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = make_double2(0.0, 0.0);
         int64_t r = r0;
-        for (; r + 1 < r1; r += 2) {
-            a0 = fma(wt[r], O[r * ldp + c], a0);
-            a1 = fma(wt[r + 1], O[(r + 1) * ldp + c], a1);
+        for (; r + 3 < r1; r += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double2 o = *reinterpret_cast<const double2 *>(O + (r + u) * ldp + c);
+                const double w = wt[r + u];
+                a[u].x = fma(w, o.x, a[u].x);
+                a[u].y = fma(w, o.y, a[u].y);
+            }
         }
-        if (r < r1) a0 = fma(wt[r], O[r * ldp + c], a0);
-        out[c] = a0 + a1;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            if (r + u < r1) {
+                const double2 o = *reinterpret_cast<const double2 *>(O + (r + u) * ldp + c);
+                a[u].x = fma(wt[r + u], o.x, a[u].x);
+                a[u].y = fma(wt[r + u], o.y, a[u].y);
+            }
+        }
+        out[c] = (a[0].x + a[1].x) + (a[2].x + a[3].x);
+        out[c + 1] = (a[0].y + a[1].y) + (a[2].y + a[3].y);
     }
     if (threadIdx.x == 0) {
         double sw = 0.0, se = 0.0;
@@ -1086,39 +1103,71 @@ __device__ __forceinline__ float2 to_low<float2>(double x) {
 // Centre in place (FP64) and write the optional low-precision copies:
 //   O_c(x,0) = 1, G'_c(x,0) = E_loc - E,
 //   O_c(x,k) = O - <O_k>, G'_c(x,k) = G - <O_k> E_loc - E O_c(x,k),
-// and normalise the weights.
+// and normalise the weights. One warp per row, lanes over column pairs (16-byte
+// loads and stores; ldp is a multiple of 8 and rows start 64-byte aligned).
 template <typename TL>
-__global__ void k_centre(double *O, double *G, const double *eloc, double *wt,
-                         const double *stats, int64_t n, int ldp, int P1, double e_core,
-                         TL *Olo, TL *Glo, float2 *wlo) {
+__device__ __forceinline__ void store_low2(TL *p, double a, double b) {
+    p[0] = to_low<TL>(a);
+    p[1] = to_low<TL>(b);
+}
+template <>
+__device__ __forceinline__ void store_low2<float>(float *p, double a, double b) {
+    *reinterpret_cast<float2 *>(p) = make_float2((float)a, (float)b);
+}
+template <>
+__device__ __forceinline__ void store_low2<float2>(float2 *p, double a, double b) {
+    const float2 x = to_low<float2>(a), y = to_low<float2>(b);
+    *reinterpret_cast<float4 *>(p) = make_float4(x.x, x.y, y.x, y.y);
+}
+template <>
+__device__ __forceinline__ void store_low2<__nv_bfloat16>(__nv_bfloat16 *p, double a, double b) {
+    __nv_bfloat162 v;
+    v.x = __double2bfloat16(a);
+    v.y = __double2bfloat16(b);
+    *reinterpret_cast<__nv_bfloat162 *>(p) = v;
+}
+
+template <typename TL>
+__global__ void k_centre(double *__restrict__ O, double *__restrict__ G,
+                         const double *__restrict__ eloc, double *__restrict__ wt,
+                         const double *__restrict__ stats, int64_t n, int ldp, int P1,
+                         double e_core, TL *__restrict__ Olo, TL *__restrict__ Glo,
+                         float2 *__restrict__ wlo) {
     const double E = stats[1];
     const double isw = 1.0 / stats[0];
-    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    const int lane = threadIdx.x & 31, hp = ldp / 2;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nw) {
         const double el = eloc[r];  // E_loc already includes e_core
-        double *Or = O + r * ldp;
-        double *Gr = G + r * ldp;
-        for (int c = threadIdx.x; c < ldp; c += blockDim.x) {
-            double oc, gc;
-            if (c == 0) {
-                oc = 1.0;
-                gc = el - E;
-            } else if (c < P1) {
-                double ob = stats[8 + c];
-                oc = Or[c] - ob;
-                gc = fma(-ob, el, Gr[c]);
-                gc = fma(-E, oc, gc);
-            } else {
-                oc = 0.0;
-                gc = 0.0;
+        double *Or = O + r * ldp, *Gr = G + r * ldp;
+        for (int c = 2 * lane; c < 2 * hp; c += 64) {
+            const double2 o = *reinterpret_cast<const double2 *>(Or + c);
+            const double2 g = *reinterpret_cast<const double2 *>(Gr + c);
+            const double2 ob = *reinterpret_cast<const double2 *>(stats + 8 + c);
+            double oc[2], gc[2];
+            const double ov[2] = {o.x, o.y}, gv[2] = {g.x, g.y}, bv[2] = {ob.x, ob.y};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int cc = c + u;
+                if (cc == 0) {
+                    oc[u] = 1.0;
+                    gc[u] = el - E;
+                } else if (cc < P1) {
+                    oc[u] = ov[u] - bv[u];
+                    gc[u] = fma(-E, oc[u], fma(-bv[u], el, gv[u]));
+                } else {
+                    oc[u] = 0.0;
+                    gc[u] = 0.0;
+                }
             }
-            Or[c] = oc;
-            Gr[c] = gc;
+            *reinterpret_cast<double2 *>(Or + c) = make_double2(oc[0], oc[1]);
+            *reinterpret_cast<double2 *>(Gr + c) = make_double2(gc[0], gc[1]);
             if (Olo) {
-                Olo[r * ldp + c] = to_low<TL>(oc);
-                Glo[r * ldp + c] = to_low<TL>(gc);
+                store_low2<TL>(Olo + r * ldp + c, oc[0], oc[1]);
+                store_low2<TL>(Glo + r * ldp + c, gc[0], gc[1]);
             }
         }
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             const double wn = wt[r] * isw;
             wt[r] = wn;
             const df d = df_from_double(wn);
@@ -1343,7 +1392,7 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     k_stats_final<<<(p->ldp + 31) / 32, 256, 0, s>>>(spart, nst, p->ldp, p->stats);
     lm_note_launch(ctx);
     if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_stats_final")) return rc;
-    int cgrid = (int)std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * 16);
+    int cgrid = (int)std::min<int64_t>((p->n_rows + 7) / 8, (int64_t)ctx->sms * 16);
     if (p->prec == LM_FP32)
         k_centre<float><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
                                               p->ldp, p->P1, p->e_core, (float *)p->Olo,
