@@ -545,6 +545,12 @@ __device__ __forceinline__ df df_add1(df z, float one) {
     const df s = df_ts(z.h, one);
     return df_fts(s.h, __fadd_rn(s.l, z.l));
 }
+// 1 + Z for Z >= 0 with the tail left unnormalised (the reciprocal and the
+// products that take it are error-free on the head)
+__device__ __forceinline__ df df_add1_lazy(df z) {
+    const df s = df_ts(z.h, 1.f);
+    return df_make(s.h, __fadd_rn(s.l, z.l));
+}
 
 // Single excitation s of a row (i -> a): alpha singles first, then beta.
 __device__ __forceinline__ void single_of(const SysView &S, const RowLists &L, int s, int &i,
@@ -809,13 +815,15 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 // (1 + Z_j) stays >= 1 and is rescaled past 2^60
 #pragma unroll 2
                 for (int j = sub; j < nh; j += BDF_TPC) {
-                    df z = A.fuseB ? df_mul(ld_df(sGd + j), ld_df(sB + s1 * ldA + j)) : ld_df(a1 + j);
-                    if (s2 >= 0) z = df_mul(z, ld_df(b2 + j));
-                    const df zp = df_add1(z, 1.f);
+                    df z = A.fuseB ? df_mul_lazy(ld_df(sGd + j), ld_df(sB + s1 * ldA + j))
+                                   : ld_df(a1 + j);
+                    if (s2 >= 0) z = df_mul_lazy(z, ld_df(b2 + j));
+                    const df zp = df_add1_lazy(z);
                     st_df(Frow + j, df_rcp_ge1(zp));  // u_j
-                    rp = df_mul(rp, zp);
+                    rp = df_mul_lazy(rp, zp);
                     if (rp.h > 0x1p60f) df_renorm(rp, re);
                 }
+                rp = df_fts(rp.h, rp.l);
             }
             // combine the partial products of the BDF_TPC lanes of a connection
             // (all lanes take part; inactive ones carry 1 * 2^0)
@@ -848,7 +856,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             c.l = __shfl_sync(0xffffffffu, c.l, lane & ~(BDF_TPC - 1));
             if (active) {
                 float2 *Frow = sF + kk * A.ldF;
-                for (int j = sub; j < nh; j += BDF_TPC) st_df(Frow + j, df_mul(c, ld_df(Frow + j)));
+                for (int j = sub; j < nh; j += BDF_TPC) st_df(Frow + j, df_mul_lazy(c, ld_df(Frow + j)));
             }
             __syncthreads();
             if (scatter_thread) {

@@ -66,6 +66,18 @@ __device__ __forceinline__ df df_mul(df a, df b) {
     return df_fts(p, e);
 }
 
+// a * b with the tail left unnormalised (|l| may reach a few ulp(h)): exact
+// head product by FMA, cross terms gathered in the tail. For chains whose next
+// step is itself error-free on the head (a product, a TwoSum) and renormalises
+// at the end; the relative error stays near 2^-46.
+__device__ __forceinline__ df df_mul_lazy(df a, df b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return df_make(p, e);
+}
+
 // a / b: FP32 quotient q1, exact remainder a - b*q1 from TwoProduct, one correction
 __device__ __forceinline__ df df_div(df a, df b) {
     const float rb = __frcp_rn(b.h);
