@@ -185,6 +185,7 @@ struct lm_pencil {
     double *stats;      // [0] sum w, [1] E, [2] max lnpsi, [8..8+ldp) mean O
     double *part;       // reduction partials
     int64_t part_len;
+    int order_rev;      // the product being enqueued walks each CTA's rows backwards
     int g_pencil;       // CTAs of a product on the stored factors (tunable); an FP64
                         // product of a low-precision pencil always runs on every SM
     // IRL workspace
@@ -256,8 +257,11 @@ int lm_launch_connections(lm_ctx *ctx, int n, int na, int nb, const double *h,
 // partial products of the pencil over row blocks; y_H into part[b][0..ldp),
 // y_S into part[b][ldp..2ldp); FP64 values, or double-float pairs in the same
 // 8-byte slots when out_df is set
+// reverse: walk each CTA's rows backwards (consecutive Lanczos products
+// alternate, so each starts on the rows the previous one left in L2)
 int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_s,
-                     const int *skip, cudaStream_t s, int out_df = 0);
+                     const int *skip, cudaStream_t s, int out_df = 0,
+                     int reverse = 0);
 int lm_launch_reduce_partials(lm_pencil *p, int prec, double *yH, double *yS, cudaStream_t s);
 // CTAs (= partial vector pairs) of a product of precision prec on pencil p
 int lm_pencil_ctas(const lm_pencil *p, int prec);

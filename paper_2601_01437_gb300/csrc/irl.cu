@@ -1296,8 +1296,11 @@ int lanczos_step(Run &R, int j) {
     lm_pencil *p = R.p;
     R.la.V = p->V;
     const double *vj = p->V + (size_t)j * p->ldp;
+    // consecutive steps walk the rows in opposite directions, so each product
+    // starts on the rows the previous one left in L2; fixed by j, so a rerun
+    // repeats the same order
     if (int rc = lm_launch_pencil(p, vj, R.sym, R.prec, 0, &p->st->broke, R.s,
-                                  R.lz_mode == LZ_CLUSTER))
+                                  R.lz_mode == LZ_CLUSTER, j & 1))
         return rc;
     R.n_matvec++;
     lm_prof_begin(p->ctx, PROF_LANCZOS, R.s);

@@ -183,6 +183,7 @@ struct PencilArgs {
     const int *skip;
     int *flags;
     int out_df;     // partials as double-float pairs (same 8-byte slots) instead of FP64
+    int reverse;    // take this CTA's tiles last to first
 };
 
 // Columns per lane per 16-byte shared-memory access (8 BF16, 4 FP32, 2 FP64 or
@@ -346,9 +347,10 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
                 }
                 if (*(volatile int *)&s_abort) break;
                 // the tile's rows are consecutive in O and in G: one copy per matrix
-                const int nr = min(R, nrows - i * R);
+                const int t = a.reverse ? ntiles - 1 - i : i;
+                const int nr = min(R, nrows - t * R);
                 const uint32_t bytes = (uint32_t)(nr * row_elems * sizeof(T));
-                const int64_t row = r0 + (int64_t)i * R;
+                const int64_t row = r0 + (int64_t)t * R;
                 T *dst = stage_base + (size_t)s * nmat * tile_elems;
                 mbar_arrive_expect_tx(&full[s], nmat * bytes);
                 bulk_g2s(dst, a.O + row * ldp, bytes, &full[s]);
@@ -372,11 +374,12 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
                 }
                 break;
             }
-            const int nr = min(R, nrows - i * R);
+            const int t = a.reverse ? ntiles - 1 - i : i;
+            const int nr = min(R, nrows - t * R);
             for (int rr = 0; rr < nr; ++rr) {
                 const T *ro = stage_base + (size_t)s * nmat * tile_elems + (size_t)rr * row_elems;
                 consume_row<T, NJ, MODE>(ro, ro + tile_elems, vs, ldp, lane,
-                                         P::weight(a.w, a.wlo, r0 + (int64_t)i * R + rr), y);
+                                         P::weight(a.w, a.wlo, r0 + (int64_t)t * R + rr), y);
             }
             if ((i / ncons) % 16 == 15)  // fold lazily accumulated tails now and then
 #pragma unroll
@@ -468,6 +471,7 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
     a.skip = skip;
     a.flags = p->d_flags;
     a.out_df = out_df;
+    a.reverse = p->order_rev;
     cudaError_t e = cudaFuncSetAttribute(k_pencil<T, NJ, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return lm_cuda_check(p->ctx, e, "pencil smem attribute");
@@ -517,8 +521,9 @@ int lm_pencil_ctas(const lm_pencil *p, int prec) {
 }
 
 int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_s,
-                     const int *skip, cudaStream_t s, int out_df) {
+                     const int *skip, cudaStream_t s, int out_df, int reverse) {
     const int half = (sym == LM_SYM_HALF);
+    p->order_rev = reverse;  // read by the launch below, on this host thread
     if (prec == LM_FP64 || p->prec == LM_FP64 || p->Olo == nullptr)
         return dispatch_nc<double>(p, p->O, p->G, v, half, want_s, skip, out_df, s);
     if (p->prec == LM_FP32)
@@ -575,6 +580,7 @@ int raw_launch(const double *O, const double *G, const double *w, int64_t n_rows
     a.skip = nullptr;
     a.flags = flags;
     a.out_df = 0;
+    a.reverse = 0;
     if (cudaFuncSetAttribute(k_pencil<double, NJ, MODE>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return LM_ERR_CUDA;
