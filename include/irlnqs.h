@@ -65,11 +65,13 @@ enum {
     LM_STATIONARY = 4            /* lambda_min > -tol: theta is stationary    */
 };
 
-/* Storage of the pencil factors used by the Lanczos products. FP64 factors are
- * always kept (exports, final refinement); the others are extra copies:
- * FP32 / BF16 (FP32 accumulation, refined by FP64 restarts) and DF64
- * (double-float FP32 pairs, 48-bit significand, products accurate to ~1e-14
- * relative, computed on the FP32 pipes). */
+/* Storage of the pencil factors used by the Lanczos products. FP64: the
+ * centred factors in FP64. FP32 / BF16: low-precision copies beside the FP64
+ * factors (FP32 accumulation; the FP64 factors serve the FP64 continuation,
+ * the final refinement and exports). DF64: the centred factors only as
+ * double-float FP32 pairs (48-bit significand, products accurate to ~1e-14
+ * relative, computed on the FP32 pipes); FP64 product requests, the final
+ * refinement and exports are served from them (exports convert). */
 typedef enum { LM_FP64 = 0, LM_FP32 = 1, LM_BF16 = 2, LM_DF64 = 3 } lm_precision;
 
 /* symmetrisation of H~' inside the Lanczos operator */
@@ -158,7 +160,8 @@ const char *lm_last_error(const lm_ctx *ctx);
  *           normalised by their sum; NULL = |psi(x)|^2 / sum |psi|^2.
  *   prec    FP64 only, or FP64 plus an FP32 / BF16 / DF64 copy of O_c and
  *           G'_c for the Lanczos products.
- * Layout on the device: O_c, G'_c row-major N_s x ld FP64 (columns >= P+1 zero),
+ * Layout on the device: O_c, G'_c row-major N_s x ld FP64 (columns >= P+1 zero;
+ *   DF64 pencils hold them as double-float pairs in the same layout),
  *   O_c(x,0) = 1, G'_c(x,0) = E_loc(x) - E, and for k >= 1
  *   O_c(x,k) = O_k(x) - <O_k>, G'_c(x,k) = G_k(x) - <O_k> E_loc(x) - E O_c(x,k).
  * *inout: NULL to create a pencil, or an existing pencil of the same system
@@ -175,7 +178,8 @@ int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *theta, const ui
  * Matrix-free pencil product (Methods, eq. matrix_vec_prod, with the G form of
  * eq. heff): Hv = H~' v (symmetrised per `sym`), Sv = S~ v, both P+1 FP64.
  * v: P+1 FP64. Either output may be NULL. `prec` selects the FP64 factors or
- * the pencil's low-precision copy. Reads O_c and G'_c once.
+ * the pencil's low-precision copy (a DF64 pencil answers both from its
+ * double-float factors). Reads O_c and G'_c once.
  */
 int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double *Sv, int sym, int prec,
                     void *stream);
@@ -183,8 +187,9 @@ int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double *Sv, int s
 /*
  * Lowest eigenpair of the SHEP H~' c = lambda c (eq. standard_evp) by
  * implicitly restarted Lanczos (Algorithms 1 and 2) with full FP64
- * reorthogonalisation, followed by an explicit FP64 residual / Rayleigh
- * refinement. Writes (all optional, host or device):
+ * reorthogonalisation, followed by an explicit residual / Rayleigh
+ * refinement in FP64 (with FP64-accurate products: the FP64 factors, or the
+ * double-float ones of a DF64 pencil). Writes (all optional, host or device):
  *   c_out      P+1, unit Ritz vector with c[0] >= 0;
  *   dtheta_out P,   the update c[1:]/c[0] (linearised wavefunction, c = [1, v]);
  *   theta_inout P,  theta += dtheta when status is IRL_OK/BREAKDOWN.

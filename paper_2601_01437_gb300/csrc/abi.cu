@@ -410,6 +410,13 @@ extern "C" int lm_pencil_export(lm_pencil *p, int what, void *dst, void *stream)
     const void *src = nullptr;
     size_t bytes = 0;
     const size_t nr = (size_t)p->n_rows;
+    if ((what == 0 || what == 1) && p->prec == LM_DF64 && p->Olo) {
+        // the centred factors of a double-float pencil exist only as pairs:
+        // convert into the (otherwise unused after the build) FP64 buffer
+        double *dstd = what == 0 ? p->O : p->G;
+        const float2 *srcp = (const float2 *)(what == 0 ? p->Olo : p->Glo);
+        if (int rc = lm_launch_df_to_fp64(ctx, srcp, dstd, (int64_t)nr * p->ldp, s)) return rc;
+    }
     switch (what) {
         case 0: src = p->O; bytes = nr * p->ldp * sizeof(double); break;
         case 1: src = p->G; bytes = nr * p->ldp * sizeof(double); break;

@@ -1184,6 +1184,66 @@ __global__ void k_centre(double *__restrict__ O, double *__restrict__ G,
     }
 }
 
+// Centring for double-float pencils: the same formulas in double-float
+// arithmetic on the FP32 pipes (inputs split by integer operations), stored
+// only as double-float pairs. The FP64 buffers keep the uncentred build output;
+// GB300's FP64 pipe would otherwise bound this pass (three FP64 operations per
+// element).
+__global__ void k_centre_df(const double *__restrict__ O, const double *__restrict__ G,
+                            const double *__restrict__ eloc, double *__restrict__ wt,
+                            const double *__restrict__ stats, int64_t n, int ldp, int P1,
+                            float2 *__restrict__ Olo, float2 *__restrict__ Glo,
+                            float2 *__restrict__ wlo) {
+    const df E = df_split_bits(stats[1]);
+    const double isw = 1.0 / stats[0];
+    const int lane = threadIdx.x & 31, hp = ldp / 2;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nw) {
+        const df el = df_split_bits(eloc[r]);  // E_loc already includes e_core
+        const df g0 = df_sub(el, E);
+        const double *Or = O + r * ldp, *Gr = G + r * ldp;
+        for (int c = 2 * lane; c < 2 * hp; c += 64) {
+            const double2 o = *reinterpret_cast<const double2 *>(Or + c);
+            const double2 g = *reinterpret_cast<const double2 *>(Gr + c);
+            const double2 ob = *reinterpret_cast<const double2 *>(stats + 8 + c);
+            df oc[2], gc[2];
+            const double ov[2] = {o.x, o.y}, gv[2] = {g.x, g.y}, bv[2] = {ob.x, ob.y};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int cc = c + u;
+                if (cc == 0) {
+                    oc[u] = df_make(1.f, 0.f);
+                    gc[u] = g0;
+                } else if (cc < P1) {
+                    const df b = df_split_bits(bv[u]);
+                    oc[u] = df_sub(df_split_bits(ov[u]), b);
+                    gc[u] = df_sub(df_sub(df_split_bits(gv[u]), df_mul(b, el)), df_mul(E, oc[u]));
+                } else {
+                    oc[u] = df_make(0.f, 0.f);
+                    gc[u] = df_make(0.f, 0.f);
+                }
+            }
+            *reinterpret_cast<float4 *>(Olo + r * ldp + c) = make_float4(oc[0].h, oc[0].l, oc[1].h, oc[1].l);
+            *reinterpret_cast<float4 *>(Glo + r * ldp + c) = make_float4(gc[0].h, gc[0].l, gc[1].h, gc[1].l);
+        }
+        if (lane == 0) {
+            const double wn = wt[r] * isw;
+            wt[r] = wn;
+            const df d = df_from_double(wn);
+            wlo[r] = make_float2(d.h, d.l);
+        }
+    }
+}
+
+// FP64 copy of double-float pairs (exports of a double-float pencil)
+__global__ void k_df_to_fp64(const float2 *__restrict__ src, double *__restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = src[i];
+        dst[i] = (double)v.x + (double)v.y;
+    }
+}
+
 // ------------------------------------------------ debug: connection lists
 __global__ void k_connections(SysView S, const uint64_t *rows, int64_t n_rows, int cap,
                               uint64_t *od, int8_t *osg, double *oh, int32_t *cnt,
@@ -1406,9 +1466,8 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
                                               p->ldp, p->P1, p->e_core, (float *)p->Olo,
                                               (float *)p->Glo, p->wlo);
     else if (p->prec == LM_DF64)
-        k_centre<float2><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
-                                               p->ldp, p->P1, p->e_core, (float2 *)p->Olo,
-                                               (float2 *)p->Glo, p->wlo);
+        k_centre_df<<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows, p->ldp,
+                                          p->P1, (float2 *)p->Olo, (float2 *)p->Glo, p->wlo);
     else if (p->prec == LM_BF16)
         k_centre<__nv_bfloat16><<<cgrid, 256, 0, s>>>(
             p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows, p->ldp, p->P1, p->e_core,
@@ -1420,6 +1479,13 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     lm_prof_end(ctx, PROF_PREP, s);
     lm_note_launch(ctx);
     return lm_cuda_check(ctx, cudaGetLastError(), "k_centre");
+}
+
+int lm_launch_df_to_fp64(lm_ctx *ctx, const float2 *src, double *dst, int64_t n, cudaStream_t s) {
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ctx->sms * 8));
+    k_df_to_fp64<<<blocks, 256, 0, s>>>(src, dst, n);
+    lm_note_launch(ctx);
+    return lm_cuda_check(ctx, cudaGetLastError(), "k_df_to_fp64");
 }
 
 int lm_launch_connections(lm_ctx *ctx, int n, int na, int nb, const double *h, const double *eri,

@@ -265,6 +265,7 @@ int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_
 int lm_launch_reduce_partials(lm_pencil *p, int prec, double *yH, double *yS, cudaStream_t s);
 // CTAs (= partial vector pairs) of a product of precision prec on pencil p
 int lm_pencil_ctas(const lm_pencil *p, int prec);
+int lm_launch_df_to_fp64(lm_ctx *ctx, const float2 *src, double *dst, int64_t n, cudaStream_t s);
 int lm_pencil_grid(lm_pencil *p);
 
 // pencil.cu: the FP64 pencil product on caller-provided scratch (no allocation):

@@ -516,7 +516,7 @@ int lm_pencil_grid(lm_pencil *p) { return p->ctx->sms; }
 // continuation and refinement of a mixed-precision step) always take every SM,
 // whatever grid the low-precision products were tuned to.
 int lm_pencil_ctas(const lm_pencil *p, int prec) {
-    const bool fp64 = prec == LM_FP64 || p->Olo == nullptr;
+    const bool fp64 = (prec == LM_FP64 || p->Olo == nullptr) && p->prec != LM_DF64;
     return fp64 && p->prec != LM_FP64 ? p->ctx->sms : p->g_pencil;
 }
 
@@ -524,6 +524,11 @@ int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_
                      const int *skip, cudaStream_t s, int out_df, int reverse) {
     const int half = (sym == LM_SYM_HALF);
     p->order_rev = reverse;  // read by the launch below, on this host thread
+    // a double-float pencil keeps no centred FP64 factors: FP64-accurate
+    // requests use its double-float pairs
+    if (p->prec == LM_DF64 && p->Olo)
+        return dispatch_nc<float2>(p, (const float2 *)p->Olo, (const float2 *)p->Glo, v, half,
+                                   want_s, skip, out_df, s);
     if (prec == LM_FP64 || p->prec == LM_FP64 || p->Olo == nullptr)
         return dispatch_nc<double>(p, p->O, p->G, v, half, want_s, skip, out_df, s);
     if (p->prec == LM_FP32)

@@ -305,6 +305,18 @@ def test_irl_f2_full_size_df64_pencil(ctx, abi):
     pen.free()
 
 
+@pytest.mark.parametrize("name", ["tiny_6o6e", "f2_10o14e"])
+def test_build_parity_df64_storage(ctx, abi, name):
+    """A double-float pencil keeps its centred factors only as FP32 pairs (centred
+    in double-float arithmetic); exports convert them to FP64 and must meet the
+    FP64 build's bar."""
+    w = synth.WORKLOADS[name]
+    h, eri, th, _, _ = w.inputs()
+    pen, pd = _build_both(ctx, abi, w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th, prec=3)
+    _check_build(abi, pen, pd)
+    pen.free()
+
+
 def test_pencil_products_f2_df64(ctx, abi):
     w = synth.WORKLOADS["f2_10o14e"]
     h, eri, th, _, _ = w.inputs()
