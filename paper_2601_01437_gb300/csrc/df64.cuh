@@ -123,7 +123,14 @@ __device__ __forceinline__ df df_split_bits(double x) {
     const unsigned hb = (((unsigned)(ex - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)) + up;
     const int rt = (int)(lo & 0x1fffffffu) - (int)(up << 29);  // tail in units of 2^(ex - 1075)
     const float scale = __uint_as_float((unsigned)(ex - 948) << 23);  // 2^(ex - 1075)
-    const float l = __int2float_rn(rt) * scale;
+    // rt as FP32 without an integer-to-float conversion (those issue at the FP64
+    // rate on this part): rt = th 2^14 + tl with |th| < 2^15, 0 <= tl < 2^14, each
+    // exact in FP32 by adding it into the mantissa of 1.5 * 2^23 and subtracting
+    // that again; one FMA then rounds th 2^14 + tl to nearest, as a conversion would.
+    const int th = rt >> 14, tl = rt & 0x3fff;
+    const float fh = __fsub_rn(__int_as_float(0x4B400000 + th), 12582912.0f);
+    const float fl = __fsub_rn(__int_as_float(0x4B400000 + tl), 12582912.0f);
+    const float l = __fmul_rn(__fmaf_rn(fh, 16384.0f, fl), scale);
     return df_make(__uint_as_float(sign | hb), sign ? -l : l);
 }
 
