@@ -34,9 +34,34 @@ __device__ __forceinline__ uint64_t unrank_colex(int n, int k, uint64_t r) {
     return x;
 }
 
-// pair (lo < hi) with colex rank q
+// Division by a fixed divisor d without a divide (which converts to and from
+// floating point, and conversions issue at the FP64 rate on this part): with
+// l = ceil(log2 d) and m = ceil(2^(31+l) / d) < 2^32, x / d = (x m) >> (31 + l)
+// exactly for 0 <= x < 2^31 (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994).
+struct FastDiv {
+    uint32_t m, s, d;
+};
+inline FastDiv make_fastdiv(int divisor) {
+    const uint32_t d = divisor > 0 ? (uint32_t)divisor : 1u;
+    uint32_t l = 0;
+    while ((1u << l) < d) ++l;
+    FastDiv f;
+    f.m = (uint32_t)(((1ull << (31 + l)) + d - 1) / d);
+    f.s = 31 + l;
+    f.d = d;
+    return f;
+}
+__device__ __forceinline__ int fdiv(int x, FastDiv f) {
+    return (int)(((uint64_t)(uint32_t)x * f.m) >> f.s);
+}
+
+// pair (lo < hi) with colex rank q (q < 2^22): the float of q and the nearest
+// integer of the root by exact magic-number arithmetic, then exact corrections
 __device__ __forceinline__ void unrank_pair(int q, int &lo, int &hi) {
-    int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)q)) * 0.5f);
+    const float fq = __fsub_rn(__int_as_float(0x4B400000 + q), 12582912.0f);
+    const float r = 0.5f * (1.0f + sqrtf(fmaf(8.0f, fq, 1.0f)));
+    int y = __float_as_int(__fadd_rn(r, 12582912.0f)) - 0x4B400000;
     while (y * (y - 1) / 2 > q) --y;
     while ((y + 1) * y / 2 <= q) ++y;
     hi = y;
@@ -50,6 +75,7 @@ __device__ __forceinline__ int parity_below(uint64_t x, int p) {
 struct SysView {
     int n, na, nb, nva, nvb;
     int ns_a, ns_b, nd_aa, nd_bb, nd_ab, conn;
+    FastDiv fd_nva, fd_nvb, fd_pva, fd_pvb, fd_nbe;  // by nva, nvb, C(nva,2), C(nvb,2), ns_b
     const double *h, *eri;
 };
 
@@ -82,46 +108,49 @@ __device__ __forceinline__ Exc decode_exc(const SysView &S, const RowLists &L, i
     e.j = -1;
     e.b = -1;
     if (k < S.ns_a) {
-        e.i = L.oa[k / S.nva];
-        e.a = L.va[k % S.nva];
+        const int q = fdiv(k, S.fd_nva);
+        e.i = L.oa[q];
+        e.a = L.va[k - q * S.nva];
         return e;
     }
     k -= S.ns_a;
     if (k < S.ns_b) {
-        e.i = L.ob[k / S.nvb];
-        e.a = L.vb[k % S.nvb];
+        const int q = fdiv(k, S.fd_nvb);
+        e.i = L.ob[q];
+        e.a = L.vb[k - q * S.nvb];
         return e;
     }
     k -= S.ns_b;
     int lo, hi;
     if (k < S.nd_aa) {
-        int nvp = S.nva * (S.nva - 1) / 2;
-        unrank_pair(k / nvp, lo, hi);
+        const int nvp = S.nva * (S.nva - 1) / 2, q = fdiv(k, S.fd_pva);
+        unrank_pair(q, lo, hi);
         e.i = L.oa[lo];
         e.j = L.oa[hi];
-        unrank_pair(k % nvp, lo, hi);
+        unrank_pair(k - q * nvp, lo, hi);
         e.a = L.va[lo];
         e.b = L.va[hi];
         return e;
     }
     k -= S.nd_aa;
     if (k < S.nd_bb) {
-        int nvp = S.nvb * (S.nvb - 1) / 2;
-        unrank_pair(k / nvp, lo, hi);
+        const int nvp = S.nvb * (S.nvb - 1) / 2, q = fdiv(k, S.fd_pvb);
+        unrank_pair(q, lo, hi);
         e.i = L.ob[lo];
         e.j = L.ob[hi];
-        unrank_pair(k % nvp, lo, hi);
+        unrank_pair(k - q * nvp, lo, hi);
         e.a = L.vb[lo];
         e.b = L.vb[hi];
         return e;
     }
     k -= S.nd_bb;
-    int nbe = S.nb * S.nvb;
-    int sa = k / nbe, sb = k % nbe;
-    e.i = L.oa[sa / S.nva];
-    e.a = L.va[sa % S.nva];
-    e.j = L.ob[sb / S.nvb];
-    e.b = L.vb[sb % S.nvb];
+    const int nbe = S.nb * S.nvb;
+    const int sa = fdiv(k, S.fd_nbe), sb = k - sa * nbe;
+    const int qa = fdiv(sa, S.fd_nva), qb = fdiv(sb, S.fd_nvb);
+    e.i = L.oa[qa];
+    e.a = L.va[sa - qa * S.nva];
+    e.j = L.ob[qb];
+    e.b = L.vb[sb - qb * S.nvb];
     return e;
 }
 
@@ -205,6 +234,11 @@ SysView make_view(int n, int na, int nb, const double *h, const double *eri) {
     S.nd_bb = (nb * (nb - 1) / 2) * (S.nvb * (S.nvb - 1) / 2);
     S.nd_ab = S.ns_a * S.ns_b;
     S.conn = S.ns_a + S.ns_b + S.nd_aa + S.nd_bb + S.nd_ab;
+    S.fd_nva = make_fastdiv(S.nva);
+    S.fd_nvb = make_fastdiv(S.nvb);
+    S.fd_pva = make_fastdiv(S.nva * (S.nva - 1) / 2);
+    S.fd_pvb = make_fastdiv(S.nvb * (S.nvb - 1) / 2);
+    S.fd_nbe = make_fastdiv(S.ns_b);
     S.h = h;
     S.eri = eri;
     return S;
@@ -474,6 +508,7 @@ struct BuildDfArgs {
     SysView S;
     int nh, M, M1, P1, ldp;
     int ldF, ldS, nslice, ns;  // ns = number of single excitations of a row
+    FastDiv fd_nh, fd_M1;      // division by Nh and by M + 1
     int fuseB;  // keep only the B table; A_s[j] = g_j B_s[j] formed on the fly
     const double *theta;
     const float2 *tdf;  // df tables (see k_tables_df)
@@ -556,12 +591,14 @@ __device__ __forceinline__ df df_add1_lazy(df z) {
 __device__ __forceinline__ void single_of(const SysView &S, const RowLists &L, int s, int &i,
                                           int &a) {
     if (s < S.ns_a) {
-        i = L.oa[s / S.nva];
-        a = L.va[s % S.nva];
+        const int q = fdiv(s, S.fd_nva);
+        i = L.oa[q];
+        a = L.va[s - q * S.nva];
     } else {
         s -= S.ns_a;
-        i = L.ob[s / S.nvb];
-        a = L.vb[s % S.nvb];
+        const int q = fdiv(s, S.fd_nvb);
+        i = L.ob[q];
+        a = L.vb[s - q * S.nvb];
     }
 }
 
@@ -580,26 +617,26 @@ __device__ __forceinline__ void singles_of_conn(const SysView &S, int k, int &s1
     k -= S.ns_b;
     int lo, hi, vlo, vhi;
     if (k < S.nd_aa) {
-        const int nvp = S.nva * (S.nva - 1) / 2;
-        unrank_pair(k / nvp, lo, hi);
-        unrank_pair(k % nvp, vlo, vhi);
+        const int nvp = S.nva * (S.nva - 1) / 2, q = fdiv(k, S.fd_pva);
+        unrank_pair(q, lo, hi);
+        unrank_pair(k - q * nvp, vlo, vhi);
         s1 = lo * S.nva + vlo;
         s2 = hi * S.nva + vhi;
         return;
     }
     k -= S.nd_aa;
     if (k < S.nd_bb) {
-        const int nvp = S.nvb * (S.nvb - 1) / 2;
-        unrank_pair(k / nvp, lo, hi);
-        unrank_pair(k % nvp, vlo, vhi);
+        const int nvp = S.nvb * (S.nvb - 1) / 2, q = fdiv(k, S.fd_pvb);
+        unrank_pair(q, lo, hi);
+        unrank_pair(k - q * nvp, vlo, vhi);
         s1 = S.ns_a + lo * S.nvb + vlo;
         s2 = S.ns_a + hi * S.nvb + vhi;
         return;
     }
     k -= S.nd_bb;
     const int nbe = S.nb * S.nvb;
-    s1 = k / nbe;
-    s2 = S.ns_a + k % nbe;
+    s1 = fdiv(k, S.fd_nbe);
+    s2 = S.ns_a + (k - s1 * nbe);
 }
 
 // Same computation as k_build_rows, in double-float arithmetic on the FP32
@@ -763,7 +800,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
         __syncthreads();
         // per single excitation: V_s (FP64 exp), B_s[j], A_s[j] (df)
         for (int e = tid; e < NS * nh; e += BDF_THREADS) {
-            const int s = e / nh, j = e % nh;
+            const int s = fdiv(e, A.fd_nh), j = e - s * nh;
             int i, a;
             single_of(A.S, *sL, s, i, a);
             const bool pos = sSig[j] > 0.f;
@@ -933,7 +970,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
         for (int e = tid; e < A.ldp; e += BDF_THREADS) {
             double ov = 0.0, gv = 0.0;
             if (e < A.P1) {
-                const int r = e / M1, c = e % M1;
+                const int r = fdiv(e, A.fd_M1), c = e - r * M1;
                 const bool xc = (c == 0) || ((x >> (c - 1)) & 1ull);
                 ov = xc ? (r == 0 ? 1.0 : sT[r - 1]) : 0.0;
                 df a = ld_df(sAf + r);
@@ -1364,6 +1401,8 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         B.ldS = p->M | 1;
         B.nslice = std::max(1, BDF_THREADS / (p->nh + 1));
         B.ns = A.S.ns_a + A.S.ns_b;
+        B.fd_nh = make_fastdiv(p->nh);
+        B.fd_M1 = make_fastdiv(p->M1);
         B.fuseB = 0;
         B.theta = p->theta;
         B.tdf = p->tdf;
