@@ -572,12 +572,26 @@ __device__ __forceinline__ void cluster_dots(const float2 *Vs, int le, const LcS
     if (part == 0 && i <= j) stf(pd + i, t);
 }
 
+// floor(t / d) for 0 <= t, d < 2^22 without a divide (a divide converts to and
+// from floating point, and conversions issue at the FP64 rate on this part):
+// t and d are exact in FP32 by adding them into the mantissa of 1.5 * 2^23,
+// t * (1/d) rounded to an integer is within one of the quotient, and one exact
+// integer comparison each way fixes it. rd = __frcp_rn(d as FP32).
+__device__ __forceinline__ float small_float(int v) {
+    return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
+}
+__device__ __forceinline__ int small_div(int t, int d, float rd) {
+    int q = __float_as_int(__fadd_rn(__fmul_rn(small_float(t), rd), 12582912.0f)) - 0x4B400000;
+    q -= (q * d > t) ? 1 : 0;
+    q += ((q + 1) * d <= t) ? 1 : 0;
+    return q;
+}
+
 // w[e] -= sum_{i<=j} Vs[i][e] h[i]: thread (g, e) sums i = g, g + ng, ...; the
 // ng group sums are combined in group order.
 __device__ __forceinline__ void cluster_update(const float2 *Vs, int le, LcShared &S, int E, int EP,
-                                               int ng, int j) {
+                                               int ng, int j, int g, int e) {
     const int tid = threadIdx.x;
-    const int g = tid / EP, e = tid % EP;
     df s0 = df_make(0.f, 0.f), s1 = df_make(0.f, 0.f);
     if (g < ng && e < E) {
         int i = g;
@@ -603,11 +617,14 @@ __global__ void __launch_bounds__(CT, 1) k_lz_cluster(LzArgs a, int j) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int C = (int)cluster_ncta(), q = (int)cluster_rank();
     const int R = a.nrow_grid;
-    const int rlo = q * R / C, rhi = (q + 1) * R / C;
+    const float rC = __frcp_rn(small_float(C));
+    const int rlo = small_div(q * R, C, rC), rhi = small_div((q + 1) * R, C, rC);
     const int e0 = rlo * a.M1;
     const int E = (q == C - 1 ? a.ldp : rhi * a.M1) - e0;
     const int EP = E > 0 ? (E + 31) & ~31 : 32;
-    const int ng = max(1, min(16, CT / EP));
+    const float rEP = __frcp_rn(small_float(EP));
+    const int ng = max(1, min(16, small_div(CT, EP, rEP)));
+    const int tg = small_div(tid, EP, rEP), te = tid - tg * EP;
     // state that CTA 0 overwrites at the end, read before the first barrier
     const double tn0 = a.st->tnorm;
     const double bprev = j > 0 ? a.st->beta[j - 1] : 0.0;
@@ -617,16 +634,19 @@ __global__ void __launch_bounds__(CT, 1) k_lz_cluster(LzArgs a, int j) {
     // fall in different banks)
     extern __shared__ float2 Vs[];
     const int le = E | 1;
-    for (int t = tid; t < (j + 1) * E; t += CT) {
-        const int i = t / E, e = t - i * E;
-        stf(Vs + (size_t)i * le + e, df_split_bits(a.V[(size_t)i * a.ldp + e0 + e]));
+    {
+        const float rE = __frcp_rn(small_float(max(E, 1)));
+        for (int t = tid; t < (j + 1) * E; t += CT) {
+            const int i = small_div(t, E, rE), e = t - i * E;
+            stf(Vs + (size_t)i * le + e, df_split_bits(a.V[(size_t)i * a.ldp + e0 + e]));
+        }
     }
 
     // (a) w = sum over the pencil CTAs' double-float partials: batches of 8
     // independent loads summed pairwise, batches in order, groups in order
     {
         const float2 *part = reinterpret_cast<const float2 *>(a.part);
-        const int g = tid / EP, e = tid % EP;
+        const int g = tg, e = te;
         df acc = df_make(0.f, 0.f);
         if (g < ng && e < E) {
             const float2 *src = part + e0 + e;
@@ -662,14 +682,14 @@ __global__ void __launch_bounds__(CT, 1) k_lz_cluster(LzArgs a, int j) {
     __syncthreads();
     const df h1j = ldf(S.h + j);
     if (q == 0 && tid <= j) stf(S.h1s + tid, ldf(S.h + tid));  // kept for the state
-    cluster_update(Vs, le, S, E, EP, ng, j);
+    cluster_update(Vs, le, S, E, EP, ng, j, tg, te);
     // (c) pass 2: h2 = V^T w, w -= V h2; alpha_j = h1_j + h2_j
     cluster_dots(Vs, le, S, E, j, S.pd2);
     cluster_sync();  // also orders the reads of S.h above before it is overwritten
     for (int i = tid; i <= j; i += CT) stf(S.h + i, cluster_tree_sum(S.pd2 + i, C));
     __syncthreads();
     const df alpha = df_add(h1j, ldf(S.h + j));
-    cluster_update(Vs, le, S, E, EP, ng, j);
+    cluster_update(Vs, le, S, E, EP, ng, j, tg, te);
     // (d) particle-number null space, per grid row (warp per row); the row sums
     // in double-float, the 2 x 2 solve in FP64 by one lane
     if (a.deflate) {
@@ -710,8 +730,9 @@ __global__ void __launch_bounds__(CT, 1) k_lz_cluster(LzArgs a, int j) {
             }
         }
         __syncthreads();
-        for (int t = tid; t < nr * (2 * n + 1); t += CT) {
-            const int lr = t / (2 * n + 1), c = t % (2 * n + 1);
+        const float rM1 = __frcp_rn(small_float(a.M1));
+        for (int t = tid; t < nr * a.M1; t += CT) {
+            const int lr = small_div(t, a.M1, rM1), c = t - lr * a.M1;
             float2 *wr = S.w + (size_t)lr * a.M1;
             if (c == 0) {
                 if (rlo + lr > 0) stf(wr, df_add(ldf(wr), ldf(&S.red[lr])));

@@ -337,10 +337,11 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
     if (warp == NCW) {
         // producer
         if (lane == 0) {
-            int issued = 0;
+            // stage s = i mod S and round = i / S kept incrementally: a divide
+            // converts to and from floating point, at the FP64 rate on this part
+            int issued = 0, s = 0, round = 0;
             for (int i = 0; i < ntiles; ++i) {
-                const int s = i % S;
-                if (i >= S && !mbar_wait_bounded(&empty[s], (uint32_t)(((i / S) - 1) & 1))) {
+                if (round > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)((round - 1) & 1))) {
                     atomicOr(a.flags, FLAG_TIMEOUT);
                     atomicExch(&s_abort, 1);
                     break;
@@ -356,16 +357,28 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
                 bulk_g2s(dst, a.O + row * ldp, bytes, &full[s]);
                 if (MODE != MODE_S) bulk_g2s(dst + tile_elems, a.G + row * ldp, bytes, &full[s]);
                 issued = i + 1;
+                if (++s == S) {
+                    s = 0;
+                    ++round;
+                }
             }
             // every issued copy lands before the CTA may exit (bounded)
-            for (int i = max(0, issued - S); i < issued; ++i)
-                (void)mbar_wait_bounded(&full[i % S], (uint32_t)((i / S) & 1));
+            const int i0 = max(0, issued - S);
+            for (int i = i0, ds = i0 % S, dr = i0 / S; i < issued; ++i) {
+                (void)mbar_wait_bounded(&full[ds], (uint32_t)(dr & 1));
+                if (++ds == S) {
+                    ds = 0;
+                    ++dr;
+                }
+            }
         }
     } else if (warp < ncons) {
-        for (int i = warp; i < ntiles; i += ncons) {
-            const int s = i % S;
+        // stage s = i mod S and parity (i / S) & 1, kept incrementally (S is a
+        // multiple of ncons, so s wraps at most once per step)
+        int s = warp, ph = 0, it = 0;
+        for (int i = warp; i < ntiles; i += ncons, ++it) {
             bool ok = true;
-            if (lane == 0) ok = mbar_wait_bounded(&full[s], (uint32_t)((i / S) & 1));
+            if (lane == 0) ok = mbar_wait_bounded(&full[s], (uint32_t)ph);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok || *(volatile int *)&s_abort) {
                 if (lane == 0) {
@@ -381,13 +394,18 @@ __global__ void __launch_bounds__(NCW * 32 + 32, 1) k_pencil(PencilArgs<T> a) {
                 consume_row<T, NJ, MODE>(ro, ro + tile_elems, vs, ldp, lane,
                                          P::weight(a.w, a.wlo, r0 + (int64_t)t * R + rr), y);
             }
-            if ((i / ncons) % 16 == 15)  // fold lazily accumulated tails now and then
+            if ((it & 15) == 15)  // fold lazily accumulated tails now and then
 #pragma unroll
                 for (int k = 0; k < NCV<T, NJ>::value; ++k)
 #pragma unroll
                     for (int v = 0; v < VEC<T>::value; ++v) P::renorm(y[k][v]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
+            s += ncons;
+            if (s >= S) {
+                s -= S;
+                ph ^= 1;
+            }
         }
     }
     __syncthreads();
