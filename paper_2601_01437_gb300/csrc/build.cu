@@ -68,8 +68,16 @@ __device__ __forceinline__ void unrank_pair(int q, int &lo, int &hi) {
     lo = q - y * (y - 1) / 2;
 }
 
+// parity of the occupied spin orbitals below p, on 32-bit words
 __device__ __forceinline__ int parity_below(uint64_t x, int p) {
-    return __popcll(x & ((1ull << p) - 1ull)) & 1;
+    const unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
+    const int c = p < 32 ? __popc(lo & ((1u << p) - 1u))
+                         : __popc(lo) + __popc(hi & ((1u << (p - 32)) - 1u));
+    return c & 1;
+}
+// occupation of spin orbital p (p < 64), on 32-bit words
+__device__ __forceinline__ bool occ_bit(uint64_t x, int p) {
+    return ((p < 32 ? (unsigned)x >> p : (unsigned)(x >> 32) >> (p - 32)) & 1u) != 0u;
 }
 
 struct SysView {
@@ -91,9 +99,9 @@ struct RowLists {
 __device__ void make_lists(const SysView &S, uint64_t x, RowLists &L) {
     int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     for (int p = 0; p < S.n; ++p) {
-        if ((x >> p) & 1ull) L.oa[c0++] = p; else L.va[c1++] = p;
+        if (occ_bit(x, p)) L.oa[c0++] = p; else L.va[c1++] = p;
         int q = p + S.n;
-        if ((x >> q) & 1ull) L.ob[c2++] = q; else L.vb[c3++] = q;
+        if (occ_bit(x, q)) L.ob[c2++] = q; else L.vb[c3++] = q;
     }
 }
 
@@ -765,7 +773,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 lg += sL1[j];
             }
             for (int p = tid; p < M; p += 32)
-                if ((x >> p) & 1ull) lp += A.theta[p];
+                if (occ_bit(x, p)) lp += A.theta[p];
             lp = warp_sum(lp);
             lg = warp_sum(lg);
             if (tid == 0) {
@@ -971,7 +979,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             double ov = 0.0, gv = 0.0;
             if (e < A.P1) {
                 const int r = fdiv(e, A.fd_M1), c = e - r * M1;
-                const bool xc = (c == 0) || ((x >> (c - 1)) & 1ull);
+                const bool xc = (c == 0) || occ_bit(x, c - 1);
                 ov = xc ? (r == 0 ? 1.0 : sT[r - 1]) : 0.0;
                 df a = ld_df(sAf + r);
                 if (r > 0) a = to_tanh(ld_df(sAf), a, r);
@@ -986,7 +994,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                         s0 = df_add(s0, df_norm(ld_df(sS + (s2 * (nh + 1)) * A.ldS + c - 1)));
                     }
                     if (r > 0) sv = to_tanh(s0, sv, r);
-                    gv = df_to_double(((x >> (c - 1)) & 1ull) ? df_sub(at, sv) : sv);
+                    gv = df_to_double(occ_bit(x, c - 1) ? df_sub(at, sv) : sv);
                 }
             }
             Orow[e] = ov;

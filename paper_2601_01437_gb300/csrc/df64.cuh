@@ -113,10 +113,10 @@ __device__ __forceinline__ df df_fma(df a, df b, df c) {
 // tail within 2^-24 of itself: |x - h - l| <= 2^-48 |x|. Values outside
 // [2^-70, 2^100] other than zero take the FP64 route.
 __device__ __forceinline__ df df_split_bits(double x) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+    // the two 32-bit words directly (no 64-bit integer operations)
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
     const int ex = (int)((hi >> 20) & 0x7ffu);
-    if ((u << 1) == 0ull) return df_make(__uint_as_float(hi & 0x80000000u), 0.f);  // +-0
+    if (((hi << 1) | lo) == 0u) return df_make(__uint_as_float(hi & 0x80000000u), 0.f);  // +-0
     if (ex < 1023 - 70 || ex > 1023 + 100) return df_from_double(x);
     const unsigned sign = hi & 0x80000000u;
     const unsigned up = (lo >> 28) & 1u;  // first dropped bit: round the head up
