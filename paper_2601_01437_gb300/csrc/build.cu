@@ -583,11 +583,6 @@ __device__ __forceinline__ void df_acc(df &acc, df f) {
 }
 __device__ __forceinline__ df df_norm(df a) { return df_fts(a.h, a.l); }
 
-// Z +- 1 for Z > 0 in double-float
-__device__ __forceinline__ df df_add1(df z, float one) {
-    const df s = df_ts(z.h, one);
-    return df_fts(s.h, __fadd_rn(s.l, z.l));
-}
 // 1 + Z for Z >= 0 with the tail left unnormalised (the reciprocal and the
 // products that take it are error-free on the head)
 __device__ __forceinline__ df df_add1_lazy(df z) {
@@ -1147,11 +1142,6 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 to_low<__nv_bfloat16>(double x) {
     return __double2bfloat16(x);
 }
-template <>
-__device__ __forceinline__ float2 to_low<float2>(double x) {
-    const df d = df_split_bits(x);  // integer split: the centring kernel is FP64-pipe bound
-    return make_float2(d.h, d.l);
-}
 
 // Centre in place (FP64) and write the optional low-precision copies:
 //   O_c(x,0) = 1, G'_c(x,0) = E_loc - E,
@@ -1166,11 +1156,6 @@ __device__ __forceinline__ void store_low2(TL *p, double a, double b) {
 template <>
 __device__ __forceinline__ void store_low2<float>(float *p, double a, double b) {
     *reinterpret_cast<float2 *>(p) = make_float2((float)a, (float)b);
-}
-template <>
-__device__ __forceinline__ void store_low2<float2>(float2 *p, double a, double b) {
-    const float2 x = to_low<float2>(a), y = to_low<float2>(b);
-    *reinterpret_cast<float4 *>(p) = make_float4(x.x, x.y, y.x, y.y);
 }
 template <>
 __device__ __forceinline__ void store_low2<__nv_bfloat16>(__nv_bfloat16 *p, double a, double b) {

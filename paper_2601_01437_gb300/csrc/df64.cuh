@@ -162,11 +162,6 @@ __device__ __forceinline__ df df_rsqrt(df s) {
     return df_fts(y0, __fmul_rn(__fmul_rn(0.5f, y0), r));
 }
 
-// 1 - a for 0 <= a <= 2 (TwoSum of 1 and -a.h, then the tail)
-__device__ __forceinline__ df df_one_minus(df a) {
-    const df s = df_ts(1.0f, -a.h);
-    return df_ts(s.h, __fsub_rn(s.l, a.l));
-}
 
 // Multiply by 2^e exactly (as long as the result stays in the FP32 normal range)
 __device__ __forceinline__ df df_ldexp(df a, int e) { return df_make(ldexpf(a.h, e), ldexpf(a.l, e)); }
