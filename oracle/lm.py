@@ -70,6 +70,15 @@ def symmetrise(Hp, mode: str):
     raise ValueError(mode)
 
 
+def eloc_form(Oc, eloc, E):
+    """G'_c of the paper's E_loc estimator (Methods, "Practical Matrix-Free
+    Implementation", eq. matrix_vec_prod: [H_eff]_ij = E[O_i (E_loc - E) O_j]) on
+    the centred basis: G'_c(x,k) = (E_loc(x) - E) O_c(x,k). The exact form keeps
+    one more term, G'_c(x,k) = (E_loc(x) - E) O_c(x,k) + d E_loc(x) / d theta_k
+    (k >= 1), which this estimator drops; column 0 is the same in both."""
+    return (np.asarray(eloc) - E)[:, None] * Oc
+
+
 def pencil_apply(Oc, Gpc, w, v, mode="none"):
     """y_H = O_c^T W (G'_c v) (mode none) or 1/2 (O_c^T W G'_c v + G'_c^T W O_c v)
     (mode half), y_S = O_c^T W (O_c v): the products the paper's matrix-free MVP

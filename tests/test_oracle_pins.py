@@ -127,6 +127,39 @@ def test_G_identity_with_finite_differences():
     assert np.abs(G[:, 0] - eloc).max() <= 1e-13 * np.abs(eloc).max()
 
 
+def test_eloc_estimator_against_finite_differences():
+    """The paper's E_loc estimator (G'_c -> (E_loc - E) O_c) against finite
+    differences of the oracle's local energy and energy: it differs from the exact
+    H~' by O_c^T W dE_loc/dtheta, and its row 0 is half the energy gradient
+    (exact |psi|^2 weights); it is symmetric and vanishes on the particle-number
+    null space."""
+    n, na, nb, nh = 4, 2, 1, 4
+    h, eri = synth.integrals(n, 4)
+    theta = synth.rbm_theta(n, nh, 4, sigma=0.3)
+    pd = lm.build_pencil(n, na, nb, nh, h, eri, theta)
+    _, Hp = lm.pencil_matrices(pd.Oc, pd.Gpc, pd.w)
+    _, He = lm.pencil_matrices(pd.Oc, lm.eloc_form(pd.Oc, pd.eloc, pd.E), pd.w)
+    step = 1e-5
+    D = np.zeros_like(pd.Oc)
+    grad = np.zeros(theta.size)
+    for k in range(theta.size):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += step
+        tm[k] -= step
+        lp, _, ep, _ = native.rows(n, na, nb, nh, h, eri, tp, pd.rows, False, False)
+        lq, _, eq, _ = native.rows(n, na, nb, nh, h, eri, tm, pd.rows, False, False)
+        D[:, k + 1] = (ep - eq) / (2 * step)
+        grad[k] = (lm.weights_exact(lp) @ ep - lm.weights_exact(lq) @ eq) / (2 * step)
+    scale = np.abs(Hp).max()
+    diff = (pd.Oc * pd.w[:, None]).T @ D
+    assert np.abs((Hp - He) - diff).max() <= 1e-7 * scale
+    assert np.abs(He[0, 1:] - 0.5 * grad).max() <= 1e-7 * max(1.0, np.abs(grad).max())
+    assert abs(He[0, 0]) <= 1e-13 * scale
+    assert np.abs(He - He.T).max() <= 1e-14 * np.abs(He).max()
+    nv = lm.null_vectors(n, na, nb, nh)
+    assert np.abs(He @ nv).max() <= 1e-12 * np.abs(He).max()
+
+
 def test_pencil_equals_phi_route():
     """Exact enumeration: H~' = Phi^T (H - E) Phi with Phi = psi O_c / |psi| (no G involved)."""
     w0 = synth.WORKLOADS["tiny_6o6e"]
