@@ -78,7 +78,11 @@ typedef enum { LM_FP64 = 0, LM_FP32 = 1, LM_BF16 = 2, LM_DF64 = 3 } lm_precision
 typedef enum {
     LM_SYM_AUTO = 0, /* NONE for the full enumerated sector, HALF otherwise    */
     LM_SYM_NONE = 1, /* y = O_c^T W G'_c v                                     */
-    LM_SYM_HALF = 2  /* y = 1/2 (O_c^T W G'_c v + G'_c^T W O_c v)              */
+    LM_SYM_HALF = 2, /* y = 1/2 (O_c^T W G'_c v + G'_c^T W O_c v)              */
+    LM_SYM_ELOC = 3  /* the paper's E_loc estimator of H~' (Methods, eq.
+                        matrix_vec_prod): y = O_c^T W diag(E_loc - E) O_c v, i.e.
+                        G'_c -> (E_loc - E) O_c, dropping dE_loc/dtheta; reads O_c
+                        only, symmetric by construction                          */
 } lm_sym;
 
 typedef struct lm_ctx lm_ctx;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libirlnqs.so")
 LM_OK, LM_ERR_ARG, LM_ERR_SIZE, LM_ERR_OOM, LM_ERR_CUDA, LM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 IRL_OK, IRL_BREAKDOWN_INVARIANT, IRL_MAX_RESTARTS, LM_C0_TINY, LM_STATIONARY = 0, 1, 2, 3, 4
 LM_FP64, LM_FP32, LM_BF16, LM_DF64 = 0, 1, 2, 3
-LM_SYM_AUTO, LM_SYM_NONE, LM_SYM_HALF = 0, 1, 2
+LM_SYM_AUTO, LM_SYM_NONE, LM_SYM_HALF, LM_SYM_ELOC = 0, 1, 2, 3
 LM_ARITH_DF64, LM_ARITH_FP64 = 0, 1
 LM_NOALLOC_MAX_LD = 2048
 EXPORT_O, EXPORT_G, EXPORT_LNPSI, EXPORT_ELOC, EXPORT_W, EXPORT_OBAR, EXPORT_ROWS = range(7)

@@ -109,7 +109,7 @@ void pencil_release(lm_pencil *p) {
     void *bufs[] = {p->rows, p->wt,   p->lnpsi, p->eloc, p->O,    p->G,   p->Olo,
                     p->Glo,  p->h,    p->eri,   p->theta, p->tabs, p->stats, p->part,
                     p->V,    p->wvec, p->yvec,  p->hy,   p->sy,   p->tvec, p->dots,
-                    p->st,   p->tdf,  p->wlo, p->bar};
+                    p->st,   p->tdf,  p->wlo, p->wel, p->wello, p->bar};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->hs) cudaFreeHost(p->hs);
@@ -230,6 +230,8 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
         rc = rc ? rc : dalloc(ctx, &p->rows, nr);
         rc = rc ? rc : dalloc(ctx, &p->wt, nr);
         rc = rc ? rc : dalloc(ctx, &p->wlo, nr);
+        rc = rc ? rc : dalloc(ctx, &p->wel, nr);
+        rc = rc ? rc : dalloc(ctx, &p->wello, nr);
         rc = rc ? rc : dalloc(ctx, &p->lnpsi, nr);
         rc = rc ? rc : dalloc(ctx, &p->eloc, nr);
         rc = rc ? rc : dalloc(ctx, &p->O, nr * L);
@@ -340,7 +342,7 @@ extern "C" int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double
     if (!p || !v) return LM_ERR_ARG;
     lm_ctx *ctx = p->ctx;
     cudaSetDevice(ctx->device);
-    if (sym < 0 || sym > 2 || prec < 0 || prec > 3) return lm_fail(ctx, LM_ERR_ARG, "bad sym/prec");
+    if (sym < 0 || sym > 3 || prec < 0 || prec > 3) return lm_fail(ctx, LM_ERR_ARG, "bad sym/prec");
     cudaStream_t s = (cudaStream_t)stream;
     const int sy = sym == LM_SYM_AUTO ? p->sym : sym;
     // the kernels read ldp >= P+1 entries: stage v with zero padding
@@ -385,7 +387,7 @@ size_t lm_pencil_footprint(lm_ctx *ctx, int n, int nh, int64_t n_rows, int prec)
     const size_t M = 2 * n, P1 = (nh + 1) * (M + 1), L = (P1 + 7) / 8 * 8, nr = n_rows;
     const size_t es = prec == LM_FP64 ? 0 : (prec == LM_FP32 ? 4 : (prec == LM_DF64 ? 8 : 2));
     size_t b = nr * L * (16 + 2 * es);              // O, G and the low-precision copies
-    b += nr * (8 * 5 + 8);                         // rows, weights (x2), ln psi, E_loc
+    b += nr * (8 * 7 + 8);                         // rows, weights (x4), ln psi, E_loc
     b += (size_t)n * n * n * n * 16 + 2 * 4 * nh * M * 8;  // integrals and tables
     b += (size_t)ctx->sms * 2 * L * 8;             // partial products
     b += 2 * (LM_MAXKRYLOV + 1) * L * 8 + 16 * L * 8 + (1 << 20);  // bases, vectors, state

@@ -1265,6 +1265,21 @@ __global__ void k_centre_df(const double *__restrict__ O, const double *__restri
     }
 }
 
+// Weights of the E_loc-estimator product: w(x) (E_loc(x) - E), FP64 and
+// double-float (both E_loc and E include the core energy)
+__global__ void k_eloc_weights(const double *__restrict__ wt, const double *__restrict__ eloc,
+                               const double *__restrict__ stats, int64_t n,
+                               double *__restrict__ wel, float2 *__restrict__ wello) {
+    const double E = stats[1];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const double we = wt[r] * (eloc[r] - E);
+        wel[r] = we;
+        const df d = df_split_bits(we);
+        wello[r] = make_float2(d.h, d.l);
+    }
+}
+
 // FP64 copy of double-float pairs (exports of a double-float pencil)
 __global__ void k_df_to_fp64(const float2 *__restrict__ src, double *__restrict__ dst, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -1508,9 +1523,14 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         k_centre<double><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
                                                p->ldp, p->P1, p->e_core, (double *)nullptr,
                                                (double *)nullptr, p->wlo);
+    lm_note_launch(ctx);
+    if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_centre")) return rc;
+    k_eloc_weights<<<(int)std::max<int64_t>(1, std::min<int64_t>((p->n_rows + 255) / 256,
+                                                                 ctx->sms * 4)),
+                     256, 0, s>>>(p->wt, p->eloc, p->stats, p->n_rows, p->wel, p->wello);
     lm_prof_end(ctx, PROF_PREP, s);
     lm_note_launch(ctx);
-    return lm_cuda_check(ctx, cudaGetLastError(), "k_centre");
+    return lm_cuda_check(ctx, cudaGetLastError(), "k_eloc_weights");
 }
 
 int lm_launch_df_to_fp64(lm_ctx *ctx, const float2 *src, double *dst, int64_t n, cudaStream_t s) {

@@ -177,6 +177,8 @@ struct lm_pencil {
     uint64_t *rows;
     double *wt, *lnpsi, *eloc;
     float2 *wlo;        // normalised weights as double-float
+    double *wel;        // w (E_loc - E): the weights of the E_loc-estimator product
+    float2 *wello;      // ... as double-float
     double *O, *G;      // N_s x ldp, centred in place
     void *Olo, *Glo;    // low-precision copies (float or bf16) or null
     double *h, *eri, *theta, *tabs;

@@ -1529,7 +1529,7 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
     if (prm->m > LM_MAXKRYLOV || prm->m < 2 || prm->k < 1 || prm->k >= prm->m || prm->m > p->P1)
         return lm_fail(ctx, LM_ERR_SIZE, "need 1 <= k < m <= min(64, P+1); got k=%d m=%d", prm->k,
                        prm->m);
-    if (prm->sym < 0 || prm->sym > 2 || prm->precision < 0 || prm->precision > 3)
+    if (prm->sym < 0 || prm->sym > 3 || prm->precision < 0 || prm->precision > 3)
         return lm_fail(ctx, LM_ERR_ARG, "bad sym or precision");
     IrlJob *J = new IrlJob();
     J->p = p;

@@ -455,8 +455,8 @@ __global__ void k_reduce_partials(const double *part, int nparts, int ldp, doubl
 }
 
 template <typename T, int NJ, int MODE>
-int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out, const int *skip,
-             int out_df, cudaStream_t s) {
+int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
+             const double *w, const float2 *wl, const int *skip, int out_df, cudaStream_t s) {
     const int nmat = MODE == MODE_S ? 1 : 2;
     const size_t row_bytes = (size_t)nmat * p->ldp * sizeof(T);
     // ring of stages filling the shared memory (at most 32). A stage holds R
@@ -477,8 +477,8 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
     PencilArgs<T> a;
     a.O = O;
     a.G = G;
-    a.w = p->wt;
-    a.wlo = p->wlo;
+    a.w = w;
+    a.wlo = wl;
     a.n_rows = p->n_rows;
     a.ldp = p->ldp;
     a.v = v;
@@ -502,26 +502,33 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
     return lm_cuda_check(p->ctx, cudaGetLastError(), "k_pencil");
 }
 
+// hmode 0: y_H = O_c^T W G'_c v; 1: its symmetrised form; 2: the E_loc
+// estimator O_c^T W diag(E_loc - E) O_c v, the S product with weights w (E_loc - E)
 template <typename T, int NJ>
-int dispatch_mode(lm_pencil *p, const T *O, const T *G, const double *v, int half, int want_s,
+int dispatch_mode(lm_pencil *p, const T *O, const T *G, const double *v, int hmode, int want_s,
                   const int *skip, int out_df, cudaStream_t s) {
-    int rc = half ? launch_t<T, NJ, MODE_H_HALF>(p, O, G, v, p->part, skip, out_df, s)
-                  : launch_t<T, NJ, MODE_H_NONE>(p, O, G, v, p->part, skip, out_df, s);
+    int rc;
+    if (hmode == 2)
+        rc = launch_t<T, NJ, MODE_S>(p, O, G, v, p->part, p->wel, p->wello, skip, out_df, s);
+    else if (hmode == 1)
+        rc = launch_t<T, NJ, MODE_H_HALF>(p, O, G, v, p->part, p->wt, p->wlo, skip, out_df, s);
+    else
+        rc = launch_t<T, NJ, MODE_H_NONE>(p, O, G, v, p->part, p->wt, p->wlo, skip, out_df, s);
     if (!rc && want_s)
-        rc = launch_t<T, NJ, MODE_S>(p, O, G, v, p->part + p->ldp, skip, out_df, s);
+        rc = launch_t<T, NJ, MODE_S>(p, O, G, v, p->part + p->ldp, p->wt, p->wlo, skip, out_df, s);
     return rc;
 }
 
 template <typename T>
-int dispatch_nc(lm_pencil *p, const T *O, const T *G, const double *v, int half, int want_s,
+int dispatch_nc(lm_pencil *p, const T *O, const T *G, const double *v, int hmode, int want_s,
                 const int *skip, int out_df, cudaStream_t s) {
     const int nj = (p->ldp + 31) / 32;
-    if (nj <= 8) return dispatch_mode<T, 8>(p, O, G, v, half, want_s, skip, out_df, s);
-    if (nj <= 16) return dispatch_mode<T, 16>(p, O, G, v, half, want_s, skip, out_df, s);
-    if (nj <= 28) return dispatch_mode<T, 28>(p, O, G, v, half, want_s, skip, out_df, s);
-    if (nj <= 40) return dispatch_mode<T, 40>(p, O, G, v, half, want_s, skip, out_df, s);
-    if (nj <= 52) return dispatch_mode<T, 52>(p, O, G, v, half, want_s, skip, out_df, s);
-    if (nj <= 64) return dispatch_mode<T, 64>(p, O, G, v, half, want_s, skip, out_df, s);
+    if (nj <= 8) return dispatch_mode<T, 8>(p, O, G, v, hmode, want_s, skip, out_df, s);
+    if (nj <= 16) return dispatch_mode<T, 16>(p, O, G, v, hmode, want_s, skip, out_df, s);
+    if (nj <= 28) return dispatch_mode<T, 28>(p, O, G, v, hmode, want_s, skip, out_df, s);
+    if (nj <= 40) return dispatch_mode<T, 40>(p, O, G, v, hmode, want_s, skip, out_df, s);
+    if (nj <= 52) return dispatch_mode<T, 52>(p, O, G, v, hmode, want_s, skip, out_df, s);
+    if (nj <= 64) return dispatch_mode<T, 64>(p, O, G, v, hmode, want_s, skip, out_df, s);
     return lm_fail(p->ctx, LM_ERR_SIZE, "P+1 = %d above the supported 2048", p->P1);
 }
 
@@ -540,23 +547,23 @@ int lm_pencil_ctas(const lm_pencil *p, int prec) {
 
 int lm_launch_pencil(lm_pencil *p, const double *v, int sym, int prec, int want_s,
                      const int *skip, cudaStream_t s, int out_df, int reverse) {
-    const int half = (sym == LM_SYM_HALF);
+    const int hmode = sym == LM_SYM_ELOC ? 2 : sym == LM_SYM_HALF ? 1 : 0;  // see dispatch_mode
     p->order_rev = reverse;  // read by the launch below, on this host thread
     // a double-float pencil keeps no centred FP64 factors: FP64-accurate
     // requests use its double-float pairs
     if (p->prec == LM_DF64 && p->Olo)
-        return dispatch_nc<float2>(p, (const float2 *)p->Olo, (const float2 *)p->Glo, v, half,
+        return dispatch_nc<float2>(p, (const float2 *)p->Olo, (const float2 *)p->Glo, v, hmode,
                                    want_s, skip, out_df, s);
     if (prec == LM_FP64 || p->prec == LM_FP64 || p->Olo == nullptr)
-        return dispatch_nc<double>(p, p->O, p->G, v, half, want_s, skip, out_df, s);
+        return dispatch_nc<double>(p, p->O, p->G, v, hmode, want_s, skip, out_df, s);
     if (p->prec == LM_FP32)
-        return dispatch_nc<float>(p, (const float *)p->Olo, (const float *)p->Glo, v, half,
+        return dispatch_nc<float>(p, (const float *)p->Olo, (const float *)p->Glo, v, hmode,
                                   want_s, skip, out_df, s);
     if (p->prec == LM_DF64)
-        return dispatch_nc<float2>(p, (const float2 *)p->Olo, (const float2 *)p->Glo, v, half,
+        return dispatch_nc<float2>(p, (const float2 *)p->Olo, (const float2 *)p->Glo, v, hmode,
                                    want_s, skip, out_df, s);
     return dispatch_nc<__nv_bfloat16>(p, (const __nv_bfloat16 *)p->Olo,
-                                      (const __nv_bfloat16 *)p->Glo, v, half, want_s, skip,
+                                      (const __nv_bfloat16 *)p->Glo, v, hmode, want_s, skip,
                                       out_df, s);
 }
 

@@ -258,6 +258,44 @@ def _irl_case(ctx, abi, w, theta=None, rows=None, counts=None, prec=0):
     return pen, ref, res, c, dth
 
 
+# ------------------------------------------------------------ E_loc estimator
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (3, 1e-10), (1, 2e-6)], ids=["fp64", "df64", "fp32"])
+def test_pencil_products_eloc_estimator(ctx, abi, prec, tol):
+    """The paper's E_loc estimator (sym = LM_SYM_ELOC): y_H = O_c^T W diag(E_loc - E) O_c v
+    against the oracle's explicit matrix; y_S unchanged."""
+    h, eri = synth.integrals(14, 111)
+    th = synth.rbm_theta(14, 56, 111)
+    rows, cnt = _mc_rows(14, 7, 7, 1000, 111, h)
+    pen, pd = _build_both(ctx, abi, 14, 7, 7, 56, h, eri, th, rows, cnt, prec=prec)
+    S, He = lm.pencil_matrices(pd.Oc, lm.eloc_form(pd.Oc, pd.eloc, pd.E), pd.w)
+    rng = np.random.default_rng(9)
+    for _ in range(3):
+        v = rng.standard_normal(S.shape[0])
+        Hv, Sv = np.zeros_like(v), np.zeros_like(v)
+        pen.apply(v, Hv, Sv, sym=abi.LM_SYM_ELOC, prec=prec)
+        assert _rel(Hv, He @ v) <= tol
+        assert _rel(Sv, S @ v) <= tol
+    pen.free()
+
+
+@pytest.mark.parametrize("name,prec", [("tiny_6o6e", 0), ("f2_10o14e", 3)])
+def test_irl_eloc_estimator(ctx, abi, name, prec):
+    """IRL on the E_loc-estimator operator against the lowest eigenvalue of the
+    oracle's explicit O_c^T W diag(E_loc - E) O_c."""
+    w = synth.WORKLOADS[name]
+    h, eri, th, _, _ = w.inputs()
+    pen, pd = _build_both(ctx, abi, w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th,
+                          prec=prec)
+    _, He = lm.pencil_matrices(pd.Oc, lm.eloc_form(pd.Oc, pd.eloc, pd.E), pd.w)
+    lam_ref = lm.shep(He)[0]
+    assert lam_ref < -1e-8  # not stationary at these parameters
+    res = pen.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=500, sym=abi.LM_SYM_ELOC, prec=prec)
+    assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
+    assert res.lambda_ == pytest.approx(lam_ref, rel=1e-10)
+    assert res.residual <= 1e-10
+    pen.free()
+
+
 def test_irl_tiny_paper_settings(ctx, abi):
     """k=1, m=20, tol=1e-12 (the paper's settings) on the 6-orbital workload."""
     w = synth.WORKLOADS["tiny_6o6e"]
