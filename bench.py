@@ -408,22 +408,29 @@ def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10, n_rows=262144, precs=None
             continue
         pen = ctx.build_OG(sysd, th_d, rows=rows_d, weights=wts_d, n_rows=w.n_rows, prec=pr,
                            stream=s)
-        cases = [(name, pr, b)] + ([("fp64", abi.LM_FP64, 8)] if name == "fp32" else [])
-        for nm, pp, bb in cases:
+        # (name, storage, bytes per element, operator, matrices streamed); the
+        # paper's E_loc estimator streams O_c only
+        cases = [(name, pr, b, abi.LM_SYM_HALF, 2)]
+        if name == "fp32":
+            cases += [("fp64", abi.LM_FP64, 8, abi.LM_SYM_HALF, 2),
+                      ("fp32_eloc_estimator", abi.LM_FP32, 4, abi.LM_SYM_ELOC, 1)]
+        for nm, pp, bb, sy, nmat in cases:
             for _ in range(3):
-                pen.apply(v, hv, None, sym=abi.LM_SYM_HALF, prec=pp, stream=s)
+                pen.apply(v, hv, None, sym=sy, prec=pp, stream=s)
             torch.cuda.synchronize()
             ctx.stats_reset(profile=True)
             for _ in range(reps):
-                pen.apply(v, hv, None, sym=abi.LM_SYM_HALF, prec=pp, stream=s)
+                pen.apply(v, hv, None, sym=sy, prec=pp, stream=s)
             st = ctx.stats()
             d = st.pencil_ms / st.pencil_count / 1e3
-            nbytes = w.n_rows * p1 * 2 * bb + 8 * w.n_rows
+            nbytes = w.n_rows * p1 * nmat * bb + 8 * w.n_rows
             out[nm] = {"avg_ms": d * 1e3, "achieved": nbytes / d / 1e9, "unit": "GB/s",
                        "peak": hbm, "frac": nbytes / d / 1e9 / hbm, "bytes": nbytes,
                        "launches": int(st.pencil_count),
                        "traffic": (NCU_TRAFFIC[("k_pencil_fp32", "licl_14o14e_mc")]
-                                   if nm == "fp32" and n_rows == 262144 else None)}
+                                   if nm == "fp32" and n_rows == 262144 else None),
+                       "operator": "E_loc estimator O_c^T W diag(E_loc - E) O_c v"
+                                   if sy == abi.LM_SYM_ELOC else "symmetrised H~'"}
         pen.free()
     out["workload"] = (f"{w.name}: {w.n_rows} MC rows x P+1 = {p1}, symmetrised H~' product, "
                        f"peak = {hbm_src} hbm_gbs")
