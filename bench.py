@@ -159,7 +159,7 @@ NCU_TRAFFIC = {("k_build_rows_df", "f2_10o14e"): 138.88e6,
 
 
 def algorithmic_units(w, arith="df64"):
-    """Per-launch algorithmic work of the two dominant kernels (derivation in the design doc).
+    """Per-launch algorithmic work of the two dominant kernels.
 
     Row build: per connection x hidden unit (ratio factor, tanh) and per
     connection x augmented row (accumulation into G), counted in the arithmetic
