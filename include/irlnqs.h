@@ -35,8 +35,9 @@
  *   across the ABI. lm_last_error gives a one-line description of the last
  *   failure on a context.
  * Limits: M = 2*n_orb <= 64, Nh <= 127, P+1 <= 2048, Krylov dimension m <= 64.
- * Tuning overrides (environment, read at each launch; results are exact either
- *   way): IRLNQS_LANCZOS=cluster|coop|split restricts the Lanczos-step kernel
+ * Tuning overrides (environment, read at each launch; they change reduction
+ *   orders, so the last bits of results, within the same parity bars):
+ *   IRLNQS_LANCZOS=cluster|coop|split restricts the Lanczos-step kernel
  *   choice; IRLNQS_BUILD_LAYOUT=<slices>:<0|1> fixes the double-float row
  *   build's scatter slices and whether its A table is dropped.
  */
