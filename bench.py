@@ -154,8 +154,7 @@ class ClockSampler:
 NCU_TRAFFIC = {("k_build_rows_df", "f2_10o14e"): 138.88e6,
                # Lanczos products alternate their row order: with the L2 left warm
                # (ncu --cache-control none) a product reads 113 MB of its 198.5 MB
-               ("k_pencil", "f2_10o14e"): 117.0e6,
-               ("k_pencil_fp32", "licl_14o14e_mc"): 3.488e9}
+               ("k_pencil", "f2_10o14e"): 117.0e6}
 
 
 def algorithmic_units(w, arith="df64"):
