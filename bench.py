@@ -35,9 +35,12 @@ METRIC = "LM steps/sec"
 UNIT = "LM steps/s"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# ALU peaks measured by the project's probe on this machine's GB300 (FMA = 2 flops)
-FP64_PEAK_TFLOPS = 1.20
-FP32_PEAK_TFLOPS = 74.6
+# ALU peaks from the unit counts and the maximum SM clock (FMA = 2 flops):
+# 152 SMs at 2070 MHz, 128 FP32 lanes and 2 FP64 lanes per SM. (The project's
+# probe measured 74.6 and 1.20 TFLOP/s on this machine's GB300.)
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.6
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 1.26
 
 
 def parse():
@@ -286,8 +289,9 @@ def run_gpu(args, rank, world, local):
                          "traffic": NCU_TRAFFIC.get((kname, w.name)) if args.arith == "df64" else None,
                          "avg_ms": d * 1e3,
                          "launches": int(st.build_count), "total_ms": st.build_ms,
-                         "peak_source": ("FP32 FFMA" if args.arith == "df64" else "FP64 DFMA") +
-                         " throughput measured by the project probe (FMA = 2 flops)"}
+                         "peak_source": ("152 SMs x 128 FP32 lanes" if args.arith == "df64"
+                                         else "152 SMs x 2 FP64 lanes") +
+                         " x 2 flops (FMA) x 2070 MHz, from the unit counts and clocks"}
     if st.pencil_count:
         d = st.pencil_ms / st.pencil_count / 1e3
         ach = pencil_bytes / d / 1e9
