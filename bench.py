@@ -150,10 +150,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ workload
 # DRAM bytes (read + write) per launch from the ncu captures summarised in
-# profiles/ (k_build_rows_df_f2_10o14e.md, k_pencil_df64_f2_10o14e.md,
-# k_pencil_fp32_licl_mc.md, the last scaled from 65,536 to 262,144 rows). They
-# describe the kernels as committed with them; set an entry to None when its
-# kernel changes until it is captured again.
+# profiles/ (k_build_rows_df_f2_10o14e.md, k_pencil_df64_f2_10o14e.md). They
+# describe the kernels as committed with them; drop an entry when its kernel
+# changes until it is captured again.
 NCU_TRAFFIC = {("k_build_rows_df", "f2_10o14e"): 138.88e6,
                # Lanczos products alternate their row order: with the L2 left warm
                # (ncu --cache-control none) a product reads 113 MB of its 198.5 MB
