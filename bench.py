@@ -35,6 +35,8 @@ METRIC = "LM steps/sec"
 UNIT = "LM steps/s"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+# GB300's published HBM3e bandwidth, reported beside the measured copy rate
+HBM_NOMINAL_GBS = 7900.0
 # ALU peaks from the unit counts and the maximum SM clock (FMA = 2 flops):
 # 152 SMs at 2070 MHz, 128 FP32 lanes and 2 FP64 lanes per SM. (The project's
 # probe measured 74.6 and 1.20 TFLOP/s on this machine's GB300.)
@@ -55,6 +57,10 @@ def parse():
     ap.add_argument("--no-pencil-c2", action="store_true",
                     help="skip the pencil-matvec HBM measurement on the LiCl-shaped MC pencil")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance batch")
+    ap.add_argument("--no-fp64-c1", action="store_true",
+                    help="skip the native-FP64 F2-shaped LM steps")
+    ap.add_argument("--no-mixed-c2", action="store_true",
+                    help="skip the LiCl-shaped mixed-precision LM steps")
     ap.add_argument("--no-serving", action="store_true", help="skip the Poisson serving run")
     ap.add_argument("--serve-seconds", type=float, default=1.0,
                     help="length of the Poisson arrival stream of the serving run")
@@ -159,31 +165,157 @@ NCU_TRAFFIC = {("k_build_rows_df", "f2_10o14e"): 138.88e6,
                ("k_pencil", "f2_10o14e"): 117.0e6}
 
 
-def algorithmic_units(w, arith="df64"):
-    """Per-launch algorithmic work of the two dominant kernels.
-
-    Row build: per connection x hidden unit (ratio factor, tanh) and per
-    connection x augmented row (accumulation into G), counted in the arithmetic
-    the kernel uses. df64: FP32 flops of the double-float formulation (add/mul
-    1, fma 2, rcp 1; df product 10, 1 + Z 10, reciprocal 16, lazy sum 8): per
-    hidden unit 1 + Z, 1/(1 + Z), the running product and the scaling by c
-    (doubles also Z = A B), per augmented row one lazy sum per moved orbital
-    (singles also the all-connection sum): singles 46 + 24, doubles 56 + 32.
-    fp64: FP64 flops (divide 1): singles 9 + 4, doubles 13 + 6.
-    Pencil: O_c and G'_c read once, N_s (P+1) (b_O + b_G) + 8 N_s bytes.
-    """
-    n, na, nb, nh = w.n_orb, w.n_alpha, w.n_beta, w.n_hidden
+def connections(w):
+    """Connected determinants per row (singles + doubles conserving N_alpha, N_beta)."""
+    n, na, nb = w.n_orb, w.n_alpha, w.n_beta
     va, vb = n - na, n - nb
     singles = na * va + nb * vb
     doubles = (na * (na - 1) // 2) * (va * (va - 1) // 2) + \
               (nb * (nb - 1) // 2) * (vb * (vb - 1) // 2) + na * va * nb * vb
-    c = {"df64": (46, 24, 56, 32), "fp64": (9, 4, 13, 6)}[arith]
-    flops_row = singles * (nh * c[0] + (nh + 1) * c[1]) + doubles * (nh * c[2] + (nh + 1) * c[3])
-    build_flops = flops_row * w.n_rows
-    P1 = (nh + 1) * (2 * n + 1)
+    return singles, doubles
+
+
+def algorithmic_units(w):
+    """Per-launch algorithmic work of the two dominant kernels.
+
+    Row build: the method's own count, 2 N_s conn (P+1) flops (one multiply-add
+    per connection and augmented-basis entry of G), whatever arithmetic carries
+    it out. Pencil: O_c and G'_c read once, N_s (P+1) (b_O + b_G) + 8 N_s bytes.
+    """
+    singles, doubles = connections(w)
+    P1 = (w.n_hidden + 1) * (2 * w.n_orb + 1)
+    build_flops = 2 * w.n_rows * (singles + doubles) * P1
     bytes_for = {"f64": 16, "f32": 8, "bf16": 4}
     pencil_bytes = w.n_rows * P1 * bytes_for[w.precision] + 8 * w.n_rows
     return build_flops, pencil_bytes
+
+
+def implementation_flops(w, arith="df64"):
+    """Instructions-level flop count of the row build as implemented, for comparison
+    with the algorithmic count: per connection x hidden unit (ratio factor, tanh) and
+    per connection x augmented row (accumulation into G). df64: FP32 flops of the
+    double-float formulation (add/mul 1, fma 2, rcp 1; df product 10, 1 + Z 10,
+    reciprocal 16, lazy sum 8): singles 46 + 24, doubles 56 + 32. fp64: FP64 flops
+    (divide 1): singles 9 + 4, doubles 13 + 6."""
+    singles, doubles = connections(w)
+    nh = w.n_hidden
+    c = {"df64": (46, 24, 56, 32), "fp64": (9, 4, 13, 6)}[arith]
+    flops_row = singles * (nh * c[0] + (nh + 1) * c[1]) + doubles * (nh * c[2] + (nh + 1) * c[3])
+    return flops_row * w.n_rows
+
+
+def build_roofline(st, w, arith):
+    """Roofline entry of the row build from the live event timings in `st`: achieved
+    = the algorithmic 2 N_s conn (P+1) flops per launch / average launch time,
+    against the peak of the pipe the arithmetic runs on (double-float: FP32 lanes;
+    native FP64: FP64 lanes); the implementation's own flop count beside it."""
+    build_flops, _ = algorithmic_units(w)
+    d = st.build_ms / st.build_count / 1e3
+    ach = build_flops / d / 1e12
+    pk = FP32_PEAK_TFLOPS if arith == "df64" else FP64_PEAK_TFLOPS
+    kname = "k_build_rows_df" if arith == "df64" else "k_build_rows"
+    impl = implementation_flops(w, arith)
+    return {"kernel": kname, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+            "frac": ach / pk,
+            "traffic": NCU_TRAFFIC.get((kname, w.name)),
+            "algorithmic_flops": build_flops,
+            "algorithmic": "2 N_s conn (P+1): one multiply-add per connection and "
+                           "augmented-basis entry of G",
+            "impl_flops": impl, "impl_tflops": impl / d / 1e12,
+            "impl_flop_count": ("FP32 flops of the double-float formulation" if arith == "df64"
+                                else "FP64 flops"),
+            "avg_ms": d * 1e3, "launches": int(st.build_count), "total_ms": st.build_ms,
+            "peak_source": ("152 SMs x 128 FP32 lanes" if arith == "df64"
+                            else "152 SMs x 2 FP64 lanes") +
+            " x 2 flops (FMA) x 2070 MHz, from the unit counts and clocks"}
+
+
+def timed_lm_steps(abi, ctx, s, sysd, w, theta0, rows_d, wts_d, prec, steps, warmup):
+    """LM steps of workload w on stream s (build, IRL, refinement, theta += dtheta; theta
+    restarts from theta0 every w.lm_steps steps): CUDA-event time of `steps` steps after
+    `warmup`, the last result and the context's counters over the timed steps."""
+    import torch
+    theta = theta0.clone()
+    dth = torch.zeros_like(theta0)
+    state = {"pen": None, "res": None, "first": None}
+
+    def one(i):
+        if i % w.lm_steps == 0:
+            with torch.cuda.stream(s):
+                theta.copy_(theta0)
+        state["pen"] = ctx.build_OG(sysd, theta, rows=rows_d, weights=wts_d, n_rows=w.n_rows,
+                                    prec=prec, stream=s, pencil=state["pen"])
+        state["res"] = state["pen"].irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200,
+                                             prec=prec, dtheta_out=dth, theta_inout=theta,
+                                             stream=s)
+        if state["first"] is None:
+            state["first"] = state["res"]
+
+    for i in range(warmup):
+        one(i)
+    torch.cuda.synchronize()
+    ctx.stats_reset(profile=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for i in range(steps):
+        one(warmup + i)
+    e1.record(s)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    state["pen"].free()
+    return e0.elapsed_time(e1), state["res"], state["first"], st
+
+
+def native_fp64_c1(abi, ctx, s, dev, w, steps=5, warmup=2):
+    """The F2-shaped LM step with the configuration's plain FP64 taken literally: native
+    FP64 row build (k_build_rows) and FP64 pencil factors in every Lanczos product."""
+    import torch
+    h, eri, th0, rows, counts = w.inputs()
+    sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, torch.from_numpy(h).to(dev),
+                      torch.from_numpy(eri).to(dev), arith=abi.LM_ARITH_FP64)
+    ms, res, _, st = timed_lm_steps(abi, ctx, s, sysd, w, torch.from_numpy(th0).to(dev), None,
+                                    None, abi.LM_FP64, steps, warmup)
+    return {"workload": f"{w.name}, native FP64 build and FP64 pencil factors",
+            "value": steps / (ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "dtype": "f64",
+            "build": build_roofline(st, w, "fp64"),
+            "pencil_avg_ms": st.pencil_ms / max(st.pencil_count, 1),
+            "last_step": {"lambda": res.lambda_, "n_matvec": res.n_matvec,
+                          "residual": res.residual}}
+
+
+def mixed_c2(abi, ctx, s, dev, steps=2, warmup=1):
+    """The LiCl-shaped mixed-precision LM step (14 spatial orbitals, 14 electrons, 262,144
+    MC rows, Nh = 56, P+1 = 1,653): FP32 then BF16 O_c/G'_c copies for the first IRL phase
+    with FP64 continuation and refinement, against the plain FP64 path (FP64 factors in
+    every product) on the same rows and theta; |lambda - lambda_FP64| of the first step
+    of each precision."""
+    import torch
+    w = synth.WORKLOADS["licl_14o14e_mc"]
+    h, eri, th0, rows, counts = w.inputs()
+    sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, torch.from_numpy(h).to(dev),
+                      torch.from_numpy(eri).to(dev))
+    rows_d = torch.from_numpy(rows.view(np.int64)).to(dev)
+    wts_d = torch.from_numpy(counts.astype(np.float64)).to(dev)
+    th_d = torch.from_numpy(th0).to(dev)
+    out = {"workload": (f"{w.name}: {w.n_rows} MC rows, P+1 = {w.n_params + 1}, "
+                        f"{w.lm_steps}-step LM trajectories, IRL m={w.m} k={w.k} tol={w.tol:g}")}
+    lam = {}
+    for name, pr in (("fp64", abi.LM_FP64), ("fp32", abi.LM_FP32), ("bf16", abi.LM_BF16)):
+        ms, res, first, st = timed_lm_steps(abi, ctx, s, sysd, w, th_d, rows_d, wts_d, pr, steps,
+                                            warmup)
+        lam[name] = first.lambda_
+        out[name] = {"value": steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "build_ms": st.build_ms / max(st.build_count, 1),
+                     "pencil_ms_total_per_step": st.pencil_ms / steps,
+                     "lambda_first_step": first.lambda_, "n_matvec": first.n_matvec,
+                     "n_matvec_lowp": first.n_matvec_lowp, "residual": first.residual}
+    for name in ("fp32", "bf16"):
+        out[name]["abs_err_vs_fp64_ha"] = abs(lam[name] - lam["fp64"])
+        out[name]["speedup_vs_fp64"] = out[name]["value"] / out["fp64"]["value"]
+    out["steps"], out["warmup"] = steps, warmup
+    return out
 
 
 def run_gpu(args, rank, world, local):
@@ -252,7 +384,10 @@ def run_gpu(args, rank, world, local):
         "metric": METRIC, "value": args.steps * world / (ms / 1e3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": w.precision, "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": ("df64" if w.precision == "f64" and "df64" in (args.arith, args.pencil)
+                  else w.precision),
+        "data": "synthetic",
         "config": {
             "workload": (f"{w.name}: {w.n_orb} spatial orbitals, {w.n_alpha + w.n_beta} electrons, "
                          f"{w.n_rows} {'determinants (exact sector)' if w.exact else 'MC rows'}, "
@@ -274,28 +409,17 @@ def run_gpu(args, rank, world, local):
                       "residual": res.residual},
     }
     # roofline of the dominant kernel, live CUDA-event durations over the timed region
-    build_flops, pencil_bytes = algorithmic_units(w, args.arith)
+    build_flops, pencil_bytes = algorithmic_units(w)
     hbm, hbm_src = peaks()
     kern = {}
     if st.build_count:
-        d = st.build_ms / st.build_count / 1e3
-        ach = build_flops / d / 1e12
-        pk = FP32_PEAK_TFLOPS if args.arith == "df64" else FP64_PEAK_TFLOPS
-        kname = "k_build_rows_df" if args.arith == "df64" else "k_build_rows"
-        kern["build"] = {"kernel": kname,
-                         "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                         "frac": ach / pk,
-                         "traffic": NCU_TRAFFIC.get((kname, w.name)) if args.arith == "df64" else None,
-                         "avg_ms": d * 1e3,
-                         "launches": int(st.build_count), "total_ms": st.build_ms,
-                         "peak_source": ("152 SMs x 128 FP32 lanes" if args.arith == "df64"
-                                         else "152 SMs x 2 FP64 lanes") +
-                         " x 2 flops (FMA) x 2070 MHz, from the unit counts and clocks"}
+        kern["build"] = build_roofline(st, w, args.arith)
     if st.pencil_count:
         d = st.pencil_ms / st.pencil_count / 1e3
         ach = pencil_bytes / d / 1e9
         kern["pencil"] = {"kernel": "k_pencil", "bound": "hbm", "achieved": ach, "peak": hbm,
                           "unit": "GB/s", "frac": ach / hbm,
+                          "peak_nominal": HBM_NOMINAL_GBS, "frac_of_nominal": ach / HBM_NOMINAL_GBS,
                           "traffic": NCU_TRAFFIC.get(("k_pencil", w.name))
                           if args.pencil == "df64" and w.precision == "f64" else None,
                           "avg_ms": d * 1e3, "launches": int(st.pencil_count),
@@ -373,6 +497,11 @@ def run_gpu(args, rank, world, local):
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         pen2.free()
     state["pen"].free()
+    if not args.no_fp64_c1 and rank == 0 and world == 1 and w.name == "f2_10o14e" and \
+            (args.arith, args.pencil) != ("fp64", "fp64"):
+        out["native_fp64_c1"] = native_fp64_c1(abi, ctx, s, dev, w)
+    if not args.no_mixed_c2 and rank == 0 and world == 1 and w.name != "licl_14o14e_mc":
+        out["mixed_c2"] = mixed_c2(abi, ctx, s, dev)
     if not args.no_pencil_c2 and rank == 0 and world == 1:
         out["pencil_c2"] = pencil_c2(abi, ctx, s, dev, hbm, hbm_src)
     if not args.no_batched and rank == 0 and world == 1:
@@ -428,6 +557,8 @@ def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10, n_rows=262144, precs=None
             nbytes = w.n_rows * p1 * nmat * bb + 8 * w.n_rows
             out[nm] = {"avg_ms": d * 1e3, "achieved": nbytes / d / 1e9, "unit": "GB/s",
                        "peak": hbm, "frac": nbytes / d / 1e9 / hbm, "bytes": nbytes,
+                       "peak_nominal": HBM_NOMINAL_GBS,
+                       "frac_of_nominal": nbytes / d / 1e9 / HBM_NOMINAL_GBS,
                        "launches": int(st.pencil_count),
                        # the FP32 c2 capture predates the divide-free pipeline
                        # counters: no traffic figure until it is taken again

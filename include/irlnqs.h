@@ -175,7 +175,7 @@ const char *lm_last_error(const lm_ctx *ctx);
  *   O_c(x,k) = O_k(x) - <O_k>, G'_c(x,k) = G_k(x) - <O_k> E_loc(x) - E O_c(x,k).
  * *inout: NULL to create a pencil, or an existing pencil of the same system
  *   and row count to rebuild in place (buffers are reused).
- * Errors: LM_ERR_SIZE for M > 64 or Nh > 256 or bad electron counts;
+ * Errors: LM_ERR_SIZE for M > 64 or Nh > 127 or P+1 > 2048 or bad electron counts;
  *   LM_ERR_ARG if a given row lies outside the sector (detected on the device,
  *   reported by this call).
  */
@@ -240,32 +240,44 @@ int lm_debug_connections(lm_ctx *ctx, const lm_system *sys, const uint64_t *rows
  *        4 normalised weights (N_s), 5 mean O (ld), 6 rows (N_s, as uint64 bits). */
 int lm_pencil_export(lm_pencil *p, int what, void *dst, void *stream);
 
+/* Per-cycle record of the last irl_step on p (Algorithm 1, step 3: the Ritz
+ * values of T_m and the residual test of each cycle): for cycle i (0 = the
+ * first Lanczos cycle, then one per implicit restart, a low-precision phase's
+ * cycles before its FP64 continuation's), lam[i] is the lowest Ritz value of
+ * T_m, res[i] the residual estimate beta_m |e_m^T u| and lowp[i] is 1 if the
+ * cycle used the low-precision factors. Up to cap entries are written (any
+ * output may be NULL); *n receives the number of cycles recorded (at most
+ * 1024). Host memory; call after irl_step has returned. */
+int lm_irl_history(lm_pencil *p, double *lam, double *res, int *lowp, int cap, int *n);
+
 /* ---- pencil product without allocation -------------------------------- */
 
-/* The paper has no counterpart: this is an operational entry point for callers
- * that cannot allocate device memory -- code inside a CUDA stream capture that
- * must not create allocations, allocators that own all device memory (a
- * framework's caching pool, an embedded runtime with a fixed budget), or
- * real-time loops that must not wait on the allocator.
+/* The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need a product -- a framework whose
+ * caching allocator has reserved the device memory and forbids allocations
+ * behind its back, an embedded solver given a fixed memory budget at start-up,
+ * or a time-critical loop that cannot afford the synchronisation an
+ * allocation or a free may cause.
  *
  * Same product as lm_apply_pencil with FP64 factors, but on the caller's
  * arrays instead of a pencil handle: O_c and G_c are n_rows x ld row-major
  * FP64 (columns >= p1 ignored), w holds the n_rows normalised weights, v has
  * p1 entries, Hv and Sv (either may be NULL, not both) receive p1 entries.
- * sym is LM_SYM_NONE or LM_SYM_HALF. Every array must be device memory, and
- * O_c, G_c 16-byte aligned (LM_ERR_ARG otherwise); ld must be a multiple of 8
- * and at most
- * LM_NOALLOC_MAX_LD (LM_ERR_SIZE otherwise).
+ * sym is LM_SYM_NONE or LM_SYM_HALF. Every array must be memory of the current
+ * device (or managed memory), and O_c, G_c 16-byte aligned (LM_ERR_ARG
+ * otherwise); ld must be a multiple of 8 and at most LM_NOALLOC_MAX_LD
+ * (LM_ERR_SIZE otherwise).
  *
  * It calls no allocator: its scratch (partial products, padded v, a status
  * word) lives in one 4 MiB file-scope device array that every GPU loading the
- * library holds until the process exits. The first call on a device resolves
- * that array's address (cudaGetSymbolAddress) and should come before any
- * stream capture. All calls share the array and each call overwrites it, so
- * calls that can overlap on a GPU (other streams, other host threads) race
- * and must be serialised by the caller. If a bounded wait inside the kernel
- * gives up, Hv and Sv are filled with NaN. Work is enqueued on `stream`; the
- * call does not synchronise. */
+ * library holds until the process exits. The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture. All calls share the array
+ * and each call overwrites it (the status word and the padded v are cleared
+ * or rewritten by every call), so calls that can overlap on a GPU (other
+ * streams, other host threads) race and must be serialised by the caller. If
+ * a bounded wait inside the kernel gives up, Hv and Sv are filled with NaN.
+ * Work is enqueued on `stream`; the call does not synchronise. */
 #define LM_NOALLOC_MAX_LD 2048
 int lm_apply_pencil_noalloc(const double *O_c, const double *G_c, const double *w, int64_t n_rows,
                             int ld, int p1, const double *v, double *Hv, double *Sv, int sym,

@@ -102,6 +102,7 @@ _SIGNATURES = {
     "lm_server_poll": (c_int, [c_vp, c_vp, c_int, ctypes.POINTER(c_int)]),
     "lm_server_pending": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "lm_server_free": (c_int, [c_vp]),
+    "lm_irl_history": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, ctypes.POINTER(c_int)]),
     "lm_stats_reset": (c_int, [c_vp, c_int]),
     "lm_stats_get": (c_int, [c_vp, ctypes.POINTER(lm_stats)]),
 }
@@ -265,6 +266,18 @@ class Pencil:
                             ptr(dtheta_out), ptr(theta_inout), stream_handle(stream))
         self.ctx.check(rc, "irl_step")
         return res
+
+    def irl_history(self):
+        """lm_irl_history: per-cycle (lowest Ritz value, residual estimate, low-precision flag)
+        of the last irl_step, as three arrays."""
+        n = c_int()
+        self.ctx.check(lib().lm_irl_history(self.handle, None, None, None, 0, ctypes.byref(n)),
+                       "lm_irl_history")
+        k = n.value
+        lam, res, lowp = np.zeros(k), np.zeros(k), np.zeros(k, dtype=np.int32)
+        self.ctx.check(lib().lm_irl_history(self.handle, ptr(lam), ptr(res), ptr(lowp), k,
+                                            ctypes.byref(n)), "lm_irl_history")
+        return lam, res, lowp
 
     def export(self, what, out=None):
         inf = self.info()

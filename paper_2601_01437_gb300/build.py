@@ -20,6 +20,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libirlnqs.so")
 SOURCES = ["abi.cu", "build.cu", "pencil.cu", "irl.cu", "noalloc.cu", "engine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+HEADERS = sorted([os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+                 + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")])
 
 
 def nvcc() -> str:
@@ -37,7 +39,8 @@ def _flags(extra=()):
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "internal.cuh"), os.path.join(INCLUDE, "irlnqs.h")]
+    # every shared header of the sources (internal.cuh, df64.cuh, ...) and the ABI header
+    deps = [src, *HEADERS]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

@@ -13,6 +13,7 @@
 #define LM_MAXM 64      // spin orbitals
 #define LM_MAXH 256     // hidden units
 #define LM_MAXKRYLOV 64 // Krylov dimension
+#define LM_HIST_MAX 1024 // IRL cycles recorded per solve (lm_irl_history)
 
 // Bound on polls of one mbarrier phase before a kernel gives up (each
 // try_wait may itself suspend for a short, hardware-defined time).
@@ -206,6 +207,12 @@ struct lm_pencil {
     int *d_flags;       // &st->flags: error flags of this pencil's kernels
     unsigned *bar;      // grid-barrier words of the cooperative Lanczos kernel
     double E_host;
+    // per IRL cycle of the last irl_step on this pencil (host side): the lowest
+    // Ritz value of T_m, the residual estimate beta_m |u_m|, and whether the
+    // cycle ran on the low-precision factors
+    int n_hist;
+    double hist_lam[LM_HIST_MAX], hist_res[LM_HIST_MAX];
+    int hist_lowp[LM_HIST_MAX];
 };
 
 // ---------------------------------------------------------------------------

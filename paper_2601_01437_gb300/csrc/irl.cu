@@ -1536,6 +1536,7 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
     J->s = s;
     J->prm = *prm;
     J->state = JOB_INIT;
+    p->n_hist = 0;
     if (cudaEventCreateWithFlags(&J->ev, cudaEventDisableTiming) != cudaSuccess) {
         delete J;
         return lm_fail(ctx, LM_ERR_CUDA, "cudaEventCreate");
@@ -1621,6 +1622,12 @@ int irl_job_advance(IrlJob *J, int *done) {
         const IrlState &h = *p->st_host;
         if (h.flags & FLAG_TIMEOUT)
             return lm_fail(ctx, LM_ERR_TIMEOUT, "pencil pipeline wait timed out");
+        if (p->n_hist < LM_HIST_MAX) {
+            p->hist_lam[p->n_hist] = h.lam;
+            p->hist_res[p->n_hist] = h.res;
+            p->hist_lowp[p->n_hist] = J->in_lowp ? 1 : 0;
+            p->n_hist++;
+        }
         if (!(h.conv || h.broke || J->cycle >= J->max_restarts)) {
             // implicit restart, then the next cycle from j = k
             double *Vnew = p->V + (size_t)(LM_MAXKRYLOV + 1) * p->ldp;
@@ -1708,4 +1715,17 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
     if (!rc) irl_job_result(J, out);
     irl_job_free(J);
     return rc;
+}
+
+extern "C" int lm_irl_history(lm_pencil *p, double *lam, double *res, int *lowp, int cap,
+                              int *n) {
+    if (!p || !n || cap < 0) return LM_ERR_ARG;
+    const int k = std::min(cap, p->n_hist);
+    for (int i = 0; i < k; ++i) {
+        if (lam) lam[i] = p->hist_lam[i];
+        if (res) res[i] = p->hist_res[i];
+        if (lowp) lowp[i] = p->hist_lowp[i];
+    }
+    *n = p->n_hist;
+    return LM_OK;
 }

@@ -1,16 +1,17 @@
 // lm_apply_pencil_noalloc: the FP64 pencil product for callers that cannot
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA stream
-// capture that must not create allocations, allocators that own all device
-// memory and forbid side allocations (a framework's caching pool, an embedded
-// runtime with a fixed memory budget), or real-time loops that must not block
-// on the allocator. lm_apply_pencil needs a pencil handle whose buffers the
-// library allocated; this entry point instead takes the caller's O_c, G'_c,
-// weights, v and outputs, and keeps its scratch (the per-CTA partial
-// products, the zero-padded copy of v and a status word) in one file-scope
-// device array of fixed size. Every GPU that loads the library holds that
-// array until the process exits.
+// Some callers of this library cannot call cudaMalloc at the point where they
+// need a pencil product: a framework whose caching allocator has reserved the
+// device memory and forbids allocations behind its back, an embedded solver
+// that was given a fixed memory budget at start-up, or a time-critical loop
+// that cannot afford the device-wide synchronisation an allocation or a free
+// may cause. lm_apply_pencil needs a pencil handle whose buffers the library
+// allocated; this entry point instead takes the caller's O_c, G'_c, weights, v
+// and outputs, and keeps its own scratch (the per-CTA partial products, the
+// zero-padded copy of v and a status word) in one file-scope device array of
+// fixed size. Every GPU that loads the library holds that array until the
+// process exits.
 #include <algorithm>
 #include <mutex>
 
@@ -64,14 +65,18 @@ __global__ void k_noalloc_prep(double *scratch, const double *v, int p1, int ld)
     if (i < ld) scratch[32 + i] = i < p1 ? v[i] : 0.0;
 }
 
-bool on_device(const void *p) {
+// A device array of the current device `dev` (or managed memory). Memory of
+// another GPU is refused: the kernel would read it over the peer path, which
+// faults when peer access is not enabled.
+bool on_device(const void *p, int dev) {
     if (!p) return false;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -86,11 +91,11 @@ extern "C" int lm_apply_pencil_noalloc(const double *O_c, const double *G_c, con
     // the kernel copies whole rows with the bulk-copy engine: 16-byte aligned starts
     if ((reinterpret_cast<uintptr_t>(O_c) | reinterpret_cast<uintptr_t>(G_c)) % 16 != 0)
         return LM_ERR_ARG;
-    if (!on_device(O_c) || !on_device(G_c) || !on_device(w) || !on_device(v) ||
-        (Hv && !on_device(Hv)) || (Sv && !on_device(Sv)))
-        return LM_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LM_ERR_CUDA;
+    if (!on_device(O_c, dev) || !on_device(G_c, dev) || !on_device(w, dev) ||
+        !on_device(v, dev) || (Hv && !on_device(Hv, dev)) || (Sv && !on_device(Sv, dev)))
+        return LM_ERR_ARG;
     NoallocDevice *d = nullptr;
     if (int rc = noalloc_setup(dev, &d)) return rc;
     // partial products of at most as many CTAs as fit beside v in the array

@@ -89,18 +89,53 @@ def _build_both(ctx, abi, n, na, nb, nh, h, eri, theta, rows=None, counts=None, 
     return pen, pd
 
 
+def _colwise(got, ref, tol, what):
+    """Column by column: max_x |got(x,k) - ref(x,k)| <= tol * max_x |ref(x,k)| for every
+    column k, so an error confined to the small hidden-unit columns (t_j ~ 1e-2 at the
+    workloads' theta) cannot hide behind the large visible-bias columns. A column that is
+    zero in the oracle must be zero on the GPU too."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    d = np.abs(got - ref).max(axis=0)
+    s = np.abs(ref).max(axis=0)
+    zero = s == 0
+    assert np.all(d[zero] == 0), f"{what}: nonzero entries in columns that are zero"
+    r = d[~zero] / s[~zero]
+    if r.size:
+        k = int(np.flatnonzero(~zero)[int(np.argmax(r))])
+        assert r.max() <= tol, f"{what}: column {k} relative error {r.max():.3e} > {tol:.0e}"
+    return float(r.max()) if r.size else 0.0
+
+
+def _elementwise(got, ref, tol, what, floor=0.0):
+    """Entry by entry: |got(x) - ref(x)| <= tol * max(|ref(x)|, floor)."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    r = np.abs(got - ref) / np.maximum(np.abs(ref), floor)
+    assert np.all(np.isfinite(r)) and r.max() <= tol, \
+        f"{what}: entry {int(np.argmax(r))} relative error {r.max():.3e} > {tol:.0e}"
+
+
 def _check_build(abi, pen, pd):
+    """The FP64-accurate build against the oracle, element by element (1e-12 relative per
+    column of O_c and G'_c; per entry for ln psi, E_loc and the weights), plus the energy."""
     P1 = pd.Oc.shape[1]
     inf = pen.info()
     assert inf.energy == pytest.approx(pd.E, rel=1e-12)
     Oc = pen.export(abi.EXPORT_O)
     Gc = pen.export(abi.EXPORT_G)
     assert np.all(Oc[:, P1:] == 0) and np.all(Gc[:, P1:] == 0)
+    _colwise(Oc[:, :P1], pd.Oc, 1e-12, "O_c")
+    _colwise(Gc[:, :P1], pd.Gpc, 1e-12, "G'_c")
+    # whole-matrix norms as well (the earlier, weaker bar; kept beside the column test)
     assert _rel(Oc[:, :P1], pd.Oc) <= 1e-12
     assert _rel(Gc[:, :P1], pd.Gpc) <= 1e-12
-    assert _rel(pen.export(abi.EXPORT_W), pd.w) <= 1e-12
-    assert _rel(pen.export(abi.EXPORT_LNPSI), pd.lnpsi) <= 1e-13
-    assert _rel(pen.export(abi.EXPORT_ELOC), pd.eloc) <= 1e-12
+    _elementwise(pen.export(abi.EXPORT_W), pd.w, 1e-12, "weights")
+    lnpsi = pen.export(abi.EXPORT_LNPSI)
+    _elementwise(lnpsi, pd.lnpsi, 1e-13, "ln psi", floor=np.abs(pd.lnpsi).max())
+    eloc = pen.export(abi.EXPORT_ELOC)
+    _elementwise(eloc, pd.eloc, 1e-12, "E_loc", floor=1e-3 * np.abs(pd.eloc).max())
+    _colwise(pen.export(abi.EXPORT_OBAR)[None, 1:P1], pd.Obar[None, 1:], 1e-12, "mean O")
     assert np.array_equal(pen.export(abi.EXPORT_ROWS), pd.rows)
 
 
@@ -414,6 +449,72 @@ def test_irl_mixed_precision_refined_to_fp64(ctx, abi, prec):
     assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
     assert abs(res.lambda_ - ref["lam"]) <= 1e-9
     assert res.n_matvec_lowp > 0
+    pen.free()
+
+
+@pytest.mark.parametrize("sigma,seed,m,k", [(0.01, 111, 6, 2), (0.3, 9, 5, 1), (0.1, 111, 6, 2)])
+def test_irl_restarts_follow_the_oracle(ctx, abi, sigma, seed, m, k):
+    """Algorithm 1's implicit restart on the GPU, cycle by cycle: a small Krylov dimension
+    forces several restarts (mu = m - k exact shifts each); the GPU must restart exactly as
+    often as the oracle's CPU IRL (same operator, start vector, seed and null-space
+    deflation) and its lowest Ritz value after every cycle must follow the oracle's."""
+    from oracle import irl as oirl
+    h, eri = synth.integrals(6, 111)
+    th = synth.rbm_theta(6, 24, seed, sigma=sigma)
+    pen, pd = _build_both(ctx, abi, 6, 3, 3, 24, h, eri, th)
+    S, Hp = lm.pencil_matrices(pd.Oc, pd.Gpc, pd.w)
+    Hs = 0.5 * (Hp + Hp.T)
+    ref = oirl.irl_lowest(lambda v: Hs @ v, Hs.shape[0], m=m, k=k, tol=1e-12, max_restarts=200,
+                          seed=111, null_basis=lm.null_vectors(6, 3, 3, 24), return_history=True)
+    res = pen.irl_step(m=m, k=k, tol=1e-12, max_restarts=200, sym=abi.LM_SYM_NONE)
+    lam_h, res_h, lowp_h = pen.irl_history()
+    assert ref["n_restart"] >= 3  # the case exercises the restart
+    assert res.status == abi.IRL_OK
+    assert res.n_restart == ref["n_restart"]
+    assert len(lam_h) == len(ref["history"]) == res.n_restart + 1
+    assert not lowp_h.any()
+    assert res.n_matvec == ref["n_matvec"] + 1  # + the explicit refinement product
+    for i, (_, lam_o, res_o) in enumerate(ref["history"]):
+        assert lam_h[i] == pytest.approx(lam_o, rel=1e-9), f"cycle {i}"
+        # residual estimates beta_m |u_m| agree while they are above rounding level
+        if res_o > 1e-9:
+            assert res_h[i] == pytest.approx(res_o, rel=1e-4), f"cycle {i}"
+        else:
+            assert res_h[i] < 1e-7, f"cycle {i}"
+    assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-10)
+    pen.free()
+
+
+@pytest.fixture(scope="module")
+def licl_32k():
+    """LiCl-shaped system (28 spin orbitals, Nh = 56, P+1 = 1,653) on 32,768 Monte Carlo rows
+    with multiplicities, and the oracle's FP64 step on them (SHEP eigenvalue)."""
+    h, eri = synth.integrals(14, 111)
+    th = synth.rbm_theta(14, 56, 111)
+    rows, cnt = _mc_rows(14, 7, 7, 32768, 111, h)
+    ref = lm.lm_step(14, 7, 7, 56, h, eri, th, rows, cnt)
+    return h, eri, th, rows, cnt, ref
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["fp32", "bf16"])
+def test_irl_mixed_precision_32k_rows_vs_oracle(ctx, abi, licl_32k, prec):
+    """The mixed-precision LM step at 32,768 LiCl-shaped rows: FP32 / BF16 factors for the
+    first IRL phase, FP64 continuation and refinement, against the FP64 oracle's dense SHEP
+    eigenvalue: |lambda - lambda_oracle| <= 1e-9 Ha (printed per result)."""
+    h, eri, th, rows, cnt, ref = licl_32k
+    sysd = ctx.system(14, 7, 7, 56, h, eri)
+    pen = ctx.build_OG(sysd, th, rows=rows, weights=cnt.astype(np.float64), prec=prec)
+    dth = np.zeros(th.shape[0])
+    res = pen.irl_step(m=20, k=1, tol=1e-12, max_restarts=500, prec=prec, dtheta_out=dth)
+    err = abs(res.lambda_ - ref["lam"])
+    print(f"\n32k LiCl-shaped rows, {('FP32', 'BF16')[prec - 1]} factors: lambda = "
+          f"{res.lambda_:.15f}, oracle {ref['lam']:.15f}, |error| = {err:.2e} Ha, "
+          f"{res.n_matvec_lowp} low-precision + {res.n_matvec - res.n_matvec_lowp} FP64 products")
+    assert res.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), res.status
+    assert err <= 1e-9
+    assert res.n_matvec_lowp > 0
+    assert res.energy == pytest.approx(ref["E"], rel=1e-12)
+    assert _rel(dth, ref["dtheta"]) <= 1e-6
     pen.free()
 
 

@@ -1,11 +1,11 @@
 """lm_apply_pencil_noalloc: the pencil product for callers that cannot allocate
-device memory (inside a stream capture, under an allocator that owns all device
-memory, in loops that must not wait on the allocator). Its scratch lives in a
-fixed file-scope device array, so the test checks it against the regular
-lm_apply_pencil on the same factors, for two calls in a row (the second call
-reuses the scratch the first one left), and that it rejects what it cannot do
-without allocating. Collected last (file name) so a stop-at-first-failure run
-has already run every other test."""
+device memory when they need it (a framework whose caching allocator owns the
+device memory, a solver with a fixed memory budget, a loop that cannot wait on
+an allocation). Its scratch lives in a fixed file-scope device array, so the
+test checks it against the regular lm_apply_pencil on the same factors, for two
+calls in a row (the second call reuses the scratch the first one left), and
+that it rejects what it cannot do without allocating. Collected last (file
+name) so a stop-at-first-failure run has already run every other test."""
 import numpy as np
 import pytest
 
