@@ -162,7 +162,10 @@ class ClockSampler:
 NCU_TRAFFIC = {("k_build_rows_df", "f2_10o14e"): 138.88e6,
                # Lanczos products alternate their row order: with the L2 left warm
                # (ncu --cache-control none) a product reads 113 MB of its 198.5 MB
-               ("k_pencil", "f2_10o14e"): 117.0e6}
+               ("k_pencil", "f2_10o14e"): 117.0e6,
+               # FP32 factors of the LiCl-shaped pencil: 868.9 MB per launch at 65,536 rows
+               # (profiles/k_pencil_fp32_licl_mc.md), scaled by the rows to 262,144
+               ("k_pencil_fp32", "licl_14o14e_mc"): 4 * 868.9e6}
 
 
 def connections(w):
@@ -560,9 +563,8 @@ def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10, n_rows=262144, precs=None
                        "peak_nominal": HBM_NOMINAL_GBS,
                        "frac_of_nominal": nbytes / d / 1e9 / HBM_NOMINAL_GBS,
                        "launches": int(st.pencil_count),
-                       # the FP32 c2 capture predates the divide-free pipeline
-                       # counters: no traffic figure until it is taken again
-                       "traffic": None,
+                       "traffic": (NCU_TRAFFIC.get(("k_pencil_fp32", w.name))
+                                   if nm == "fp32" and w.n_rows == 262144 else None),
                        "operator": "E_loc estimator O_c^T W diag(E_loc - E) O_c v"
                                    if sy == abi.LM_SYM_ELOC else "symmetrised H~'"}
         pen.free()

@@ -54,6 +54,26 @@ def centre(O, G, eloc, w):
     return E, Obar, Oc, Gpc
 
 
+def condition_scales(pd, n_orb, n_alpha, n_beta, n_hidden, h, eri, theta):
+    """Absolute-value scales of every entry the build produces, for componentwise error
+    bars: the sum of |terms| that forms the entry (a relative error u in every term moves
+    the entry by at most u times its scale).
+
+    E_loc(x) = sum_x' c_x':                       A_E(x)   = sum_x' |c_x'|
+    O_c(x,k) = O_k(x) - <O_k>  (k >= 1):          A_O(x,k) = |O_k(x)| + |<O_k>|
+    G'_c(x,k) = sum_x' c_x' O_k(x') - <O_k> E_loc(x) - E O_c(x,k)  (k >= 1):
+        A_G(x,k) = sum_x' |c_x'| |O_k(x')| + |<O_k>| A_E(x) + |E| |O_c(x,k)|
+    column 0: O_c = 1 exactly (A_O = 1), G'_c = E_loc - E (A_G = A_E + |E|).
+    """
+    ea, ga = native.rows_abs(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, pd.rows)
+    ob = np.abs(pd.Obar)
+    AO = np.abs(pd.Oc + pd.Obar[None, :]) + ob[None, :]
+    AO[:, 0] = 1.0
+    AG = ga + ob[None, :] * ea[:, None] + abs(pd.E) * np.abs(pd.Oc)
+    AG[:, 0] = ea + abs(pd.E)
+    return ea, AO, AG
+
+
 def pencil_matrices(Oc, Gpc, w):
     """Explicit S~ = O_c^T W O_c and H~' = O_c^T W G'_c, both (P+1)x(P+1)."""
     WO = Oc * w[:, None]

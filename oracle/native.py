@@ -40,6 +40,9 @@ def lib():
         L.oracle_rows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   dp, dp, dp, up, ctypes.c_int64, dp, dp, dp, dp]
         L.oracle_rows.restype = ctypes.c_int
+        L.oracle_rows_abs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      dp, dp, dp, up, ctypes.c_int64, dp, dp]
+        L.oracle_rows_abs.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -87,3 +90,23 @@ def rows(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, dets, want_o=True, wan
     if rc != 0:
         raise RuntimeError(f"oracle_rows failed ({rc})")
     return lnpsi, O, eloc, G
+
+
+def rows_abs(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, dets):
+    """Condition scales of the per-row sums: (sum_x' |c_x'|, sum_x' |c_x'| |O_k(x')|) with
+    c_x' = H_xx' psi(x')/psi(x), the absolute-value sums of the terms of E_loc(x) and G_k(x)."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    dets = np.ascontiguousarray(dets, dtype=np.uint64)
+    nr = dets.shape[0]
+    p1 = (n_hidden + 1) * (2 * n_orb + 1)
+    ea = np.zeros(nr)
+    ga = np.zeros((nr, p1))
+    rc = lib().oracle_rows_abs(n_orb, n_alpha, n_beta, n_hidden, _p(h, ctypes.c_double),
+                               _p(eri, ctypes.c_double), _p(theta, ctypes.c_double),
+                               _p(dets, ctypes.c_uint64), nr, _p(ea, ctypes.c_double),
+                               _p(ga, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oracle_rows_abs failed ({rc})")
+    return ea, ga

@@ -254,3 +254,57 @@ int oracle_rows(int n_orb, int n_alpha, int n_beta, int n_hidden, const double *
     }
     return err;
 }
+
+/*
+ * Condition scales of the same sums, for componentwise error bars: with
+ * c_x' = H_xx' psi(x')/psi(x), eloc_abs[i] = sum_x' |c_x'| and
+ * G_abs[i][k] = sum_x' |c_x'| |O_k(x')|, the sums of absolute values of the
+ * terms that E_loc(x) and G_k(x) add up (a rounding error of relative size u
+ * in every term moves the sum by at most u times this scale).
+ */
+int oracle_rows_abs(int n_orb, int n_alpha, int n_beta, int n_hidden, const double *h,
+                    const double *eri, const double *theta, const uint64_t *rows, int64_t n_rows,
+                    double *eloc_abs, double *G_abs) {
+    if (check_sys(n_orb, n_alpha, n_beta, n_hidden)) return -1;
+    int m = 2 * n_orb;
+    int p1 = (n_hidden + 1) * (m + 1);
+    osys s = {n_orb, n_alpha, n_beta, n_hidden, m, p1, h, eri, theta};
+    int cap = max_conn(n_orb, n_alpha, n_beta);
+    int err = 0;
+#pragma omp parallel
+    {
+        uint64_t *cd = (uint64_t *)malloc(sizeof(uint64_t) * cap);
+        double *ch = (double *)malloc(sizeof(double) * cap);
+        int *cs = (int *)malloc(sizeof(int) * cap);
+        double *t = (double *)malloc(sizeof(double) * (n_hidden + 1));
+        double *tp = (double *)malloc(sizeof(double) * (n_hidden + 1));
+        double *orow = (double *)malloc(sizeof(double) * p1);
+        double *grow = (double *)malloc(sizeof(double) * p1);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < n_rows; i++) {
+            uint64_t x = rows[i];
+            double lp = rbm_lnpsi(&s, x, t);
+            int nc = connections(&s, x, cap, cd, ch, cs);
+            if (nc < 0) {
+#pragma omp atomic write
+                err = -2;
+                continue;
+            }
+            double el = 0.0;
+            for (int c = 0; c < p1; c++) grow[c] = 0.0;
+            for (int k = 0; k < nc; k++) {
+                double lpk = rbm_lnpsi(&s, cd[k], tp);
+                double ck = fabs(ch[k] * exp(lpk - lp));
+                el += ck;
+                if (G_abs) {
+                    rbm_orow(&s, cd[k], tp, orow);
+                    for (int c = 0; c < p1; c++) grow[c] += ck * fabs(orow[c]);
+                }
+            }
+            if (eloc_abs) eloc_abs[i] = el;
+            if (G_abs) memcpy(G_abs + i * (int64_t)p1, grow, sizeof(double) * p1);
+        }
+        free(cd); free(ch); free(cs); free(t); free(tp); free(orow); free(grow);
+    }
+    return err;
+}

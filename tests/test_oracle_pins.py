@@ -127,6 +127,45 @@ def test_G_identity_with_finite_differences():
     assert np.abs(G[:, 0] - eloc).max() <= 1e-13 * np.abs(eloc).max()
 
 
+def test_condition_scales_bound_the_sums():
+    """The componentwise error scales: sum |terms| bounds |E_loc| and |G| entry by entry,
+    column 0 of G's scale is E_loc's (O(x,0) = 1), and with a diagonal Hamiltonian
+    (every off-diagonal element zero) each scale is exactly the magnitude of its sum."""
+    n, na, nb, nh = 5, 2, 3, 6
+    h, eri = synth.integrals(n, 12)
+    theta = synth.rbm_theta(n, nh, 12, sigma=0.3)
+    dets = fock.sector_dets(n, na, nb)
+    _, _, eloc, G = native.rows(n, na, nb, nh, h, eri, theta, dets)
+    ea, ga = native.rows_abs(n, na, nb, nh, h, eri, theta, dets)
+    assert np.all(np.abs(eloc) <= ea * (1 + 1e-14))
+    assert np.all(np.abs(G) <= ga * (1 + 1e-14))
+    assert np.array_equal(ga[:, 0], ea)
+    hd = np.diag(np.diag(h))
+    _, _, eloc_d, G_d = native.rows(n, na, nb, nh, hd, np.zeros_like(eri), theta, dets)
+    ea_d, ga_d = native.rows_abs(n, na, nb, nh, hd, np.zeros_like(eri), theta, dets)
+    assert np.array_equal(ea_d, np.abs(eloc_d))
+    assert np.allclose(ga_d, np.abs(G_d), rtol=1e-15, atol=0)
+
+
+def test_componentwise_bar_catches_a_small_column_error():
+    """An error confined to the hidden-unit columns at 1e-11 of their own size passes the
+    whole-matrix norm bar (those columns are much smaller than the visible-bias ones at
+    theta ~ N(0, 0.01)) but fails the componentwise bar the GPU build is held to."""
+    from parity_tools import componentwise
+    w = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, th, _, _ = w.inputs()
+    pd = lm.build_pencil(6, 3, 3, 24, h, eri, th)
+    AE, AO, AG = lm.condition_scales(pd, 6, 3, 3, 24, h, eri, th)
+    assert np.all(AG >= np.abs(pd.Gpc) * (1 - 1e-14))
+    bad = pd.Gpc.copy()
+    bad[:, 2 * 13 + 1:2 * 13 + 13] *= 1 + 1e-11   # W columns of hidden unit 1
+    rel = np.linalg.norm(bad - pd.Gpc) / np.linalg.norm(pd.Gpc)
+    assert rel < 1e-12  # invisible to the norm bar
+    componentwise(pd.Gpc * (1 + 1e-15), pd.Gpc, AG, 1e-12, "rounding-level change")
+    with pytest.raises(AssertionError):
+        componentwise(bad, pd.Gpc, AG, 1e-12, "planted")
+
+
 def test_eloc_estimator_against_finite_differences():
     """The paper's E_loc estimator (G'_c -> (E_loc - E) O_c) against finite
     differences of the oracle's local energy and energy: it differs from the exact
