@@ -58,7 +58,8 @@ enum {
     LM_ERR_SIZE = -2,    /* M > 64, N_alpha > n_orb, m > 64, ...            */
     LM_ERR_OOM = -3,     /* device allocation failed                        */
     LM_ERR_CUDA = -4,    /* a CUDA runtime call or kernel launch failed     */
-    LM_ERR_TIMEOUT = -5  /* a bounded device wait gave up                   */
+    LM_ERR_TIMEOUT = -5, /* a bounded device wait gave up                   */
+    LM_ERR_CALLBACK = -6 /* the caller's reduction callback returned nonzero */
 };
 
 /* irl_result.status (Algorithm 1 outcomes and the update's validity) */
@@ -218,6 +219,60 @@ int lm_pencil_free(lm_pencil *p);
  * instance run alone with the grid a batch chose reproduces the batch result
  * exactly. */
 int lm_pencil_set_grid(lm_pencil *p, int ctas);
+
+/* ---- row shards (one pencil per GPU over a partition of the rows) ------ */
+
+/*
+ * The build and the products split by rows (Methods, eqs. heff and
+ * centered_hamiltonian: every statistic is a weighted sum over rows, and the
+ * matrix-free product of eq. matrix_vec_prod is a sum of per-row terms). Each
+ * shard -- typically one GPU of several, each holding its own rows -- runs:
+ *   1. lm_shard_build: the row build (ln psi, O, E_loc, G) of the shard's rows;
+ *      *lnpsi_max receives the largest ln psi of the shard. The caller takes
+ *      the maximum over all shards (it fixes the shift of the |psi|^2
+ *      weights; ignored when weights are given).
+ *   2. lm_shard_sums(p, lnpsi_max, sums): the shard's unnormalised weights
+ *      w = exp(2 (ln psi - lnpsi_max)) (or the given weights) and its P+3 sums
+ *      sums[0] = sum w, sums[1] = sum w E_loc, sums[2 + k] = sum w O_k
+ *      (k = 0..P; host array). The caller adds them over all shards.
+ *   3. lm_shard_centre(p, sums): centring with the summed statistics
+ *      (E = sums[1] / sums[0], <O_k> = sums[2 + k] / sums[0], weights
+ *      normalised by sums[0]). The pencil is then a shard of the global
+ *      pencil: lm_apply_pencil gives this shard's term of the global product,
+ *      and the terms of all shards add up to the product of the unsharded
+ *      pencil (up to summation order).
+ * rows must be given explicitly (lm_enumerate_sector, sliced, for an exact
+ * sector); weights NULL means |psi|^2. Host arrays; each call synchronises.
+ * irl_step refuses a pencil between steps 1 and 3.
+ */
+int lm_shard_build(lm_ctx *ctx, const lm_system *sys, const double *theta, const uint64_t *rows,
+                   const double *weights, int64_t n_rows, lm_precision prec, void *stream,
+                   lm_pencil **inout, double *lnpsi_max);
+int lm_shard_sums(lm_pencil *p, double lnpsi_max, double *sums, void *stream);
+int lm_shard_centre(lm_pencil *p, const double *sums, void *stream);
+
+/* The caller's sum over shards of a vector of n doubles, in place (one call
+ * per pencil product on every shard, in the same order on every shard, with
+ * the same n). where = LM_REDUCE_HOST: vec is pinned host memory holding this
+ * shard's vector (the stream has been synchronised); the callback returns
+ * when vec holds the sum, e.g. after an MPI or gloo all-reduce.
+ * where = LM_REDUCE_DEVICE: vec is device memory of this GPU; the callback
+ * enqueues an in-place sum on `stream` (a cudaStream_t), e.g. an NCCL
+ * all-reduce, and returns. Every shard must receive bitwise the same sum (an
+ * all-reduce does), so that the replicated Lanczos work stays identical.
+ * A nonzero return aborts the solve with LM_ERR_CALLBACK. */
+typedef int (*lm_reduce_fn)(double *vec, int n, void *stream, void *user);
+enum { LM_REDUCE_HOST = 0, LM_REDUCE_DEVICE = 1 };
+
+/* irl_step over row shards (Algorithms 1 and 2 with the row-partitioned
+ * product): every product is this shard's term of the global product
+ * followed by reduce(); the Lanczos vectors, the tridiagonal work and the
+ * refinement are replicated on every shard. Each shard calls it with the
+ * same prm; results and outputs are those of irl_step on the unsharded
+ * pencil, up to the summation order of the products. */
+int irl_step_sharded(lm_pencil *p, const irl_params *prm, lm_reduce_fn reduce, void *user,
+                     int where, irl_result *out, double *c_out, double *dtheta_out,
+                     double *theta_inout, void *stream);
 
 /* ---- inspection (tests and tools; not on the timed path) -------------- */
 

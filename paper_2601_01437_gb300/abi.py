@@ -15,6 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libirlnqs.so")
 
 LM_OK, LM_ERR_ARG, LM_ERR_SIZE, LM_ERR_OOM, LM_ERR_CUDA, LM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+LM_ERR_CALLBACK = -6
+LM_REDUCE_HOST, LM_REDUCE_DEVICE = 0, 1
 IRL_OK, IRL_BREAKDOWN_INVARIANT, IRL_MAX_RESTARTS, LM_C0_TINY, LM_STATIONARY = 0, 1, 2, 3, 4
 LM_FP64, LM_FP32, LM_BF16, LM_DF64 = 0, 1, 2, 3
 LM_SYM_AUTO, LM_SYM_NONE, LM_SYM_HALF, LM_SYM_ELOC = 0, 1, 2, 3
@@ -70,6 +72,9 @@ class lm_stats(ctypes.Structure):
                 ("prep_count", c_int64), ("tri_ms", c_double), ("tri_count", c_int64)]
 
 
+# int reduce(double *vec, int n, void *stream, void *user)
+REDUCE_FN = ctypes.CFUNCTYPE(c_int, c_vp, c_int, c_vp, c_vp)
+
 _lib = None
 
 _SIGNATURES = {
@@ -103,6 +108,12 @@ _SIGNATURES = {
     "lm_server_pending": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "lm_server_free": (c_int, [c_vp]),
     "lm_irl_history": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, ctypes.POINTER(c_int)]),
+    "lm_shard_build": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_vp, c_vp, c_int64, c_int,
+                               c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_double)]),
+    "lm_shard_sums": (c_int, [c_vp, c_double, c_vp, c_vp]),
+    "lm_shard_centre": (c_int, [c_vp, c_vp, c_vp]),
+    "irl_step_sharded": (c_int, [c_vp, ctypes.POINTER(irl_params), REDUCE_FN, c_vp, c_int,
+                                 ctypes.POINTER(irl_result), c_vp, c_vp, c_vp, c_vp]),
     "lm_stats_reset": (c_int, [c_vp, c_int]),
     "lm_stats_get": (c_int, [c_vp, ctypes.POINTER(lm_stats)]),
 }
@@ -209,6 +220,17 @@ class Context:
             return pencil
         return Pencil(self, h)
 
+    def shard_build(self, sys, theta, rows, weights=None, prec=LM_FP64, stream=None,
+                    pencil=None):
+        """lm_shard_build: the row build of one shard; returns (Pencil, largest ln psi)."""
+        h = c_vp(pencil.handle if pencil is not None else None)
+        m = c_double()
+        rc = lib().lm_shard_build(self.handle, ctypes.byref(sys), ptr(theta), ptr(rows),
+                                  ptr(weights), int(rows.shape[0]), int(prec),
+                                  stream_handle(stream), ctypes.byref(h), ctypes.byref(m))
+        self.check(rc, "lm_shard_build")
+        return (pencil if pencil is not None else Pencil(self, h)), m.value
+
     def stats_reset(self, profile=False):
         self.check(lib().lm_stats_reset(self.handle, int(profile)), "lm_stats_reset")
 
@@ -265,6 +287,45 @@ class Pencil:
         rc = lib().irl_step(self.handle, ctypes.byref(prm), ctypes.byref(res), ptr(c_out),
                             ptr(dtheta_out), ptr(theta_inout), stream_handle(stream))
         self.ctx.check(rc, "irl_step")
+        return res
+
+    def shard_sums(self, lnpsi_max, stream=None):
+        """lm_shard_sums: this shard's P+3 sums [sum w, sum w E_loc, sum w O_0..P]."""
+        out = np.zeros(self.info().n_params + 3)
+        self.ctx.check(lib().lm_shard_sums(self.handle, float(lnpsi_max), ptr(out),
+                                           stream_handle(stream)), "lm_shard_sums")
+        return out
+
+    def shard_centre(self, sums, stream=None):
+        sums = np.ascontiguousarray(sums, dtype=np.float64)
+        self.ctx.check(lib().lm_shard_centre(self.handle, ptr(sums), stream_handle(stream)),
+                       "lm_shard_centre")
+
+    def irl_step_sharded(self, reduce, where=LM_REDUCE_HOST, m=20, k=1, tol=1e-12,
+                         max_restarts=200, seed=111, sym=LM_SYM_AUTO, prec=LM_FP64,
+                         deflate_null=1, c_out=None, dtheta_out=None, theta_inout=None,
+                         stream=None):
+        """irl_step_sharded. reduce(vec, n, stream) sums the n-vector over the shards in
+        place: with where = LM_REDUCE_HOST, vec is a NumPy view of pinned host memory;
+        with LM_REDUCE_DEVICE, the raw device pointer (an int). Returns 0 on success."""
+        def cb(vp, n, st, _user):
+            try:
+                if where == LM_REDUCE_HOST:
+                    vec = np.ctypeslib.as_array((c_double * n).from_address(vp))
+                else:
+                    vec = vp
+                rc = reduce(vec, n, st)
+                return int(rc or 0)
+            except Exception:
+                return 1
+        fn = REDUCE_FN(cb)
+        prm = irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null),
+                         None)
+        res = irl_result()
+        rc = lib().irl_step_sharded(self.handle, ctypes.byref(prm), fn, None, int(where),
+                                    ctypes.byref(res), ptr(c_out), ptr(dtheta_out),
+                                    ptr(theta_inout), stream_handle(stream))
+        self.ctx.check(rc, "irl_step_sharded")
         return res
 
     def irl_history(self):

@@ -1,6 +1,7 @@
 // C ABI of the library: contexts, pencil lifecycle, host/device pointer
 // handling and the non-IRL entry points (irl_step lives in irl.cu).
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
@@ -109,7 +110,7 @@ void pencil_release(lm_pencil *p) {
     void *bufs[] = {p->rows, p->wt,   p->lnpsi, p->eloc, p->O,    p->G,   p->Olo,
                     p->Glo,  p->h,    p->eri,   p->theta, p->tabs, p->stats, p->part,
                     p->V,    p->wvec, p->yvec,  p->hy,   p->sy,   p->tvec, p->dots,
-                    p->st,   p->tdf,  p->wlo, p->wel, p->wello, p->bar};
+                    p->st,   p->tdf,  p->wlo, p->wel, p->wello, p->bar, p->shv};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (p->hs) cudaFreeHost(p->hs);
@@ -181,7 +182,7 @@ extern "C" const char *lm_last_error(const lm_ctx *ctx) { return ctx ? ctx->err 
 // ---------------------------------------------------------------- build
 int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
                      const uint64_t *rows, const double *weights, int64_t n_rows,
-                     lm_precision prec, void *stream, lm_pencil **inout) {
+                     lm_precision prec, void *stream, lm_pencil **inout, int rows_only) {
     if (!ctx || !inout || !theta) return lm_fail(ctx, LM_ERR_ARG, "null argument");
     ctx->err[0] = 0;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return LM_ERR_CUDA;
@@ -310,6 +311,13 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
         return rc;
     if ((rc = lm_cuda_check(ctx, cudaMemsetAsync(p->d_flags, 0, sizeof(int), s), "memset")))
         return rc;
+    p->shard_state = rows_only ? 1 : 0;
+    if (rows_only) {
+        if ((rc = lm_launch_build_rows(p, s))) return rc;
+        return lm_cuda_check(ctx, cudaMemcpyAsync(&p->hs->flags, p->d_flags, sizeof(int),
+                                                  cudaMemcpyDeviceToHost, s),
+                             "flags read-back");
+    }
     if ((rc = lm_launch_build(p, s))) return rc;
     cudaError_t e = cudaMemcpyAsync(&p->hs->E, p->stats + 1, sizeof(double),
                                     cudaMemcpyDeviceToHost, s);
@@ -337,12 +345,90 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
     return lm_build_finish(*inout);
 }
 
+// ---------------------------------------------------------------- row shards
+extern "C" int lm_shard_build(lm_ctx *ctx, const lm_system *sys, const double *theta,
+                              const uint64_t *rows, const double *weights, int64_t n_rows,
+                              lm_precision prec, void *stream, lm_pencil **inout,
+                              double *lnpsi_max) {
+    if (!lnpsi_max) return lm_fail(ctx, LM_ERR_ARG, "null lnpsi_max");
+    if (int rc = lm_build_enqueue(ctx, sys, theta, rows, weights, n_rows, prec, stream, inout, 1))
+        return rc;
+    lm_pencil *p = *inout;
+    cudaStream_t s = (cudaStream_t)stream;
+    int nmax = 0;
+    if (int rc = lm_launch_shard_max(p, s, &nmax)) return rc;
+    if (int rc = lm_cuda_check(ctx, cudaMemcpyAsync(p->hs->xfer, p->part, nmax * sizeof(double),
+                                                    cudaMemcpyDeviceToHost, s),
+                               "shard max read-back"))
+        return rc;
+    if (int rc = lm_cuda_check(ctx, cudaStreamSynchronize(s), "lm_shard_build")) return rc;
+    p->hs->E = NAN;
+    if (int rc = lm_build_finish(p)) return rc;
+    double m = -INFINITY;
+    for (int i = 0; i < nmax; ++i) m = std::max(m, p->hs->xfer[i]);
+    *lnpsi_max = m;
+    return LM_OK;
+}
+
+extern "C" int lm_shard_sums(lm_pencil *p, double lnpsi_max, double *sums, void *stream) {
+    if (!p || !sums) return LM_ERR_ARG;
+    lm_ctx *ctx = p->ctx;
+    cudaSetDevice(ctx->device);
+    if (p->shard_state != 1 && p->shard_state != 2)
+        return lm_fail(ctx, LM_ERR_ARG, "lm_shard_sums needs a pencil from lm_shard_build");
+    if (!p->given_weights && !std::isfinite(lnpsi_max))
+        return lm_fail(ctx, LM_ERR_ARG, "lnpsi_max must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = lm_launch_shard_sums(p, lnpsi_max, s)) return rc;
+    if (int rc = lm_cuda_check(ctx, cudaMemcpyAsync(p->hs->xfer, p->stats,
+                                                    (8 + p->ldp) * sizeof(double),
+                                                    cudaMemcpyDeviceToHost, s),
+                               "shard sums read-back"))
+        return rc;
+    if (int rc = lm_cuda_check(ctx, cudaStreamSynchronize(s), "lm_shard_sums")) return rc;
+    const double *st = p->hs->xfer;
+    sums[0] = st[0];
+    sums[1] = st[1];
+    for (int k = 0; k < p->P1; ++k) sums[2 + k] = st[8 + k];
+    p->shard_state = 2;
+    return LM_OK;
+}
+
+extern "C" int lm_shard_centre(lm_pencil *p, const double *sums, void *stream) {
+    if (!p || !sums) return LM_ERR_ARG;
+    lm_ctx *ctx = p->ctx;
+    cudaSetDevice(ctx->device);
+    if (p->shard_state != 2)
+        return lm_fail(ctx, LM_ERR_ARG, "lm_shard_centre needs lm_shard_sums first");
+    if (!(sums[0] > 0.0) || !std::isfinite(sums[0]))
+        return lm_fail(ctx, LM_ERR_ARG, "the summed weight must be positive and finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the statistics the unsharded build forms on the device, from the sums of
+    // every shard: sum w, E = sum w E_loc / sum w, <O_k> = sum w O_k / sum w
+    double *st = p->hs->xfer;
+    std::memset(st, 0, (8 + p->ldp) * sizeof(double));
+    st[0] = sums[0];
+    st[1] = sums[1] / sums[0];
+    for (int k = 0; k < p->P1; ++k) st[8 + k] = sums[2 + k] / sums[0];
+    if (int rc = lm_cuda_check(ctx, cudaMemcpyAsync(p->stats, st, (8 + p->ldp) * sizeof(double),
+                                                    cudaMemcpyHostToDevice, s),
+                               "shard statistics"))
+        return rc;
+    if (int rc = lm_launch_centre(p, s)) return rc;
+    if (int rc = lm_cuda_check(ctx, cudaStreamSynchronize(s), "lm_shard_centre")) return rc;
+    p->hs->E = sums[1] / sums[0];
+    p->E_host = p->hs->E;
+    p->shard_state = 0;
+    return LM_OK;
+}
+
 extern "C" int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double *Sv, int sym,
                                int prec, void *stream) {
     if (!p || !v) return LM_ERR_ARG;
     lm_ctx *ctx = p->ctx;
     cudaSetDevice(ctx->device);
     if (sym < 0 || sym > 3 || prec < 0 || prec > 3) return lm_fail(ctx, LM_ERR_ARG, "bad sym/prec");
+    if (p->shard_state) return lm_fail(ctx, LM_ERR_ARG, "row shard not centred (lm_shard_centre)");
     cudaStream_t s = (cudaStream_t)stream;
     const int sy = sym == LM_SYM_AUTO ? p->sym : sym;
     // the kernels read ldp >= P+1 entries: stage v with zero padding

@@ -1034,6 +1034,15 @@ __global__ void k_weights(const double *lnpsi, const double *given, double *wt, 
         wt[r] = given ? given[r] : exp(2.0 * (lnpsi[r] - sMax));
 }
 
+// Unnormalised weights with a given shift (row shards: the maximum of ln psi
+// over every shard): w = exp(2 (ln psi - lnpsi_max)), or the given weight.
+__global__ void k_weights_shift(const double *lnpsi, const double *given, double *wt, int64_t n,
+                                double lnpsi_max) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        wt[r] = given ? given[r] : exp(2.0 * (lnpsi[r] - lnpsi_max));
+}
+
 // Per-CTA partial sums over a contiguous row chunk: sum w, sum w E_loc,
 // sum w O[:, c].
 __global__ void k_stats_partial(const double *O, const double *eloc, const double *wt, int64_t n,
@@ -1082,8 +1091,9 @@ __global__ void k_stats_partial(const double *O, const double *eloc, const doubl
 // [32 b, 32 b + 32): warp q sums the partials q, q + 8, ... of its lane's
 // column, then the 8 warp sums are added in warp order. Every CTA forms sum w
 // itself (the same fixed order), so no second pass is needed.
+// raw = 1: the sums themselves (stats[1] = sum w E_loc, stats[8 + c] = sum w O_c).
 __global__ void __launch_bounds__(256) k_stats_final(const double *part, int nparts, int ldp,
-                                                      double *stats) {
+                                                      double *stats, int raw) {
     __shared__ double red[8][33];
     __shared__ double s_sw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1110,7 +1120,7 @@ __global__ void __launch_bounds__(256) k_stats_final(const double *part, int npa
             s_sw = ta;
             if (blockIdx.x == 0) {
                 stats[0] = ta;
-                stats[1] = tb / ta;
+                stats[1] = raw ? tb : tb / ta;
             }
         }
         __syncthreads();
@@ -1130,7 +1140,7 @@ __global__ void __launch_bounds__(256) k_stats_final(const double *part, int npa
     if (warp == 0 && c < ldp) {
         double t = 0.0;
         for (int w = 0; w < 8; ++w) t += red[w][lane];
-        stats[8 + c] = t / s_sw;
+        stats[8 + c] = raw ? t : t / s_sw;
     }
 }
 
@@ -1341,6 +1351,12 @@ static size_t build_smem_bytes(int nh, int M, int ldF, int ldS, int nslice) {
 }
 
 int lm_launch_build(lm_pencil *p, cudaStream_t s) {
+    if (int rc = lm_launch_build_rows(p, s)) return rc;
+    return lm_launch_build_prep(p, s);
+}
+
+// K2-K6: ln psi, O, E_loc and G of every row (uncentred)
+int lm_launch_build_rows(lm_pencil *p, cudaStream_t s) {
     lm_ctx *ctx = p->ctx;
     BuildArgs A;
     A.S = make_view(p->n, p->na, p->nb, p->h, p->eri);
@@ -1486,7 +1502,12 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
         if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_build_rows_df")) return rc;
     }
 
-    // weights, E, <O>
+    return LM_OK;
+}
+
+// K7: weights, E, <O>, then the centring
+int lm_launch_build_prep(lm_pencil *p, cudaStream_t s) {
+    lm_ctx *ctx = p->ctx;
     const int nmax = std::max(1, std::min(ctx->sms, (int)((p->n_rows + 255) / 256)));
     double *maxpart = p->part;  // reuse the partials buffer (nmax doubles first)
     double *given = p->given_weights ? p->wt : nullptr;
@@ -1504,9 +1525,50 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     k_stats_partial<<<nst, 256, 0, s>>>(p->O, p->eloc, p->wt, p->n_rows, p->ldp, spart);
     lm_note_launch(ctx);
     if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_stats_partial")) return rc;
-    k_stats_final<<<(p->ldp + 31) / 32, 256, 0, s>>>(spart, nst, p->ldp, p->stats);
+    k_stats_final<<<(p->ldp + 31) / 32, 256, 0, s>>>(spart, nst, p->ldp, p->stats, 0);
     lm_note_launch(ctx);
     if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_stats_final")) return rc;
+    const int rc = lm_launch_centre(p, s);
+    lm_prof_end(ctx, PROF_PREP, s);
+    return rc;
+}
+
+// Local statistics of a row shard: the per-CTA maxima of ln psi into
+// part[0 .. nmax) (returns nmax).
+int lm_launch_shard_max(lm_pencil *p, cudaStream_t s, int *nparts) {
+    lm_ctx *ctx = p->ctx;
+    const int nmax = std::max(1, std::min(ctx->sms, (int)((p->n_rows + 255) / 256)));
+    k_lnpsi_max_partial<<<nmax, 256, 0, s>>>(p->lnpsi, p->n_rows, p->part);
+    lm_note_launch(ctx);
+    *nparts = nmax;
+    return lm_cuda_check(ctx, cudaGetLastError(), "k_lnpsi_max");
+}
+
+// Unnormalised weights of a row shard with the shift lnpsi_max shared by all
+// shards (or the caller's weights), and the shard's raw sums into stats:
+// stats[0] = sum w, stats[1] = sum w E_loc, stats[8 + c] = sum w O_c.
+int lm_launch_shard_sums(lm_pencil *p, double lnpsi_max, cudaStream_t s) {
+    lm_ctx *ctx = p->ctx;
+    double *given = p->given_weights ? p->wt : nullptr;
+    const int nst = (int)std::max<int64_t>(1, std::min<int64_t>(p->n_rows, ctx->sms * 2));
+    double *spart = p->part + 256;
+    lm_prof_begin(ctx, PROF_PREP, s);
+    k_weights_shift<<<(int)std::min<int64_t>((p->n_rows + 255) / 256, ctx->sms * 4), 256, 0, s>>>(
+        p->lnpsi, given, p->wt, p->n_rows, lnpsi_max);
+    lm_note_launch(ctx);
+    k_stats_partial<<<nst, 256, 0, s>>>(p->O, p->eloc, p->wt, p->n_rows, p->ldp, spart);
+    lm_note_launch(ctx);
+    k_stats_final<<<(p->ldp + 31) / 32, 256, 0, s>>>(spart, nst, p->ldp, p->stats, 1);
+    lm_prof_end(ctx, PROF_PREP, s);
+    lm_note_launch(ctx);
+    return lm_cuda_check(ctx, cudaGetLastError(), "shard sums");
+}
+
+// Centring with the statistics in p->stats (stats[0] = sum w over every row of
+// every shard, stats[1] = E, stats[8 + c] = <O_c>): O_c, G'_c, the normalised
+// weights and the E_loc-estimator weights.
+int lm_launch_centre(lm_pencil *p, cudaStream_t s) {
+    lm_ctx *ctx = p->ctx;
     int cgrid = (int)std::min<int64_t>((p->n_rows + 7) / 8, (int64_t)ctx->sms * 16);
     if (p->prec == LM_FP32)
         k_centre<float><<<cgrid, 256, 0, s>>>(p->O, p->G, p->eloc, p->wt, p->stats, p->n_rows,
@@ -1528,7 +1590,6 @@ int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     k_eloc_weights<<<(int)std::max<int64_t>(1, std::min<int64_t>((p->n_rows + 255) / 256,
                                                                  ctx->sms * 4)),
                      256, 0, s>>>(p->wt, p->eloc, p->stats, p->n_rows, p->wel, p->wello);
-    lm_prof_end(ctx, PROF_PREP, s);
     lm_note_launch(ctx);
     return lm_cuda_check(ctx, cudaGetLastError(), "k_eloc_weights");
 }

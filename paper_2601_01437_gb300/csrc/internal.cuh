@@ -163,6 +163,9 @@ struct PencilHost {
     IrlState st;
     double E;
     int flags;
+    // staging of small vectors between device and host: shard statistics,
+    // vectors handed to a caller's reduction (irl_step_sharded)
+    double xfer[2 * 2048 + 64];
 };
 
 struct lm_pencil {
@@ -213,6 +216,11 @@ struct lm_pencil {
     int n_hist;
     double hist_lam[LM_HIST_MAX], hist_res[LM_HIST_MAX];
     int hist_lowp[LM_HIST_MAX];
+    // row shards (lm_shard_*): 1 after lm_shard_build, 2 after lm_shard_sums,
+    // 0 once centred (the pencil is usable); shv holds a shard's local product
+    // for the caller's reduction (2 ldp doubles, allocated on first use)
+    int shard_state;
+    double *shv;
 };
 
 // ---------------------------------------------------------------------------
@@ -225,9 +233,10 @@ int lm_read_flags(lm_ctx *ctx, cudaStream_t s, int *flags);
 // lm_build_OG in two halves: enqueue the build (and the read-back of E and the
 // flags into pinned memory) on `stream`; after that work has completed,
 // lm_build_finish checks the flags and publishes E.
+// rows_only = 1 stops after the row build (K2-K6), for row shards.
 int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
                      const uint64_t *rows, const double *weights, int64_t n_rows,
-                     lm_precision prec, void *stream, lm_pencil **inout);
+                     lm_precision prec, void *stream, lm_pencil **inout, int rows_only = 0);
 int lm_build_finish(lm_pencil *p);
 size_t lm_pencil_footprint(lm_ctx *ctx, int n, int nh, int64_t n_rows, int prec);
 // Staging regions: h at 0, eri after it, theta after that (ldp doubles), rows
@@ -246,8 +255,11 @@ void lm_pencil_release(lm_pencil *p);  // frees without a device-wide synchronis
 // and records the job's event; call it again once that event has completed
 // (the first call starts the job). *done = 1 when the result is final.
 struct IrlJob;
+// reduce (nullable): sum every product over the row shards (irl_step_sharded)
 int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *dtheta_out,
-                   double *theta_inout, cudaStream_t s, IrlJob **out);
+                   double *theta_inout, cudaStream_t s, IrlJob **out,
+                   lm_reduce_fn reduce = nullptr, void *reduce_user = nullptr,
+                   int reduce_where = LM_REDUCE_HOST);
 int irl_job_advance(IrlJob *job, int *done);
 cudaEvent_t irl_job_event(const IrlJob *job);
 void irl_job_result(const IrlJob *job, irl_result *out);
@@ -256,7 +268,14 @@ void irl_job_free(IrlJob *job);
 // build.cu
 int lm_launch_enumerate(lm_ctx *ctx, int n, int na, int nb, uint64_t *out, int64_t count,
                         cudaStream_t s);
-int lm_launch_build(lm_pencil *p, cudaStream_t s);
+int lm_launch_build(lm_pencil *p, cudaStream_t s);   // rows, then statistics and centring
+int lm_launch_build_rows(lm_pencil *p, cudaStream_t s);
+int lm_launch_build_prep(lm_pencil *p, cudaStream_t s);
+// row shards (lm_shard_*): local maxima of ln psi into p->part[0 .. *nparts),
+// raw local sums into p->stats with a given shift, centring with p->stats
+int lm_launch_shard_max(lm_pencil *p, cudaStream_t s, int *nparts);
+int lm_launch_shard_sums(lm_pencil *p, double lnpsi_max, cudaStream_t s);
+int lm_launch_centre(lm_pencil *p, cudaStream_t s);
 int lm_launch_connections(lm_ctx *ctx, int n, int na, int nb, const double *h,
                           const double *eri, const uint64_t *rows, int64_t n_rows, int cap,
                           uint64_t *od, int8_t *osg, double *oh, int32_t *cnt, double e_core,

@@ -1232,7 +1232,33 @@ struct Run {
     int lz_mode;   // LZ_*
     int cluster;   // CTAs per cluster for LZ_CLUSTER
     int cluster_emax;  // largest entry count of one cluster CTA
+    // row shards: each product is summed over the shards by the caller
+    lm_reduce_fn reduce;
+    void *reduce_user;
+    int reduce_where;
 };
+
+// Sum a device vector of n doubles over the row shards with the caller's
+// reduction (see irl_step_sharded), in place.
+int shard_reduce(Run &R, double *dvec, int n) {
+    lm_pencil *p = R.p;
+    lm_ctx *ctx = p->ctx;
+    if (R.reduce_where == LM_REDUCE_DEVICE) {
+        if (int rc = R.reduce(dvec, n, (void *)R.s, R.reduce_user))
+            return lm_fail(ctx, LM_ERR_CALLBACK, "reduction callback returned %d", rc);
+        return lm_cuda_check(ctx, cudaGetLastError(), "after the reduction callback");
+    }
+    double *h = p->hs->xfer;
+    cudaError_t e = cudaMemcpyAsync(h, dvec, n * sizeof(double), cudaMemcpyDeviceToHost, R.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(R.s);
+    if (int rc = lm_cuda_check(ctx, e, "shard vector read-back")) return rc;
+    if (int rc = R.reduce(h, n, (void *)R.s, R.reduce_user))
+        return lm_fail(ctx, LM_ERR_CALLBACK, "reduction callback returned %d", rc);
+    // the next read-back into the same staging is ordered after this copy
+    return lm_cuda_check(ctx, cudaMemcpyAsync(dvec, h, n * sizeof(double),
+                                              cudaMemcpyHostToDevice, R.s),
+                         "shard vector upload");
+}
 
 // Dynamic shared memory of k_lz_cluster for Lanczos step j: the V[:, 0..j]
 // slice with an odd leading dimension.
@@ -1260,7 +1286,9 @@ void choose_lanczos(Run &R, lm_ctx *ctx) {
     const bool any = !env || !*env;
     R.lz_mode = LZ_SPLIT;
     R.cluster = 0;
-    if (any || !strcmp(env, "cluster")) {
+    // the cluster step sums the pencil CTAs' double-float partials itself; a
+    // sharded solve hands it one reduced FP64 vector instead
+    if ((any || !strcmp(env, "cluster")) && !R.reduce) {
         for (int C : {16, 8}) {
             int emax = 0, rmax = 0;
             cluster_extent(R.la.nrow_grid, R.la.M1, R.la.ldp, C, emax, rmax);
@@ -1324,6 +1352,11 @@ int lanczos_step(Run &R, int j) {
                                   R.lz_mode == LZ_CLUSTER, j & 1))
         return rc;
     R.n_matvec++;
+    if (R.reduce) {
+        // this shard's term of the product, summed over the shards
+        if (int rc = lm_launch_reduce_partials(p, R.prec, p->shv, nullptr, R.s)) return rc;
+        if (int rc = shard_reduce(R, p->shv, p->ldp)) return rc;
+    }
     lm_prof_begin(p->ctx, PROF_LANCZOS, R.s);
     const int rc = lanczos_vectors(R, j);
     lm_prof_end(p->ctx, PROF_LANCZOS, R.s);
@@ -1473,6 +1506,10 @@ int job_phase_start(IrlJob *J) {
         }
     }
     R.la.nparts = lm_pencil_ctas(p, R.prec);
+    if (R.reduce) {
+        R.la.part = p->shv;  // the reduced product, one "partial"
+        R.la.nparts = 1;
+    }
     J->cycle = 0;
     cudaMemsetAsync(p->st, 0, sizeof(IrlState), R.s);
     cudaMemsetAsync(p->bar, 0, 64 * sizeof(unsigned), R.s);
@@ -1493,6 +1530,10 @@ int job_refine(IrlJob *J) {
     cudaStream_t s = J->s;
     if (int rc = lm_launch_pencil(p, p->yvec, R.sym, LM_FP64, 1, nullptr, s)) return rc;
     if (int rc = lm_launch_reduce_partials(p, LM_FP64, p->hy, p->sy, s)) return rc;
+    if (R.reduce) {
+        if (int rc = shard_reduce(R, p->hy, p->ldp)) return rc;
+        if (int rc = shard_reduce(R, p->sy, p->ldp)) return rc;
+    }
     R.n_matvec++;
     const size_t stage_vec = (size_t)8 * p->ldp;
     if (J->theta_inout && !J->t_dev)
@@ -1523,9 +1564,17 @@ int job_refine(IrlJob *J) {
 }  // namespace
 
 int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *dtheta_out,
-                   double *theta_inout, cudaStream_t s, IrlJob **out) {
+                   double *theta_inout, cudaStream_t s, IrlJob **out, lm_reduce_fn reduce,
+                   void *reduce_user, int reduce_where) {
     if (!p || !prm || !out) return LM_ERR_ARG;
     lm_ctx *ctx = p->ctx;
+    if (p->shard_state) return lm_fail(ctx, LM_ERR_ARG, "row shard not centred (lm_shard_centre)");
+    if (reduce && reduce_where != LM_REDUCE_HOST && reduce_where != LM_REDUCE_DEVICE)
+        return lm_fail(ctx, LM_ERR_ARG, "bad reduction location %d", reduce_where);
+    if (reduce && !p->shv &&
+        lm_cuda_check(ctx, cudaMalloc(&p->shv, 2 * (size_t)p->ldp * sizeof(double)),
+                      "cudaMalloc"))
+        return LM_ERR_OOM;
     if (prm->m > LM_MAXKRYLOV || prm->m < 2 || prm->k < 1 || prm->k >= prm->m || prm->m > p->P1)
         return lm_fail(ctx, LM_ERR_SIZE, "need 1 <= k < m <= min(64, P+1); got k=%d m=%d", prm->k,
                        prm->m);
@@ -1549,6 +1598,9 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
     R.sym = prm->sym == LM_SYM_AUTO ? p->sym : prm->sym;
     R.n_matvec = 0;
     R.n_restart = 0;
+    R.reduce = reduce;
+    R.reduce_user = reduce_user;
+    R.reduce_where = reduce_where;
     R.la.V = p->V;
     R.la.w = p->wvec;
     R.la.part = p->part;
@@ -1711,6 +1763,27 @@ extern "C" int irl_step(lm_pencil *p, const irl_params *prm, irl_result *out, do
         rc = irl_job_advance(J, &done);
         if (!rc && !done)
             rc = lm_cuda_check(ctx, cudaEventSynchronize(J->ev), "irl_step");
+    }
+    if (!rc) irl_job_result(J, out);
+    irl_job_free(J);
+    return rc;
+}
+
+extern "C" int irl_step_sharded(lm_pencil *p, const irl_params *prm, lm_reduce_fn reduce,
+                                void *user, int where, irl_result *out, double *c_out,
+                                double *dtheta_out, double *theta_inout, void *stream) {
+    if (!p || !prm || !out || !reduce) return LM_ERR_ARG;
+    lm_ctx *ctx = p->ctx;
+    cudaSetDevice(ctx->device);
+    IrlJob *J = nullptr;
+    if (int rc = irl_job_create(p, prm, c_out, dtheta_out, theta_inout, (cudaStream_t)stream, &J,
+                                reduce, user, where))
+        return rc;
+    int done = 0, rc = LM_OK;
+    while (!rc && !done) {
+        rc = irl_job_advance(J, &done);
+        if (!rc && !done)
+            rc = lm_cuda_check(ctx, cudaEventSynchronize(J->ev), "irl_step_sharded");
     }
     if (!rc) irl_job_result(J, out);
     irl_job_free(J);

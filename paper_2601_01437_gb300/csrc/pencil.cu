@@ -620,9 +620,11 @@ int raw_launch(const double *O, const double *G, const double *w, int64_t n_rows
 
 template <int NJ>
 int raw_modes(const double *O, const double *G, const double *w, int64_t n_rows, int ldp,
-              const double *vpad, double *part, int grid, int half, int want_s, int smem_optin,
-              int *flags, cudaStream_t s) {
-    int rc = half ? raw_launch<NJ, MODE_H_HALF>(O, G, w, n_rows, ldp, vpad, part, 2 * ldp, grid,
+              const double *vpad, double *part, int grid, int half, int want_h, int want_s,
+              int smem_optin, int *flags, cudaStream_t s) {
+    int rc = LM_OK;
+    if (want_h)
+        rc = half ? raw_launch<NJ, MODE_H_HALF>(O, G, w, n_rows, ldp, vpad, part, 2 * ldp, grid,
                                                 smem_optin, flags, s)
                   : raw_launch<NJ, MODE_H_NONE>(O, G, w, n_rows, ldp, vpad, part, 2 * ldp, grid,
                                                 smem_optin, flags, s);
@@ -661,14 +663,14 @@ int lm_pencil_fp64_on_scratch(const double *O, const double *G, const double *w,
                               int ldp, int p1, const double *vpad, double *part, int grid, int half,
                               double *yH, double *yS, int smem_optin, int *flags, cudaStream_t s) {
     const int nj = (ldp + 31) / 32;
-    const int want_s = yS != nullptr;
+    const int want_s = yS != nullptr, want_h = yH != nullptr;
     int rc;
-    if (nj <= 8) rc = raw_modes<8>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
-    else if (nj <= 16) rc = raw_modes<16>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
-    else if (nj <= 28) rc = raw_modes<28>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
-    else if (nj <= 40) rc = raw_modes<40>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
-    else if (nj <= 52) rc = raw_modes<52>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
-    else if (nj <= 64) rc = raw_modes<64>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_s, smem_optin, flags, s);
+    if (nj <= 8) rc = raw_modes<8>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_h, want_s, smem_optin, flags, s);
+    else if (nj <= 16) rc = raw_modes<16>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_h, want_s, smem_optin, flags, s);
+    else if (nj <= 28) rc = raw_modes<28>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_h, want_s, smem_optin, flags, s);
+    else if (nj <= 40) rc = raw_modes<40>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_h, want_s, smem_optin, flags, s);
+    else if (nj <= 52) rc = raw_modes<52>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_h, want_s, smem_optin, flags, s);
+    else if (nj <= 64) rc = raw_modes<64>(O, G, w, n_rows, ldp, vpad, part, grid, half, want_h, want_s, smem_optin, flags, s);
     else return LM_ERR_SIZE;
     if (rc != LM_OK) return rc;
     k_reduce_partials_flagged<<<(2 * ldp + 31) / 32, 256, 0, s>>>(part, grid, ldp, p1, flags, yH, yS);
