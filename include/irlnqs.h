@@ -134,7 +134,15 @@ typedef struct {
                         /* solve is refined by FP64 restarts before returning     */
     int deflate_null;   /* 1: remove the particle-number null space of O_c        */
     const double *v0;   /* optional start vector (P+1), NULL = random             */
+    int reorth;         /* IRL_REORTH_FULL (0): classical Gram-Schmidt twice      */
+                        /* against the whole basis; IRL_REORTH_NONE (1): the      */
+                        /* paper's three-term recurrence of Algorithm 2 only      */
+    int mode;           /* IRL_MODE_SHEP (0): the paper's S ~ I eigenproblem      */
+                        /* (eq. standard_evp); no other mode is accepted          */
 } irl_params;
+
+enum { IRL_REORTH_FULL = 0, IRL_REORTH_NONE = 1 };
+enum { IRL_MODE_SHEP = 0 };
 
 typedef struct {
     double lambda;        /* lowest eigenvalue of the SHEP (eq. standard_evp): the  */
@@ -304,6 +312,15 @@ int lm_pencil_export(lm_pencil *p, int what, void *dst, void *stream);
  * output may be NULL); *n receives the number of cycles recorded (at most
  * 1024). Host memory; call after irl_step has returned. */
 int lm_irl_history(lm_pencil *p, double *lam, double *res, int *lowp, int cap, int *n);
+
+/* Test of the timeout path (no counterpart in the paper): run one bounded
+ * device wait that nothing ends -- which = 0, the grid barrier of the
+ * cooperative Lanczos kernel with a CTA that never arrives; which = 1, an
+ * mbarrier phase of the pencil pipeline that no copy completes -- with a wall
+ * limit of limit_ns (1 ns .. 2 s; the library's own waits use 2 s). Returns
+ * LM_ERR_TIMEOUT when the wait gave up, as it should; the context stays usable.
+ * Synchronises the device. */
+int lm_debug_wait_timeout(lm_ctx *ctx, int which, int64_t limit_ns);
 
 /* ---- pencil product without allocation -------------------------------- */
 

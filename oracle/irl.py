@@ -77,11 +77,16 @@ def implicit_qr_sweep(a, b, nu, Q):
 
 
 def irl_lowest(matvec, n, m=20, k=1, tol=1e-12, max_restarts=200, seed=111, v0=None,
-               null_basis=None, return_history=False):
+               null_basis=None, return_history=False, reorth="full"):
     """Lowest eigenpair of the symmetric operator ``matvec`` by IRL.
 
+    reorth="full": classical Gram-Schmidt twice against the whole basis after the
+    three-term step; reorth="none": Algorithm 2 as printed, w = A v_j - beta_{j-1}
+    v_{j-1}, alpha_j = <w, v_j>, w = w - alpha_j v_j, and nothing else.
     Returns dict(lam, y, residual, status, n_matvec, n_restart[, history]).
     """
+    if reorth not in ("full", "none"):
+        raise ValueError(reorth)
     if not (1 <= k < m <= n):
         raise ValueError("need 1 <= k < m <= n")
 
@@ -108,14 +113,20 @@ def irl_lowest(matvec, n, m=20, k=1, tol=1e-12, max_restarts=200, seed=111, v0=N
         for j in range(j0, m):
             w = matvec(V[:, j])
             n_mv += 1
-            alpha[j] = V[:, j] @ w
-            w = w - alpha[j] * V[:, j]
-            if j > 0:
-                w = w - beta[j - 1] * V[:, j - 1]
-            for _ in range(2):
-                cc = V[:, :j + 1].T @ w
-                w = w - V[:, :j + 1] @ cc
-                alpha[j] += cc[j]
+            if reorth == "none":
+                if j > 0:
+                    w = w - beta[j - 1] * V[:, j - 1]
+                alpha[j] = w @ V[:, j]
+                w = w - alpha[j] * V[:, j]
+            else:
+                alpha[j] = V[:, j] @ w
+                w = w - alpha[j] * V[:, j]
+                if j > 0:
+                    w = w - beta[j - 1] * V[:, j - 1]
+                for _ in range(2):
+                    cc = V[:, :j + 1].T @ w
+                    w = w - V[:, :j + 1] @ cc
+                    alpha[j] += cc[j]
             w = proj(w)
             beta[j] = np.linalg.norm(w)
             tnorm = max(np.abs(alpha[:j + 1]).max(), np.abs(beta[:j + 1]).max())

@@ -21,6 +21,8 @@ IRL_OK, IRL_BREAKDOWN_INVARIANT, IRL_MAX_RESTARTS, LM_C0_TINY, LM_STATIONARY = 0
 LM_FP64, LM_FP32, LM_BF16, LM_DF64 = 0, 1, 2, 3
 LM_SYM_AUTO, LM_SYM_NONE, LM_SYM_HALF, LM_SYM_ELOC = 0, 1, 2, 3
 LM_ARITH_DF64, LM_ARITH_FP64 = 0, 1
+IRL_REORTH_FULL, IRL_REORTH_NONE = 0, 1
+IRL_MODE_SHEP = 0
 LM_NOALLOC_MAX_LD = 2048
 EXPORT_O, EXPORT_G, EXPORT_LNPSI, EXPORT_ELOC, EXPORT_W, EXPORT_OBAR, EXPORT_ROWS = range(7)
 
@@ -41,7 +43,7 @@ class lm_pencil_info(ctypes.Structure):
 class irl_params(ctypes.Structure):
     _fields_ = [("m", c_int), ("k", c_int), ("tol", c_double), ("max_restarts", c_int),
                 ("seed", c_uint64), ("sym", c_int), ("precision", c_int),
-                ("deflate_null", c_int), ("v0", c_vp)]
+                ("deflate_null", c_int), ("v0", c_vp), ("reorth", c_int), ("mode", c_int)]
 
 
 class irl_result(ctypes.Structure):
@@ -108,6 +110,7 @@ _SIGNATURES = {
     "lm_server_pending": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "lm_server_free": (c_int, [c_vp]),
     "lm_irl_history": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, ctypes.POINTER(c_int)]),
+    "lm_debug_wait_timeout": (c_int, [c_vp, c_int, c_int64]),
     "lm_shard_build": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_vp, c_vp, c_int64, c_int,
                                c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_double)]),
     "lm_shard_sums": (c_int, [c_vp, c_double, c_vp, c_vp]),
@@ -231,6 +234,10 @@ class Context:
         self.check(rc, "lm_shard_build")
         return (pencil if pencil is not None else Pencil(self, h)), m.value
 
+    def debug_wait_timeout(self, which, limit_ns):
+        """lm_debug_wait_timeout: the status code (LM_ERR_TIMEOUT when the wait gave up)."""
+        return lib().lm_debug_wait_timeout(self.handle, int(which), int(limit_ns))
+
     def stats_reset(self, profile=False):
         self.check(lib().lm_stats_reset(self.handle, int(profile)), "lm_stats_reset")
 
@@ -280,9 +287,9 @@ class Pencil:
 
     def irl_step(self, m=20, k=1, tol=1e-12, max_restarts=200, seed=111, sym=LM_SYM_AUTO,
                  prec=LM_FP64, deflate_null=1, v0=None, c_out=None, dtheta_out=None,
-                 theta_inout=None, stream=None):
+                 theta_inout=None, stream=None, reorth=IRL_REORTH_FULL):
         prm = irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null),
-                         ptr(v0))
+                         ptr(v0), int(reorth), IRL_MODE_SHEP)
         res = irl_result()
         rc = lib().irl_step(self.handle, ctypes.byref(prm), ctypes.byref(res), ptr(c_out),
                             ptr(dtheta_out), ptr(theta_inout), stream_handle(stream))
@@ -320,7 +327,7 @@ class Pencil:
                 return 1
         fn = REDUCE_FN(cb)
         prm = irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null),
-                         None)
+                         None, IRL_REORTH_FULL, IRL_MODE_SHEP)
         res = irl_result()
         rc = lib().irl_step_sharded(self.handle, ctypes.byref(prm), fn, None, int(where),
                                     ctypes.byref(res), ptr(c_out), ptr(dtheta_out),
@@ -364,8 +371,9 @@ class Pencil:
 
 
 def irl_settings(m=20, k=1, tol=1e-12, max_restarts=200, seed=111, sym=LM_SYM_AUTO,
-                 prec=LM_FP64, deflate_null=1):
-    return irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null), None)
+                 prec=LM_FP64, deflate_null=1, reorth=IRL_REORTH_FULL):
+    return irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null), None,
+                      int(reorth), IRL_MODE_SHEP)
 
 
 class Batch:

@@ -92,12 +92,15 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 // Bounded wait on one phase of an mbarrier: false once LM_SPIN_LIMIT polls or
-// two seconds of wall time have passed without the phase completing.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// limit_ns of wall time (two seconds unless a test asks for less) have passed
+// without the phase completing.
+#define LM_WAIT_LIMIT_NS 2000000000ull
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns = LM_WAIT_LIMIT_NS) {
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < LM_SPIN_LIMIT; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255u) == 255u && global_ns() - t0 > 2000000000ull) return false;
+        if ((i & 255u) == 255u && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

@@ -44,6 +44,7 @@ struct LzArgs {
     int ldp, M1, P1, nrow_grid;  // nrow_grid = Nh + 1 = number of CTAs
     int n_orb, na, nb;
     int deflate;
+    int three_term;     // IRL_REORTH_NONE: the paper's three-term recurrence, no CGS
     IrlState *st;
     unsigned *bar;      // [0] arrival count, [1] generation (cooperative kernel)
     int *flags;
@@ -166,6 +167,8 @@ __global__ void __launch_bounds__(LT) k_lz_a(LzArgs a, int j) {
             if (part == 0 && ee < E) {
                 double t = 0.0;
                 for (int q = 0; q < 8; ++q) t += S.red[threadIdx.x + q];
+                // three-term recurrence (Algorithm 2): w = A v_j - beta_{j-1} v_{j-1}
+                if (a.three_term && j > 0) t = fma(-a.st->beta[j - 1], S.V[(j - 1) * LE + ee], t);
                 S.w[ee] = t;
                 a.w[e0 + ee] = t;
             }
@@ -183,6 +186,10 @@ __global__ void __launch_bounds__(LT) k_lz_b(LzArgs a, int j) {
     const int E = e1 - e0;
     load_block(a, S, e0, e1, j, true);
     sum_dots(a, S, 0, j);
+    // three-term recurrence: only alpha_j = v_j . w is removed
+    if (a.three_term)
+        for (int i = threadIdx.x; i < j; i += LT) S.h[i] = 0.0;
+    __syncthreads();
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i <= j; i += LT) a.st->h1[i] = S.h[i];
     block_update(S, E, j);
@@ -198,7 +205,9 @@ __global__ void __launch_bounds__(LT) k_lz_c(LzArgs a, int j) {
     cta_range(a, e0, e1);
     const int E = e1 - e0;
     load_block(a, S, e0, e1, j, true);
-    if (j >= 0) {
+    if (j >= 0 && a.three_term) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.st->alpha[j] = a.st->h1[j];
+    } else if (j >= 0) {
         sum_dots(a, S, 1, j);
         if (blockIdx.x == 0 && threadIdx.x == 0) a.st->alpha[j] = a.st->h1[j] + S.h[j];
         if (blockIdx.x == 0)
@@ -314,7 +323,8 @@ __global__ void __launch_bounds__(LT) k_lz_d(LzArgs a, int j, int jout, int mode
 // the cooperative launch). The last CTA to arrive resets the count and bumps
 // the generation; the others poll it. The poll gives up after two seconds of
 // wall time, sets FLAG_TIMEOUT and lets the CTA continue, so it cannot hang.
-__device__ __forceinline__ void grid_barrier(unsigned *bar, int *flags) {
+__device__ __forceinline__ void grid_barrier(unsigned *bar, int *flags,
+                                             uint64_t limit_ns = LM_WAIT_LIMIT_NS) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *gen = bar + 1;
@@ -327,7 +337,7 @@ __device__ __forceinline__ void grid_barrier(unsigned *bar, int *flags) {
         } else {
             const uint64_t t0 = global_ns();
             while (*gen == g) {
-                if (global_ns() - t0 > 2000000000ull) {
+                if (global_ns() - t0 > limit_ns) {
                     atomicOr(flags, FLAG_TIMEOUT);
                     break;
                 }
@@ -1213,6 +1223,26 @@ __global__ void __launch_bounds__(1024) k_refine(double *y, const double *hy, co
     }
 }
 
+
+// Waits that nothing ends, for tests of the timeout path: which = 0, the grid
+// barrier of the cooperative Lanczos kernel with a CTA that leaves without
+// arriving (2 CTAs); which = 1, an mbarrier phase that no thread or copy
+// completes (the wait of the pencil pipeline). Both give up after limit_ns.
+__global__ void k_debug_wait(int which, uint64_t limit_ns, unsigned *bar, int *flags) {
+    if (which == 0) {
+        if (blockIdx.x != 0) return;
+        grid_barrier(bar, flags, limit_ns);
+        return;
+    }
+    __shared__ uint64_t mb;
+    if (threadIdx.x == 0) {
+        mbar_init(&mb, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&mb, 0, limit_ns)) atomicOr(flags, FLAG_TIMEOUT);
+}
+
 }  // namespace
 
 // =========================================================================
@@ -1287,8 +1317,9 @@ void choose_lanczos(Run &R, lm_ctx *ctx) {
     R.lz_mode = LZ_SPLIT;
     R.cluster = 0;
     // the cluster step sums the pencil CTAs' double-float partials itself; a
-    // sharded solve hands it one reduced FP64 vector instead
-    if ((any || !strcmp(env, "cluster")) && !R.reduce) {
+    // sharded solve hands it one reduced FP64 vector instead. The three-term
+    // recurrence (no reorthogonalisation) runs in the four-kernel form only.
+    if ((any || !strcmp(env, "cluster")) && !R.reduce && !R.la.three_term) {
         for (int C : {16, 8}) {
             int emax = 0, rmax = 0;
             cluster_extent(R.la.nrow_grid, R.la.M1, R.la.ldp, C, emax, rmax);
@@ -1330,7 +1361,7 @@ void choose_lanczos(Run &R, lm_ctx *ctx) {
             }
         }
     }
-    if (any || !strcmp(env, "coop")) {
+    if ((any || !strcmp(env, "coop")) && !R.la.three_term) {
         // the cooperative step needs all nh+1 CTAs resident at once
         int dev_coop = 0, per_sm = 0;
         cudaDeviceGetAttribute(&dev_coop, cudaDevAttrCooperativeLaunch, ctx->device);
@@ -1580,6 +1611,10 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
                        prm->m);
     if (prm->sym < 0 || prm->sym > 3 || prm->precision < 0 || prm->precision > 3)
         return lm_fail(ctx, LM_ERR_ARG, "bad sym or precision");
+    if (prm->reorth != IRL_REORTH_FULL && prm->reorth != IRL_REORTH_NONE)
+        return lm_fail(ctx, LM_ERR_ARG, "bad reorth %d", prm->reorth);
+    if (prm->mode != IRL_MODE_SHEP)
+        return lm_fail(ctx, LM_ERR_ARG, "bad mode %d", prm->mode);
     IrlJob *J = new IrlJob();
     J->p = p;
     J->s = s;
@@ -1613,6 +1648,7 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
     R.la.na = p->na;
     R.la.nb = p->nb;
     R.la.deflate = prm->deflate_null;
+    R.la.three_term = prm->reorth == IRL_REORTH_NONE;
     R.la.st = p->st;
     R.la.bar = p->bar;
     R.la.flags = p->d_flags;
@@ -1800,5 +1836,32 @@ extern "C" int lm_irl_history(lm_pencil *p, double *lam, double *res, int *lowp,
         if (lowp) lowp[i] = p->hist_lowp[i];
     }
     *n = p->n_hist;
+    return LM_OK;
+}
+
+extern "C" int lm_debug_wait_timeout(lm_ctx *ctx, int which, int64_t limit_ns) {
+    if (!ctx) return LM_ERR_ARG;
+    if ((which != 0 && which != 1) || limit_ns < 1 || limit_ns > (int64_t)LM_WAIT_LIMIT_NS)
+        return lm_fail(ctx, LM_ERR_ARG, "which must be 0 or 1, limit in [1 ns, 2 s]");
+    cudaSetDevice(ctx->device);
+    unsigned *buf = nullptr;
+    if (cudaMalloc(&buf, 4 * sizeof(unsigned)) != cudaSuccess)
+        return lm_fail(ctx, LM_ERR_OOM, "cudaMalloc");
+    int rc = lm_cuda_check(ctx, cudaMemset(buf, 0, 4 * sizeof(unsigned)), "memset");
+    if (!rc) {
+        k_debug_wait<<<which == 0 ? 2 : 1, 32>>>(which, (uint64_t)limit_ns, buf,
+                                                 reinterpret_cast<int *>(buf + 2));
+        lm_note_launch(ctx);
+        rc = lm_cuda_check(ctx, cudaGetLastError(), "k_debug_wait");
+    }
+    if (!rc) rc = lm_cuda_check(ctx, cudaDeviceSynchronize(), "k_debug_wait");
+    int flags = 0;
+    if (!rc)
+        rc = lm_cuda_check(ctx, cudaMemcpy(&flags, buf + 2, sizeof(int), cudaMemcpyDeviceToHost),
+                           "flags");
+    cudaFree(buf);
+    if (rc) return rc;
+    if (flags & FLAG_TIMEOUT)
+        return lm_fail(ctx, LM_ERR_TIMEOUT, "the bounded wait gave up (as the test intends)");
     return LM_OK;
 }

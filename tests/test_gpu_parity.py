@@ -479,6 +479,50 @@ def test_irl_restarts_follow_the_oracle(ctx, abi, sigma, seed, m, k):
     pen.free()
 
 
+@pytest.mark.parametrize("m,k", [(20, 1), (12, 3), (6, 2)])
+def test_irl_three_term_recurrence_follows_the_oracle(ctx, abi, m, k):
+    """reorth = IRL_REORTH_NONE: Algorithm 2 as printed (w = A v_j - beta_{j-1} v_{j-1},
+    alpha_j = <w, v_j>, w -= alpha_j v_j, no Gram-Schmidt) inside Algorithm 1's restarts,
+    against the oracle's IRL with the same recurrence: the same restart count and Ritz
+    history, and the dense SHEP eigenvalue."""
+    from oracle import irl as oirl
+    w = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, th, _, _ = w.inputs()
+    pen, pd = _build_both(ctx, abi, 6, 3, 3, 24, h, eri, th)
+    S, Hp = lm.pencil_matrices(pd.Oc, pd.Gpc, pd.w)
+    Hs = 0.5 * (Hp + Hp.T)
+    ref = oirl.irl_lowest(lambda v: Hs @ v, Hs.shape[0], m=m, k=k, tol=1e-12, max_restarts=200,
+                          seed=111, null_basis=lm.null_vectors(6, 3, 3, 24), return_history=True,
+                          reorth="none")
+    res = pen.irl_step(m=m, k=k, tol=1e-12, max_restarts=200, sym=abi.LM_SYM_NONE,
+                       reorth=abi.IRL_REORTH_NONE)
+    lam_h, _, _ = pen.irl_history()
+    assert res.status == abi.IRL_OK
+    assert res.n_restart == ref["n_restart"]
+    for i, (_, lam_o, _) in enumerate(ref["history"]):
+        assert lam_h[i] == pytest.approx(lam_o, rel=1e-9), f"cycle {i}"
+    assert res.lambda_ == pytest.approx(lm.shep(Hs)[0], rel=1e-10)
+    pen.free()
+
+
+def test_bounded_waits_time_out_and_the_context_survives(ctx, abi):
+    """The timeout path of the library's bounded device waits, made to run out on purpose
+    with a wait that nothing ends (a grid-barrier arrival that never comes; an mbarrier
+    phase no copy completes), 1 ms limit: LM_ERR_TIMEOUT comes back instead of a hang,
+    and the context then solves a normal LM step correctly."""
+    import time
+    for which in (0, 1):
+        t0 = time.perf_counter()
+        rc = ctx.debug_wait_timeout(which, 1_000_000)
+        assert rc == abi.LM_ERR_TIMEOUT, rc
+        assert time.perf_counter() - t0 < 1.0
+    assert ctx.debug_wait_timeout(2, 1000) == abi.LM_ERR_ARG
+    w = synth.WORKLOADS["tiny_6o6e"]
+    pen, ref, res, c, dth = _irl_case(ctx, abi, w)
+    assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-10)
+    pen.free()
+
+
 @pytest.fixture(scope="module")
 def licl_32k():
     """LiCl-shaped system (28 spin orbitals, Nh = 56, P+1 = 1,653) on 32,768 Monte Carlo rows

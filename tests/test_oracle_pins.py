@@ -319,6 +319,21 @@ def test_irl_laplacian_closed_form():
     assert np.linalg.norm(A @ r["y"] - r["lam"] * r["y"]) < 1e-11
 
 
+def test_irl_three_term_laplacian_closed_form():
+    """Algorithm 2 as printed (three-term recurrence, no reorthogonalisation) inside the
+    implicit restart still converges to the closed-form lowest eigenvalue of the 1-D
+    Laplacian tridiag(-1, 2, -1): 2 - 2 cos(pi / (N + 1))."""
+    n = 200
+    A = np.diag(2.0 * np.ones(n)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)
+    exact = 2.0 - 2.0 * math.cos(math.pi / (n + 1))
+    for m, k in ((20, 4), (30, 8)):
+        out = irl.irl_lowest(lambda v: A @ v, n, m=m, k=k, tol=1e-10, max_restarts=2000,
+                             reorth="none")
+        assert out["status"] == irl.IRL_OK
+        assert out["lam"] == pytest.approx(exact, abs=1e-12)
+        assert out["n_restart"] >= 1
+
+
 def test_irl_diagonal_with_gap_and_random_symmetric():
     rng = np.random.default_rng(3)
     d = np.concatenate([[-5.0], rng.uniform(0, 10, 299)])
