@@ -55,21 +55,26 @@ def centre(O, G, eloc, w):
 
 
 def condition_scales(pd, n_orb, n_alpha, n_beta, n_hidden, h, eri, theta):
-    """Absolute-value scales of every entry the build produces, for componentwise error
-    bars: the sum of |terms| that forms the entry (a relative error u in every term moves
-    the entry by at most u times its scale).
+    """First-order rounding scales of every entry the build produces, for componentwise
+    error bars: how far a relative change u in every rounded quantity can move the entry,
+    divided by u.
 
-    E_loc(x) = sum_x' c_x':                       A_E(x)   = sum_x' |c_x'|
-    O_c(x,k) = O_k(x) - <O_k>  (k >= 1):          A_O(x,k) = |O_k(x)| + |<O_k>|
-    G'_c(x,k) = sum_x' c_x' O_k(x') - <O_k> E_loc(x) - E O_c(x,k)  (k >= 1):
-        A_G(x,k) = sum_x' |c_x'| |O_k(x')| + |<O_k>| A_E(x) + |E| |O_c(x,k)|
+    Oa(x,k): |O_k(x)| on visible entries (exact 0/1); on hidden unit j,
+        (|tanh z_j| + (1 - tanh^2 z_j)(|b_j| + sum_p |W_jp| x_p)) x_c (tanh's condition).
+    E_loc(x) = sum_x' c_x':                        A_E(x)   = sum_x' |c_x'|
+    O_c(x,k) = O_k(x) - <O_k>:                     A_O(x,k) = Oa(x,k) + <Oa_k>
+    G'_c(x,k) = sum_x' c_x' O_k(x') - <O_k> E_loc(x) - E O_c(x,k):
+        A_G(x,k) = sum_x' |c_x'| Oa(x',k) + |<O_k>| A_E(x) + <Oa_k> |E_loc(x)| + |E| A_O(x,k)
     column 0: O_c = 1 exactly (A_O = 1), G'_c = E_loc - E (A_G = A_E + |E|).
+    (<.> is the weighted mean over the rows.)
     """
-    ea, ga = native.rows_abs(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, pd.rows)
+    ea, ga, oa = native.rows_abs(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, pd.rows)
     ob = np.abs(pd.Obar)
-    AO = np.abs(pd.Oc + pd.Obar[None, :]) + ob[None, :]
+    oam = pd.w @ oa
+    AO = oa + oam[None, :]
     AO[:, 0] = 1.0
-    AG = ga + ob[None, :] * ea[:, None] + abs(pd.E) * np.abs(pd.Oc)
+    AG = ga + ob[None, :] * ea[:, None] + oam[None, :] * np.abs(pd.eloc)[:, None] + \
+        abs(pd.E) * AO
     AG[:, 0] = ea + abs(pd.E)
     return ea, AO, AG
 

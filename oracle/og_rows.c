@@ -256,15 +256,42 @@ int oracle_rows(int n_orb, int n_alpha, int n_beta, int n_hidden, const double *
 }
 
 /*
- * Condition scales of the same sums, for componentwise error bars: with
- * c_x' = H_xx' psi(x')/psi(x), eloc_abs[i] = sum_x' |c_x'| and
- * G_abs[i][k] = sum_x' |c_x'| |O_k(x')|, the sums of absolute values of the
- * terms that E_loc(x) and G_k(x) add up (a rounding error of relative size u
- * in every term moves the sum by at most u times this scale).
+ * First-order rounding scale of every O_k(x): for hidden unit j,
+ * O = tanh(z_j) x_c with z_j = b_j + sum_p W_jp x_p, and a relative change u
+ * of every term of z_j moves tanh(z_j) by at most u (1 - tanh^2) S_j with
+ * S_j = |b_j| + sum_p |W_jp| x_p; so the scale is (|t_j| + (1 - t_j^2) S_j) x_c
+ * (x_0 = 1). Visible-unit entries (0/1) and entry (0,0) are exact: scale |O|.
+ */
+static void rbm_oscale(const osys *s, uint64_t x, double *oa) {
+    int m1 = s->m + 1;
+    for (int c = 0; c <= s->m; c++)
+        oa[c] = (c == 0) ? 1.0 : (double)((x >> (c - 1)) & 1ULL);
+    for (int j = 0; j < s->nh; j++) {
+        double z = th_b(s, j), sz = fabs(th_b(s, j));
+        for (int p = 0; p < s->m; p++)
+            if ((x >> p) & 1ULL) {
+                z += th_w(s, j, p);
+                sz += fabs(th_w(s, j, p));
+            }
+        double t = tanh(z);
+        double u = fabs(t) + (1.0 - t * t) * sz;
+        for (int c = 0; c <= s->m; c++) {
+            double v = (c == 0) ? 1.0 : (double)((x >> (c - 1)) & 1ULL);
+            oa[(j + 1) * m1 + c] = u * v;
+        }
+    }
+}
+
+/*
+ * Condition scales of the per-row sums, for componentwise error bars: with
+ * c_x' = H_xx' psi(x')/psi(x) and the scale Oa_k(x') above,
+ * eloc_abs[i] = sum_x' |c_x'|, G_abs[i][k] = sum_x' |c_x'| Oa_k(x'), and
+ * O_abs[i][k] = Oa_k(x): a relative change u in every rounded quantity moves
+ * E_loc, G and O by at most about u times these.
  */
 int oracle_rows_abs(int n_orb, int n_alpha, int n_beta, int n_hidden, const double *h,
                     const double *eri, const double *theta, const uint64_t *rows, int64_t n_rows,
-                    double *eloc_abs, double *G_abs) {
+                    double *eloc_abs, double *G_abs, double *O_abs) {
     if (check_sys(n_orb, n_alpha, n_beta, n_hidden)) return -1;
     int m = 2 * n_orb;
     int p1 = (n_hidden + 1) * (m + 1);
@@ -284,6 +311,7 @@ int oracle_rows_abs(int n_orb, int n_alpha, int n_beta, int n_hidden, const doub
         for (int64_t i = 0; i < n_rows; i++) {
             uint64_t x = rows[i];
             double lp = rbm_lnpsi(&s, x, t);
+            if (O_abs) rbm_oscale(&s, x, O_abs + i * (int64_t)p1);
             int nc = connections(&s, x, cap, cd, ch, cs);
             if (nc < 0) {
 #pragma omp atomic write
@@ -297,8 +325,8 @@ int oracle_rows_abs(int n_orb, int n_alpha, int n_beta, int n_hidden, const doub
                 double ck = fabs(ch[k] * exp(lpk - lp));
                 el += ck;
                 if (G_abs) {
-                    rbm_orow(&s, cd[k], tp, orow);
-                    for (int c = 0; c < p1; c++) grow[c] += ck * fabs(orow[c]);
+                    rbm_oscale(&s, cd[k], orow);
+                    for (int c = 0; c < p1; c++) grow[c] += ck * orow[c];
                 }
             }
             if (eloc_abs) eloc_abs[i] = el;

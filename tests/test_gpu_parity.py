@@ -101,10 +101,12 @@ def _elementwise(got, ref, tol, what, floor=0.0):
         f"{what}: entry {int(np.argmax(r))} relative error {r.max():.3e} > {tol:.0e}"
 
 
-# The FP64-accurate builds' componentwise bars: |error| <= tol * (sum of |terms|) per entry.
-# Native FP64 (unit roundoff 2^-53) is held to 1e-12; the double-float build (pairs of FP32,
-# unit roundoff ~2^-48 per operation, ~2^-44 after its error-free transformations) to 4e-12.
-BUILD_TOL = {0: 4e-12, 1: 1e-12}
+# The FP64-accurate builds' componentwise bars: |error| <= tol * (first-order rounding scale)
+# per entry (lm.condition_scales). Native FP64 (unit roundoff 2^-53 = 1.1e-16) is held to
+# 1e-12 (~9,000 u); the double-float build (pairs of FP32 carried through error-free
+# transformations, ~2^-44 = 5.7e-14 per operation) to 1e-11 (~175 of its u). Measured on
+# GB300: FP64 <= 3e-13 and double-float <= 5e-12 of the scale over the cases below.
+BUILD_TOL = {0: 1e-11, 1: 1e-12}
 
 
 def _check_build(abi, pen, pd):

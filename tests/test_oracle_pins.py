@@ -136,15 +136,18 @@ def test_condition_scales_bound_the_sums():
     theta = synth.rbm_theta(n, nh, 12, sigma=0.3)
     dets = fock.sector_dets(n, na, nb)
     _, _, eloc, G = native.rows(n, na, nb, nh, h, eri, theta, dets)
-    ea, ga = native.rows_abs(n, na, nb, nh, h, eri, theta, dets)
+    _, O, _, _ = native.rows(n, na, nb, nh, h, eri, theta, dets)
+    ea, ga, oa = native.rows_abs(n, na, nb, nh, h, eri, theta, dets)
     assert np.all(np.abs(eloc) <= ea * (1 + 1e-14))
     assert np.all(np.abs(G) <= ga * (1 + 1e-14))
+    assert np.all(np.abs(O) <= oa * (1 + 1e-15))
     assert np.array_equal(ga[:, 0], ea)
     hd = np.diag(np.diag(h))
     _, _, eloc_d, G_d = native.rows(n, na, nb, nh, hd, np.zeros_like(eri), theta, dets)
-    ea_d, ga_d = native.rows_abs(n, na, nb, nh, hd, np.zeros_like(eri), theta, dets)
+    ea_d, ga_d, oa_d = native.rows_abs(n, na, nb, nh, hd, np.zeros_like(eri), theta, dets)
     assert np.array_equal(ea_d, np.abs(eloc_d))
-    assert np.allclose(ga_d, np.abs(G_d), rtol=1e-15, atol=0)
+    # a diagonal Hamiltonian: G = E_loc O, so its scale is |E_loc| times O's
+    assert np.allclose(ga_d, np.abs(eloc_d)[:, None] * oa_d, rtol=1e-14, atol=0)
 
 
 def test_componentwise_bar_catches_a_small_column_error():
