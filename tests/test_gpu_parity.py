@@ -104,8 +104,7 @@ def _elementwise(got, ref, tol, what, floor=0.0):
 # The FP64-accurate builds' componentwise bars: |error| <= tol * (first-order rounding scale)
 # per entry (lm.condition_scales). Native FP64 (unit roundoff 2^-53 = 1.1e-16) is held to
 # 1e-12 (~9,000 u); the double-float build (pairs of FP32 carried through error-free
-# transformations, ~2^-44 = 5.7e-14 per operation) to 1e-11 (~175 of its u). Measured on
-# GB300: FP64 <= 3e-13 and double-float <= 5e-12 of the scale over the cases below.
+# transformations, ~2^-44 = 5.7e-14 per operation) to 1e-11 (~175 of its u).
 BUILD_TOL = {0: 1e-11, 1: 1e-12}
 
 
