@@ -282,6 +282,31 @@ int irl_step_sharded(lm_pencil *p, const irl_params *prm, lm_reduce_fn reduce, v
                      int where, irl_result *out, double *c_out, double *dtheta_out,
                      double *theta_inout, void *stream);
 
+/* ---- block product on the tensor cores --------------------------------- */
+
+/*
+ * The pencil product of a block of nvec <= 16 vectors at once (Discussion: the
+ * block-Lanczos extension of the method; Methods, eq. matrix_vec_prod per
+ * vector): HV = H~' V and SV = S~ V for V = [v_1 .. v_nvec], computed as the
+ * two dense tall-skinny contractions O_c^T W (G'_c V) and O_c^T W (O_c V)
+ * (HALF: HV = 1/2 (O_c^T W G'_c V + G'_c^T W O_c V)) on the tensor cores with
+ * the pencil's BF16 factors, V rounded to BF16 and FP32 accumulation; each
+ * factor is read once from HBM per call. Vector k of V, HV, SV starts at
+ * k * ldv (P+1 FP64 entries used; ldv >= P+1); all three are device arrays,
+ * HV or SV may be NULL. sym: NONE, HALF or AUTO. Needs a pencil built with
+ * LM_BF16 and P+1 <= 1920 (LM_ERR_ARG / LM_ERR_SIZE otherwise). Asynchronous
+ * on `stream`; a bounded wait that gives up fills HV and SV with NaN.
+ */
+int lm_apply_pencil_block(lm_pencil *p, const double *V, int ldv, int nvec, double *HV,
+                          double *SV, int sym, void *stream);
+/* The same with test hooks: dbg (device, nullable) receives the FP32 products
+ * O_c V and G'_c V of the first 128 rows ([2][128][16]); lbo_mn, sbo_mn are the
+ * shared-memory strides used for the transposed operand (16384 and 1024 in
+ * lm_apply_pencil_block). */
+int lm_debug_pencil_block(lm_pencil *p, const double *V, int ldv, int nvec, double *HV,
+                          double *SV, int sym, float *dbg, unsigned lbo_mn, unsigned sbo_mn,
+                          void *stream);
+
 /* ---- inspection (tests and tools; not on the timed path) -------------- */
 
 /* Enumerate the (n_alpha, n_beta) sector in ascending order into out

@@ -111,6 +111,9 @@ _SIGNATURES = {
     "lm_server_free": (c_int, [c_vp]),
     "lm_irl_history": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, ctypes.POINTER(c_int)]),
     "lm_debug_wait_timeout": (c_int, [c_vp, c_int, c_int64]),
+    "lm_apply_pencil_block": (c_int, [c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_int, c_vp]),
+    "lm_debug_pencil_block": (c_int, [c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_int, c_vp,
+                                      ctypes.c_uint, ctypes.c_uint, c_vp]),
     "lm_shard_build": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_vp, c_vp, c_int64, c_int,
                                c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_double)]),
     "lm_shard_sums": (c_int, [c_vp, c_double, c_vp, c_vp]),
@@ -334,6 +337,22 @@ class Pencil:
                                     ptr(theta_inout), stream_handle(stream))
         self.ctx.check(rc, "irl_step_sharded")
         return res
+
+    def apply_block(self, V, HV=None, SV=None, sym=LM_SYM_AUTO, stream=None, nvec=None,
+                    ldv=None):
+        """lm_apply_pencil_block on device arrays: V holds nvec vectors of P+1 entries with
+        stride ldv (a (nvec, ldv) row-major CUDA tensor); HV, SV likewise (either None)."""
+        nvec = int(V.shape[0]) if nvec is None else int(nvec)
+        ldv = int(V.shape[1]) if ldv is None else int(ldv)
+        rc = lib().lm_apply_pencil_block(self.handle, ptr(V), ldv, nvec, ptr(HV), ptr(SV),
+                                         int(sym), stream_handle(stream))
+        self.ctx.check(rc, "lm_apply_pencil_block")
+
+    def debug_block(self, V, HV, SV, sym, dbg, lbo_mn=16384, sbo_mn=1024, stream=None):
+        rc = lib().lm_debug_pencil_block(self.handle, ptr(V), int(V.shape[1]), int(V.shape[0]),
+                                         ptr(HV), ptr(SV), int(sym), ptr(dbg), int(lbo_mn),
+                                         int(sbo_mn), stream_handle(stream))
+        self.ctx.check(rc, "lm_debug_pencil_block")
 
     def irl_history(self):
         """lm_irl_history: per-cycle (lowest Ritz value, residual estimate, low-precision flag)

@@ -113,6 +113,7 @@ void pencil_release(lm_pencil *p) {
                     p->st,   p->tdf,  p->wlo, p->wel, p->wello, p->bar, p->shv};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    lm_block_release(p);
     if (p->hs) cudaFreeHost(p->hs);
     if (p->hstage) cudaFreeHost(p->hstage);
     delete p;

@@ -224,6 +224,9 @@ struct lm_pencil {
     // for the caller's reduction (2 ldp doubles, allocated on first use)
     int shard_state;
     double *shv;
+    // tensor-core block product (block.cu): tensor maps and scratch, created on
+    // first use
+    struct BlockState *blk;
 };
 
 // ---------------------------------------------------------------------------
@@ -298,6 +301,12 @@ int lm_launch_reduce_partials(lm_pencil *p, int prec, double *yH, double *yS, cu
 int lm_pencil_ctas(const lm_pencil *p, int prec);
 int lm_launch_df_to_fp64(lm_ctx *ctx, const float2 *src, double *dst, int64_t n, cudaStream_t s);
 int lm_pencil_grid(lm_pencil *p);
+
+// block.cu: the tensor-core block product (dbg / descriptor strides for tests)
+int lm_launch_pencil_block(lm_pencil *p, const double *V, int ldv, int nvec, double *HV,
+                           double *SV, int sym, float *dbg, uint32_t lbo_mn, uint32_t sbo_mn,
+                           cudaStream_t s);
+void lm_block_release(lm_pencil *p);
 
 // pencil.cu: the FP64 pencil product on caller-provided scratch (no allocation):
 // vpad holds v padded to ldp, part holds grid x 2 ldp partials, flags one int
