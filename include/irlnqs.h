@@ -300,7 +300,7 @@ int irl_step_sharded(lm_pencil *p, const irl_params *prm, lm_reduce_fn reduce, v
 int lm_apply_pencil_block(lm_pencil *p, const double *V, int ldv, int nvec, double *HV,
                           double *SV, int sym, void *stream);
 /* The same with test hooks: dbg (device, nullable) receives the FP32 products
- * O_c V and G'_c V of the first 128 rows ([2][128][16]); lbo_mn, sbo_mn are the
+ * O_c V and G'_c V of the first 64 rows ([2][64][16]); lbo_mn, sbo_mn are the
  * shared-memory strides used for the transposed operand (16384 and 1024 in
  * lm_apply_pencil_block). */
 int lm_debug_pencil_block(lm_pencil *p, const double *V, int ldv, int nvec, double *HV,

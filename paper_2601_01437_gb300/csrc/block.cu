@@ -8,24 +8,27 @@
 //
 // Both contractions are dense and tall-skinny, so they run as tcgen05 MMAs
 // (M = 128, N = 16, K = 16 per instruction) fed by TMA:
-//   phase 1, per tile of 128 rows: X_O = O_tile V and X_G = G_tile V, summed
-//     over the 128-column chunks of the row into TMEM (FP32);
+//   phase 1, per tile of 64 rows: [X_O; X_G] = [O_tile; G_tile] V, the tile's
+//     O rows stacked over its G rows as one 128-row operand, summed over the
+//     row's 128-column chunks into TMEM (FP32);
 //   epilogue: X' = W X (the tile's weights), rounded to BF16 into shared
 //     memory as the next phase's B operand;
-//   phase 2: for every 128-column chunk m, D_S[m] += O_chunk^T X'_O and
-//     D_H[m] += O_chunk^T X'_G (+ G_chunk^T X'_O for HALF), the chunks read
-//     again (from L2) as MN-major A operands; D stays in TMEM across all the
-//     tiles a CTA owns.
+//   phase 2: for every 128-column chunk m, D_S[m] += O_m^T X'_O and
+//     D_H[m] += O_m^T X'_G (+ G_m^T X'_O for HALF), the chunks read again
+//     (from L2: a tile is 64 rows, so the rows in flight between the two reads
+//     stay well inside L2) as MN-major A operands; D stays in TMEM across all
+//     the tiles a CTA owns.
 // At the end each CTA writes its D as FP32 partials; a second kernel adds the
 // partials of all CTAs in CTA order into FP64 outputs (deterministic).
 //
 // Roles (192 threads): warp 0 issues the TMA loads, warp 1 allocates TMEM and
 // one of its threads issues every MMA, warps 2-5 are the epilogue (one TMEM
-// lane quarter each). Each ring stage holds 128 columns of O and G (two
-// 64-column 128-byte-swizzled boxes each) and the matching 128 columns of V.
+// lane quarter each). A ring stage holds 128 columns of the tile's O and G
+// (64-column, 128-byte-swizzled boxes, O and G of a chunk back to back) and the
+// matching 128 columns of V.
 // Every wait is bounded: a timeout sets FLAG_TIMEOUT, every role stops, TMA
-// loads still in flight are waited for (bounded), TMEM is freed, and the host
-// reports LM_ERR_TIMEOUT.
+// loads still in flight are waited for (bounded), TMEM is freed, and the
+// products come back as NaN.
 #include <cuda.h>
 
 #include <algorithm>
@@ -35,17 +38,21 @@
 
 namespace {
 
-constexpr int BM = 128;                             // rows per tile (MMA M of phase 1)
+// A tile is BM = 64 rows. Phase 1 stacks the tile's 64 rows of O over its 64
+// rows of G into one M = 128 operand (both 64-row boxes of a 64-column chunk
+// lie back to back), so one MMA yields X_O in TMEM lanes 0-63 and X_G in lanes
+// 64-127. Phase 2 takes K = 64 rows per column chunk.
+constexpr int BM = 64;                              // rows per tile
 constexpr int NV = 16;                              // vectors per block (MMA N)
 constexpr int CW = 128;                             // columns per ring stage
-constexpr int NSTAGE = 3;
+constexpr int NSTAGE = 6;
 constexpr int BLK_THREADS = 192;
-constexpr uint32_t BOX_BYTES = BM * 64 * 2;         // 16 KB: 128 rows x 64 BF16
-constexpr uint32_t MAT_BYTES = 2 * BOX_BYTES;       // 32 KB: 128 rows x 128 columns
+constexpr uint32_t BOX_BYTES = BM * 64 * 2;         // 8 KB: 64 rows x 64 BF16
+constexpr uint32_t PAIR_BYTES = 2 * BOX_BYTES;      // O box then G box of one 64-column chunk
 constexpr uint32_t VBOX_BYTES = NV * 64 * 2;        // 2 KB: 16 vectors x 64 BF16
-constexpr uint32_t STAGE_BYTES = 2 * MAT_BYTES + 2 * VBOX_BYTES;  // 68 KB
-constexpr uint32_t X_BYTES = NV * BM * 2;           // 4 KB: one X' operand
-constexpr int MAX_NCH = 15;                         // TMEM: 32 + 2 * 16 * nch <= 512 columns
+constexpr uint32_t STAGE_BYTES = 2 * PAIR_BYTES + 2 * VBOX_BYTES;  // 36 KB
+constexpr uint32_t X_BYTES = NV * BM * 2;           // 2 KB: one X' operand
+constexpr int MAX_NCH = 15;                         // TMEM: 16 + 2 * 16 * nch <= 512 columns
 constexpr uint32_t TMEM_COLS = 512;
 
 struct BlkArgs {
@@ -57,7 +64,7 @@ struct BlkArgs {
     float *part;         // [gridDim.x][2][NV][ldo]
     float hscale;        // 1/2 for HALF, 1 for NONE
     int *flags;
-    float *dbg;          // nullable: X_O, X_G (unweighted) of CTA 0's first tile, [2][BM][NV]
+    float *dbg;          // nullable: X_O, X_G (unweighted) of CTA 0's first tile, [2][64][NV]
     uint32_t lbo_mn;     // MN-major A operand: byte stride between 64-column atoms
     uint32_t sbo_mn;     // ... and between 8-row groups
 };
@@ -144,10 +151,10 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uin
 }
 // Instruction descriptor, kind::f16: FP32 D (bits 4-5 = 1), BF16 A and B (bits
 // 7-9 and 10-12 = 1), A K-major or MN-major (bit 15), B K-major, N >> 3 at
-// bits 17-22, M >> 4 at bits 24-28.
+// bits 17-22, M >> 4 at bits 24-28 (M = 128 in both phases).
 __host__ __device__ constexpr uint32_t mma_idesc(bool a_mn) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
-           ((uint32_t)(NV >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+           ((uint32_t)(NV >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -162,9 +169,8 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
     unsigned char *sbase = smem_raw + (base - raw);
     const uint32_t sXO = base + NSTAGE * STAGE_BYTES;
     const uint32_t sXG = sXO + X_BYTES;
-    unsigned char *pXO = sbase + NSTAGE * STAGE_BYTES;
-    unsigned char *pXG = pXO + X_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(pXG + X_BYTES);
+    unsigned char *pX = sbase + NSTAGE * STAGE_BYTES;  // X'_O, then X'_G
+    uint64_t *bars = reinterpret_cast<uint64_t *>(pX + 2 * X_BYTES);
     uint64_t *full = bars, *empty = bars + NSTAGE;
     uint64_t *xready = bars + 2 * NSTAGE, *xfull = xready + 1, *done = xready + 2;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * NSTAGE + 3);
@@ -193,9 +199,11 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const uint32_t tD = tmem + 16;  // D_H[m] at tD + 16 m, D_S[m] at tD + 16 (nch + m)
 
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer: per tile, the row's chunks for phase 1
+        // (O, G, V), then again for phase 2 (O; G too for HALF)
         if (lane == 0) {
             int s = 0;
             uint32_t ph = 0;
@@ -214,20 +222,20 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
                         const uint32_t st = base + s * STAGE_BYTES;
                         const bool wantG = pass == 0 || HALF;
                         const bool wantV = pass == 0;
-                        const uint32_t bytes = MAT_BYTES + (wantG ? MAT_BYTES : 0u) +
+                        const uint32_t bytes = 2 * BOX_BYTES * (wantG ? 2u : 1u) +
                                                (wantV ? 2u * VBOX_BYTES : 0u);
                         const uint32_t fb = smem_u32(full + s);
                         mbar_expect_tx(fb, bytes);
                         const int x = c * CW;
                         tma_load_2d(st, &tO, x, row0, fb);
-                        tma_load_2d(st + BOX_BYTES, &tO, x + 64, row0, fb);
+                        tma_load_2d(st + PAIR_BYTES, &tO, x + 64, row0, fb);
                         if (wantG) {
-                            tma_load_2d(st + MAT_BYTES, &tG, x, row0, fb);
-                            tma_load_2d(st + MAT_BYTES + BOX_BYTES, &tG, x + 64, row0, fb);
+                            tma_load_2d(st + BOX_BYTES, &tG, x, row0, fb);
+                            tma_load_2d(st + PAIR_BYTES + BOX_BYTES, &tG, x + 64, row0, fb);
                         }
                         if (wantV) {
-                            tma_load_2d(st + 2 * MAT_BYTES, &tV, x, 0, fb);
-                            tma_load_2d(st + 2 * MAT_BYTES + VBOX_BYTES, &tV, x + 64, 0, fb);
+                            tma_load_2d(st + 2 * PAIR_BYTES, &tV, x, 0, fb);
+                            tma_load_2d(st + 2 * PAIR_BYTES + VBOX_BYTES, &tV, x + 64, 0, fb);
                         }
                         pend[s] = true;
                         pend_ph[s] = ph;
@@ -251,7 +259,7 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
             bool first = true;
             constexpr uint32_t id_k = mma_idesc(false), id_mn = mma_idesc(true);
             for (int t = blockIdx.x; t < a.ntiles && !*abort_flag; t += gridDim.x, ++it) {
-                // phase 1: X_O = O_tile V, X_G = G_tile V over the row's column chunks
+                // phase 1: [X_O; X_G] = [O_tile; G_tile] V over the row's column chunks
                 for (int c = 0; c < a.nch; ++c) {
                     if (!mbar_wait_u32(smem_u32(full + s), ph)) {
                         *abort_flag = 1;
@@ -262,13 +270,11 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
                     const uint32_t st = base + s * STAGE_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
-                        const uint32_t koff = (kk >> 2) * BOX_BYTES + (kk & 3) * 32;
+                        const uint32_t koff = (kk >> 2) * PAIR_BYTES + (kk & 3) * 32;
                         const uint32_t voff = (kk >> 2) * VBOX_BYTES + (kk & 3) * 32;
-                        const uint64_t bv = sw128_desc(st + 2 * MAT_BYTES + voff, 16, 1024);
-                        const uint32_t acc = (c | kk) ? 1u : 0u;
-                        tc_mma(tmem + 0, sw128_desc(st + koff, 16, 1024), bv, id_k, acc);
-                        tc_mma(tmem + 16, sw128_desc(st + MAT_BYTES + koff, 16, 1024), bv, id_k,
-                               acc);
+                        tc_mma(tmem, sw128_desc(st + koff, 16, 1024),
+                               sw128_desc(st + 2 * PAIR_BYTES + voff, 16, 1024), id_k,
+                               (c | kk) ? 1u : 0u);
                     }
                     tc_commit(smem_u32(empty + s));
                     if (++s == NSTAGE) {
@@ -294,19 +300,18 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t st = base + s * STAGE_BYTES;
-                    const uint32_t dH = tmem + 32 + 16 * m;
-                    const uint32_t dS = tmem + 32 + 16 * a.nch + 16 * m;
+                    const uint32_t dH = tD + 16 * m;
+                    const uint32_t dS = tD + 16 * a.nch + 16 * m;
 #pragma unroll
-                    for (int kk = 0; kk < 8; ++kk) {
+                    for (int kk = 0; kk < 4; ++kk) {
                         const uint64_t aO = sw128_desc(st + kk * 2048, a.lbo_mn, a.sbo_mn);
-                        const uint32_t xoff = (kk >> 2) * 2048 + (kk & 3) * 32;
-                        const uint64_t bXO = sw128_desc(sXO + xoff, 16, 1024);
-                        const uint64_t bXG = sw128_desc(sXG + xoff, 16, 1024);
+                        const uint64_t bXO = sw128_desc(sXO + kk * 32, 16, 1024);
+                        const uint64_t bXG = sw128_desc(sXG + kk * 32, 16, 1024);
                         const uint32_t acc = (first && kk == 0) ? 0u : 1u;
                         tc_mma(dS, aO, bXO, id_mn, acc);
                         tc_mma(dH, aO, bXG, id_mn, acc);
                         if (HALF)
-                            tc_mma(dH, sw128_desc(st + MAT_BYTES + kk * 2048, a.lbo_mn, a.sbo_mn),
+                            tc_mma(dH, sw128_desc(st + BOX_BYTES + kk * 2048, a.lbo_mn, a.sbo_mn),
                                    bXO, id_mn, 1u);
                     }
                     tc_commit(smem_u32(empty + s));
@@ -321,10 +326,13 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
             tc_commit(smem_u32(done));
         }
     } else {
-        // ---------------- epilogue: warps 2..5, one TMEM lane quarter each
+        // ---------------- epilogue: warps 2..5, one TMEM lane quarter each;
+        // quarters 0-1 hold X_O (rows 0-63), quarters 2-3 hold X_G
         const int q = warp & 3;
-        const int r = 32 * q + lane;  // row of the tile = TMEM lane
+        const int which = q >> 1;
+        const int r = 32 * (q & 1) + lane;  // row of the tile
         const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+        unsigned char *pXw = pX + which * X_BYTES;
         uint32_t it = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
@@ -340,26 +348,20 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            float xo[16], xg[16];
-            tc_ld16(tmem + lane_addr + 0, xo);
-            tc_ld16(tmem + lane_addr + 16, xg);
+            float x[16];
+            tc_ld16(tmem + lane_addr, x);
             const int64_t row = (int64_t)t * BM + r;
             const float wr = row < a.n_rows ? (float)a.w[row] : 0.f;
             if (a.dbg && blockIdx.x == 0 && it == 0) {
 #pragma unroll
-                for (int n = 0; n < NV; ++n) {
-                    a.dbg[r * NV + n] = xo[n];
-                    a.dbg[(BM + r) * NV + n] = xg[n];
-                }
+                for (int n = 0; n < NV; ++n) a.dbg[(which * BM + r) * NV + n] = x[n];
             }
             // X'[n][k = r], K-major with the 128-byte swizzle (16-byte chunk ^ line % 8)
-            const uint32_t hh = (uint32_t)r >> 6, kk = (uint32_t)r & 63u;
+            const uint32_t kk = (uint32_t)r;
 #pragma unroll
             for (int n = 0; n < NV; ++n) {
-                const uint32_t off =
-                    hh * 2048u + n * 128u + ((((kk >> 3) ^ (uint32_t)(n & 7))) << 4) + (kk & 7u) * 2u;
-                *reinterpret_cast<__nv_bfloat16 *>(pXO + off) = __float2bfloat16_rn(wr * xo[n]);
-                *reinterpret_cast<__nv_bfloat16 *>(pXG + off) = __float2bfloat16_rn(wr * xg[n]);
+                const uint32_t off = n * 128u + ((((kk >> 3) ^ (uint32_t)(n & 7))) << 4) + (kk & 7u) * 2u;
+                *reinterpret_cast<__nv_bfloat16 *>(pXw + off) = __float2bfloat16_rn(wr * x[n]);
             }
             fence_async_smem();
             tc_fence_before();
@@ -372,13 +374,14 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
         if (!d_ok && lane == 0) atomicOr(a.flags, FLAG_TIMEOUT);
         if (d_ok) {
             tc_fence_after();
+            const int rc = 32 * q + lane;  // column within a 128-column chunk = TMEM lane
             float *pH = a.part + (size_t)blockIdx.x * 2 * NV * a.ldo;
             float *pS = pH + (size_t)NV * a.ldo;
             for (int m = 0; m < a.nch; ++m) {
                 float h[16], sv[16];
-                tc_ld16(tmem + lane_addr + 32 + 16 * m, h);
-                tc_ld16(tmem + lane_addr + 32 + 16 * a.nch + 16 * m, sv);
-                const int col = m * CW + r;
+                tc_ld16(tD + lane_addr + 16 * m, h);
+                tc_ld16(tD + lane_addr + 16 * a.nch + 16 * m, sv);
+                const int col = m * CW + rc;
 #pragma unroll
                 for (int n = 0; n < NV; ++n) {
                     pH[(size_t)n * a.ldo + col] = ok ? h[n] * a.hscale : 0.f;

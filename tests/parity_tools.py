@@ -11,7 +11,11 @@ def componentwise(got, ref, scale, tol, what):
     d = np.abs(got - ref)
     z = scale == 0
     assert np.all(d[z] == 0), f"{what}: entries with zero scale differ"
-    r = d[~z] / scale[~z]
+    r = np.zeros_like(d)
+    r[~z] = d[~z] / scale[~z]
     worst = float(r.max()) if r.size else 0.0
-    assert worst <= tol, f"{what}: componentwise error {worst:.3e} > {tol:.0e}"
+    if worst > tol:
+        i = np.unravel_index(int(np.argmax(r)), r.shape)
+        raise AssertionError(f"{what}: componentwise error {worst:.3e} > {tol:.0e} at {i}: "
+                             f"got {got[i]!r}, oracle {ref[i]!r}, scale {scale[i]!r}")
     return worst
