@@ -70,6 +70,9 @@ def parse():
                     help="rows of the LiCl-shaped pencil used for the c2 pencil measurement")
     ap.add_argument("--pencil-only", action="store_true",
                     help="only the c2 pencil measurement (profiling runs)")
+    ap.add_argument("--block-only", action="store_true",
+                    help="only the c2 BF16 pencil with the tensor-core block product "
+                         "(profiling runs)")
     ap.add_argument("--pencil", default="df64", choices=["df64", "fp64"],
                     help="storage of the FP64 workload's Lanczos pencil factors (both "
                          "FP64-accurate; the final refinement always uses FP64)")
@@ -548,6 +551,8 @@ def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10, n_rows=262144, precs=None
         if name == "fp32":
             cases += [("fp64", abi.LM_FP64, 8, abi.LM_SYM_HALF, 2),
                       ("fp32_eloc_estimator", abi.LM_FP32, 4, abi.LM_SYM_ELOC, 1)]
+        if name == "bf16":
+            out["bf16_block16"] = block_product(abi, ctx, s, pen, w, hbm, reps)
         for nm, pp, bb, sy, nmat in cases:
             for _ in range(3):
                 pen.apply(v, hv, None, sym=sy, prec=pp, stream=s)
@@ -571,6 +576,46 @@ def pencil_c2(abi, ctx, s, dev, hbm, hbm_src, reps=10, n_rows=262144, precs=None
     out["workload"] = (f"{w.name}: {w.n_rows} MC rows x P+1 = {p1}, symmetrised H~' product, "
                        f"peak = {hbm_src} hbm_gbs")
     return out
+
+
+def block_product(abi, ctx, s, pen, w, hbm, reps=10):
+    """The tensor-core block product (16 vectors, symmetrised H~' and S~, BF16 factors) on a
+    BF16 pencil: live CUDA-event time of k_pencil_block, its algorithmic bytes (O_c and G'_c
+    read once: N_s (P+1) 2 x 2 + 8 N_s), against 16 single-vector BF16 products."""
+    import torch
+    p1 = w.n_params + 1
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device="cpu").manual_seed(7)
+    V = torch.randn(16, p1, dtype=torch.float64, generator=g).to(dev)
+    HV, SV = torch.zeros_like(V), torch.zeros_like(V)
+    for _ in range(3):
+        pen.apply_block(V, HV, SV, sym=abi.LM_SYM_HALF, stream=s)
+    torch.cuda.synchronize()
+    ctx.stats_reset(profile=True)
+    for _ in range(reps):
+        pen.apply_block(V, HV, SV, sym=abi.LM_SYM_HALF, stream=s)
+    st = ctx.stats()
+    d = st.pencil_ms / st.pencil_count / 1e3
+    nbytes = w.n_rows * p1 * 4 + 8 * w.n_rows
+    v1 = V[0].contiguous()
+    h1 = torch.zeros_like(v1)
+    for _ in range(3):
+        pen.apply(v1, h1, None, sym=abi.LM_SYM_HALF, prec=abi.LM_BF16, stream=s)
+    torch.cuda.synchronize()
+    ctx.stats_reset(profile=True)
+    for _ in range(reps):
+        pen.apply(v1, h1, None, sym=abi.LM_SYM_HALF, prec=abi.LM_BF16, stream=s)
+    st1 = ctx.stats()
+    d1 = st1.pencil_ms / st1.pencil_count / 1e3
+    return {"kernel": "k_pencil_block", "vectors": 16, "avg_ms": d * 1e3,
+            "achieved": nbytes / d / 1e9, "unit": "GB/s", "peak": hbm,
+            "frac": nbytes / d / 1e9 / hbm, "peak_nominal": HBM_NOMINAL_GBS,
+            "frac_of_nominal": nbytes / d / 1e9 / HBM_NOMINAL_GBS, "bytes": nbytes,
+            "tensor_tflops": 2 * 2 * 3 * w.n_rows * p1 * 16 / d / 1e12,
+            "single_vector_bf16_ms": d1 * 1e3,
+            "speedup_per_vector_vs_single": 16 * d1 / d,
+            "operator": "symmetrised H~' and S~ of 16 vectors, BF16 operands, FP32 accumulation "
+                        "in TMEM (tcgen05)"}
 
 
 def batched_c3(abi, ctx, steps=3, warmup=1, n_streams=16):
@@ -792,7 +837,7 @@ def main():
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
-    if args.pencil_only:
+    if args.pencil_only or args.block_only:
         import torch
         import __graft_entry__ as entry
         entry.build()
@@ -803,7 +848,8 @@ def main():
         hbm, hbm_src = peaks()
         print(json.dumps({"pencil_c2": pencil_c2(abi, ctx, torch.cuda.Stream(device=dev), dev, hbm,
                                                  hbm_src, reps=3, n_rows=args.c2_rows,
-                                                 precs=("fp32",))}), flush=True)
+                                                 precs=("bf16",) if args.block_only
+                                                 else ("fp32",))}), flush=True)
         ctx.close()
         return
     out = run_gpu(args, rank, world, local)
