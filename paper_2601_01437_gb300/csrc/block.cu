@@ -45,12 +45,16 @@ namespace {
 constexpr int BM = 64;                              // rows per tile
 constexpr int NV = 16;                              // vectors per block (MMA N)
 constexpr int CW = 128;                             // columns per ring stage
-constexpr int NSTAGE = 6;
-constexpr int BLK_THREADS = 192;
+constexpr int NSTAGE_A = 4;                         // phase-1 ring (HBM loads)
+constexpr int NSTAGE_B = 2;                         // phase-2 ring (re-reads from L2)
+constexpr int BLK_THREADS = 224;
 constexpr uint32_t BOX_BYTES = BM * 64 * 2;         // 8 KB: 64 rows x 64 BF16
 constexpr uint32_t PAIR_BYTES = 2 * BOX_BYTES;      // O box then G box of one 64-column chunk
 constexpr uint32_t VBOX_BYTES = NV * 64 * 2;        // 2 KB: 16 vectors x 64 BF16
-constexpr uint32_t STAGE_BYTES = 2 * PAIR_BYTES + 2 * VBOX_BYTES;  // 36 KB
+constexpr uint32_t STAGE_A_BYTES = 2 * PAIR_BYTES + 2 * VBOX_BYTES;  // 36 KB: O, G, V
+constexpr uint32_t STAGE_B_BYTES = 2 * PAIR_BYTES;                   // 32 KB: O, G
+constexpr uint32_t RING_A_BYTES = NSTAGE_A * STAGE_A_BYTES;
+constexpr uint32_t RING_BYTES = RING_A_BYTES + NSTAGE_B * STAGE_B_BYTES;
 constexpr uint32_t X_BYTES = NV * BM * 2;           // 2 KB: one X' operand
 constexpr int MAX_NCH = 15;                         // TMEM: 16 + 2 * 16 * nch <= 512 columns
 constexpr uint32_t TMEM_COLS = 512;
@@ -167,20 +171,26 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *sbase = smem_raw + (base - raw);
-    const uint32_t sXO = base + NSTAGE * STAGE_BYTES;
+    const uint32_t baseB = base + RING_A_BYTES;
+    const uint32_t sXO = base + RING_BYTES;
     const uint32_t sXG = sXO + X_BYTES;
-    unsigned char *pX = sbase + NSTAGE * STAGE_BYTES;  // X'_O, then X'_G
+    unsigned char *pX = sbase + RING_BYTES;  // X'_O, then X'_G
     uint64_t *bars = reinterpret_cast<uint64_t *>(pX + 2 * X_BYTES);
-    uint64_t *full = bars, *empty = bars + NSTAGE;
-    uint64_t *xready = bars + 2 * NSTAGE, *xfull = xready + 1, *done = xready + 2;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * NSTAGE + 3);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NSTAGE + 4);
+    uint64_t *fullA = bars, *emptyA = bars + NSTAGE_A;
+    uint64_t *fullB = bars + 2 * NSTAGE_A, *emptyB = fullB + NSTAGE_B;
+    uint64_t *xready = emptyB + NSTAGE_B, *xfull = xready + 1, *done = xready + 2;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(done + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(full + s, 1);
-            mbar_init(empty + s, 1);
+        for (int s = 0; s < NSTAGE_A; ++s) {
+            mbar_init(fullA + s, 1);
+            mbar_init(emptyA + s, 1);
+        }
+        for (int s = 0; s < NSTAGE_B; ++s) {
+            mbar_init(fullB + s, 1);
+            mbar_init(emptyB + s, 1);
         }
         mbar_init(xready, 1);
         mbar_init(xfull, 128);
@@ -201,73 +211,76 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t tD = tmem + 16;  // D_H[m] at tD + 16 m, D_S[m] at tD + 16 (nch + m)
 
-    if (warp == 0) {
-        // ---------------- TMA producer: per tile, the row's chunks for phase 1
-        // (O, G, V), then again for phase 2 (O; G too for HALF)
+    if (warp == 0 || warp == 6) {
+        // ---------------- TMA producers: warp 0 feeds phase 1 (O, G, V chunks of
+        // every tile, from HBM) through ring A; warp 6 feeds phase 2 (the same
+        // O chunks, and G for HALF, again: L2 hits) through ring B. Separate rings
+        // let the next tile's HBM loads run while phase 2 waits for the epilogue.
         if (lane == 0) {
+            const bool ringA = warp == 0;
+            const int nst = ringA ? NSTAGE_A : NSTAGE_B;
+            uint64_t *full = ringA ? fullA : fullB, *empty = ringA ? emptyA : emptyB;
+            const uint32_t rbase = ringA ? base : baseB;
+            const uint32_t sbytes = ringA ? STAGE_A_BYTES : STAGE_B_BYTES;
+            const bool wantG = ringA || HALF;
+            const uint32_t bytes = 2 * BOX_BYTES * (wantG ? 2u : 1u) + (ringA ? 2u * VBOX_BYTES : 0u);
             int s = 0;
             uint32_t ph = 0;
-            uint32_t pend_ph[NSTAGE];
-            bool pend[NSTAGE];
-            for (int i = 0; i < NSTAGE; ++i) pend[i] = false;
+            uint32_t pend_ph[NSTAGE_A];
+            bool pend[NSTAGE_A];
+            for (int i = 0; i < NSTAGE_A; ++i) pend[i] = false;
             for (int t = blockIdx.x; t < a.ntiles && !*abort_flag; t += gridDim.x) {
                 const int row0 = t * BM;
-                for (int pass = 0; pass < 2 && !*abort_flag; ++pass) {
-                    for (int c = 0; c < a.nch; ++c) {
-                        if (!mbar_wait_u32(smem_u32(empty + s), ph ^ 1u)) {
-                            *abort_flag = 1;
-                            atomicOr(a.flags, FLAG_TIMEOUT);
-                            break;
-                        }
-                        const uint32_t st = base + s * STAGE_BYTES;
-                        const bool wantG = pass == 0 || HALF;
-                        const bool wantV = pass == 0;
-                        const uint32_t bytes = 2 * BOX_BYTES * (wantG ? 2u : 1u) +
-                                               (wantV ? 2u * VBOX_BYTES : 0u);
-                        const uint32_t fb = smem_u32(full + s);
-                        mbar_expect_tx(fb, bytes);
-                        const int x = c * CW;
-                        tma_load_2d(st, &tO, x, row0, fb);
-                        tma_load_2d(st + PAIR_BYTES, &tO, x + 64, row0, fb);
-                        if (wantG) {
-                            tma_load_2d(st + BOX_BYTES, &tG, x, row0, fb);
-                            tma_load_2d(st + PAIR_BYTES + BOX_BYTES, &tG, x + 64, row0, fb);
-                        }
-                        if (wantV) {
-                            tma_load_2d(st + 2 * PAIR_BYTES, &tV, x, 0, fb);
-                            tma_load_2d(st + 2 * PAIR_BYTES + VBOX_BYTES, &tV, x + 64, 0, fb);
-                        }
-                        pend[s] = true;
-                        pend_ph[s] = ph;
-                        if (++s == NSTAGE) {
-                            s = 0;
-                            ph ^= 1u;
-                        }
+                for (int c = 0; c < a.nch; ++c) {
+                    if (!mbar_wait_u32(smem_u32(empty + s), ph ^ 1u)) {
+                        *abort_flag = 1;
+                        atomicOr(a.flags, FLAG_TIMEOUT);
+                        break;
+                    }
+                    const uint32_t st = rbase + s * sbytes;
+                    const uint32_t fb = smem_u32(full + s);
+                    mbar_expect_tx(fb, bytes);
+                    const int x = c * CW;
+                    tma_load_2d(st, &tO, x, row0, fb);
+                    tma_load_2d(st + PAIR_BYTES, &tO, x + 64, row0, fb);
+                    if (wantG) {
+                        tma_load_2d(st + BOX_BYTES, &tG, x, row0, fb);
+                        tma_load_2d(st + PAIR_BYTES + BOX_BYTES, &tG, x + 64, row0, fb);
+                    }
+                    if (ringA) {
+                        tma_load_2d(st + 2 * PAIR_BYTES, &tV, x, 0, fb);
+                        tma_load_2d(st + 2 * PAIR_BYTES + VBOX_BYTES, &tV, x + 64, 0, fb);
+                    }
+                    pend[s] = true;
+                    pend_ph[s] = ph;
+                    if (++s == nst) {
+                        s = 0;
+                        ph ^= 1u;
                     }
                 }
             }
             // no load may still be landing when the CTA leaves (bounded)
-            for (int i = 0; i < NSTAGE; ++i)
+            for (int i = 0; i < nst; ++i)
                 if (pend[i] && !mbar_wait_u32(smem_u32(full + i), pend_ph[i]))
                     atomicOr(a.flags, FLAG_TIMEOUT);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
-            int s = 0;
-            uint32_t ph = 0, it = 0;
+            int sa = 0, sb = 0;
+            uint32_t pha = 0, phb = 0, it = 0;
             bool first = true;
             constexpr uint32_t id_k = mma_idesc(false), id_mn = mma_idesc(true);
             for (int t = blockIdx.x; t < a.ntiles && !*abort_flag; t += gridDim.x, ++it) {
                 // phase 1: [X_O; X_G] = [O_tile; G_tile] V over the row's column chunks
                 for (int c = 0; c < a.nch; ++c) {
-                    if (!mbar_wait_u32(smem_u32(full + s), ph)) {
+                    if (!mbar_wait_u32(smem_u32(fullA + sa), pha)) {
                         *abort_flag = 1;
                         atomicOr(a.flags, FLAG_TIMEOUT);
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = base + s * STAGE_BYTES;
+                    const uint32_t st = base + sa * STAGE_A_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
                         const uint32_t koff = (kk >> 2) * PAIR_BYTES + (kk & 3) * 32;
@@ -276,10 +289,10 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
                                sw128_desc(st + 2 * PAIR_BYTES + voff, 16, 1024), id_k,
                                (c | kk) ? 1u : 0u);
                     }
-                    tc_commit(smem_u32(empty + s));
-                    if (++s == NSTAGE) {
-                        s = 0;
-                        ph ^= 1u;
+                    tc_commit(smem_u32(emptyA + sa));
+                    if (++sa == NSTAGE_A) {
+                        sa = 0;
+                        pha ^= 1u;
                     }
                 }
                 if (*abort_flag) break;
@@ -293,13 +306,13 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
                 tc_fence_after();
                 // phase 2: D_S[m] += O_m^T X'_O, D_H[m] += O_m^T X'_G (+ G_m^T X'_O)
                 for (int m = 0; m < a.nch; ++m) {
-                    if (!mbar_wait_u32(smem_u32(full + s), ph)) {
+                    if (!mbar_wait_u32(smem_u32(fullB + sb), phb)) {
                         *abort_flag = 1;
                         atomicOr(a.flags, FLAG_TIMEOUT);
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = base + s * STAGE_BYTES;
+                    const uint32_t st = baseB + sb * STAGE_B_BYTES;
                     const uint32_t dH = tD + 16 * m;
                     const uint32_t dS = tD + 16 * a.nch + 16 * m;
 #pragma unroll
@@ -314,10 +327,10 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
                             tc_mma(dH, sw128_desc(st + BOX_BYTES + kk * 2048, a.lbo_mn, a.sbo_mn),
                                    bXO, id_mn, 1u);
                     }
-                    tc_commit(smem_u32(empty + s));
-                    if (++s == NSTAGE) {
-                        s = 0;
-                        ph ^= 1u;
+                    tc_commit(smem_u32(emptyB + sb));
+                    if (++sb == NSTAGE_B) {
+                        sb = 0;
+                        phb ^= 1u;
                     }
                 }
                 first = false;
@@ -325,7 +338,7 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
             // completes once every MMA issued above has
             tc_commit(smem_u32(done));
         }
-    } else {
+    } else if (warp <= 5) {
         // ---------------- epilogue: warps 2..5, one TMEM lane quarter each;
         // quarters 0-1 hold X_O (rows 0-63), quarters 2-3 hold X_G
         const int q = warp & 3;
@@ -484,7 +497,7 @@ bool encode_2d(CUtensorMap *m, const void *ptr, int64_t rows, int cols, int ld, 
 }
 
 size_t block_smem_bytes() {
-    return 1024 + (size_t)NSTAGE * STAGE_BYTES + 2 * X_BYTES + (2 * NSTAGE + 6) * 8;
+    return 1024 + (size_t)RING_BYTES + 2 * X_BYTES + (2 * NSTAGE_A + 2 * NSTAGE_B + 6) * 8;
 }
 
 int block_setup(lm_pencil *p) {
