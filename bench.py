@@ -236,7 +236,8 @@ def build_roofline(st, w, arith):
             " x 2 flops (FMA) x 2070 MHz, from the unit counts and clocks"}
 
 
-def timed_lm_steps(abi, ctx, s, sysd, w, theta0, rows_d, wts_d, prec, steps, warmup):
+def timed_lm_steps(abi, ctx, s, sysd, w, theta0, rows_d, wts_d, prec, steps, warmup, block=0,
+                   m=None):
     """LM steps of workload w on stream s (build, IRL, refinement, theta += dtheta; theta
     restarts from theta0 every w.lm_steps steps): CUDA-event time of `steps` steps after
     `warmup`, the last result and the context's counters over the timed steps."""
@@ -251,9 +252,9 @@ def timed_lm_steps(abi, ctx, s, sysd, w, theta0, rows_d, wts_d, prec, steps, war
                 theta.copy_(theta0)
         state["pen"] = ctx.build_OG(sysd, theta, rows=rows_d, weights=wts_d, n_rows=w.n_rows,
                                     prec=prec, stream=s, pencil=state["pen"])
-        state["res"] = state["pen"].irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200,
+        state["res"] = state["pen"].irl_step(m=m or w.m, k=w.k, tol=w.tol, max_restarts=200,
                                              prec=prec, dtheta_out=dth, theta_inout=theta,
-                                             stream=s)
+                                             stream=s, block=block)
         if state["first"] is None:
             state["first"] = state["res"]
 
@@ -294,9 +295,9 @@ def native_fp64_c1(abi, ctx, s, dev, w, steps=5, warmup=2):
 def mixed_c2(abi, ctx, s, dev, steps=2, warmup=1):
     """The LiCl-shaped mixed-precision LM step (14 spatial orbitals, 14 electrons, 262,144
     MC rows, Nh = 56, P+1 = 1,653): FP32 then BF16 O_c/G'_c copies for the first IRL phase
-    with FP64 continuation and refinement, against the plain FP64 path (FP64 factors in
-    every product) on the same rows and theta; |lambda - lambda_FP64| of the first step
-    of each precision."""
+    (single-vector Lanczos, or block Lanczos on the tensor-core block product) with FP64
+    continuation and refinement, against the plain FP64 path (FP64 factors in every
+    product) on the same rows and theta; |lambda - lambda_FP64| of the first step of each."""
     import torch
     w = synth.WORKLOADS["licl_14o14e_mc"]
     h, eri, th0, rows, counts = w.inputs()
@@ -308,16 +309,19 @@ def mixed_c2(abi, ctx, s, dev, steps=2, warmup=1):
     out = {"workload": (f"{w.name}: {w.n_rows} MC rows, P+1 = {w.n_params + 1}, "
                         f"{w.lm_steps}-step LM trajectories, IRL m={w.m} k={w.k} tol={w.tol:g}")}
     lam = {}
-    for name, pr in (("fp64", abi.LM_FP64), ("fp32", abi.LM_FP32), ("bf16", abi.LM_BF16)):
+    for name, pr, blk in (("fp64", abi.LM_FP64, 0), ("fp32", abi.LM_FP32, 0),
+                          ("bf16", abi.LM_BF16, 0), ("bf16_block16", abi.LM_BF16, 16)):
         ms, res, first, st = timed_lm_steps(abi, ctx, s, sysd, w, th_d, rows_d, wts_d, pr, steps,
-                                            warmup)
+                                            warmup, block=blk, m=64 if blk else None)
         lam[name] = first.lambda_
         out[name] = {"value": steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
                      "build_ms": st.build_ms / max(st.build_count, 1),
                      "pencil_ms_total_per_step": st.pencil_ms / steps,
                      "lambda_first_step": first.lambda_, "n_matvec": first.n_matvec,
                      "n_matvec_lowp": first.n_matvec_lowp, "residual": first.residual}
-    for name in ("fp32", "bf16"):
+    out["bf16_block16"]["solver"] = ("block Lanczos, 4 blocks of 16 vectors on the tensor-core "
+                                     "block product, then FP64 continuation and refinement")
+    for name in ("fp32", "bf16", "bf16_block16"):
         out[name]["abs_err_vs_fp64_ha"] = abs(lam[name] - lam["fp64"])
         out[name]["speedup_vs_fp64"] = out[name]["value"] / out["fp64"]["value"]
     out["steps"], out["warmup"] = steps, warmup

@@ -139,6 +139,11 @@ typedef struct {
                         /* paper's three-term recurrence of Algorithm 2 only      */
     int mode;           /* IRL_MODE_SHEP (0): the paper's S ~ I eigenproblem      */
                         /* (eq. standard_evp); no other mode is accepted          */
+    int block;          /* 0: single-vector Lanczos. 16: the low-precision phase  */
+                        /* is block Lanczos (m / 16 blocks of 16 vectors, m in    */
+                        /* 16..64) on the tensor-core block product; needs a      */
+                        /* BF16 pencil and precision LM_BF16. Its Ritz vector     */
+                        /* starts the FP64 continuation and refinement.           */
 } irl_params;
 
 enum { IRL_REORTH_FULL = 0, IRL_REORTH_NONE = 1 };

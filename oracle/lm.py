@@ -54,7 +54,7 @@ def centre(O, G, eloc, w):
     return E, Obar, Oc, Gpc
 
 
-def condition_scales(pd, n_orb, n_alpha, n_beta, n_hidden, h, eri, theta):
+def condition_scales(pd, n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, union_occ=False):
     """First-order rounding scales of every entry the build produces, for componentwise
     error bars: how far a relative change u in every rounded quantity can move the entry,
     divided by u.
@@ -67,8 +67,12 @@ def condition_scales(pd, n_orb, n_alpha, n_beta, n_hidden, h, eri, theta):
         A_G(x,k) = sum_x' |c_x'| Oa(x',k) + |<O_k>| A_E(x) + <Oa_k> |E_loc(x)| + |E| A_O(x,k)
     column 0: O_c = 1 exactly (A_O = 1), G'_c = E_loc - E (A_G = A_E + |E|).
     (<.> is the weighted mean over the rows.)
+    union_occ: the sum over x' in A_G counts every connection whose x or x' occupies the
+    orbital of column k -- the scale of G formed, for orbitals occupied in x, as the sum
+    over all connections minus the sum over those that empty the orbital.
     """
-    ea, ga, oa = native.rows_abs(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, pd.rows)
+    ea, ga, oa = native.rows_abs(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, pd.rows,
+                                 union_occ)
     ob = np.abs(pd.Obar)
     oam = pd.w @ oa
     AO = oa + oam[None, :]

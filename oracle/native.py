@@ -41,7 +41,7 @@ def lib():
                                   dp, dp, dp, up, ctypes.c_int64, dp, dp, dp, dp]
         L.oracle_rows.restype = ctypes.c_int
         L.oracle_rows_abs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                      dp, dp, dp, up, ctypes.c_int64, dp, dp, dp]
+                                      dp, dp, dp, up, ctypes.c_int64, dp, dp, dp, ctypes.c_int]
         L.oracle_rows_abs.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -92,10 +92,11 @@ def rows(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, dets, want_o=True, wan
     return lnpsi, O, eloc, G
 
 
-def rows_abs(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, dets):
+def rows_abs(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, dets, union_occ=False):
     """Condition scales of the per-row quantities: (sum_x' |c_x'|, sum_x' |c_x'| Oa(x'), Oa(x))
     with c_x' = H_xx' psi(x')/psi(x) and Oa the first-order rounding scale of the O row
-    (|tanh z| + (1 - tanh^2 z) (|b| + sum |W x|) on hidden rows, |O| elsewhere)."""
+    (|tanh z| + (1 - tanh^2 z) (|b| + sum |W x|) on hidden rows, |O| elsewhere).
+    union_occ: in the G scale, Oa(x') takes its visible factors from x' | x."""
     h = np.ascontiguousarray(h, dtype=np.float64)
     eri = np.ascontiguousarray(eri, dtype=np.float64)
     theta = np.ascontiguousarray(theta, dtype=np.float64)
@@ -108,7 +109,8 @@ def rows_abs(n_orb, n_alpha, n_beta, n_hidden, h, eri, theta, dets):
     rc = lib().oracle_rows_abs(n_orb, n_alpha, n_beta, n_hidden, _p(h, ctypes.c_double),
                                _p(eri, ctypes.c_double), _p(theta, ctypes.c_double),
                                _p(dets, ctypes.c_uint64), nr, _p(ea, ctypes.c_double),
-                               _p(ga, ctypes.c_double), _p(oa, ctypes.c_double))
+                               _p(ga, ctypes.c_double), _p(oa, ctypes.c_double),
+                               int(bool(union_occ)))
     if rc != 0:
         raise RuntimeError(f"oracle_rows_abs failed ({rc})")
     return ea, ga, oa

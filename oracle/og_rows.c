@@ -262,10 +262,11 @@ int oracle_rows(int n_orb, int n_alpha, int n_beta, int n_hidden, const double *
  * S_j = |b_j| + sum_p |W_jp| x_p; so the scale is (|t_j| + (1 - t_j^2) S_j) x_c
  * (x_0 = 1). Visible-unit entries (0/1) and entry (0,0) are exact: scale |O|.
  */
-static void rbm_oscale(const osys *s, uint64_t x, double *oa) {
+static void rbm_oscale(const osys *s, uint64_t x, uint64_t occ, double *oa) {
+    /* hidden factors from x, visible factors from the occupation mask occ */
     int m1 = s->m + 1;
     for (int c = 0; c <= s->m; c++)
-        oa[c] = (c == 0) ? 1.0 : (double)((x >> (c - 1)) & 1ULL);
+        oa[c] = (c == 0) ? 1.0 : (double)((occ >> (c - 1)) & 1ULL);
     for (int j = 0; j < s->nh; j++) {
         double z = th_b(s, j), sz = fabs(th_b(s, j));
         for (int p = 0; p < s->m; p++)
@@ -276,7 +277,7 @@ static void rbm_oscale(const osys *s, uint64_t x, double *oa) {
         double t = tanh(z);
         double u = fabs(t) + (1.0 - t * t) * sz;
         for (int c = 0; c <= s->m; c++) {
-            double v = (c == 0) ? 1.0 : (double)((x >> (c - 1)) & 1ULL);
+            double v = (c == 0) ? 1.0 : (double)((occ >> (c - 1)) & 1ULL);
             oa[(j + 1) * m1 + c] = u * v;
         }
     }
@@ -288,10 +289,13 @@ static void rbm_oscale(const osys *s, uint64_t x, double *oa) {
  * eloc_abs[i] = sum_x' |c_x'|, G_abs[i][k] = sum_x' |c_x'| Oa_k(x'), and
  * O_abs[i][k] = Oa_k(x): a relative change u in every rounded quantity moves
  * E_loc, G and O by at most about u times these.
+ * union_occ = 1: in G_abs, the visible factor of Oa_k(x') is 1 when orbital k
+ * is occupied in x or in x' (the scale of a G formed, for orbitals occupied in
+ * x, as a sum over all connections minus the sum over those that empty k).
  */
 int oracle_rows_abs(int n_orb, int n_alpha, int n_beta, int n_hidden, const double *h,
                     const double *eri, const double *theta, const uint64_t *rows, int64_t n_rows,
-                    double *eloc_abs, double *G_abs, double *O_abs) {
+                    double *eloc_abs, double *G_abs, double *O_abs, int union_occ) {
     if (check_sys(n_orb, n_alpha, n_beta, n_hidden)) return -1;
     int m = 2 * n_orb;
     int p1 = (n_hidden + 1) * (m + 1);
@@ -311,7 +315,7 @@ int oracle_rows_abs(int n_orb, int n_alpha, int n_beta, int n_hidden, const doub
         for (int64_t i = 0; i < n_rows; i++) {
             uint64_t x = rows[i];
             double lp = rbm_lnpsi(&s, x, t);
-            if (O_abs) rbm_oscale(&s, x, O_abs + i * (int64_t)p1);
+            if (O_abs) rbm_oscale(&s, x, x, O_abs + i * (int64_t)p1);
             int nc = connections(&s, x, cap, cd, ch, cs);
             if (nc < 0) {
 #pragma omp atomic write
@@ -325,7 +329,7 @@ int oracle_rows_abs(int n_orb, int n_alpha, int n_beta, int n_hidden, const doub
                 double ck = fabs(ch[k] * exp(lpk - lp));
                 el += ck;
                 if (G_abs) {
-                    rbm_oscale(&s, cd[k], orow);
+                    rbm_oscale(&s, cd[k], union_occ ? (cd[k] | x) : cd[k], orow);
                     for (int c = 0; c < p1; c++) grow[c] += ck * orow[c];
                 }
             }

@@ -43,7 +43,8 @@ class lm_pencil_info(ctypes.Structure):
 class irl_params(ctypes.Structure):
     _fields_ = [("m", c_int), ("k", c_int), ("tol", c_double), ("max_restarts", c_int),
                 ("seed", c_uint64), ("sym", c_int), ("precision", c_int),
-                ("deflate_null", c_int), ("v0", c_vp), ("reorth", c_int), ("mode", c_int)]
+                ("deflate_null", c_int), ("v0", c_vp), ("reorth", c_int), ("mode", c_int),
+                ("block", c_int)]
 
 
 class irl_result(ctypes.Structure):
@@ -290,9 +291,9 @@ class Pencil:
 
     def irl_step(self, m=20, k=1, tol=1e-12, max_restarts=200, seed=111, sym=LM_SYM_AUTO,
                  prec=LM_FP64, deflate_null=1, v0=None, c_out=None, dtheta_out=None,
-                 theta_inout=None, stream=None, reorth=IRL_REORTH_FULL):
+                 theta_inout=None, stream=None, reorth=IRL_REORTH_FULL, block=0):
         prm = irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null),
-                         ptr(v0), int(reorth), IRL_MODE_SHEP)
+                         ptr(v0), int(reorth), IRL_MODE_SHEP, int(block))
         res = irl_result()
         rc = lib().irl_step(self.handle, ctypes.byref(prm), ctypes.byref(res), ptr(c_out),
                             ptr(dtheta_out), ptr(theta_inout), stream_handle(stream))
@@ -330,7 +331,7 @@ class Pencil:
                 return 1
         fn = REDUCE_FN(cb)
         prm = irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null),
-                         None, IRL_REORTH_FULL, IRL_MODE_SHEP)
+                         None, IRL_REORTH_FULL, IRL_MODE_SHEP, 0)
         res = irl_result()
         rc = lib().irl_step_sharded(self.handle, ctypes.byref(prm), fn, None, int(where),
                                     ctypes.byref(res), ptr(c_out), ptr(dtheta_out),
@@ -392,7 +393,7 @@ class Pencil:
 def irl_settings(m=20, k=1, tol=1e-12, max_restarts=200, seed=111, sym=LM_SYM_AUTO,
                  prec=LM_FP64, deflate_null=1, reorth=IRL_REORTH_FULL):
     return irl_params(m, k, tol, max_restarts, seed, int(sym), int(prec), int(deflate_null), None,
-                      int(reorth), IRL_MODE_SHEP)
+                      int(reorth), IRL_MODE_SHEP, 0)
 
 
 class Batch:

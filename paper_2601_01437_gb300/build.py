@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libirlnqs.so")
-SOURCES = ["abi.cu", "build.cu", "pencil.cu", "irl.cu", "noalloc.cu", "engine.cu", "block.cu"]
+SOURCES = ["abi.cu", "build.cu", "pencil.cu", "irl.cu", "noalloc.cu", "engine.cu", "block.cu", "blocklz.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HEADERS = sorted([os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
                  + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")])

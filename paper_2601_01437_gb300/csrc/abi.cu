@@ -110,7 +110,7 @@ void pencil_release(lm_pencil *p) {
     void *bufs[] = {p->rows, p->wt,   p->lnpsi, p->eloc, p->O,    p->G,   p->Olo,
                     p->Glo,  p->h,    p->eri,   p->theta, p->tabs, p->stats, p->part,
                     p->V,    p->wvec, p->yvec,  p->hy,   p->sy,   p->tvec, p->dots,
-                    p->st,   p->tdf,  p->wlo, p->wel, p->wello, p->bar, p->shv};
+                    p->st,   p->tdf,  p->wlo, p->wel, p->wello, p->bar, p->shv, p->blz};
     for (void *b : bufs)
         if (b) cudaFree(b);
     lm_block_release(p);

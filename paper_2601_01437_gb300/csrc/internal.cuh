@@ -227,6 +227,9 @@ struct lm_pencil {
     // tensor-core block product (block.cu): tensor maps and scratch, created on
     // first use
     struct BlockState *blk;
+    // block Lanczos workspace (blocklz.cu), allocated on first use
+    double *blz;
+    size_t blz_len;
 };
 
 // ---------------------------------------------------------------------------
@@ -307,6 +310,10 @@ int lm_launch_pencil_block(lm_pencil *p, const double *V, int ldv, int nvec, dou
                            double *SV, int sym, float *dbg, uint32_t lbo_mn, uint32_t sbo_mn,
                            cudaStream_t s);
 void lm_block_release(lm_pencil *p);
+// blocklz.cu: the block Lanczos phase (nsteps blocks of 16 vectors on the
+// tensor-core product); the Ritz vector of the lowest Ritz value goes to u_out
+int lm_launch_block_lanczos(lm_pencil *p, int sym, int nsteps, uint64_t seed, int deflate,
+                            double *u_out, cudaStream_t s);
 
 // pencil.cu: the FP64 pencil product on caller-provided scratch (no allocation):
 // vpad holds v padded to ldp, part holds grid x 2 ldp partials, flags one int

@@ -1474,6 +1474,7 @@ struct IrlJob {
     int state;
     bool lowp, dfp, in_lowp;
     int n_lowp, cycle, max_restarts;
+    bool block;  // the low-precision phase is block Lanczos
     double rel;
     const double *v0_dev;
     double *c_out, *dtheta_out, *theta_inout, *dth_tmp;
@@ -1615,6 +1616,12 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
         return lm_fail(ctx, LM_ERR_ARG, "bad reorth %d", prm->reorth);
     if (prm->mode != IRL_MODE_SHEP)
         return lm_fail(ctx, LM_ERR_ARG, "bad mode %d", prm->mode);
+    if (prm->block != 0 &&
+        (prm->block != 16 || prm->m % 16 != 0 || prm->m > 64 || p->prec != LM_BF16 ||
+         !p->Olo || prm->precision != LM_BF16 || reduce))
+        return lm_fail(ctx, LM_ERR_ARG,
+                       "block = 16 needs m in {16, 32, 48, 64}, a BF16 pencil, precision BF16 "
+                       "and no row shards");
     IrlJob *J = new IrlJob();
     J->p = p;
     J->s = s;
@@ -1673,6 +1680,8 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
     J->dfp = prm->precision != LM_FP64 && p->Olo != nullptr && p->prec == LM_DF64;
     J->in_lowp = J->lowp;
     J->n_lowp = 0;
+    J->block = prm->block == 16;
+    if (J->block) J->in_lowp = false;  // the block phase replaces the single-vector one
     J->v0_dev = nullptr;
     J->c_out = c_out;
     J->dtheta_out = dtheta_out;
@@ -1704,6 +1713,17 @@ int irl_job_advance(IrlJob *J, int *done) {
     Run &R = J->R;
     if (J->state == JOB_INIT) {
         J->state = JOB_CYCLE;
+        if (J->block) {
+            // block Lanczos on the tensor-core product; its Ritz vector starts
+            // the FP64 phase (short cycles, as after any low-precision phase)
+            const int nsteps = J->prm.m / 16;
+            if (int rc = lm_launch_block_lanczos(p, R.sym, nsteps, J->prm.seed,
+                                                 J->prm.deflate_null, p->hy, R.s))
+                return rc;
+            R.n_matvec += 16 * nsteps;
+            J->n_lowp = 16 * nsteps;
+            J->v0_dev = p->hy;
+        }
         return job_phase_start(J);
     }
     if (J->state == JOB_CYCLE) {

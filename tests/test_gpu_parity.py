@@ -120,7 +120,9 @@ def _check_build(abi, pen, pd):
     Oc = pen.export(abi.EXPORT_O)
     Gc = pen.export(abi.EXPORT_G)
     assert np.all(Oc[:, P1:] == 0) and np.all(Gc[:, P1:] == 0)
-    AE, AO, AG = lm.condition_scales(pd, *pen.sysargs)
+    # the build forms G of an orbital occupied in x as (all connections) - (connections
+    # that empty it), so its rounding scales with both sums: union-occupation scale
+    AE, AO, AG = lm.condition_scales(pd, *pen.sysargs, union_occ=True)
     eo = componentwise(Oc[:, :P1], pd.Oc, AO, tol, "O_c")
     eg = componentwise(Gc[:, :P1], pd.Gpc, AG, tol, "G'_c")
     ee = componentwise(pen.export(abi.EXPORT_ELOC), pd.eloc, AE, tol, "E_loc")

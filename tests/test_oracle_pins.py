@@ -142,6 +142,9 @@ def test_condition_scales_bound_the_sums():
     assert np.all(np.abs(G) <= ga * (1 + 1e-14))
     assert np.all(np.abs(O) <= oa * (1 + 1e-15))
     assert np.array_equal(ga[:, 0], ea)
+    # the union-occupation scale only adds terms
+    _, gu, _ = native.rows_abs(n, na, nb, nh, h, eri, theta, dets, union_occ=True)
+    assert np.all(gu >= ga) and np.array_equal(gu[:, 0], ga[:, 0])
     hd = np.diag(np.diag(h))
     _, _, eloc_d, G_d = native.rows(n, na, nb, nh, hd, np.zeros_like(eri), theta, dets)
     ea_d, ga_d, oa_d = native.rows_abs(n, na, nb, nh, hd, np.zeros_like(eri), theta, dets)
@@ -158,7 +161,7 @@ def test_componentwise_bar_catches_a_small_column_error():
     w = synth.WORKLOADS["tiny_6o6e"]
     h, eri, th, _, _ = w.inputs()
     pd = lm.build_pencil(6, 3, 3, 24, h, eri, th)
-    AE, AO, AG = lm.condition_scales(pd, 6, 3, 3, 24, h, eri, th)
+    AE, AO, AG = lm.condition_scales(pd, 6, 3, 3, 24, h, eri, th, union_occ=True)
     assert np.all(AG >= np.abs(pd.Gpc) * (1 - 1e-14))
     bad = pd.Gpc.copy()
     bad[:, 2 * 13 + 1:2 * 13 + 13] *= 1 + 1e-11   # W columns of hidden unit 1
