@@ -233,6 +233,28 @@ int lm_pencil_free(lm_pencil *p);
  * exactly. */
 int lm_pencil_set_grid(lm_pencil *p, int ctas);
 
+/* ---- streamed rows (N_s beyond what O_c and G'_c may occupy) ---------- */
+
+/*
+ * A pencil whose O_c and G'_c are never resident (Methods, "Practical
+ * Matrix-Free Implementation": every product is a sum of per-row terms, so the
+ * rows can be rebuilt when a product needs them). It keeps the rows, weights,
+ * ln psi and E_loc (a few numbers per row) and one chunk buffer of chunk_rows
+ * rows of O_c and G'_c (and their copy of precision prec). The build makes one
+ * pass over the chunks for the statistics (E, <O>, the weights' normaliser; the
+ * chunks' sums combined in chunk order with the common ln psi shift); every
+ * product -- lm_apply_pencil, each Lanczos step and the refinement of
+ * irl_step -- rebuilds, centres and applies the chunks in order and adds their
+ * products. Results equal those of lm_build_OG's pencil up to summation
+ * order; each product costs one row build. Arguments as lm_build_OG plus
+ * chunk_rows >= 1; rows NULL enumerates the sector. O_c and G'_c cannot be
+ * exported, and the block product, row shards and the block-Lanczos phase
+ * refuse a streamed pencil (LM_ERR_ARG).
+ */
+int lm_build_streamed(lm_ctx *ctx, const lm_system *sys, const double *theta,
+                      const uint64_t *rows, const double *weights, int64_t n_rows,
+                      int64_t chunk_rows, lm_precision prec, void *stream, lm_pencil **inout);
+
 /* ---- row shards (one pencil per GPU over a partition of the rows) ------ */
 
 /*

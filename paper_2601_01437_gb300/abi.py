@@ -112,6 +112,8 @@ _SIGNATURES = {
     "lm_server_free": (c_int, [c_vp]),
     "lm_irl_history": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, ctypes.POINTER(c_int)]),
     "lm_debug_wait_timeout": (c_int, [c_vp, c_int, c_int64]),
+    "lm_build_streamed": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_vp, c_vp, c_int64,
+                                  c_int64, c_int, c_vp, ctypes.POINTER(c_vp)]),
     "lm_apply_pencil_block": (c_int, [c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_int, c_vp]),
     "lm_debug_pencil_block": (c_int, [c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_int, c_vp,
                                       ctypes.c_uint, ctypes.c_uint, c_vp]),
@@ -226,6 +228,18 @@ class Context:
         if pencil is not None:
             return pencil
         return Pencil(self, h)
+
+    def build_streamed(self, sys, theta, chunk_rows, rows=None, weights=None, n_rows=0,
+                       prec=LM_FP64, stream=None, pencil=None):
+        """lm_build_streamed: a pencil whose O_c, G'_c are rebuilt chunk by chunk per product."""
+        h = c_vp(pencil.handle if pencil is not None else None)
+        if rows is not None and n_rows == 0:
+            n_rows = int(rows.shape[0])
+        rc = lib().lm_build_streamed(self.handle, ctypes.byref(sys), ptr(theta), ptr(rows),
+                                     ptr(weights), int(n_rows), int(chunk_rows), int(prec),
+                                     stream_handle(stream), ctypes.byref(h))
+        self.check(rc, "lm_build_streamed")
+        return pencil if pencil is not None else Pencil(self, h)
 
     def shard_build(self, sys, theta, rows, weights=None, prec=LM_FP64, stream=None,
                     pencil=None):

@@ -110,7 +110,8 @@ void pencil_release(lm_pencil *p) {
     void *bufs[] = {p->rows, p->wt,   p->lnpsi, p->eloc, p->O,    p->G,   p->Olo,
                     p->Glo,  p->h,    p->eri,   p->theta, p->tabs, p->stats, p->part,
                     p->V,    p->wvec, p->yvec,  p->hy,   p->sy,   p->tvec, p->dots,
-                    p->st,   p->tdf,  p->wlo, p->wel, p->wello, p->bar, p->shv, p->blz};
+                    p->st,   p->tdf,  p->wlo, p->wel, p->wello, p->bar, p->shv, p->blz,
+                    p->cstats};
     for (void *b : bufs)
         if (b) cudaFree(b);
     lm_block_release(p);
@@ -183,7 +184,8 @@ extern "C" const char *lm_last_error(const lm_ctx *ctx) { return ctx ? ctx->err 
 // ---------------------------------------------------------------- build
 int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
                      const uint64_t *rows, const double *weights, int64_t n_rows,
-                     lm_precision prec, void *stream, lm_pencil **inout, int rows_only) {
+                     lm_precision prec, void *stream, lm_pencil **inout, int rows_only,
+                     int64_t chunk_rows) {
     if (!ctx || !inout || !theta) return lm_fail(ctx, LM_ERR_ARG, "null argument");
     ctx->err[0] = 0;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return LM_ERR_CUDA;
@@ -208,7 +210,8 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
     lm_pencil *p = *inout;
     if (p) {
         if (p->ctx != ctx || p->n != n || p->na != sys->n_alpha || p->nb != sys->n_beta ||
-            p->nh != nh || p->n_rows != n_rows || p->prec != (int)prec)
+            p->nh != nh || p->n_rows != n_rows || p->prec != (int)prec ||
+            p->chunk != (chunk_rows > 0 ? std::min(chunk_rows, n_rows) : 0))
             return lm_fail(ctx, LM_ERR_ARG, "pencil shape differs from the requested build");
     } else {
         p = new lm_pencil();
@@ -225,7 +228,10 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
         p->n_rows = n_rows;
         p->prec = prec;
         p->g_pencil = lm_pencil_grid(p);
+        p->chunk = chunk_rows > 0 ? std::min(chunk_rows, n_rows) : 0;
         const size_t nr = (size_t)n_rows, L = (size_t)ldp;
+        // O, G and their copies hold every row, or one chunk of a streamed pencil
+        const size_t nrf = p->chunk ? (size_t)p->chunk : nr;
         const int nst = (int)std::min<int64_t>(n_rows, ctx->sms * 2);
         p->part_len = std::max<int64_t>((int64_t)p->g_pencil * 2 * L, 256 + (int64_t)nst * (L + 2));
         int rc = 0;
@@ -236,12 +242,17 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
         rc = rc ? rc : dalloc(ctx, &p->wello, nr);
         rc = rc ? rc : dalloc(ctx, &p->lnpsi, nr);
         rc = rc ? rc : dalloc(ctx, &p->eloc, nr);
-        rc = rc ? rc : dalloc(ctx, &p->O, nr * L);
-        rc = rc ? rc : dalloc(ctx, &p->G, nr * L);
+        rc = rc ? rc : dalloc(ctx, &p->O, nrf * L);
+        rc = rc ? rc : dalloc(ctx, &p->G, nrf * L);
         if (!rc && prec != LM_FP64) {
             const size_t es = prec == LM_FP32 ? 4 : (prec == LM_DF64 ? 8 : 2);
-            rc = lm_cuda_check(ctx, cudaMalloc(&p->Olo, nr * L * es), "cudaMalloc");
-            rc = rc ? rc : lm_cuda_check(ctx, cudaMalloc(&p->Glo, nr * L * es), "cudaMalloc");
+            rc = lm_cuda_check(ctx, cudaMalloc(&p->Olo, nrf * L * es), "cudaMalloc");
+            rc = rc ? rc : lm_cuda_check(ctx, cudaMalloc(&p->Glo, nrf * L * es), "cudaMalloc");
+        }
+        if (!rc && p->chunk) {
+            const size_t nch = (nr + p->chunk - 1) / p->chunk;
+            rc = dalloc(ctx, &p->cstats, nch * (8 + L));
+            rc = rc ? rc : dalloc(ctx, &p->shv, 2 * L);
         }
         rc = rc ? rc : dalloc(ctx, &p->h, (size_t)n * n);
         rc = rc ? rc : dalloc(ctx, &p->eri, (size_t)n * n * n * n);
@@ -313,6 +324,14 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
     if ((rc = lm_cuda_check(ctx, cudaMemsetAsync(p->d_flags, 0, sizeof(int), s), "memset")))
         return rc;
     p->shard_state = rows_only ? 1 : 0;
+    if (p->chunk) {
+        if ((rc = lm_launch_stream_stats(p, s))) return rc;
+        cudaError_t e = cudaMemcpyAsync(&p->hs->E, p->stats + 1, sizeof(double),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&p->hs->flags, p->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+        return lm_cuda_check(ctx, e, "energy read-back");
+    }
     if (rows_only) {
         if ((rc = lm_launch_build_rows(p, s))) return rc;
         return lm_cuda_check(ctx, cudaMemcpyAsync(&p->hs->flags, p->d_flags, sizeof(int),
@@ -343,6 +362,20 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (int rc = lm_cuda_check(ctx, cudaStreamSynchronize(s), "build")) return rc;
+    return lm_build_finish(*inout);
+}
+
+// ---------------------------------------------------------------- streamed rows
+extern "C" int lm_build_streamed(lm_ctx *ctx, const lm_system *sys, const double *theta,
+                                 const uint64_t *rows, const double *weights, int64_t n_rows,
+                                 int64_t chunk_rows, lm_precision prec, void *stream,
+                                 lm_pencil **inout) {
+    if (chunk_rows < 1) return lm_fail(ctx, LM_ERR_ARG, "chunk_rows must be positive");
+    if (int rc = lm_build_enqueue(ctx, sys, theta, rows, weights, n_rows, prec, stream, inout, 0,
+                                  chunk_rows))
+        return rc;
+    if (int rc = lm_cuda_check(ctx, cudaStreamSynchronize((cudaStream_t)stream), "build"))
+        return rc;
     return lm_build_finish(*inout);
 }
 
@@ -437,8 +470,13 @@ extern "C" int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double
     cudaMemsetAsync(p->tvec, 0, p->ldp * sizeof(double), s);
     if (int rc = to_device(ctx, p->tvec, v, p->P1 * sizeof(double), s)) return rc;
     const double *vd = p->tvec;
-    if (int rc = lm_launch_pencil(p, vd, sy, prec, Sv != nullptr, nullptr, s)) return rc;
-    if (int rc = lm_launch_reduce_partials(p, prec, p->hy, p->sy, s)) return rc;
+    if (p->chunk) {
+        if (int rc = lm_launch_stream_product(p, vd, sy, prec, Sv != nullptr, p->hy, p->sy, s))
+            return rc;
+    } else {
+        if (int rc = lm_launch_pencil(p, vd, sy, prec, Sv != nullptr, nullptr, s)) return rc;
+        if (int rc = lm_launch_reduce_partials(p, prec, p->hy, p->sy, s)) return rc;
+    }
     bool h1 = false, h2 = false;
     if (Hv)
         if (int rc = from_device(ctx, Hv, p->hy, p->P1 * sizeof(double), s, h1)) return rc;
@@ -499,6 +537,8 @@ extern "C" int lm_pencil_export(lm_pencil *p, int what, void *dst, void *stream)
     const void *src = nullptr;
     size_t bytes = 0;
     const size_t nr = (size_t)p->n_rows;
+    if ((what == 0 || what == 1) && p->chunk)
+        return lm_fail(ctx, LM_ERR_ARG, "a streamed pencil keeps no O_c, G'_c to export");
     if ((what == 0 || what == 1) && p->prec == LM_DF64 && p->Olo) {
         // the centred factors of a double-float pencil exist only as pairs:
         // convert into the (otherwise unused after the build) FP64 buffer

@@ -1275,6 +1275,76 @@ __global__ void k_centre_df(const double *__restrict__ O, const double *__restri
     }
 }
 
+// Streamed pencils: slot[2] = the chunk's largest ln psi (from the per-CTA maxima)
+__global__ void k_chunk_max(const double *part, int nparts, double *slot) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double m = -INFINITY;
+    for (int b = 0; b < nparts; ++b) m = fmax(m, part[b]);
+    slot[2] = m;
+}
+
+// Streamed pencils: combine the chunks' raw sums (slot c: [0] sum w, [1] sum w
+// E_loc, [2] the chunk's ln psi shift, [8 + k] sum w O_k, each with weights
+// exp(2 (ln psi - shift_c)) or the given weights) in chunk order, with the
+// common shift M = max_c shift_c: stats[1] = E, stats[8 + k] = <O_k>,
+// stats[2] = M, stats[3] = the total weight, stats[0] = 1 (the weights are
+// normalised once, by k_stream_weights, so later centrings leave them alone).
+__global__ void k_stream_combine(const double *cst, int nchunks, int ldp, int given,
+                                 double *stats) {
+    const int ld = 8 + ldp;
+    __shared__ double sM, sW;
+    if (threadIdx.x == 0) {
+        double M = 0.0;
+        if (!given) {
+            M = -INFINITY;
+            for (int c = 0; c < nchunks; ++c) M = fmax(M, cst[(size_t)c * ld + 2]);
+        }
+        double w = 0.0, we = 0.0;
+        for (int c = 0; c < nchunks; ++c) {
+            const double f = given ? 1.0 : exp(2.0 * (cst[(size_t)c * ld + 2] - M));
+            w += f * cst[(size_t)c * ld];
+            we += f * cst[(size_t)c * ld + 1];
+        }
+        sM = M;
+        sW = w;
+        stats[0] = 1.0;
+        stats[1] = we / w;
+        stats[2] = M;
+        stats[3] = w;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < ldp; k += blockDim.x) {
+        double a = 0.0;
+        for (int c = 0; c < nchunks; ++c) {
+            const double f = given ? 1.0 : exp(2.0 * (cst[(size_t)c * ld + 2] - sM));
+            a += f * cst[(size_t)c * ld + 8 + k];
+        }
+        stats[8 + k] = a / sW;
+    }
+}
+
+// Streamed pencils: the normalised weights of every row, once:
+// w = exp(2 (ln psi - M)) / W, or the given weight / W (in place)
+__global__ void k_stream_weights(const double *lnpsi, double *wt, int64_t n, int given,
+                                 const double *stats) {
+    const double M = stats[2], iw = 1.0 / stats[3];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        wt[r] = (given ? wt[r] : exp(2.0 * (lnpsi[r] - M))) * iw;
+}
+
+// y (+)= sum of the CTA partials (CTA order): streamed products add chunk by chunk
+__global__ void k_reduce_partials_add(const double *part, int nparts, int ldp, double *yH,
+                                      double *yS, int first) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * ldp) return;
+    double t = 0.0;
+    for (int b = 0; b < nparts; ++b) t += part[(size_t)b * 2 * ldp + e];
+    double *y = e < ldp ? yH : yS;
+    const int i = e < ldp ? e : e - ldp;
+    if (y) y[i] = first ? t : y[i] + t;
+}
+
 // Weights of the E_loc-estimator product: w(x) (E_loc(x) - E), FP64 and
 // double-float (both E_loc and E include the core energy)
 __global__ void k_eloc_weights(const double *__restrict__ wt, const double *__restrict__ eloc,
@@ -1592,6 +1662,85 @@ int lm_launch_centre(lm_pencil *p, cudaStream_t s) {
                      256, 0, s>>>(p->wt, p->eloc, p->stats, p->n_rows, p->wel, p->wello);
     lm_note_launch(ctx);
     return lm_cuda_check(ctx, cudaGetLastError(), "k_eloc_weights");
+}
+
+// A chunk of a streamed pencil: the same pencil with its per-row arrays
+// offset to rows [r0, r0 + n) (O, G and their copies are the chunk buffers)
+static lm_pencil chunk_view(const lm_pencil *p, int64_t r0, int64_t n) {
+    lm_pencil v = *p;
+    v.rows += r0;
+    v.wt += r0;
+    v.wlo += r0;
+    v.wel += r0;
+    v.wello += r0;
+    v.lnpsi += r0;
+    v.eloc += r0;
+    v.n_rows = n;
+    return v;
+}
+
+// First pass over a streamed pencil: per chunk, the row build, the chunk's
+// ln psi shift and raw sums; then the combined statistics and the normalised
+// weights of every row.
+int lm_launch_stream_stats(lm_pencil *p, cudaStream_t s) {
+    lm_ctx *ctx = p->ctx;
+    const int64_t C = p->chunk;
+    const int nch = (int)((p->n_rows + C - 1) / C);
+    const int ld = 8 + p->ldp;
+    lm_prof_begin(ctx, PROF_PREP, s);
+    for (int c = 0; c < nch; ++c) {
+        const int64_t r0 = (int64_t)c * C, n = std::min(C, p->n_rows - r0);
+        lm_pencil v = chunk_view(p, r0, n);
+        if (int rc = lm_launch_build_rows(&v, s)) return rc;
+        double *slot = p->cstats + (size_t)c * ld;
+        const int nmax = std::max(1, std::min(ctx->sms, (int)((n + 255) / 256)));
+        double *given = p->given_weights ? v.wt : nullptr;
+        if (!given) {
+            k_lnpsi_max_partial<<<nmax, 256, 0, s>>>(v.lnpsi, n, p->part);
+            k_chunk_max<<<1, 32, 0, s>>>(p->part, nmax, slot);
+            lm_note_launch(ctx, 2);
+        }
+        k_weights<<<(int)std::min<int64_t>((n + 255) / 256, ctx->sms * 4), 256, 0, s>>>(
+            v.lnpsi, given, v.wt, n, p->part, nmax);
+        const int nst = (int)std::max<int64_t>(1, std::min<int64_t>(n, ctx->sms * 2));
+        k_stats_partial<<<nst, 256, 0, s>>>(v.O, v.eloc, v.wt, n, p->ldp, p->part + 256);
+        // raw sums into the slot (its [2] keeps the shift written above)
+        k_stats_final<<<(p->ldp + 31) / 32, 256, 0, s>>>(p->part + 256, nst, p->ldp, p->stats, 1);
+        cudaMemcpyAsync(slot, p->stats, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(slot + 8, p->stats + 8, p->ldp * sizeof(double), cudaMemcpyDeviceToDevice,
+                        s);
+        lm_note_launch(ctx, 3);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "stream statistics")) return rc;
+    }
+    k_stream_combine<<<1, 256, 0, s>>>(p->cstats, nch, p->ldp, p->given_weights, p->stats);
+    k_stream_weights<<<(int)std::min<int64_t>((p->n_rows + 255) / 256, ctx->sms * 4), 256, 0, s>>>(
+        p->lnpsi, p->wt, p->n_rows, p->given_weights, p->stats);
+    lm_prof_end(ctx, PROF_PREP, s);
+    lm_note_launch(ctx, 2);
+    (void)ld;
+    return lm_cuda_check(ctx, cudaGetLastError(), "stream statistics");
+}
+
+// A product on a streamed pencil: per chunk, rebuild the rows, centre them
+// with the pencil's statistics, apply the pencil (partials) and add the
+// chunk's product into yH / yS (chunk order).
+int lm_launch_stream_product(lm_pencil *p, const double *v, int sym, int prec, int want_s,
+                             double *yH, double *yS, cudaStream_t s) {
+    lm_ctx *ctx = p->ctx;
+    const int64_t C = p->chunk;
+    const int nch = (int)((p->n_rows + C - 1) / C);
+    for (int c = 0; c < nch; ++c) {
+        const int64_t r0 = (int64_t)c * C, n = std::min(C, p->n_rows - r0);
+        lm_pencil w = chunk_view(p, r0, n);
+        if (int rc = lm_launch_build_rows(&w, s)) return rc;
+        if (int rc = lm_launch_centre(&w, s)) return rc;
+        if (int rc = lm_launch_pencil(&w, v, sym, prec, want_s, nullptr, s)) return rc;
+        k_reduce_partials_add<<<(2 * p->ldp + 255) / 256, 256, 0, s>>>(
+            p->part, lm_pencil_ctas(&w, prec), p->ldp, yH, want_s ? yS : nullptr, c == 0);
+        lm_note_launch(ctx);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "stream product")) return rc;
+    }
+    return LM_OK;
 }
 
 int lm_launch_df_to_fp64(lm_ctx *ctx, const float2 *src, double *dst, int64_t n, cudaStream_t s) {

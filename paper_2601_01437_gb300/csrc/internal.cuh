@@ -230,6 +230,10 @@ struct lm_pencil {
     // block Lanczos workspace (blocklz.cu), allocated on first use
     double *blz;
     size_t blz_len;
+    // streamed pencil (lm_build_streamed): rows per chunk (0: O and G resident),
+    // the chunks' raw statistics [n_chunks][8 + ldp]
+    int64_t chunk;
+    double *cstats;
 };
 
 // ---------------------------------------------------------------------------
@@ -243,9 +247,12 @@ int lm_read_flags(lm_ctx *ctx, cudaStream_t s, int *flags);
 // flags into pinned memory) on `stream`; after that work has completed,
 // lm_build_finish checks the flags and publishes E.
 // rows_only = 1 stops after the row build (K2-K6), for row shards.
+// chunk_rows > 0 makes a streamed pencil: O and G buffers of chunk_rows rows,
+// statistics gathered chunk by chunk, products rebuilding the chunks.
 int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
                      const uint64_t *rows, const double *weights, int64_t n_rows,
-                     lm_precision prec, void *stream, lm_pencil **inout, int rows_only = 0);
+                     lm_precision prec, void *stream, lm_pencil **inout, int rows_only = 0,
+                     int64_t chunk_rows = 0);
 int lm_build_finish(lm_pencil *p);
 size_t lm_pencil_footprint(lm_ctx *ctx, int n, int nh, int64_t n_rows, int prec);
 // Staging regions: h at 0, eri after it, theta after that (ldp doubles), rows
@@ -285,6 +292,10 @@ int lm_launch_build_prep(lm_pencil *p, cudaStream_t s);
 int lm_launch_shard_max(lm_pencil *p, cudaStream_t s, int *nparts);
 int lm_launch_shard_sums(lm_pencil *p, double lnpsi_max, cudaStream_t s);
 int lm_launch_centre(lm_pencil *p, cudaStream_t s);
+// streamed pencils: the first statistics pass, and one product (chunk by chunk)
+int lm_launch_stream_stats(lm_pencil *p, cudaStream_t s);
+int lm_launch_stream_product(lm_pencil *p, const double *v, int sym, int prec, int want_s,
+                             double *yH, double *yS, cudaStream_t s);
 int lm_launch_connections(lm_ctx *ctx, int n, int na, int nb, const double *h,
                           const double *eri, const uint64_t *rows, int64_t n_rows, int cap,
                           uint64_t *od, int8_t *osg, double *oh, int32_t *cnt, double e_core,

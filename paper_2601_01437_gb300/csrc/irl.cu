@@ -1319,7 +1319,7 @@ void choose_lanczos(Run &R, lm_ctx *ctx) {
     // the cluster step sums the pencil CTAs' double-float partials itself; a
     // sharded solve hands it one reduced FP64 vector instead. The three-term
     // recurrence (no reorthogonalisation) runs in the four-kernel form only.
-    if ((any || !strcmp(env, "cluster")) && !R.reduce && !R.la.three_term) {
+    if ((any || !strcmp(env, "cluster")) && !R.reduce && !R.la.three_term && !R.p->chunk) {
         for (int C : {16, 8}) {
             int emax = 0, rmax = 0;
             cluster_extent(R.la.nrow_grid, R.la.M1, R.la.ldp, C, emax, rmax);
@@ -1379,9 +1379,14 @@ int lanczos_step(Run &R, int j) {
     // consecutive steps walk the rows in opposite directions, so each product
     // starts on the rows the previous one left in L2; fixed by j, so a rerun
     // repeats the same order
-    if (int rc = lm_launch_pencil(p, vj, R.sym, R.prec, 0, &p->st->broke, R.s,
-                                  R.lz_mode == LZ_CLUSTER, j & 1))
+    if (p->chunk) {
+        // streamed pencil: rebuild, centre and apply chunk by chunk into shv
+        if (int rc = lm_launch_stream_product(p, vj, R.sym, R.prec, 0, p->shv, nullptr, R.s))
+            return rc;
+    } else if (int rc = lm_launch_pencil(p, vj, R.sym, R.prec, 0, &p->st->broke, R.s,
+                                         R.lz_mode == LZ_CLUSTER, j & 1)) {
         return rc;
+    }
     R.n_matvec++;
     if (R.reduce) {
         // this shard's term of the product, summed over the shards
@@ -1538,8 +1543,8 @@ int job_phase_start(IrlJob *J) {
         }
     }
     R.la.nparts = lm_pencil_ctas(p, R.prec);
-    if (R.reduce) {
-        R.la.part = p->shv;  // the reduced product, one "partial"
+    if (R.reduce || p->chunk) {
+        R.la.part = p->shv;  // the reduced (or chunk-summed) product, one "partial"
         R.la.nparts = 1;
     }
     J->cycle = 0;
@@ -1560,8 +1565,13 @@ int job_refine(IrlJob *J) {
     lm_pencil *p = J->p;
     lm_ctx *ctx = p->ctx;
     cudaStream_t s = J->s;
-    if (int rc = lm_launch_pencil(p, p->yvec, R.sym, LM_FP64, 1, nullptr, s)) return rc;
-    if (int rc = lm_launch_reduce_partials(p, LM_FP64, p->hy, p->sy, s)) return rc;
+    if (p->chunk) {
+        if (int rc = lm_launch_stream_product(p, p->yvec, R.sym, LM_FP64, 1, p->hy, p->sy, s))
+            return rc;
+    } else {
+        if (int rc = lm_launch_pencil(p, p->yvec, R.sym, LM_FP64, 1, nullptr, s)) return rc;
+        if (int rc = lm_launch_reduce_partials(p, LM_FP64, p->hy, p->sy, s)) return rc;
+    }
     if (R.reduce) {
         if (int rc = shard_reduce(R, p->hy, p->ldp)) return rc;
         if (int rc = shard_reduce(R, p->sy, p->ldp)) return rc;
@@ -1603,6 +1613,8 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
     if (p->shard_state) return lm_fail(ctx, LM_ERR_ARG, "row shard not centred (lm_shard_centre)");
     if (reduce && reduce_where != LM_REDUCE_HOST && reduce_where != LM_REDUCE_DEVICE)
         return lm_fail(ctx, LM_ERR_ARG, "bad reduction location %d", reduce_where);
+    if (reduce && p->chunk)
+        return lm_fail(ctx, LM_ERR_ARG, "a streamed pencil is not a row shard");
     if (reduce && !p->shv &&
         lm_cuda_check(ctx, cudaMalloc(&p->shv, 2 * (size_t)p->ldp * sizeof(double)),
                       "cudaMalloc"))
@@ -1618,7 +1630,7 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
         return lm_fail(ctx, LM_ERR_ARG, "bad mode %d", prm->mode);
     if (prm->block != 0 &&
         (prm->block != 16 || prm->m % 16 != 0 || prm->m > 64 || p->prec != LM_BF16 ||
-         !p->Olo || prm->precision != LM_BF16 || reduce))
+         !p->Olo || prm->precision != LM_BF16 || reduce || p->chunk))
         return lm_fail(ctx, LM_ERR_ARG,
                        "block = 16 needs m in {16, 32, 48, 64}, a BF16 pencil, precision BF16 "
                        "and no row shards");
