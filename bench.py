@@ -690,11 +690,17 @@ def batched_c3(abi, ctx, steps=3, warmup=1, n_streams=16):
             "grids": sorted(set(int(g) for g in grids))}
 
 
-def serving_c4(abi, ctx, seconds=1.0, rate=200.0, n_streams=16, seed=111):
-    """Poisson LM-step requests at `rate` per second for `seconds`, 60/30/10 % of
-    c0-, c1- and c2-sized systems (6, 3 and 2 systems), continuous admission under a
-    150 GB budget; latency from submit to result. Against the same requests solved
-    one after another in plain FP64 (a bounded sample)."""
+def serving_c4(abi, ctx, seconds=1.0, rate=200.0, n_streams=16, seed=111,
+               sweep=(10.0, 15.0, 20.0, 25.0, 30.0, 40.0), sweep_seconds=2.0):
+    """Poisson LM-step requests, 60/30/10 % of c0-, c1- and c2-sized systems (6, 3 and 2
+    systems), continuous admission under a 150 GB budget, latency from submit to result:
+    - at the configured rate (200 req/s for `seconds`): throughput and utilisation
+      (offered / completed rate; above 1 the queue grows and latency is queueing);
+    - a sweep of lower rates (each `sweep_seconds` of arrivals) for the largest rate the
+      GPU sustains (completed rate within 5 % of the offered one and the last request
+      done within 0.5 s of the last arrival);
+    - p50 / p99 latency at 0.8 of that rate, and the same request list replayed one request
+      after another with FP64 factors (resident pencils, the plain per-instance path)."""
     classes = []
     for name, count in (("tiny_6o6e", 6), ("f2_10o14e", 3), ("licl_14o14e_mc", 2)):
         base = synth.WORKLOADS[name]
@@ -704,6 +710,7 @@ def serving_c4(abi, ctx, seconds=1.0, rate=200.0, n_streams=16, seed=111):
             h, eri, th, rows, cnt = w.inputs()
             members.append((w, h, eri, th, rows, None if cnt is None else cnt.astype(np.float64)))
         classes.append(members)
+    names = ["c0 tiny_6o6e", "c1 f2_10o14e", "c2 licl_14o14e_mc"]
     srv = abi.Server(ctx, hbm_budget_bytes=150 << 30, n_streams=n_streams, autotune=True)
     sids = []
     for members in classes:
@@ -712,7 +719,7 @@ def serving_c4(abi, ctx, seconds=1.0, rate=200.0, n_streams=16, seed=111):
             ids.append(srv.add_system(ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri),
                                       rows=rows, weights=wts, precision=abi.LM_FP32))
         sids.append(ids)
-    # warm every system once (pencil creation, grid tuning) before the stream starts
+    # warm every system once (pencil creation, grid tuning) before any stream starts
     for c, members in enumerate(classes):
         for k, (w, *_rest) in enumerate(members):
             srv.submit(sids[c][k], members[k][3], abi.irl_settings(m=w.m, k=w.k, tol=w.tol,
@@ -720,78 +727,110 @@ def serving_c4(abi, ctx, seconds=1.0, rate=200.0, n_streams=16, seed=111):
     warm = 0
     while warm < sum(len(m) for m in classes):
         warm += len(srv.poll())
-    times, cls = synth.poisson_arrivals(rate, seconds, seed)
-    rr = [0, 0, 0]
-    reqs = []
-    for c in cls:
-        k = rr[c] % len(classes[c])
-        rr[c] += 1
-        reqs.append((c, k))
-    outs = {}
-    done = []
-    t0 = time.perf_counter()
-    i = 0
-    while len(done) < len(reqs):
-        now = time.perf_counter() - t0
-        while i < len(reqs) and times[i] <= now:
-            c, k = reqs[i]
-            w = classes[c][k][0]
-            out = np.zeros(w.n_params)
-            t = srv.submit(sids[c][k], classes[c][k][3],
-                           abi.irl_settings(m=w.m, k=w.k, tol=w.tol, prec=abi.LM_FP32), out)
-            outs[t] = (c, out)
-            i += 1
-        got = srv.poll()
-        done += got
-        if not got:
-            time.sleep(0.0002)
-    wall = time.perf_counter() - t0
-    srv.free()
-    lat = np.array([r.t_done_ms - r.t_submit_ms for r in done])
-    by_cls, svc_cls = {}, {}
-    for r in done:
-        by_cls.setdefault(outs[r.ticket][0], []).append(r.t_done_ms - r.t_submit_ms)
-        svc_cls.setdefault(outs[r.ticket][0], []).append(r.t_done_ms - r.t_admit_ms)
-    bad = sum(1 for r in done if r.status != abi.LM_OK)
-    # plain FP64 sequential baseline for the same request list: each class's solo
-    # service time (build + IRL with FP64 O/G on a resident pencil, mean of a few
-    # requests) summed over the requests of the stream
-    per_cls = {}
-    for c in sorted(set(cls.tolist())):
-        w, h, eri, th, rows, wts = classes[c][0]
-        sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri)
-        pen = ctx.build_OG(sysd, th, rows=rows, weights=wts, n_rows=w.n_rows, prec=abi.LM_FP64)
-        pen.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200, prec=abi.LM_FP64)
-        reps = 2 if c == 2 else 5
+
+    def run_stream(rate_hz, secs, sd):
+        times, cls = synth.poisson_arrivals(rate_hz, secs, sd)
+        rr = [0, 0, 0]
+        reqs = []
+        for c in cls:
+            k = rr[c] % len(classes[c])
+            rr[c] += 1
+            reqs.append((c, k))
+        outs, done = {}, []
+        t0 = time.perf_counter()
+        i = 0
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and times[i] <= now:
+                c, k = reqs[i]
+                w = classes[c][k][0]
+                out = np.zeros(w.n_params)
+                t = srv.submit(sids[c][k], classes[c][k][3],
+                               abi.irl_settings(m=w.m, k=w.k, tol=w.tol, prec=abi.LM_FP32), out)
+                outs[t] = (c, out)
+                i += 1
+            got = srv.poll()
+            done += got
+            if not got:
+                time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        lat = np.array([r.t_done_ms - r.t_submit_ms for r in done])
+        by_cls, svc_cls = {}, {}
+        for r in done:
+            by_cls.setdefault(outs[r.ticket][0], []).append(r.t_done_ms - r.t_submit_ms)
+            svc_cls.setdefault(outs[r.ticket][0], []).append(r.t_done_ms - r.t_admit_ms)
+        last_arrival = float(times[-1]) if len(times) else 0.0
+        return {"offered_rate": len(reqs) / secs, "requests": len(reqs), "completed": len(done),
+                "errors": sum(1 for r in done if r.status != abi.LM_OK),
+                "throughput": len(done) / wall, "wall_s": wall,
+                "drain_s": wall - last_arrival,
+                "utilisation": (len(reqs) / secs) / (len(done) / wall),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "by_class_p50_ms": {names[c]: float(np.percentile(v, 50))
+                                    for c, v in sorted(by_cls.items())},
+                "service_by_class_p50_ms": {names[c]: float(np.percentile(v, 50))
+                                            for c, v in sorted(svc_cls.items())}}, reqs
+
+    # the configured (overloaded) stream
+    full, _ = run_stream(rate, seconds, seed)
+    # the sustainable rate
+    sweep_out, best = [], None
+    for r in sweep:
+        res, _ = run_stream(r, sweep_seconds, seed + 1)
+        ok = res["throughput"] >= 0.95 * res["offered_rate"] and res["drain_s"] <= 0.5
+        sweep_out.append({"rate": r, "throughput": res["throughput"], "drain_s": res["drain_s"],
+                          "p99_ms": res["p99_ms"], "sustained": ok})
+        if ok:
+            best = r
+        else:
+            break
+    at80 = None
+    seq = None
+    if best is not None:
+        at80, reqs80 = run_stream(0.8 * best, sweep_seconds, seed + 2)
+        # replay the same request list, one request after another, FP64 factors
+        pens = {}
+        for c, k in set(reqs80):
+            w, h, eri, th, rows, wts = classes[c][k]
+            sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri)
+            pen = ctx.build_OG(sysd, th, rows=rows, weights=wts, n_rows=w.n_rows,
+                               prec=abi.LM_FP64)
+            pen.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200, prec=abi.LM_FP64)
+            pens[(c, k)] = (sysd, pen)
+        import torch
+        torch.cuda.synchronize()
         t1 = time.perf_counter()
-        for _ in range(reps):
+        for c, k in reqs80:
+            w, h, eri, th, rows, wts = classes[c][k]
+            sysd, pen = pens[(c, k)]
             ctx.build_OG(sysd, th, rows=rows, weights=wts, n_rows=w.n_rows, prec=abi.LM_FP64,
                          pencil=pen)
             pen.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=200, prec=abi.LM_FP64)
-        per_cls[c] = (time.perf_counter() - t1) / reps
-        pen.free()
-    seq_time = sum(per_cls[c] for c in cls.tolist())
-    seq = len(reqs) / seq_time
-    names = ["c0 tiny_6o6e", "c1 f2_10o14e", "c2 licl_14o14e_mc"]
-    return {"workload": f"serving: Poisson {rate:g} req/s for {seconds:g} s "
-                        f"({len(reqs)} requests), mix 60/30/10 % of c0/c1/c2 sizes over 6/3/2 "
-                        f"systems, FP32 O/G with FP64 refinement, {n_streams} streams, "
-                        "150 GB budget",
-            "completed": len(done), "errors": bad,
-            "throughput": len(done) / wall, "unit": "LM steps/s",
-            "offered_rate": len(reqs) / seconds,
-            "utilisation": (len(reqs) / seconds) / (len(done) / wall),
-            "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                           "p99": float(np.percentile(lat, 99)),
-                           "by_class_p50": {names[c]: float(np.percentile(v, 50))
-                                            for c, v in sorted(by_cls.items())},
-                           "service_by_class_p50": {names[c]: float(np.percentile(v, 50))
-                                                    for c, v in sorted(svc_cls.items())}},
-            "fp64_sequential": {"value": seq, "unit": "LM steps/s",
-                                "service_ms": {names[c]: t * 1e3 for c, t in per_cls.items()},
-                                "sample": "the same request list solved one after another "
-                                          "with FP64 O/G (per-class solo service times)"},
-            "speedup_vs_fp64_sequential": (len(done) / wall) / seq}
+        el = time.perf_counter() - t1
+        for _, pen in pens.values():
+            pen.free()
+        seq = {"value": len(reqs80) / el, "unit": "LM steps/s", "requests": len(reqs80),
+               "seconds": el,
+               "path": "the 0.8-rate request list replayed one after another, FP64 O/G, "
+                       "resident pencils, one stream"}
+    srv.free()
+    out = {"workload": f"serving: Poisson arrivals, mix 60/30/10 % of c0/c1/c2 sizes over "
+                       f"6/3/2 systems, FP32 O/G with FP64 refinement, {n_streams} streams, "
+                       "150 GB budget",
+           "at_configured_rate": {**full, "rate": rate, "seconds": seconds},
+           "throughput": full["throughput"], "unit": "LM steps/s",
+           "utilisation": full["utilisation"],
+           "rate_sweep": sweep_out, "max_sustained_rate": best}
+    if at80 is not None:
+        out["at_0p8_of_sustained"] = {**at80, "rate": 0.8 * best}
+        out["latency_ms"] = {"p50": at80["p50_ms"], "p99": at80["p99_ms"],
+                             "at_rate": 0.8 * best}
+        out["fp64_sequential"] = seq
+        out["speedup_vs_fp64_sequential"] = best / seq["value"]
+        out["note"] = ("speedup = the largest rate the server sustains over the rate at which "
+                       "the plain FP64 path serves the same request list one after another; "
+                       "latency is measured at 0.8 of the sustained rate")
+    return out
 
 
 # ------------------------------------------------------------------ oracle (CPU)

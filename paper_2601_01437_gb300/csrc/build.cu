@@ -694,7 +694,12 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     const int nsl = A.nslice;
     const int sc_r = tid % (nh + 1), sc_s = tid / (nh + 1);
     const bool scatter_thread = sc_s < nsl;
-    const int kk = tid / BDF_TPC, sub = tid % BDF_TPC;
+    // connection kk of the batch is handled by the BDF_TPC lanes kk % CPW,
+    // kk % CPW + CPW, ... of warp kk / CPW (CPW = 32 / BDF_TPC connections per
+    // warp): a half-warp's double-float row stores then fall on rows of
+    // different connections at stride ldF, which keeps their banks apart
+    constexpr int CPW = 32 / BDF_TPC;
+    const int kk = (tid >> 5) * CPW + (lane % CPW), sub = lane / CPW;
 
     for (int64_t row = blockIdx.x; row < A.n_rows; row += gridDim.x) {
         const uint64_t x = A.rows[row];
@@ -868,7 +873,7 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             // combine the partial products of the BDF_TPC lanes of a connection
             // (all lanes take part; inactive ones carry 1 * 2^0)
 #pragma unroll
-            for (int off = 1; off < BDF_TPC; off <<= 1) {
+            for (int off = CPW; off < 32; off <<= 1) {
                 const df o = df_make(__shfl_xor_sync(0xffffffffu, rp.h, off),
                                      __shfl_xor_sync(0xffffffffu, rp.l, off));
                 const int oe = __shfl_xor_sync(0xffffffffu, re, off);
@@ -892,8 +897,8 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             }
             // the row of the connection becomes c u_j, here where every thread
             // works, rather than in the scatter below
-            c.h = __shfl_sync(0xffffffffu, c.h, lane & ~(BDF_TPC - 1));
-            c.l = __shfl_sync(0xffffffffu, c.l, lane & ~(BDF_TPC - 1));
+            c.h = __shfl_sync(0xffffffffu, c.h, lane % CPW);
+            c.l = __shfl_sync(0xffffffffu, c.l, lane % CPW);
             if (active) {
                 float2 *Frow = sF + kk * A.ldF;
                 for (int j = sub; j < nh; j += BDF_TPC) st_df(Frow + j, df_mul_lazy(c, ld_df(Frow + j)));
