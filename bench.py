@@ -649,10 +649,19 @@ def batched_c3(abi, ctx, steps=3, warmup=1, n_streams=16):
         res, grids = b.run(items(abi.LM_FP32, thetas, dths))
     thetas = [d[3].copy() for d in data]
     torch.cuda.synchronize()
+    ctx.stats_reset(profile=True)
     t0 = time.perf_counter()
     for _ in range(steps):
         res, grids = b.run(items(abi.LM_FP32, thetas, dths))
     el = time.perf_counter() - t0
+    st = ctx.stats()
+    breakdown = {"launches_per_instance_step": st.launches / (64 * steps),
+                 "build_ms_per_batch": st.build_ms / steps,
+                 "pencil_ms_per_batch": st.pencil_ms / steps,
+                 "lanczos_ms_per_batch": st.lanczos_ms / steps,
+                 "prep_ms_per_batch": st.prep_ms / steps, "tri_ms_per_batch": st.tri_ms / steps,
+                 "note": "summed device time of each kernel class over the batch's 16 streams "
+                         "(concurrent kernels overlap, so the sum can exceed the wall time)"}
     b.free()
     # mixed vs FP64 on the same (first-step) parameters
     th0 = [d[3].copy() for d in data]
@@ -687,7 +696,8 @@ def batched_c3(abi, ctx, steps=3, warmup=1, n_streams=16):
                                 "path": "each instance alone, FP64 O/G, one stream"},
             "speedup_vs_fp64_sequential": (64 * steps / el) / (64 / el64),
             "max_abs_lambda_err_vs_fp64_ha": err,
-            "grids": sorted(set(int(g) for g in grids))}
+            "grids": sorted(set(int(g) for g in grids)),
+            "breakdown": breakdown}
 
 
 def serving_c4(abi, ctx, seconds=1.0, rate=200.0, n_streams=16, seed=111, sweep_seconds=6.0):
