@@ -23,9 +23,14 @@
 //
 // Roles (192 threads): warp 0 issues the TMA loads, warp 1 allocates TMEM and
 // one of its threads issues every MMA, warps 2-5 are the epilogue (one TMEM
-// lane quarter each). A ring stage holds 128 columns of the tile's O and G
-// (64-column, 128-byte-swizzled boxes, O and G of a chunk back to back) and the
-// matching 128 columns of V.
+// lane quarter each). A six-stage ring carries 128-column chunks of the tile's
+// O and G (64-column, 128-byte-swizzled boxes, O and G of a chunk back to
+// back) with the matching columns of V for phase 1. Round r of the software
+// pipeline interleaves, chunk by chunk, phase 2 of tile r - 1 with phase 1 of
+// tile r, so the HBM loads of tile r go on while the epilogue turns tile
+// r - 1's X into X'. The first read of a tile (phase 1) is loaded with an L2
+// evict-last policy and its re-read (phase 2) with evict-first, so the two
+// tiles live per SM between the reads stay in L2.
 // Every wait is bounded: a timeout sets FLAG_TIMEOUT, every role stops, TMA
 // loads still in flight are waited for (bounded), TMEM is freed, and the
 // products come back as NaN.
@@ -50,7 +55,8 @@ constexpr int BLK_THREADS = 192;
 constexpr uint32_t BOX_BYTES = BM * 64 * 2;         // 8 KB: 64 rows x 64 BF16
 constexpr uint32_t PAIR_BYTES = 2 * BOX_BYTES;      // O box then G box of one 64-column chunk
 constexpr uint32_t VBOX_BYTES = NV * 64 * 2;        // 2 KB: 16 vectors x 64 BF16
-constexpr uint32_t STAGE_BYTES = 2 * PAIR_BYTES + 2 * VBOX_BYTES;  // 36 KB
+constexpr uint32_t STAGE_BYTES = 2 * PAIR_BYTES + 2 * VBOX_BYTES;  // 36 KB: O, G (and V)
+constexpr uint32_t RING_BYTES = NSTAGE * STAGE_BYTES;
 constexpr uint32_t X_BYTES = NV * BM * 2;           // 2 KB: one X' operand
 constexpr int MAX_NCH = 15;                         // TMEM: 16 + 2 * 16 * nch <= 512 columns
 constexpr uint32_t TMEM_COLS = 512;
@@ -77,6 +83,24 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap *map, int x,
+                                                 int y, uint32_t bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
@@ -167,14 +191,14 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *sbase = smem_raw + (base - raw);
-    const uint32_t sXO = base + NSTAGE * STAGE_BYTES;
+    const uint32_t sXO = base + RING_BYTES;
     const uint32_t sXG = sXO + X_BYTES;
-    unsigned char *pX = sbase + NSTAGE * STAGE_BYTES;  // X'_O, then X'_G
+    unsigned char *pX = sbase + RING_BYTES;  // X'_O, then X'_G
     uint64_t *bars = reinterpret_cast<uint64_t *>(pX + 2 * X_BYTES);
     uint64_t *full = bars, *empty = bars + NSTAGE;
     uint64_t *xready = bars + 2 * NSTAGE, *xfull = xready + 1, *done = xready + 2;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * NSTAGE + 3);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NSTAGE + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(done + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -200,40 +224,52 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t tD = tmem + 16;  // D_H[m] at tD + 16 m, D_S[m] at tD + 16 (nch + m)
+    // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int ntl = (int)blockIdx.x < a.ntiles
+                        ? (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                        : 0;
 
+    // Software pipeline over rounds r = 0 .. ntl: round r interleaves, chunk by
+    // chunk, phase 2 of tile r - 1 (its re-read, from L2) with phase 1 of tile r
+    // (from HBM), so the HBM stream goes on while the epilogue turns tile r - 1's
+    // X into X', and a tile is re-read one tile's loads after it was read.
     if (warp == 0) {
-        // ---------------- TMA producer: per tile, the row's chunks for phase 1
-        // (O, G, V), then again for phase 2 (O; G too for HALF)
+        // ---------------- TMA producer (ring order = MMA consumption order)
         if (lane == 0) {
             int s = 0;
             uint32_t ph = 0;
             uint32_t pend_ph[NSTAGE];
             bool pend[NSTAGE];
+            const uint64_t pol_last = policy_evict_last(), pol_first = policy_evict_first();
             for (int i = 0; i < NSTAGE; ++i) pend[i] = false;
-            for (int t = blockIdx.x; t < a.ntiles && !*abort_flag; t += gridDim.x) {
-                const int row0 = t * BM;
-                for (int pass = 0; pass < 2 && !*abort_flag; ++pass) {
-                    for (int c = 0; c < a.nch; ++c) {
+            for (int r = 0; r <= ntl && !*abort_flag; ++r) {
+                for (int c = 0; c < a.nch && !*abort_flag; ++c) {
+                    for (int ph2 = 1; ph2 >= 0; --ph2) {  // phase 2 of tile r-1, then phase 1 of tile r
+                        const bool pass2 = ph2 == 1;
+                        if (pass2 ? r < 1 : r >= ntl) continue;
+                        const int t = blockIdx.x + (pass2 ? r - 1 : r) * gridDim.x;
                         if (!mbar_wait_u32(smem_u32(empty + s), ph ^ 1u)) {
                             *abort_flag = 1;
                             atomicOr(a.flags, FLAG_TIMEOUT);
                             break;
                         }
                         const uint32_t st = base + s * STAGE_BYTES;
-                        const bool wantG = pass == 0 || HALF;
-                        const bool wantV = pass == 0;
-                        const uint32_t bytes = 2 * BOX_BYTES * (wantG ? 2u : 1u) +
-                                               (wantV ? 2u * VBOX_BYTES : 0u);
+                        const bool wantG = !pass2 || HALF;
+                        const uint32_t bytes =
+                            2 * BOX_BYTES * (wantG ? 2u : 1u) + (pass2 ? 0u : 2u * VBOX_BYTES);
                         const uint32_t fb = smem_u32(full + s);
                         mbar_expect_tx(fb, bytes);
-                        const int x = c * CW;
-                        tma_load_2d(st, &tO, x, row0, fb);
-                        tma_load_2d(st + PAIR_BYTES, &tO, x + 64, row0, fb);
+                        const int x = c * CW, row0 = t * BM;
+                        // first read (phase 1): keep in L2; re-read (phase 2): last use
+                        const uint64_t pol = pass2 ? pol_first : pol_last;
+                        tma_load_2d_hint(st, &tO, x, row0, fb, pol);
+                        tma_load_2d_hint(st + PAIR_BYTES, &tO, x + 64, row0, fb, pol);
                         if (wantG) {
-                            tma_load_2d(st + BOX_BYTES, &tG, x, row0, fb);
-                            tma_load_2d(st + PAIR_BYTES + BOX_BYTES, &tG, x + 64, row0, fb);
+                            tma_load_2d_hint(st + BOX_BYTES, &tG, x, row0, fb, pol);
+                            tma_load_2d_hint(st + PAIR_BYTES + BOX_BYTES, &tG, x + 64, row0, fb,
+                                             pol);
                         }
-                        if (wantV) {
+                        if (!pass2) {
                             tma_load_2d(st + 2 * PAIR_BYTES, &tV, x, 0, fb);
                             tma_load_2d(st + 2 * PAIR_BYTES + VBOX_BYTES, &tV, x + 64, 0, fb);
                         }
@@ -255,77 +291,79 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
         // ---------------- MMA issuer (one thread)
         if (lane == 0) {
             int s = 0;
-            uint32_t ph = 0, it = 0;
-            bool first = true;
+            uint32_t ph = 0;
             constexpr uint32_t id_k = mma_idesc(false), id_mn = mma_idesc(true);
-            for (int t = blockIdx.x; t < a.ntiles && !*abort_flag; t += gridDim.x, ++it) {
-                // phase 1: [X_O; X_G] = [O_tile; G_tile] V over the row's column chunks
-                for (int c = 0; c < a.nch; ++c) {
-                    if (!mbar_wait_u32(smem_u32(full + s), ph)) {
+            auto next = [&]() {
+                if (++s == NSTAGE) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            };
+            auto wait_stage = [&]() {
+                if (mbar_wait_u32(smem_u32(full + s), ph)) {
+                    tc_fence_after();
+                    return true;
+                }
+                *abort_flag = 1;
+                atomicOr(a.flags, FLAG_TIMEOUT);
+                return false;
+            };
+            for (int r = 0; r <= ntl && !*abort_flag; ++r) {
+                if (r >= 1) {
+                    // the epilogue has read X of tile r - 1 out of TMEM and written X'
+                    if (!mbar_wait_u32(smem_u32(xfull), (uint32_t)(r - 1) & 1u)) {
                         *abort_flag = 1;
                         atomicOr(a.flags, FLAG_TIMEOUT);
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = base + s * STAGE_BYTES;
+                }
+                for (int c = 0; c < a.nch && !*abort_flag; ++c) {
+                    if (r >= 1) {
+                        // phase 2 of tile r - 1: D_S[c] += O_c^T X'_O,
+                        // D_H[c] += O_c^T X'_G (+ G_c^T X'_O)
+                        if (!wait_stage()) break;
+                        const uint32_t st = base + s * STAGE_BYTES;
+                        const uint32_t dH = tD + 16 * c;
+                        const uint32_t dS = tD + 16 * a.nch + 16 * c;
 #pragma unroll
-                    for (int kk = 0; kk < 8; ++kk) {
-                        const uint32_t koff = (kk >> 2) * PAIR_BYTES + (kk & 3) * 32;
-                        const uint32_t voff = (kk >> 2) * VBOX_BYTES + (kk & 3) * 32;
-                        tc_mma(tmem, sw128_desc(st + koff, 16, 1024),
-                               sw128_desc(st + 2 * PAIR_BYTES + voff, 16, 1024), id_k,
-                               (c | kk) ? 1u : 0u);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t aO = sw128_desc(st + kk * 2048, a.lbo_mn, a.sbo_mn);
+                            const uint64_t bXO = sw128_desc(sXO + kk * 32, 16, 1024);
+                            const uint64_t bXG = sw128_desc(sXG + kk * 32, 16, 1024);
+                            const uint32_t acc = (r == 1 && kk == 0) ? 0u : 1u;
+                            tc_mma(dS, aO, bXO, id_mn, acc);
+                            tc_mma(dH, aO, bXG, id_mn, acc);
+                            if (HALF)
+                                tc_mma(dH,
+                                       sw128_desc(st + BOX_BYTES + kk * 2048, a.lbo_mn, a.sbo_mn),
+                                       bXO, id_mn, 1u);
+                        }
+                        tc_commit(smem_u32(empty + s));
+                        next();
                     }
-                    tc_commit(smem_u32(empty + s));
-                    if (++s == NSTAGE) {
-                        s = 0;
-                        ph ^= 1u;
-                    }
-                }
-                if (*abort_flag) break;
-                tc_commit(smem_u32(xready));
-                // the epilogue has read X out of TMEM and written X' = W X
-                if (!mbar_wait_u32(smem_u32(xfull), it & 1u)) {
-                    *abort_flag = 1;
-                    atomicOr(a.flags, FLAG_TIMEOUT);
-                    break;
-                }
-                tc_fence_after();
-                // phase 2: D_S[m] += O_m^T X'_O, D_H[m] += O_m^T X'_G (+ G_m^T X'_O)
-                for (int m = 0; m < a.nch; ++m) {
-                    if (!mbar_wait_u32(smem_u32(full + s), ph)) {
-                        *abort_flag = 1;
-                        atomicOr(a.flags, FLAG_TIMEOUT);
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t st = base + s * STAGE_BYTES;
-                    const uint32_t dH = tD + 16 * m;
-                    const uint32_t dS = tD + 16 * a.nch + 16 * m;
+                    if (r < ntl) {
+                        // phase 1 of tile r: [X_O; X_G] += [O_c; G_c] V_c
+                        if (!wait_stage()) break;
+                        const uint32_t st = base + s * STAGE_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t aO = sw128_desc(st + kk * 2048, a.lbo_mn, a.sbo_mn);
-                        const uint64_t bXO = sw128_desc(sXO + kk * 32, 16, 1024);
-                        const uint64_t bXG = sw128_desc(sXG + kk * 32, 16, 1024);
-                        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                        tc_mma(dS, aO, bXO, id_mn, acc);
-                        tc_mma(dH, aO, bXG, id_mn, acc);
-                        if (HALF)
-                            tc_mma(dH, sw128_desc(st + BOX_BYTES + kk * 2048, a.lbo_mn, a.sbo_mn),
-                                   bXO, id_mn, 1u);
-                    }
-                    tc_commit(smem_u32(empty + s));
-                    if (++s == NSTAGE) {
-                        s = 0;
-                        ph ^= 1u;
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const uint32_t koff = (kk >> 2) * PAIR_BYTES + (kk & 3) * 32;
+                            const uint32_t voff = (kk >> 2) * VBOX_BYTES + (kk & 3) * 32;
+                            tc_mma(tmem, sw128_desc(st + koff, 16, 1024),
+                                   sw128_desc(st + 2 * PAIR_BYTES + voff, 16, 1024), id_k,
+                                   (c | kk) ? 1u : 0u);
+                        }
+                        tc_commit(smem_u32(empty + s));
+                        next();
                     }
                 }
-                first = false;
+                if (r < ntl && !*abort_flag) tc_commit(smem_u32(xready));
             }
             // completes once every MMA issued above has
             tc_commit(smem_u32(done));
         }
-    } else {
+    } else if (warp <= 5) {
         // ---------------- epilogue: warps 2..5, one TMEM lane quarter each;
         // quarters 0-1 hold X_O (rows 0-63), quarters 2-3 hold X_G
         const int q = warp & 3;
@@ -335,7 +373,7 @@ __global__ void __launch_bounds__(BLK_THREADS, 1)
         unsigned char *pXw = pX + which * X_BYTES;
         uint32_t it = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+        for (int t = blockIdx.x; it < (uint32_t)ntl; t += gridDim.x, ++it) {
             int w_ok = 1;
             if (lane == 0) w_ok = !*abort_flag && mbar_wait_u32(smem_u32(xready), it & 1u);
             w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
@@ -484,7 +522,7 @@ bool encode_2d(CUtensorMap *m, const void *ptr, int64_t rows, int cols, int ld, 
 }
 
 size_t block_smem_bytes() {
-    return 1024 + (size_t)NSTAGE * STAGE_BYTES + 2 * X_BYTES + (2 * NSTAGE + 6) * 8;
+    return 1024 + (size_t)RING_BYTES + 2 * X_BYTES + (2 * NSTAGE + 6) * 8;
 }
 
 int block_setup(lm_pencil *p) {
