@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-pencil-c2", action="store_true",
                     help="skip the pencil-matvec HBM measurement on the LiCl-shaped MC pencil")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance batch")
+    ap.add_argument("--no-eloc-estimator", action="store_true",
+                    help="skip the E_loc estimator (G-free build) timings")
     ap.add_argument("--no-fp64-c1", action="store_true",
                     help="skip the native-FP64 F2-shaped LM steps")
     ap.add_argument("--no-mixed-c2", action="store_true",
@@ -159,10 +161,10 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ workload
 # DRAM bytes (read + write) per launch from the ncu captures summarised in
-# profiles/ (k_build_rows_df_f2_10o14e.md, k_pencil_df64_f2_10o14e.md). They
+# profiles/ (k_build_rows_dg_f2_10o14e.md, k_pencil_df64_f2_10o14e.md). They
 # describe the kernels as committed with them; drop an entry when its kernel
 # changes until it is captured again.
-NCU_TRAFFIC = {("k_build_rows_df", "f2_10o14e"): 138.88e6,
+NCU_TRAFFIC = {
                # Lanczos products alternate their row order: with the L2 left warm
                # (ncu --cache-control none) a product reads 113 MB of its 198.5 MB
                ("k_pencil", "f2_10o14e"): 117.0e6,
@@ -219,7 +221,7 @@ def build_roofline(st, w, arith):
     d = st.build_ms / st.build_count / 1e3
     ach = build_flops / d / 1e12
     pk = FP32_PEAK_TFLOPS if arith == "df64" else FP64_PEAK_TFLOPS
-    kname = "k_build_rows_df" if arith == "df64" else "k_build_rows"
+    kname = "k_build_rows_dg" if arith == "df64" else "k_build_rows"
     impl = implementation_flops(w, arith)
     return {"kernel": kname, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
             "frac": ach / pk,
@@ -325,6 +327,65 @@ def mixed_c2(abi, ctx, s, dev, steps=2, warmup=1):
         out[name]["abs_err_vs_fp64_ha"] = abs(lam[name] - lam["fp64"])
         out[name]["speedup_vs_fp64"] = out[name]["value"] / out["fp64"]["value"]
     out["steps"], out["warmup"] = steps, warmup
+    return out
+
+
+def eloc_estimator(abi, ctx, s, dev, w, reps=3):
+    """The paper's E_loc estimator path: the G-free build (lm_build_O: O_c, ln psi and
+    E_loc only) against the full build of the same rows (lm_build_OG), at the F2-shaped
+    sector (double-float factors) and on the LiCl-shaped 262,144 MC rows (FP32 factors);
+    and the F2-shaped LM step on the estimator operator (lm_build_O + irl_step with
+    LM_SYM_ELOC), live CUDA-event timings of the build kernel."""
+    import torch
+    out = {}
+    licl = synth.WORKLOADS["licl_14o14e_mc"]
+    for key, wl, pr in (("f2", w, abi.LM_DF64), ("licl_c2", licl, abi.LM_FP32)):
+        h, eri, th, rows, counts = wl.inputs()
+        sysd = ctx.system(wl.n_orb, wl.n_alpha, wl.n_beta, wl.n_hidden,
+                          torch.from_numpy(h).to(dev), torch.from_numpy(eri).to(dev))
+        kw = {}
+        if rows is not None:
+            kw = dict(rows=torch.from_numpy(rows.view(np.int64)).to(dev),
+                      weights=torch.from_numpy(counts.astype(np.float64)).to(dev),
+                      n_rows=wl.n_rows)
+        th_d = torch.from_numpy(th).to(dev)
+        res = {"workload": f"{wl.name}: {wl.n_rows} rows, P+1 = {wl.n_params + 1}"}
+        for name, fn in (("gfree", ctx.build_O), ("full", ctx.build_OG)):
+            fn(sysd, th_d, prec=pr, stream=s, **kw).free()
+            torch.cuda.synchronize()
+            ctx.stats_reset(profile=True)
+            for _ in range(reps):
+                fn(sysd, th_d, prec=pr, stream=s, **kw).free()
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            res[f"{name}_build_ms"] = st.build_ms / max(st.build_count, 1)
+        res["speedup"] = res["full_build_ms"] / res["gfree_build_ms"]
+        out[key] = res
+    # steps on the estimator operator at fixed theta, F2-shaped sector: build + IRL +
+    # refinement + Delta theta per step (theta is left unchanged between steps)
+    h, eri, th0, _, _ = w.inputs()
+    sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, torch.from_numpy(h).to(dev),
+                      torch.from_numpy(eri).to(dev))
+    th_d = torch.from_numpy(th0).to(dev)
+    pen = None
+    dth = torch.zeros(w.n_params, dtype=torch.float64, device=dev)
+    steps, warmup = 5, 2
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(warmup + steps):
+        if i == warmup:
+            torch.cuda.synchronize()
+            ev0.record(s)
+        pen = ctx.build_O(sysd, th_d, prec=abi.LM_DF64, stream=s, pencil=pen)
+        r = pen.irl_step(m=w.m, k=w.k, tol=w.tol, max_restarts=500, prec=abi.LM_DF64,
+                         dtheta_out=dth, stream=s)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    out["f2_steps_fixed_theta"] = {"value": steps / (ms / 1e3), "unit": UNIT,
+                          "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+                          "lambda": r.lambda_, "n_matvec": r.n_matvec,
+                          "operator": "O_c^T W diag(E_loc - E) O_c (Methods, eq. matrix_vec_prod)"}
+    pen.free()
     return out
 
 
@@ -512,6 +573,8 @@ def run_gpu(args, rank, world, local):
         out["native_fp64_c1"] = native_fp64_c1(abi, ctx, s, dev, w)
     if not args.no_mixed_c2 and rank == 0 and world == 1 and w.name != "licl_14o14e_mc":
         out["mixed_c2"] = mixed_c2(abi, ctx, s, dev)
+    if not args.no_eloc_estimator and rank == 0 and world == 1 and w.name == "f2_10o14e":
+        out["eloc_estimator"] = eloc_estimator(abi, ctx, s, dev, w)
     if not args.no_pencil_c2 and rank == 0 and world == 1:
         out["pencil_c2"] = pencil_c2(abi, ctx, s, dev, hbm, hbm_src)
     if not args.no_batched and rank == 0 and world == 1:

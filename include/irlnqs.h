@@ -198,6 +198,24 @@ int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *theta, const ui
                 lm_pencil **inout);
 
 /*
+ * The E_loc estimator's pencil (Methods, eq. matrix_vec_prod, whose H~' uses
+ * E_loc(x) in place of the G form of eq. heff): the same build as lm_build_OG
+ * with G never formed. Per connection it keeps only the running product of
+ * (1 + Z_j) that the coefficient needs (no tanh of the connected
+ * configuration, no accumulation into G), and no G'_c or copy of it is
+ * allocated. O_c, ln psi, E_loc, the weights and E equal lm_build_OG's.
+ * The pencil answers sym = LM_SYM_ELOC (its default, also for LM_SYM_AUTO)
+ * and S~ products; lm_apply_pencil and irl_step with LM_SYM_NONE/HALF, a
+ * block phase, lm_apply_pencil_block and the export of G'_c return
+ * LM_ERR_ARG. Runs in double-float arithmetic (sys->build_arith =
+ * LM_ARITH_FP64 returns LM_ERR_ARG). Arguments, layout, ownership and the
+ * other errors as lm_build_OG; *inout may only be a pencil from lm_build_O.
+ */
+int lm_build_O(lm_ctx *ctx, const lm_system *sys, const double *theta, const uint64_t *rows,
+               const double *weights, int64_t n_rows, lm_precision prec, void *stream,
+               lm_pencil **inout);
+
+/*
  * Matrix-free pencil product (Methods, eq. matrix_vec_prod, with the G form of
  * eq. heff): Hv = H~' v (symmetrised per `sym`), Sv = S~ v, both P+1 FP64.
  * v: P+1 FP64. Either output may be NULL. `prec` selects the FP64 factors or

@@ -86,6 +86,8 @@ _SIGNATURES = {
     "lm_last_error": (ctypes.c_char_p, [c_vp]),
     "lm_build_OG": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_vp, c_vp, c_int64, c_int,
                             c_vp, ctypes.POINTER(c_vp)]),
+    "lm_build_O": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_vp, c_vp, c_int64, c_int,
+                            c_vp, ctypes.POINTER(c_vp)]),
     "lm_apply_pencil": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_vp]),
     "irl_step": (c_int, [c_vp, ctypes.POINTER(irl_params), ctypes.POINTER(irl_result), c_vp,
                          c_vp, c_vp, c_vp]),
@@ -225,6 +227,20 @@ class Context:
                                ptr(weights), int(n_rows), int(prec), stream_handle(stream),
                                ctypes.byref(h))
         self.check(rc, "lm_build_OG")
+        if pencil is not None:
+            return pencil
+        return Pencil(self, h)
+
+    def build_O(self, sys, theta, rows=None, weights=None, n_rows=0, prec=LM_FP64, stream=None,
+                pencil=None):
+        """lm_build_O: the E_loc estimator's pencil (O_c, E_loc, weights; no G'_c)."""
+        h = c_vp(pencil.handle if pencil is not None else None)
+        if rows is not None and n_rows == 0:
+            n_rows = int(rows.shape[0])
+        rc = lib().lm_build_O(self.handle, ctypes.byref(sys), ptr(theta), ptr(rows),
+                              ptr(weights), int(n_rows), int(prec), stream_handle(stream),
+                              ctypes.byref(h))
+        self.check(rc, "lm_build_O")
         if pencil is not None:
             return pencil
         return Pencil(self, h)

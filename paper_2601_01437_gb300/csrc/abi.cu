@@ -185,7 +185,7 @@ extern "C" const char *lm_last_error(const lm_ctx *ctx) { return ctx ? ctx->err 
 int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
                      const uint64_t *rows, const double *weights, int64_t n_rows,
                      lm_precision prec, void *stream, lm_pencil **inout, int rows_only,
-                     int64_t chunk_rows) {
+                     int64_t chunk_rows, int gfree) {
     if (!ctx || !inout || !theta) return lm_fail(ctx, LM_ERR_ARG, "null argument");
     ctx->err[0] = 0;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return LM_ERR_CUDA;
@@ -210,7 +210,7 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
     lm_pencil *p = *inout;
     if (p) {
         if (p->ctx != ctx || p->n != n || p->na != sys->n_alpha || p->nb != sys->n_beta ||
-            p->nh != nh || p->n_rows != n_rows || p->prec != (int)prec ||
+            p->nh != nh || p->n_rows != n_rows || p->prec != (int)prec || p->gfree != gfree ||
             p->chunk != (chunk_rows > 0 ? std::min(chunk_rows, n_rows) : 0))
             return lm_fail(ctx, LM_ERR_ARG, "pencil shape differs from the requested build");
     } else {
@@ -227,6 +227,7 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
         p->ldp = ldp;
         p->n_rows = n_rows;
         p->prec = prec;
+        p->gfree = gfree;
         p->g_pencil = lm_pencil_grid(p);
         p->chunk = chunk_rows > 0 ? std::min(chunk_rows, n_rows) : 0;
         const size_t nr = (size_t)n_rows, L = (size_t)ldp;
@@ -243,11 +244,12 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
         rc = rc ? rc : dalloc(ctx, &p->lnpsi, nr);
         rc = rc ? rc : dalloc(ctx, &p->eloc, nr);
         rc = rc ? rc : dalloc(ctx, &p->O, nrf * L);
-        rc = rc ? rc : dalloc(ctx, &p->G, nrf * L);
+        if (!gfree) rc = rc ? rc : dalloc(ctx, &p->G, nrf * L);
         if (!rc && prec != LM_FP64) {
             const size_t es = prec == LM_FP32 ? 4 : (prec == LM_DF64 ? 8 : 2);
             rc = lm_cuda_check(ctx, cudaMalloc(&p->Olo, nrf * L * es), "cudaMalloc");
-            rc = rc ? rc : lm_cuda_check(ctx, cudaMalloc(&p->Glo, nrf * L * es), "cudaMalloc");
+            if (!gfree)
+                rc = rc ? rc : lm_cuda_check(ctx, cudaMalloc(&p->Glo, nrf * L * es), "cudaMalloc");
         }
         if (!rc && p->chunk) {
             const size_t nch = (nr + p->chunk - 1) / p->chunk;
@@ -298,10 +300,12 @@ int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
     const bool have_sector = p->enumerated;  // a pencil rebuilt in place keeps its rows
     p->enumerated = enumerate;
     p->given_weights = weights != nullptr;
-    p->sym = enumerate ? LM_SYM_NONE : LM_SYM_HALF;
+    p->sym = gfree ? LM_SYM_ELOC : enumerate ? LM_SYM_NONE : LM_SYM_HALF;
     p->e_core = sys->e_core;
     if (sys->build_arith != LM_ARITH_DF64 && sys->build_arith != LM_ARITH_FP64)
         return lm_fail(ctx, LM_ERR_ARG, "bad build_arith %d", sys->build_arith);
+    if (gfree && sys->build_arith != LM_ARITH_DF64)
+        return lm_fail(ctx, LM_ERR_ARG, "the G-free build runs in double-float arithmetic");
     p->arith = sys->build_arith;
     int rc = 0;
     const size_t nn = (size_t)n * n;
@@ -359,6 +363,19 @@ extern "C" int lm_build_OG(lm_ctx *ctx, const lm_system *sys, const double *thet
                            const uint64_t *rows, const double *weights, int64_t n_rows,
                            lm_precision prec, void *stream, lm_pencil **inout) {
     if (int rc = lm_build_enqueue(ctx, sys, theta, rows, weights, n_rows, prec, stream, inout))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = lm_cuda_check(ctx, cudaStreamSynchronize(s), "build")) return rc;
+    return lm_build_finish(*inout);
+}
+
+// The E_loc estimator's pencil (Methods, eq. matrix_vec_prod with E_loc in
+// place of the G form): the build forms O, ln psi and E_loc, never G.
+extern "C" int lm_build_O(lm_ctx *ctx, const lm_system *sys, const double *theta,
+                          const uint64_t *rows, const double *weights, int64_t n_rows,
+                          lm_precision prec, void *stream, lm_pencil **inout) {
+    if (int rc = lm_build_enqueue(ctx, sys, theta, rows, weights, n_rows, prec, stream, inout, 0,
+                                  0, 1))
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (int rc = lm_cuda_check(ctx, cudaStreamSynchronize(s), "build")) return rc;
@@ -465,6 +482,8 @@ extern "C" int lm_apply_pencil(lm_pencil *p, const double *v, double *Hv, double
     if (p->shard_state) return lm_fail(ctx, LM_ERR_ARG, "row shard not centred (lm_shard_centre)");
     cudaStream_t s = (cudaStream_t)stream;
     const int sy = sym == LM_SYM_AUTO ? p->sym : sym;
+    if (p->gfree && sy != LM_SYM_ELOC)
+        return lm_fail(ctx, LM_ERR_ARG, "a pencil without G'_c answers the E_loc estimator only");
     // the kernels read ldp >= P+1 entries: stage v with zero padding
     const bool v_host = !lm_is_device_ptr(v);
     cudaMemsetAsync(p->tvec, 0, p->ldp * sizeof(double), s);
@@ -539,6 +558,7 @@ extern "C" int lm_pencil_export(lm_pencil *p, int what, void *dst, void *stream)
     const size_t nr = (size_t)p->n_rows;
     if ((what == 0 || what == 1) && p->chunk)
         return lm_fail(ctx, LM_ERR_ARG, "a streamed pencil keeps no O_c, G'_c to export");
+    if (what == 1 && p->gfree) return lm_fail(ctx, LM_ERR_ARG, "the pencil has no G'_c");
     if ((what == 0 || what == 1) && p->prec == LM_DF64 && p->Olo) {
         // the centred factors of a double-float pencil exist only as pairs:
         // convert into the (otherwise unused after the build) FP64 buffer

@@ -573,6 +573,7 @@ int lm_launch_pencil_block(lm_pencil *p, const double *V, int ldv, int nvec, dou
         return lm_fail(ctx, LM_ERR_ARG, "the block product needs a pencil with BF16 factors");
     if (p->shard_state) return lm_fail(ctx, LM_ERR_ARG, "row shard not centred (lm_shard_centre)");
     if (p->chunk) return lm_fail(ctx, LM_ERR_ARG, "the block product needs resident factors");
+    if (p->gfree) return lm_fail(ctx, LM_ERR_ARG, "the block product needs G'_c");
     if (nvec < 1 || nvec > NV || ldv < p->P1)
         return lm_fail(ctx, LM_ERR_SIZE, "need 1 <= nvec <= %d and ldv >= P+1", NV);
     const int sy = sym == LM_SYM_AUTO ? p->sym : sym;

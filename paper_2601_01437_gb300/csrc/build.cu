@@ -8,6 +8,7 @@
 // 64-byte boundary for FP64 and on 16 bytes for the low-precision copies).
 #include <cstdarg>
 #include <cstdlib>
+#include <cstring>
 
 #include "df64.cuh"
 #include "internal.cuh"
@@ -512,26 +513,6 @@ __device__ __forceinline__ df ldg_df(const float2 *p) {
 }
 __device__ __forceinline__ void st_df(float2 *p, df a) { *p = make_float2(a.h, a.l); }
 
-struct BuildDfArgs {
-    SysView S;
-    int nh, M, M1, P1, ldp;
-    int ldF, ldS, nslice, ns;  // ns = number of single excitations of a row
-    FastDiv fd_nh, fd_M1;      // division by Nh and by M + 1
-    int fuseB;  // keep only the B table; A_s[j] = g_j B_s[j] formed on the fly
-    const double *theta;
-    const float2 *tdf;  // df tables (see k_tables_df)
-    const uint64_t *rows;
-    int64_t n_rows;
-    uint64_t amask, bmask;
-    double e_core;
-    double *lnpsi, *eloc, *O, *G;
-    int *flags;
-};
-
-constexpr int BDF_THREADS = 256;
-constexpr int BDF_TPC = 4;                        // threads per connection
-constexpr int BDF_K = BDF_THREADS / BDF_TPC;      // connections per batch
-
 // Slater-Condon <x'|H|x> (without sign) in double-float, integrals from tdf.
 __device__ __forceinline__ df exc_value_df(const SysView &S, const RowLists &L, const Exc &e,
                                            const float2 *hd, const float2 *gd) {
@@ -605,44 +586,8 @@ __device__ __forceinline__ void single_of(const SysView &S, const RowLists &L, i
     }
 }
 
-// Connection k as one or two single excitations s1 (, s2) (same order as decode_exc).
-__device__ __forceinline__ void singles_of_conn(const SysView &S, int k, int &s1, int &s2) {
-    s2 = -1;
-    if (k < S.ns_a) {
-        s1 = k;
-        return;
-    }
-    k -= S.ns_a;
-    if (k < S.ns_b) {
-        s1 = S.ns_a + k;
-        return;
-    }
-    k -= S.ns_b;
-    int lo, hi, vlo, vhi;
-    if (k < S.nd_aa) {
-        const int nvp = S.nva * (S.nva - 1) / 2, q = fdiv(k, S.fd_pva);
-        unrank_pair(q, lo, hi);
-        unrank_pair(k - q * nvp, vlo, vhi);
-        s1 = lo * S.nva + vlo;
-        s2 = hi * S.nva + vhi;
-        return;
-    }
-    k -= S.nd_aa;
-    if (k < S.nd_bb) {
-        const int nvp = S.nvb * (S.nvb - 1) / 2, q = fdiv(k, S.fd_pvb);
-        unrank_pair(q, lo, hi);
-        unrank_pair(k - q * nvp, vlo, vhi);
-        s1 = S.ns_a + lo * S.nvb + vlo;
-        s2 = S.ns_a + hi * S.nvb + vhi;
-        return;
-    }
-    k -= S.nd_bb;
-    const int nbe = S.nb * S.nvb;
-    s1 = fdiv(k, S.fd_nbe);
-    s2 = S.ns_a + (k - s1 * nbe);
-}
-
-// Same computation as k_build_rows, in double-float arithmetic on the FP32
+// ------------------------------- K2-K6 in double-float, by connection class
+// K2-K6 as k_build_rows computes them, in double-float arithmetic on the FP32
 // pipes. For hidden unit j let sigma_j = -sign(z_j) (+1 if z_j < 0),
 // g_j = exp(2 sigma_j z_j) <= 1 and, for a connection moving orbitals with
 // shift d_j of the pre-activation, Z_j = g_j exp(2 sigma_j d_j). Then
@@ -657,31 +602,178 @@ __device__ __forceinline__ void singles_of_conn(const SysView &S, int k, int &s1
 // from c u_j rather than c tanh(z_j + d_j): over any connection set Q,
 // sum_Q c tanh = sigma_j (sum_Q c - 2 sum_Q c u_j), and sum_Q c is the hidden
 // row 0 of the same sums, so the conversion happens once per output element.
-__global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
+//
+// The connections of a row, class by class, as row-major grids (R rows x C columns):
+//   GC_AA  alpha-alpha doubles: occupied-pair rank x empty-pair rank (colex ranks)
+//   GC_BB  beta-beta doubles, the same over the beta orbitals
+//   GC_B   beta singles: occupied position x empty position
+//   GC_AB  alpha single s x (1 + beta singles): column 0 is the alpha single s
+//          itself, column 1 + t the alpha-beta double made of s and beta single t
+// A connection moves the orbitals of its row (the occupied pair; the occupied
+// orbital; the two orbitals of s) and of its column (the empty pair; the empty
+// orbital; the two orbitals of t; none for column 0). Decoding a connection is
+// then a division by C and table lookups: the alpha-beta double's integral is
+// (a i|b j) at an index that is the sum of a per-single part of s and of t, its
+// sign the product of the singles' signs, its Z_j = A_s[j] B_t[j].
+// The scatter into the per-orbital sums S[p][j] = sum_{x' moving p} c u_j(x')
+// walks each slice's contiguous run of connections: the sum over a run of one
+// row stays in a register and goes to the row's orbitals (and to the sum over
+// all connections) once per run; only the column's orbitals take one update
+// per connection. Each slice owns a private copy of S (no two threads write one
+// entry); the copies are added in slice order at the end (bit-reproducible).
+enum { GC_AA = 0, GC_BB = 1, GC_B = 2, GC_AB = 3, GC_N = 4 };
+
+constexpr int GDF_THREADS = 256;
+constexpr int GDF_TPC = 4;                        // threads per connection
+constexpr int GDF_K = GDF_THREADS / GDF_TPC;      // connections per tile
+
+struct GridDfArgs {
+    SysView S;
+    int nh, M, M1, P1, ldp;
+    int ldA;   // stride of the singles' table and the A rows (odd, >= nh)
+    int ldF;   // stride of a connection's row [c, c u_0 .. c u_{nh-1}] (odd, >= nh + 1)
+    int ldL;   // stride of an orbital-sum row (odd, >= nh + 1)
+    int ns;    // singles, alpha then beta
+    int nsl;   // scatter slices (each with its own orbital sums; 0 without G)
+    int gfree; // no G row: O, ln psi and E_loc only (the E_loc estimator's build)
+    int R[GC_N], C[GC_N], toff[GC_N];  // toff: class's first row-target entry
+    FastDiv fdC[GC_N], fd_nh, fd_nh1, fd_M1;
+    int ntab;  // rows of the singles' table (max of the two spins)
+    int narow; // A rows one tile of the alpha-beta class can touch
+    int ntgt;  // orbital-target entries (rows then columns of every class)
+    const double *theta;
+    const float2 *tdf;
+    const uint64_t *rows;
+    int64_t n_rows;
+    uint64_t amask, bmask;
+    double e_core;
+    double *lnpsi, *eloc, *O, *G;
+    int *flags;
+};
+
+// Byte offsets of the dynamic shared memory (host and device use the same map).
+struct GridSmem {
+    size_t lists, tgt, tab, F, Sg, arow, ones, V, Hs, Td, Gd, Red, T, Z, L1, Cs, Ve, Sgn, Pi, Sig,
+        total;
+};
+__host__ __device__ inline GridSmem grid_smem(const GridDfArgs &A) {
+    GridSmem g;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += (bytes + 15) & ~(size_t)15;
+        return at;
+    };
+    const size_t nh = A.nh, ns = A.ns;
+    g.lists = take(sizeof(RowLists));
+    g.tgt = take((size_t)A.ntgt * sizeof(int2));
+    g.tab = take((size_t)A.ntab * A.ldA * 8);
+    g.F = take(A.gfree ? 0 : (size_t)GDF_K * A.ldF * 8);
+    g.Sg = take((size_t)A.nsl * (A.M + 1) * A.ldL * 8);
+    g.arow = take((size_t)2 * A.narow * A.ldA * 8);
+    g.ones = take((size_t)A.ldA * 8);
+    g.V = take(ns * 8);
+    g.Hs = take(ns * 8);
+    g.Td = take(nh * 8);
+    g.Gd = take(nh * 8);
+    g.Red = take((size_t)(GDF_THREADS / 32) * 8);
+    g.T = take(nh * 8);
+    g.Z = take(nh * 8);
+    g.L1 = take(nh * 8);
+    g.Cs = take((size_t)2 * A.M * 8);
+    g.Ve = take(ns * 4);
+    g.Sgn = take(ns * 4);
+    g.Pi = take(ns * 4);
+    g.Sig = take(nh * 4);
+    g.total = o;
+    return g;
+}
+
+// A_s[j] = g_j B_s[j] of alpha single s, from the global exp(+-2W) tables
+__device__ __forceinline__ df grid_arow(const GridDfArgs &A, const RowLists &L, int s, int j,
+                                        const float2 *e2, const float2 *e2i, const float *sSig,
+                                        const float2 *sGd) {
+    const int q = fdiv(s, A.S.fd_nva);
+    const int i = L.oa[q], a = L.va[s - q * A.S.nva];
+    const bool pos = sSig[j] > 0.f;
+    const df b = df_mul(ldg_df((pos ? e2 : e2i) + j * A.M + a), ldg_df((pos ? e2i : e2) + j * A.M + i));
+    return df_mul(ld_df(sGd + j), b);
+}
+
+// B_t[j] of every single of one spin (spin 0: alpha singles, 1: beta)
+__device__ __forceinline__ void grid_table(const GridDfArgs &A, const RowLists &L, int spin,
+                                           const float2 *e2, const float2 *e2i, const float *sSig,
+                                           float2 *sTab) {
+    const int nsp = spin ? A.S.ns_b : A.S.ns_a, off = spin ? A.S.ns_a : 0;
+    for (int e = threadIdx.x; e < nsp * A.nh; e += GDF_THREADS) {
+        const int t = fdiv(e, A.fd_nh), j = e - t * A.nh;
+        int i, a;
+        single_of(A.S, L, off + t, i, a);
+        const bool pos = sSig[j] > 0.f;
+        st_df(sTab + t * A.ldA + j, df_mul(ldg_df((pos ? e2 : e2i) + j * A.M + a),
+                                           ldg_df((pos ? e2i : e2) + j * A.M + i)));
+    }
+}
+
+// Orbital targets of target entry e: the rows of each class, then its columns.
+__device__ __forceinline__ int2 grid_target(const GridDfArgs &A, const RowLists &L, int e) {
+    const SysView &S = A.S;
+    int c = GC_N - 1;
+    while (c > 0 && e < A.toff[c]) --c;
+    int k = e - A.toff[c];
+    const bool isrow = k < A.R[c];
+    if (!isrow) k -= A.R[c];
+    int lo, hi;
+    switch (c) {
+        case GC_AA:
+        case GC_BB: {
+            const bool al = c == GC_AA;
+            unrank_pair(k, lo, hi);
+            if (isrow) return al ? make_int2(L.oa[lo], L.oa[hi]) : make_int2(L.ob[lo], L.ob[hi]);
+            return al ? make_int2(L.va[lo], L.va[hi]) : make_int2(L.vb[lo], L.vb[hi]);
+        }
+        case GC_B:
+            return isrow ? make_int2(L.ob[k], -1) : make_int2(L.vb[k], -1);
+        default:
+            if (isrow) {
+                const int q = fdiv(k, S.fd_nva);
+                return make_int2(L.oa[q], L.va[k - q * S.nva]);
+            }
+            if (k == 0) return make_int2(-1, -1);
+            {
+                const int t = k - 1, q = fdiv(t, S.fd_nvb);
+                return make_int2(L.ob[q], L.vb[t - q * S.nvb]);
+            }
+    }
+}
+
+// GF: the G-free build of the E_loc estimator (no u_j, no scatter, no G row).
+template <bool GF>
+__global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
     extern __shared__ __align__(16) unsigned char smb[];
-    const int nh = A.nh, M = A.M, M1 = A.M1, NS = A.ns;
+    const int nh = A.nh, M = A.M, M1 = A.M1, NS = A.ns, nh1 = nh + 1;
     const int tid = threadIdx.x, lane = tid & 31;
-    int4 *sIdx = reinterpret_cast<int4 *>(smb);                 // [K] moved orbitals i, j, a, b
-    RowLists *sL = reinterpret_cast<RowLists *>(sIdx + BDF_K);  // 1
-    const int ldA = nh | 1;  // odd row stride: the connections of a warp hit distinct banks
-    float2 *sA = reinterpret_cast<float2 *>(sL + 1);            // [NS][ldA]  A_s[j] (unless fuseB)
-    float2 *sB = sA + (A.fuseB ? 0 : NS * ldA);                 // [NS][ldA]  B_s[j]
-    float2 *sV = sB + NS * ldA;                                 // [NS]
-    float2 *sHs = sV + NS;                                      // [NS] singles' <x'|H|x>
-    float2 *sTd = sHs + NS;                                     // [nh] t as df
-    float2 *sF = sTd + nh;                                      // [K][ldF]  tanh(z+d)
-    float2 *sC = sF + BDF_K * A.ldF;                            // [K]
-    float2 *sS = sC + BDF_K;                                    // [nslice][nh+1][ldS]
-    float2 *sAcc = sS + A.nslice * (nh + 1) * A.ldS;            // [nslice][nh+1]
-    float2 *sRed = sAcc + A.nslice * (nh + 1);                  // [BDF_THREADS/32]
-    float2 *sAf = sRed + BDF_THREADS / 32;                      // [nh+1] sums over all connections
-    double *sT = reinterpret_cast<double *>(sAf + (nh + 1));    // [nh] t
-    double *sZ = sT + nh;                                              // [nh] z
-    double *sL1 = sZ + nh;                                             // [nh] ln(1 + g_j)
-    double *sCs = sL1 + nh;                                            // [2][M] sum_j sigma_j W_jp
-    float2 *sGd = reinterpret_cast<float2 *>(sCs + 2 * M);             // [nh] g as df
-    float *sSig = reinterpret_cast<float *>(sGd + nh);                 // [nh] sigma
-    int *sVe = reinterpret_cast<int *>(sSig + nh);                     // [NS] exponent of V_s
+    const GridSmem lay = grid_smem(A);
+    RowLists *sL = reinterpret_cast<RowLists *>(smb + lay.lists);
+    int2 *sTgt = reinterpret_cast<int2 *>(smb + lay.tgt);        // [ntgt] orbital targets
+    float2 *sTab = reinterpret_cast<float2 *>(smb + lay.tab);    // [ntab][ldA]  B_t[j]
+    float2 *sF = reinterpret_cast<float2 *>(smb + lay.F);        // [K][ldF]  c, c u_j
+    float2 *sSg = reinterpret_cast<float2 *>(smb + lay.Sg);      // [nsl][M + 1][ldL]
+    float2 *sArow = reinterpret_cast<float2 *>(smb + lay.arow);  // [2][narow][ldA]
+    float2 *sOne = reinterpret_cast<float2 *>(smb + lay.ones);   // [ldA] ones
+    float2 *sV = reinterpret_cast<float2 *>(smb + lay.V);        // [NS]
+    float2 *sHs = reinterpret_cast<float2 *>(smb + lay.Hs);      // [NS]
+    float2 *sTd = reinterpret_cast<float2 *>(smb + lay.Td);      // [nh] t as df
+    float2 *sGd = reinterpret_cast<float2 *>(smb + lay.Gd);      // [nh] g as df
+    float2 *sRed = reinterpret_cast<float2 *>(smb + lay.Red);
+    double *sT = reinterpret_cast<double *>(smb + lay.T);
+    double *sZ = reinterpret_cast<double *>(smb + lay.Z);
+    double *sL1 = reinterpret_cast<double *>(smb + lay.L1);
+    double *sCs = reinterpret_cast<double *>(smb + lay.Cs);
+    int *sVe = reinterpret_cast<int *>(smb + lay.Ve);
+    float *sSgn = reinterpret_cast<float *>(smb + lay.Sgn);
+    int *sPi = reinterpret_cast<int *>(smb + lay.Pi);
+    float *sSig = reinterpret_cast<float *>(smb + lay.Sig);
     __shared__ double sDiag, sLn, sGinv;
     __shared__ int sGe;
     __shared__ int sBad;
@@ -690,39 +782,54 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
     const float2 *e2i = e2 + nh * M;        // exp(-2W) [nh][M]
     const float2 *hd = e2 + 2 * nh * M;     // h [n][n]
     const float2 *gd = hd + A.S.n * A.S.n;  // (pq|rs)
+    const SysView &S = A.S;
+    const int ldL = A.ldL, ldF = A.ldF, ldA = A.ldA;
 
-    const int nsl = A.nslice;
-    const int sc_r = tid % (nh + 1), sc_s = tid / (nh + 1);
-    const bool scatter_thread = sc_s < nsl;
-    // connection kk of the batch is handled by the BDF_TPC lanes kk % CPW,
-    // kk % CPW + CPW, ... of warp kk / CPW (CPW = 32 / BDF_TPC connections per
-    // warp): a half-warp's double-float row stores then fall on rows of
-    // different connections at stride ldF, which keeps their banks apart
-    constexpr int CPW = 32 / BDF_TPC;
+    // connection kk of a tile is handled by the GDF_TPC lanes kk % CPW, kk % CPW
+    // + CPW, ... of warp kk / CPW
+    constexpr int CPW = 32 / GDF_TPC;
     const int kk = (tid >> 5) * CPW + (lane % CPW), sub = lane / CPW;
+    // scatter thread: slice sl, hidden row sr
+    const int sl = tid / nh1, sr = tid - sl * nh1;
+    const bool scatter_thread = sl < A.nsl;
+    float2 *mySg = sSg + (size_t)sl * (M + 1) * ldL + sr;
+    auto next_class = [&](int c) -> int {
+        for (++c; c < GC_N; ++c)
+            if (A.R[c] > 0 && A.C[c] > 0) return c;
+        return (int)GC_N;
+    };
+    auto spin_of = [](int c) { return c == GC_AA ? 0 : 1; };
 
     for (int64_t row = blockIdx.x; row < A.n_rows; row += gridDim.x) {
         const uint64_t x = A.rows[row];
         if (tid == 0) {
-            const int bad = (__popcll(x & A.amask) != A.S.na) ||
-                            (__popcll(x & A.bmask) != A.S.nb) || (x & ~(A.amask | A.bmask)) != 0;
+            const int bad = (__popcll(x & A.amask) != S.na) || (__popcll(x & A.bmask) != S.nb) ||
+                            (x & ~(A.amask | A.bmask)) != 0;
             sBad = bad;
             if (bad) atomicOr(A.flags, FLAG_ROW_OUTSIDE_SECTOR);
-            make_lists(A.S, x, *sL);
+            make_lists(S, x, *sL);
         }
         __syncthreads();
         if (sBad) {
             __syncthreads();
             continue;
         }
-        // per hidden unit (FP64): z_j from the occupied lists; with
-        // em = expm1(-2|z|): g = e^{-2|z|} = 1 + em, tanh z = sign(z) (-em) / (2 + em)
-        // (no cancellation for small |z|), l1 = log1p(g) = ln(1 + g)
-        for (int j = tid; j < nh; j += BDF_THREADS) {
+        const RowLists &L = *sL;
+        // A rows of the first tile of the alpha-beta class (buffer 0)
+        auto first_arows = [&]() {
+            const int nr = fdiv(min(GDF_K, A.R[GC_AB] * A.C[GC_AB]) - 1, A.fdC[GC_AB]) + 1;
+            for (int e = tid; e < nr * nh; e += GDF_THREADS) {
+                const int rr = fdiv(e, A.fd_nh), j = e - rr * nh;
+                st_df(sArow + rr * ldA + j, grid_arow(A, L, rr, j, e2, e2i, sSig, sGd));
+            }
+        };
+        // per hidden unit (FP64): z_j, g = e^{-2|z|} = 1 + expm1(-2|z|) (no
+        // cancellation for small |z|), tanh z = sign(z) (-em) / (2 + em), ln(1 + g)
+        for (int j = tid; j < nh; j += GDF_THREADS) {
             const double *wj = A.theta + (size_t)(j + 1) * M1;
             double za = wj[-1], zb = 0.0;
-            for (int t = 0; t < A.S.na; ++t) za += wj[sL->oa[t]];
-            for (int t = 0; t < A.S.nb; ++t) zb += wj[sL->ob[t]];
+            for (int t = 0; t < S.na; ++t) za += wj[L.oa[t]];
+            for (int t = 0; t < S.nb; ++t) zb += wj[L.ob[t]];
             const double z = za + zb;
             sZ[j] = z;
             const double em = expm1(-2.0 * fabs(z));
@@ -733,23 +840,22 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             const df td = df_from_double(t);
             sTd[j] = make_float2(td.h, td.l);
             sSig[j] = z < 0.0 ? 1.f : -1.f;
-            const df gd = df_from_double(g);
-            sGd[j] = make_float2(gd.h, gd.l);
+            const df gdv = df_from_double(g);
+            sGd[j] = make_float2(gdv.h, gdv.l);
         }
         {
-            // <x'|H|x> of every single excitation (without sign), one warp per
-            // single: lanes over the occupied orbitals, then a fixed-order
-            // butterfly; warps that hold no hidden unit above do this
+            // <x'|H|x> of every single (without sign), one warp per single; warps
+            // that hold no hidden unit above do this
             const int w0 = (nh + 31) >> 5, warp = tid >> 5;
-            for (int sgl = warp - w0; warp >= w0 && sgl < NS; sgl += BDF_THREADS / 32 - w0) {
+            for (int sgl = warp - w0; warp >= w0 && sgl < NS; sgl += GDF_THREADS / 32 - w0) {
                 int i, a;
-                single_of(A.S, *sL, sgl, i, a);
-                const int n = A.S.n, sp = i >= n;
+                single_of(S, L, sgl, i, a);
+                const int n = S.n, sp = i >= n;
                 const int ip = i - sp * n, ap = a - sp * n;
                 df v = df_make(0.f, 0.f);
-                for (int t = lane; t < A.S.na + A.S.nb; t += 32) {
-                    const bool ta = t < A.S.na;
-                    const int kp = ta ? sL->oa[t] : sL->ob[t - A.S.na] - n;
+                for (int t = lane; t < S.na + S.nb; t += 32) {
+                    const bool ta = t < S.na;
+                    const int kp = ta ? L.oa[t] : L.ob[t - S.na] - n;
                     const float2 *gk = gd + ((size_t)ap * n + ip) * n * n;
                     v = df_add(v, ldg_df(gk + (size_t)kp * n + kp));
                     if ((ta ? 0 : 1) == sp)
@@ -762,7 +868,9 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
                 if (lane == 0) st_df(sHs + sgl, df_add(ldg_df(hd + ap * n + ip), v));
             }
         }
-        for (int e = tid; e < nsl * (nh + 1) * A.ldS; e += BDF_THREADS) sS[e] = make_float2(0.f, 0.f);
+        for (int e = tid; e < A.nsl * (M + 1) * ldL; e += GDF_THREADS) sSg[e] = make_float2(0.f, 0.f);
+        for (int e = tid; e < ldA; e += GDF_THREADS) sOne[e] = make_float2(1.f, 0.f);
+        for (int e = tid; e < A.ntgt; e += GDF_THREADS) sTgt[e] = grid_target(A, L, e);
         __syncthreads();
         if (tid < 32) {
             // ln psi = a.x + sum_j (|z_j| + ln(1 + g_j)) (the ln 2 of each cosh cancels
@@ -777,16 +885,14 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             lp = warp_sum(lp);
             lg = warp_sum(lg);
             if (tid == 0) {
-                // 1 / prod_j (1 + g_j) = sGinv * 2^sGe with sGinv in [0.5, 1): the
-                // product reaches 2^Nh, beyond the range whose double-float low
-                // word is still a normal FP32 number
+                // 1 / prod_j (1 + g_j) = sGinv 2^sGe with sGinv in [0.5, 1)
                 sLn = lp;
                 int ge = 0;
                 sGinv = frexp(exp(-lg), &ge);
                 sGe = ge;
             }
         } else if (tid < 64) {
-            const double d = diag_value_warp(A.S, *sL);
+            const double d = diag_value_warp(S, L);
             if (tid == 32) sDiag = d + A.e_core;
         } else if (tid - 64 < 2 * M) {
             // sum_j sigma_j W_jp in two interleaved halves (combined where used)
@@ -806,136 +912,230 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
             sCs[half * M + p] = c0 + c1;
         }
         __syncthreads();
-        // per single excitation: V_s (FP64 exp), B_s[j], A_s[j] (df)
-        for (int e = tid; e < NS * nh; e += BDF_THREADS) {
-            const int s = fdiv(e, A.fd_nh), j = e - s * nh;
+        // per single: V_s = exp(a_a - a_i - sum_j sigma_j d_j) (FP64 exp), its
+        // Jordan-Wigner sign and the index part of an alpha-beta double's integral;
+        // the table and A rows of the first class
+        for (int s = tid; s < NS; s += GDF_THREADS) {
             int i, a;
-            single_of(A.S, *sL, s, i, a);
-            const bool pos = sSig[j] > 0.f;
-            const df b = df_mul(ldg_df((pos ? e2 : e2i) + j * M + a),
-                                ldg_df((pos ? e2i : e2) + j * M + i));
-            st_df(sB + s * ldA + j, b);
-            if (!A.fuseB) st_df(sA + s * ldA + j, df_mul(ld_df(sGd + j), b));
-        }
-        for (int s = tid; s < NS; s += BDF_THREADS) {
-            int i, a;
-            single_of(A.S, *sL, s, i, a);
+            single_of(S, L, s, i, a);
             const double csa = sCs[a] + sCs[M + a], csi = sCs[i] + sCs[M + i];
             const double ex = (A.theta[a] - A.theta[i]) - (csa - csi);
             int ve = 0;  // V_s = mantissa * 2^ve, mantissa in [0.5, 1)
             const df v = df_from_double(frexp(exp(ex), &ve));
             sV[s] = make_float2(v.h, v.l);
             sVe[s] = ve;
+            const int par = parity_below(x, i) + parity_below(x ^ (1ull << i), a);
+            sSgn[s] = (par & 1) ? -1.f : 1.f;
+            const int n = S.n;
+            sPi[s] = s < S.ns_a ? (a * n + i) * n * n : (a - n) * n + (i - n);
+        }
+        int cls = next_class(-1);
+        if (cls < GC_N) {
+            grid_table(A, L, spin_of(cls), e2, e2i, sSig, sTab);
+            if (cls == GC_AB) first_arows();
         }
         __syncthreads();
 
         df el_part = df_make(0.f, 0.f);
-        df accA = df_make(0.f, 0.f);
-        const RowLists &L = *sL;
         const df ginv = df_from_double(sGinv);
-        for (int k0 = 0; k0 < A.S.conn; k0 += BDF_K) {
-            const int k = k0 + kk;
-            const bool active = k < A.S.conn;
-            int s1 = 0, s2 = -1;
-            df rp = df_make(1.f, 0.f);
-            int re = 0;
-            // the connection's <x'|H|x> (lane 0): singles from the row's table,
-            // doubles' integrals fetched here so their latency hides behind the
-            // hidden-unit loop
-            Exc e;
-            int sg = 1;
-            df hv = df_make(0.f, 0.f);
-            if (active && sub == 0) {
-                e = decode_exc(A.S, L, k);
-                (void)apply_exc(x, e, sg);
-                if (e.j < 0) hv = ld_df(sHs + k);
-                else hv = exc_value_df(A.S, L, e, hd, gd);
-            }
-            if (active) {
-                singles_of_conn(A.S, k, s1, s2);
-                float2 *Frow = sF + kk * A.ldF;
-                const float2 *a1 = sA + s1 * ldA;
-                const float2 *b2 = sB + (s2 >= 0 ? s2 : 0) * ldA;
-                // Z_j = A_s1[j] (B_s2[j]); u = 1 / (1 + Z); the running product of
-                // (1 + Z_j) stays >= 1 and is rescaled past 2^60
-#pragma unroll 2
-                for (int j = sub; j < nh; j += BDF_TPC) {
-                    df z = A.fuseB ? df_mul_lazy(ld_df(sGd + j), ld_df(sB + s1 * ldA + j))
-                                   : ld_df(a1 + j);
-                    if (s2 >= 0) z = df_mul_lazy(z, ld_df(b2 + j));
-                    const df zp = df_add1_lazy(z);
-                    st_df(Frow + j, df_rcp_ge1(zp));  // u_j
-                    rp = df_mul_lazy(rp, zp);
-                    if (rp.h > 0x1p60f) df_renorm(rp, re);
-                }
-                rp = df_fts(rp.h, rp.l);
-            }
-            // combine the partial products of the BDF_TPC lanes of a connection
-            // (all lanes take part; inactive ones carry 1 * 2^0)
-#pragma unroll
-            for (int off = CPW; off < 32; off <<= 1) {
-                const df o = df_make(__shfl_xor_sync(0xffffffffu, rp.h, off),
-                                     __shfl_xor_sync(0xffffffffu, rp.l, off));
-                const int oe = __shfl_xor_sync(0xffffffffu, re, off);
-                rp = df_mul(rp, o);
-                re += oe;
-                df_renorm(rp, re);
-            }
-            df c = df_make(0.f, 0.f);
-            if (active && sub == 0) {
-                if (sg < 0) hv = df_neg(hv);
-                df f = df_mul(hv, ld_df(sV + s1));
-                int fe = re + sGe + sVe[s1];
-                if (s2 >= 0) {
-                    f = df_mul(f, ld_df(sV + s2));
-                    fe += sVe[s2];
-                }
-                c = df_ldexp(df_mul(df_mul(f, ginv), rp), fe);
-                st_df(sC + kk, c);
-                sIdx[kk] = make_int4(e.i, e.j, e.a, e.b);
-                df_acc(el_part, c);
-            }
-            // the row of the connection becomes c u_j, here where every thread
-            // works, rather than in the scatter below
-            c.h = __shfl_sync(0xffffffffu, c.h, lane % CPW);
-            c.l = __shfl_sync(0xffffffffu, c.l, lane % CPW);
-            if (active) {
-                float2 *Frow = sF + kk * A.ldF;
-                for (int j = sub; j < nh; j += BDF_TPC) st_df(Frow + j, df_mul_lazy(c, ld_df(Frow + j)));
-            }
-            __syncthreads();
-            if (scatter_thread) {
-                const int kend = min(BDF_K, A.S.conn - k0);
-                float2 *Srow = sS + (sc_s * (nh + 1) + sc_r) * A.ldS;
-                const float2 *Fcol = sc_r > 0 ? sF + sc_r - 1 : sC;
-                const int ldq = sc_r > 0 ? A.ldF : 1;
-                for (int q = sc_s; q < kend; q += nsl) {
-                    const df f = ld_df(Fcol + q * ldq);
-                    const int4 ix = sIdx[q];
-                    // the orbitals a connection moves are distinct: load all, add, store
-                    df t0 = ld_df(Srow + ix.x), t1 = ld_df(Srow + ix.z);
-                    if (ix.y >= 0) {
-                        df t2 = ld_df(Srow + ix.y), t3 = ld_df(Srow + ix.w);
-                        df_acc(t0, f);
-                        df_acc(t1, f);
-                        df_acc(t2, f);
-                        df_acc(t3, f);
-                        st_df(Srow + ix.x, t0);
-                        st_df(Srow + ix.z, t1);
-                        st_df(Srow + ix.y, t2);
-                        st_df(Srow + ix.w, t3);
-                    } else {
-                        df_acc(accA, f);  // singles only (see below)
-                        df_acc(t0, f);
-                        df_acc(t1, f);
-                        st_df(Srow + ix.x, t0);
-                        st_df(Srow + ix.z, t1);
+        for (; cls < GC_N; cls = next_class(cls)) {
+            const int C = A.C[cls];
+            const FastDiv fdC = A.fdC[cls];
+            const int ne = A.R[cls] * C;
+            const bool fuse = cls != GC_AB;  // Z carries g_j from sGd
+            const int2 *rowT = sTgt + A.toff[cls], *colT = rowT + A.R[cls];
+            int tile = 0;
+            for (int e0 = 0; e0 < ne; e0 += GDF_K, ++tile) {
+                const int e1 = min(ne, e0 + GDF_K);
+                const int rf = fdiv(e0, fdC);
+                // ---- per connection: u_j = 1 / (1 + Z_j), prod_j (1 + Z_j) and c
+                const float2 *arow = sArow + (tile & 1) * A.narow * ldA;
+                if (cls == GC_AB && e1 < ne) {  // A rows of the next tile
+                    const int n1 = min(ne, e1 + GDF_K);
+                    const int nrf = fdiv(e1, fdC), nrl = fdiv(n1 - 1, fdC);
+                    float2 *dst = sArow + ((tile + 1) & 1) * A.narow * ldA;
+                    for (int e = tid; e < (nrl - nrf + 1) * nh; e += GDF_THREADS) {
+                        const int rr = fdiv(e, A.fd_nh), j = e - rr * nh;
+                        st_df(dst + rr * ldA + j, grid_arow(A, L, nrf + rr, j, e2, e2i, sSig, sGd));
                     }
                 }
+                const int e = e0 + kk;
+                const bool active = e < e1;
+                int rho = 0, gam = 0;
+                const float2 *f1 = sOne, *f2 = sOne;
+                int s1 = 0, s2 = -1;  // singles whose V_s the coefficient takes
+                if (active) {
+                    rho = fdiv(e, fdC);
+                    gam = e - rho * C;
+                    if (cls == GC_AA || cls == GC_BB) {
+                        const int nv = cls == GC_AA ? S.nva : S.nvb;
+                        const int off = cls == GC_AA ? 0 : S.ns_a;
+                        int lo, hi, vlo, vhi;
+                        unrank_pair(rho, lo, hi);
+                        unrank_pair(gam, vlo, vhi);
+                        const int t1 = lo * nv + vlo, t2 = hi * nv + vhi;
+                        f1 = sTab + t1 * ldA;
+                        f2 = sTab + t2 * ldA;
+                        s1 = off + t1;
+                        s2 = off + t2;
+                    } else if (cls == GC_B) {
+                        f1 = sTab + e * ldA;
+                        s1 = S.ns_a + e;
+                    } else {
+                        f1 = arow + (rho - rf) * ldA;
+                        s1 = rho;
+                        if (gam > 0) {
+                            f2 = sTab + (gam - 1) * ldA;
+                            s2 = S.ns_a + gam - 1;
+                        }
+                    }
+                }
+                // the coefficient's <x'|H|x> and sign (lane 0 of the connection);
+                // a double's integrals are fetched before the hidden-unit loop so
+                // that their latency hides behind it
+                df hv = df_make(0.f, 0.f);
+                float sg = 1.f;
+                if (active && sub == 0) {
+                    if (cls == GC_AA || cls == GC_BB) {
+                        const int2 o = rowT[rho], v = colT[gam];
+                        Exc ex;
+                        ex.i = o.x;
+                        ex.j = o.y;
+                        ex.a = v.x;
+                        ex.b = v.y;
+                        int sgi = 1;
+                        (void)apply_exc(x, ex, sgi);
+                        sg = (float)sgi;
+                        hv = exc_value_df(S, L, ex, hd, gd);
+                    } else if (s2 < 0) {
+                        hv = ld_df(sHs + s1);
+                        sg = sSgn[s1];
+                    } else {
+                        hv = ldg_df(gd + sPi[s1] + sPi[s2]);
+                        sg = sSgn[s1] * sSgn[s2];
+                    }
+                }
+                df rp = df_make(1.f, 0.f);
+                int re = 0;
+                float2 *Frow = sF + kk * ldF + 1;
+                if (active) {
+                    // Z_j = (g_j) f1[j] f2[j]; u = 1 / (1 + Z); the running product of
+                    // (1 + Z_j) stays >= 1 and is rescaled past 2^60
+                    if (fuse) {
+#pragma unroll 2
+                        for (int j = sub; j < nh; j += GDF_TPC) {
+                            df z = df_mul_lazy(ld_df(sGd + j), ld_df(f1 + j));
+                            z = df_mul_lazy(z, ld_df(f2 + j));
+                            const df zp = df_add1_lazy(z);
+                            if (!GF) st_df(Frow + j, df_rcp_ge1(zp));
+                            rp = df_mul_lazy(rp, zp);
+                            if (rp.h > 0x1p60f) df_renorm(rp, re);
+                        }
+                    } else {
+#pragma unroll 2
+                        for (int j = sub; j < nh; j += GDF_TPC) {
+                            const df z = df_mul_lazy(ld_df(f1 + j), ld_df(f2 + j));
+                            const df zp = df_add1_lazy(z);
+                            if (!GF) st_df(Frow + j, df_rcp_ge1(zp));
+                            rp = df_mul_lazy(rp, zp);
+                            if (rp.h > 0x1p60f) df_renorm(rp, re);
+                        }
+                    }
+                    rp = df_fts(rp.h, rp.l);
+                }
+                // combine the partial products of the GDF_TPC lanes of a connection
+                // (all lanes take part; inactive ones carry 1 * 2^0)
+#pragma unroll
+                for (int off = CPW; off < 32; off <<= 1) {
+                    const df o = df_make(__shfl_xor_sync(0xffffffffu, rp.h, off),
+                                         __shfl_xor_sync(0xffffffffu, rp.l, off));
+                    const int oe = __shfl_xor_sync(0xffffffffu, re, off);
+                    rp = df_mul(rp, o);
+                    re += oe;
+                    df_renorm(rp, re);
+                }
+                df c = df_make(0.f, 0.f);
+                if (active && sub == 0) {
+                    if (sg < 0.f) hv = df_neg(hv);
+                    df f = df_mul(hv, ld_df(sV + s1));
+                    int fe = re + sGe + sVe[s1];
+                    if (s2 >= 0) {
+                        f = df_mul(f, ld_df(sV + s2));
+                        fe += sVe[s2];
+                    }
+                    c = df_ldexp(df_mul(df_mul(f, ginv), rp), fe);
+                    if (!GF) st_df(Frow - 1, c);
+                    df_acc(el_part, c);
+                }
+                if (!GF) {
+                    // the row of the connection becomes c u_j here, where every thread works
+                    c.h = __shfl_sync(0xffffffffu, c.h, lane % CPW);
+                    c.l = __shfl_sync(0xffffffffu, c.l, lane % CPW);
+                    if (active)
+                        for (int j = sub; j < nh; j += GDF_TPC) st_df(Frow + j, df_mul_lazy(c, ld_df(Frow + j)));
+                }
+                __syncthreads();
+                // ---- scatter: slice sl takes a contiguous run of the tile; the sum over
+                // a run of one row goes to the row's orbitals and the all-connections
+                // sum, each connection to its column's orbitals
+                if (!GF && scatter_thread) {
+                    const int len = e1 - e0, per = (len + A.nsl - 1) / A.nsl;
+                    const int k0 = sl * per, k1 = min(len, k0 + per);
+                    if (k0 < k1) {
+                        int r0 = fdiv(e0 + k0, fdC), g = e0 + k0 - r0 * C;
+                        df racc = df_make(0.f, 0.f);
+                        auto flush = [&](int rr) {
+                            const int2 t = rowT[rr];
+                            float2 *d = mySg + t.x * ldL;
+                            st_df(d, df_add(ld_df(d), racc));
+                            if (t.y >= 0) {
+                                d = mySg + t.y * ldL;
+                                st_df(d, df_add(ld_df(d), racc));
+                            }
+                            d = mySg + M * ldL;
+                            st_df(d, df_add(ld_df(d), racc));
+                        };
+                        const float2 *fp = sF + k0 * ldF + sr;
+                        for (int k2 = k0; k2 < k1; ++k2, fp += ldF) {
+                            const df f = ld_df(fp);
+                            df_acc(racc, f);
+                            const int2 t = colT[g];
+                            if (t.x >= 0) {
+                                float2 *d = mySg + t.x * ldL;
+                                df v = ld_df(d);
+                                df_acc(v, f);
+                                st_df(d, v);
+                            }
+                            if (t.y >= 0) {
+                                float2 *d = mySg + t.y * ldL;
+                                df v = ld_df(d);
+                                df_acc(v, f);
+                                st_df(d, v);
+                            }
+                            if (++g == C && k2 + 1 < k1) {
+                                racc = df_norm(racc);
+                                flush(r0);
+                                racc = df_make(0.f, 0.f);
+                                g = 0;
+                                ++r0;
+                            }
+                        }
+                        racc = df_norm(racc);
+                        flush(r0);
+                    }
+                }
+                // the table and A rows of the next class, after its last tile's
+                // hidden-unit loop (the scatter reads neither)
+                if (e1 == ne) {
+                    const int nc = next_class(cls);
+                    if (nc < GC_N) {
+                        if (spin_of(nc) != spin_of(cls)) grid_table(A, L, spin_of(nc), e2, e2i, sSig, sTab);
+                        if (nc == GC_AB) first_arows();
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
-        if (scatter_thread) st_df(sAcc + sc_s * (nh + 1) + sc_r, df_norm(accA));
         // E_loc: per-warp df sums in lane order, then warps in order
         {
             df v = df_norm(el_part);
@@ -950,54 +1150,48 @@ __global__ void __launch_bounds__(BDF_THREADS) k_build_rows_df(BuildDfArgs A) {
         __syncthreads();
         if (tid == 0) {
             df el = df_from_double(sDiag);
-            for (int w = 0; w < BDF_THREADS / 32; ++w) el = df_add(el, ld_df(sRed + w));
+            for (int w = 0; w < GDF_THREADS / 32; ++w) el = df_add(el, ld_df(sRed + w));
             A.eloc[row] = df_to_double(el);
             A.lnpsi[row] = sLn;
         }
-        // The sum over all connections: a single removes one occupied orbital and
-        // a double two, so sum_all = (sum over occupied p of S[p] + sum_singles) / 2.
-        for (int r = tid; r <= nh; r += BDF_THREADS) {
-            df a = df_make(0.f, 0.f);
-            for (int s2 = 0; s2 < nsl; ++s2) {
-                const float2 *Srow = sS + (s2 * (nh + 1) + r) * A.ldS;
-                a = df_add(a, ld_df(sAcc + s2 * (nh + 1) + r));
-                for (int t = 0; t < A.S.na; ++t) a = df_add(a, df_norm(ld_df(Srow + sL->oa[t])));
-                for (int t = 0; t < A.S.nb; ++t) a = df_add(a, df_norm(ld_df(Srow + sL->ob[t])));
-            }
-            st_df(sAf + r, df_make(0.5f * a.h, 0.5f * a.l));
-        }
-        __syncthreads();
-        // O row and G row; sums of c u_j become sums of c tanh(z_j + d_j)
+        // O row and G row; sums of c u_j become sums of c tanh(z_j + d_j):
+        // sum c tanh = sigma_j (sum c - 2 sum c u_j)
         double *Orow = A.O + row * (int64_t)A.ldp;
-        double *Grow = A.G + row * (int64_t)A.ldp;
+        double *Grow = GF ? nullptr : A.G + row * (int64_t)A.ldp;
         const df hdg = df_from_double(sDiag);
         auto to_tanh = [&](df s0, df su, int r) {
             const df t = df_sub(s0, df_make(2.f * su.h, 2.f * su.l));
             return sSig[r - 1] < 0.f ? df_neg(t) : t;
         };
-        for (int e = tid; e < A.ldp; e += BDF_THREADS) {
+        // orbital sum p at hidden row r over the slices, in slice order
+        auto osum = [&](int p, int r) {
+            df a = df_make(0.f, 0.f);
+            for (int q = 0; q < A.nsl; ++q) a = df_add(a, df_norm(ld_df(sSg + ((size_t)q * (M + 1) + p) * ldL + r)));
+            return a;
+        };
+        for (int e = tid; e < A.ldp; e += GDF_THREADS) {
             double ov = 0.0, gv = 0.0;
             if (e < A.P1) {
                 const int r = fdiv(e, A.fd_M1), c = e - r * M1;
                 const bool xc = (c == 0) || occ_bit(x, c - 1);
                 ov = xc ? (r == 0 ? 1.0 : sT[r - 1]) : 0.0;
-                df a = ld_df(sAf + r);
-                if (r > 0) a = to_tanh(ld_df(sAf), a, r);
+            }
+            Orow[e] = ov;
+            if (GF) continue;
+            if (e < A.P1) {
+                const int r = fdiv(e, A.fd_M1), c = e - r * M1;
+                df a = osum(M, r);
+                if (r > 0) a = to_tanh(osum(M, 0), a, r);
                 df at = (r == 0) ? hdg : df_mul(hdg, ld_df(sTd + r - 1));
                 at = df_add(at, a);
                 if (c == 0) {
                     gv = df_to_double(at);
                 } else {
-                    df sv = df_make(0.f, 0.f), s0 = df_make(0.f, 0.f);
-                    for (int s2 = 0; s2 < nsl; ++s2) {
-                        sv = df_add(sv, df_norm(ld_df(sS + (s2 * (nh + 1) + r) * A.ldS + c - 1)));
-                        s0 = df_add(s0, df_norm(ld_df(sS + (s2 * (nh + 1)) * A.ldS + c - 1)));
-                    }
-                    if (r > 0) sv = to_tanh(s0, sv, r);
+                    df sv = osum(c - 1, r);
+                    if (r > 0) sv = to_tanh(osum(c - 1, 0), sv, r);
                     gv = df_to_double(occ_bit(x, c - 1) ? df_sub(at, sv) : sv);
                 }
             }
-            Orow[e] = ov;
             Grow[e] = gv;
         }
         __syncthreads();
@@ -1192,10 +1386,10 @@ __global__ void k_centre(double *__restrict__ O, double *__restrict__ G,
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nw) {
         const double el = eloc[r];  // E_loc already includes e_core
-        double *Or = O + r * ldp, *Gr = G + r * ldp;
+        double *Or = O + r * ldp, *Gr = G ? G + r * ldp : nullptr;  // G null: no G'_c
         for (int c = 2 * lane; c < 2 * hp; c += 64) {
             const double2 o = *reinterpret_cast<const double2 *>(Or + c);
-            const double2 g = *reinterpret_cast<const double2 *>(Gr + c);
+            const double2 g = Gr ? *reinterpret_cast<const double2 *>(Gr + c) : make_double2(0.0, 0.0);
             const double2 ob = *reinterpret_cast<const double2 *>(stats + 8 + c);
             double oc[2], gc[2];
             const double ov[2] = {o.x, o.y}, gv[2] = {g.x, g.y}, bv[2] = {ob.x, ob.y};
@@ -1214,11 +1408,9 @@ __global__ void k_centre(double *__restrict__ O, double *__restrict__ G,
                 }
             }
             *reinterpret_cast<double2 *>(Or + c) = make_double2(oc[0], oc[1]);
-            *reinterpret_cast<double2 *>(Gr + c) = make_double2(gc[0], gc[1]);
-            if (Olo) {
-                store_low2<TL>(Olo + r * ldp + c, oc[0], oc[1]);
-                store_low2<TL>(Glo + r * ldp + c, gc[0], gc[1]);
-            }
+            if (Gr) *reinterpret_cast<double2 *>(Gr + c) = make_double2(gc[0], gc[1]);
+            if (Olo) store_low2<TL>(Olo + r * ldp + c, oc[0], oc[1]);
+            if (Glo) store_low2<TL>(Glo + r * ldp + c, gc[0], gc[1]);
         }
         if (lane == 0) {
             const double wn = wt[r] * isw;
@@ -1246,10 +1438,10 @@ __global__ void k_centre_df(const double *__restrict__ O, const double *__restri
     for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nw) {
         const df el = df_split_bits(eloc[r]);  // E_loc already includes e_core
         const df g0 = df_sub(el, E);
-        const double *Or = O + r * ldp, *Gr = G + r * ldp;
+        const double *Or = O + r * ldp, *Gr = G ? G + r * ldp : nullptr;  // G null: no G'_c
         for (int c = 2 * lane; c < 2 * hp; c += 64) {
             const double2 o = *reinterpret_cast<const double2 *>(Or + c);
-            const double2 g = *reinterpret_cast<const double2 *>(Gr + c);
+            const double2 g = Gr ? *reinterpret_cast<const double2 *>(Gr + c) : make_double2(0.0, 0.0);
             const double2 ob = *reinterpret_cast<const double2 *>(stats + 8 + c);
             df oc[2], gc[2];
             const double ov[2] = {o.x, o.y}, gv[2] = {g.x, g.y}, bv[2] = {ob.x, ob.y};
@@ -1269,7 +1461,8 @@ __global__ void k_centre_df(const double *__restrict__ O, const double *__restri
                 }
             }
             *reinterpret_cast<float4 *>(Olo + r * ldp + c) = make_float4(oc[0].h, oc[0].l, oc[1].h, oc[1].l);
-            *reinterpret_cast<float4 *>(Glo + r * ldp + c) = make_float4(gc[0].h, gc[0].l, gc[1].h, gc[1].l);
+            if (Glo)
+                *reinterpret_cast<float4 *>(Glo + r * ldp + c) = make_float4(gc[0].h, gc[0].l, gc[1].h, gc[1].l);
         }
         if (lane == 0) {
             const double wn = wt[r] * isw;
@@ -1425,6 +1618,99 @@ static size_t build_smem_bytes(int nh, int M, int ldF, int ldS, int nslice) {
     return d * sizeof(double) + BUILD_THREADS * sizeof(int4) + sizeof(RowLists) + 64;
 }
 
+// The double-float row build by connection class (k_build_rows_dg): class
+// shapes, target table, scatter slices, shared-memory map and launch.
+static int launch_build_grid(lm_pencil *p, const BuildArgs &A, cudaStream_t s) {
+    lm_ctx *ctx = p->ctx;
+    GridDfArgs G;
+    G.S = A.S;
+    G.nh = p->nh;
+    G.M = p->M;
+    G.M1 = p->M1;
+    G.P1 = p->P1;
+    G.ldp = p->ldp;
+    G.ldA = p->nh | 1;
+    G.ldF = (p->nh + 1) | 1;
+    G.ldL = (p->nh + 1) | 1;
+    G.ns = A.S.ns_a + A.S.ns_b;
+    const SysView &S = A.S;
+    G.R[GC_AA] = S.na * (S.na - 1) / 2;
+    G.C[GC_AA] = S.nva * (S.nva - 1) / 2;
+    G.R[GC_BB] = S.nb * (S.nb - 1) / 2;
+    G.C[GC_BB] = S.nvb * (S.nvb - 1) / 2;
+    G.R[GC_B] = S.nb;
+    G.C[GC_B] = S.nvb;
+    G.R[GC_AB] = S.ns_a;
+    G.C[GC_AB] = S.ns_b + 1;
+    int ntgt = 0;
+    for (int c = 0; c < GC_N; ++c) {
+        G.toff[c] = ntgt;
+        ntgt += G.R[c] + G.C[c];
+        G.fdC[c] = make_fastdiv(std::max(1, G.C[c]));
+    }
+    G.ntgt = ntgt;
+    G.fd_nh = make_fastdiv(p->nh);
+    G.fd_nh1 = make_fastdiv(p->nh + 1);
+    G.fd_M1 = make_fastdiv(p->M1);
+    G.ntab = std::max(1, std::max(S.ns_a, S.ns_b));
+    G.narow = (GDF_K + G.C[GC_AB] - 2) / G.C[GC_AB] + 1;
+    G.theta = p->theta;
+    G.tdf = p->tdf;
+    G.rows = p->rows;
+    G.n_rows = p->n_rows;
+    G.amask = A.amask;
+    G.bmask = A.bmask;
+    G.e_core = p->e_core;
+    G.lnpsi = p->lnpsi;
+    G.eloc = p->eloc;
+    G.O = p->O;
+    G.G = p->G;
+    G.flags = p->d_flags;
+    G.gfree = p->gfree;
+    // 228 KB of shared memory per SM, 1 KB of it reserved per CTA. Scatter slices
+    // q against CTAs per SM: the most CTAs x min(q, 3), then the most slices.
+    // Measured (ms per build): F2-shaped rows q = 1..6 at 4,4,4,3,3,2 CTAs/SM:
+    // 4.06, 3.21, 2.80, 3.13, 3.09, 3.55; LiCl-shaped (65,536 rows) q = 1..4 at
+    // 3,2,2,2: 111.9, 106.3, 93.1, 84.0.
+    auto per_sm_of = [&](size_t bytes) { return (int)(233472 / (bytes + 1024 + 64)); };
+    const int max_sl = std::max(1, GDF_THREADS / (p->nh + 1));
+    int best = 1, best_key = -1;
+    for (int q = 1; q <= max_sl; ++q) {
+        G.nsl = q;
+        const size_t b = grid_smem(G).total;
+        if (b > (size_t)ctx->smem_optin) break;
+        const int key = (std::min(4, per_sm_of(b)) * std::min(q, 3)) * 16 + q;
+        if (key > best_key) {
+            best_key = key;
+            best = q;
+        }
+    }
+    // IRLNQS_BUILD_SLICES overrides the choice (tuning runs)
+    if (const char *env = getenv("IRLNQS_BUILD_SLICES")) {
+        const int q = atoi(env);
+        if (q >= 1 && q <= max_sl) best = q;
+    }
+    G.nsl = p->gfree ? 0 : best;
+    const size_t dsm = grid_smem(G).total;
+    if (dsm > (size_t)ctx->smem_optin)
+        return lm_fail(ctx, LM_ERR_SIZE, "df64 build kernel needs %zu B shared memory", dsm);
+    auto kern = p->gfree ? k_build_rows_dg<true> : k_build_rows_dg<false>;
+    cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    if (e2 != cudaSuccess) return lm_cuda_check(ctx, e2, "df64 build smem attribute");
+    int per_sm = std::max(1, per_sm_of(dsm));
+    per_sm = std::min(per_sm, 4);
+    int64_t grid = std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * per_sm);
+    // many rows per resident CTA: one CTA per row instead, so that other streams'
+    // kernels can be scheduled as rows finish
+    if (p->n_rows > 64 * grid) grid = std::min<int64_t>(p->n_rows, 0x7fffffff);
+    if (grid < 1) grid = 1;
+    lm_prof_begin(ctx, PROF_BUILD, s);
+    kern<<<(unsigned)grid, GDF_THREADS, dsm, s>>>(G);
+    lm_prof_end(ctx, PROF_BUILD, s);
+    lm_note_launch(ctx);
+    return lm_cuda_check(ctx, cudaGetLastError(), "k_build_rows_dg");
+}
+
 int lm_launch_build(lm_pencil *p, cudaStream_t s) {
     if (int rc = lm_launch_build_rows(p, s)) return rc;
     return lm_launch_build_prep(p, s);
@@ -1489,92 +1775,7 @@ int lm_launch_build_rows(lm_pencil *p, cudaStream_t s) {
                                                                        p->nh, n, p->tdf);
         lm_note_launch(ctx);
         if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_tables_df")) return rc;
-        BuildDfArgs B;
-        B.S = A.S;
-        B.nh = A.nh;
-        B.M = A.M;
-        B.M1 = A.M1;
-        B.P1 = A.P1;
-        B.ldp = A.ldp;
-        B.ldF = p->nh | 1;
-        B.ldS = p->M | 1;
-        B.nslice = std::max(1, BDF_THREADS / (p->nh + 1));
-        B.ns = A.S.ns_a + A.S.ns_b;
-        B.fd_nh = make_fastdiv(p->nh);
-        B.fd_M1 = make_fastdiv(p->M1);
-        B.fuseB = 0;
-        B.theta = p->theta;
-        B.tdf = p->tdf;
-        B.rows = p->rows;
-        B.n_rows = p->n_rows;
-        B.amask = A.amask;
-        B.bmask = A.bmask;
-        B.e_core = p->e_core;
-        B.lnpsi = p->lnpsi;
-        B.eloc = p->eloc;
-        B.O = p->O;
-        B.G = p->G;
-        B.flags = p->d_flags;
-        const size_t nh_ = p->nh, M_ = p->M;
-        auto smem_of = [&](int fuse, int nsl) {
-            const size_t f2 = (size_t)(fuse ? 1 : 2) * B.ns * (nh_ | 1) + 2 * B.ns + nh_ +
-                              (size_t)BDF_K * B.ldF + BDF_K + (size_t)nsl * (nh_ + 1) * B.ldS +
-                              (size_t)nsl * (nh_ + 1) + BDF_THREADS / 32 + nh_ + 1;
-            return BDF_K * sizeof(int4) + sizeof(RowLists) +
-                   f2 * sizeof(float2) + (3 * nh_ + 2 * M_) * sizeof(double) +
-                   nh_ * (sizeof(float2) + sizeof(float)) + B.ns * sizeof(int) + 64;
-        };
-        // Pick the layout with the most CTAs per SM up to three (enough to hide
-        // the phases' barriers behind each other), then the A table kept
-        // (dropping it costs one more double-float product per connection and
-        // hidden unit), then the most scatter slices. Per CTA the SM also holds
-        // 1 KB of reserved and a few bytes of static shared memory. Measured on
-        // the F2-shaped rows: 3 slices with the A table at 3 CTAs/SM 3.22 ms,
-        // 2 slices without it at 4 CTAs/SM 3.28 ms; LiCl-shaped: 2 slices
-        // without it at 2 CTAs/SM 406 ms, 3 or 4 slices at 1 CTA/SM 570-620 ms.
-        auto per_sm_of = [&](size_t bytes) { return (int)(233472 / (bytes + 1024 + 64)); };
-        {
-            int best_fuse = 1, best_nsl = 1, best_key = -1;
-            for (int nsl = 1; nsl <= B.nslice; ++nsl)
-                for (int fuse = 0; fuse <= 1; ++fuse) {
-                    const int sm = std::min(3, per_sm_of(smem_of(fuse, nsl)));
-                    const int key = (sm * 2 + (1 - fuse)) * 256 + nsl;
-                    if (key > best_key) {
-                        best_key = key;
-                        best_fuse = fuse;
-                        best_nsl = nsl;
-                    }
-                }
-            // IRLNQS_BUILD_LAYOUT="slices:fuse" overrides the choice (tuning runs)
-            const char *env = getenv("IRLNQS_BUILD_LAYOUT");
-            int e_nsl = 0, e_fuse = 0;
-            if (env && sscanf(env, "%d:%d", &e_nsl, &e_fuse) == 2 && e_nsl >= 1 &&
-                e_nsl <= B.nslice && (e_fuse == 0 || e_fuse == 1)) {
-                best_nsl = e_nsl;
-                best_fuse = e_fuse;
-            }
-            B.fuseB = best_fuse;
-            B.nslice = best_nsl;
-        }
-        const size_t dsm = smem_of(B.fuseB, B.nslice);
-        if (dsm > (size_t)ctx->smem_optin)
-            return lm_fail(ctx, LM_ERR_SIZE, "df64 build kernel needs %zu B shared memory", dsm);
-        cudaError_t e2 = cudaFuncSetAttribute(k_build_rows_df,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-        if (e2 != cudaSuccess) return lm_cuda_check(ctx, e2, "df64 build smem attribute");
-        int per_sm = std::max(1, per_sm_of(dsm));
-        per_sm = std::min(per_sm, 4);
-        int64_t grid = std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * per_sm);
-        // Many rows per resident CTA: one CTA per row instead, so that the
-        // hardware can schedule other streams' kernels (e.g. small systems of a
-        // server) as rows finish, rather than after the whole build
-        if (p->n_rows > 64 * grid) grid = std::min<int64_t>(p->n_rows, 0x7fffffff);
-        if (grid < 1) grid = 1;
-        lm_prof_begin(ctx, PROF_BUILD, s);
-        k_build_rows_df<<<(unsigned)grid, BDF_THREADS, dsm, s>>>(B);
-        lm_prof_end(ctx, PROF_BUILD, s);
-        lm_note_launch(ctx);
-        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_build_rows_df")) return rc;
+        return launch_build_grid(p, A, s);
     }
 
     return LM_OK;

@@ -179,6 +179,7 @@ struct lm_pencil {
     int given_weights;  // weights from the caller
     int prec;           // low-precision copy kind (LM_FP64 = none)
     int sym;            // resolved default symmetrisation
+    int gfree;          // the E_loc estimator's pencil: O_c, E_loc and weights, no G'_c
     double e_core;
     // device buffers (FP64 unless noted)
     uint64_t *rows;
@@ -252,7 +253,7 @@ int lm_read_flags(lm_ctx *ctx, cudaStream_t s, int *flags);
 int lm_build_enqueue(lm_ctx *ctx, const lm_system *sys, const double *theta,
                      const uint64_t *rows, const double *weights, int64_t n_rows,
                      lm_precision prec, void *stream, lm_pencil **inout, int rows_only = 0,
-                     int64_t chunk_rows = 0);
+                     int64_t chunk_rows = 0, int gfree = 0);
 int lm_build_finish(lm_pencil *p);
 size_t lm_pencil_footprint(lm_ctx *ctx, int n, int nh, int64_t n_rows, int prec);
 // Staging regions: h at 0, eri after it, theta after that (ldp doubles), rows

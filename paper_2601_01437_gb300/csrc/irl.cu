@@ -1634,6 +1634,8 @@ int irl_job_create(lm_pencil *p, const irl_params *prm, double *c_out, double *d
         return lm_fail(ctx, LM_ERR_ARG,
                        "block = 16 needs m in {16, 32, 48, 64}, a BF16 pencil, precision BF16 "
                        "and no row shards");
+    if (p->gfree && ((prm->sym != LM_SYM_AUTO && prm->sym != LM_SYM_ELOC) || prm->block))
+        return lm_fail(ctx, LM_ERR_ARG, "a pencil without G'_c answers the E_loc estimator only");
     IrlJob *J = new IrlJob();
     J->p = p;
     J->s = s;
