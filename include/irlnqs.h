@@ -164,9 +164,24 @@ typedef struct {
 
 /* ---- context ----------------------------------------------------------- */
 
+/* Context options. struct_size = sizeof(lm_ctx_params) as the caller compiled
+ * it (later versions may append fields; fields beyond struct_size keep their
+ * defaults). */
+typedef struct {
+    unsigned struct_size;
+    int profile;    /* 1: time the kernel classes with CUDA events from the start
+                       (as lm_stats_reset(ctx, 1)); 0: count launches only    */
+    double hbm_gbs; /* streaming rate in GB/s that the grid autotuner of the batch
+                       and server engines assumes (its cost model charges each
+                       product max(compute, bytes / rate)); 0: 85 % of the
+                       device's interface peak (memory clock x bus width)     */
+} lm_ctx_params;
+
 /* Create a context on CUDA device `device` (made current for every call).
- * *out receives the handle; free it with lm_destroy. */
-int lm_create(lm_ctx **out, int device);
+ * params may be NULL (all defaults). *out receives the handle; free it with
+ * lm_destroy. Errors: LM_ERR_CUDA (no such device), LM_ERR_ARG (struct_size
+ * smaller than the first two fields, negative hbm_gbs), LM_ERR_OOM. */
+int lm_create(lm_ctx **out, int device, const lm_ctx_params *params);
 int lm_destroy(lm_ctx *ctx);
 /* Description of the last failure on ctx (never NULL; "" after success). */
 const char *lm_last_error(const lm_ctx *ctx);

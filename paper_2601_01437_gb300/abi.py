@@ -30,6 +30,10 @@ c_int, c_double, c_int64, c_uint64, c_vp = (ctypes.c_int, ctypes.c_double, ctype
                                             ctypes.c_uint64, ctypes.c_void_p)
 
 
+class lm_ctx_params(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint), ("profile", c_int), ("hbm_gbs", ctypes.c_double)]
+
+
 class lm_system(ctypes.Structure):
     _fields_ = [("n_orb", c_int), ("n_alpha", c_int), ("n_beta", c_int), ("n_hidden", c_int),
                 ("h", c_vp), ("eri", c_vp), ("e_core", c_double), ("build_arith", c_int)]
@@ -81,7 +85,7 @@ REDUCE_FN = ctypes.CFUNCTYPE(c_int, c_vp, c_int, c_vp, c_vp)
 _lib = None
 
 _SIGNATURES = {
-    "lm_create": (c_int, [ctypes.POINTER(c_vp), c_int]),
+    "lm_create": (c_int, [ctypes.POINTER(c_vp), c_int, c_vp]),
     "lm_destroy": (c_int, [c_vp]),
     "lm_last_error": (ctypes.c_char_p, [c_vp]),
     "lm_build_OG": (c_int, [c_vp, ctypes.POINTER(lm_system), c_vp, c_vp, c_vp, c_int64, c_int,
@@ -190,9 +194,10 @@ def apply_pencil_noalloc(O_c, G_c, w, n_rows, ld, p1, v, Hv=None, Sv=None, sym=L
 class Context:
     """lm_create / lm_destroy."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, profile: bool = False, hbm_gbs: float = 0.0):
         h = c_vp()
-        rc = lib().lm_create(ctypes.byref(h), device)
+        prm = lm_ctx_params(ctypes.sizeof(lm_ctx_params), int(profile), float(hbm_gbs))
+        rc = lib().lm_create(ctypes.byref(h), device, ctypes.byref(prm))
         if rc != LM_OK:
             raise LMError(rc, f"lm_create(device={device}) failed")
         self.handle = h

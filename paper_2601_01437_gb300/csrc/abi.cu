@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 
 #include "internal.cuh"
@@ -136,9 +137,16 @@ int check_system(lm_ctx *ctx, const lm_system *sys) {
 }  // namespace
 
 // ---------------------------------------------------------------- context
-extern "C" int lm_create(lm_ctx **out, int device) {
+extern "C" int lm_create(lm_ctx **out, int device, const lm_ctx_params *params) {
     if (!out) return LM_ERR_ARG;
     *out = nullptr;
+    // the caller's view of the options, fields it did not compile in at their defaults
+    lm_ctx_params prm = {sizeof(lm_ctx_params), 0, 0.0};
+    if (params) {
+        if (params->struct_size < offsetof(lm_ctx_params, hbm_gbs)) return LM_ERR_ARG;
+        std::memcpy(&prm, params, std::min<size_t>(params->struct_size, sizeof(prm)));
+        if (!(prm.hbm_gbs >= 0.0)) return LM_ERR_ARG;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -155,13 +163,19 @@ extern "C" int lm_create(lm_ctx **out, int device) {
         int khz = 0, bits = 0;
         cudaDeviceGetAttribute(&khz, cudaDevAttrMemoryClockRate, device);
         cudaDeviceGetAttribute(&bits, cudaDevAttrGlobalMemoryBusWidth, device);
-        c->hbm_bytes_per_ms = 0.85 * 2.0 * (double)khz * (bits / 8);
+        c->hbm_bytes_per_ms = prm.hbm_gbs > 0.0 ? prm.hbm_gbs * 1e6
+                                                : 0.85 * 2.0 * (double)khz * (bits / 8);
     }
     cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_flags, 0, sizeof(int)) != cudaSuccess) {
         delete c;
         return LM_ERR_OOM;
+    }
+    if (prm.profile && lm_stats_reset(c, 1) != LM_OK) {
+        cudaFree(c->d_flags);
+        delete c;
+        return LM_ERR_CUDA;
     }
     *out = c;
     return LM_OK;

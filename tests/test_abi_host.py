@@ -46,6 +46,7 @@ int main(void) {
   printf("%zu %zu\\n", sizeof(lm_stats), offsetof(lm_stats, tri_count));
   printf("%zu %zu %zu %zu %zu\\n", sizeof(lm_batch_item), offsetof(lm_batch_item, irl), offsetof(lm_batch_item, theta_inout), sizeof(lm_response), offsetof(lm_response, t_done_ms));
   printf("%zu %zu\\n", sizeof(lm_pencil_info), offsetof(lm_pencil_info, grid));
+  printf("%zu %zu\\n", sizeof(lm_ctx_params), offsetof(lm_ctx_params, hbm_gbs));
   return 0; }
 """)
     exe = tmp_path / "layout"
@@ -60,7 +61,8 @@ int main(void) {
             ctypes.sizeof(lib.lm_batch_item), lib.lm_batch_item.irl.offset,
             lib.lm_batch_item.theta_inout.offset, ctypes.sizeof(lib.lm_response),
             lib.lm_response.t_done_ms.offset,
-            ctypes.sizeof(lib.lm_pencil_info), lib.lm_pencil_info.grid.offset]
+            ctypes.sizeof(lib.lm_pencil_info), lib.lm_pencil_info.grid.offset,
+            ctypes.sizeof(lib.lm_ctx_params), lib.lm_ctx_params.hbm_gbs.offset]
     assert [int(x) for x in out] == want
 
 

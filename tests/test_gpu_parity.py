@@ -614,3 +614,19 @@ def test_error_paths(ctx, abi):
         pen.irl_step(m=10, k=10)
     assert e.value.code == abi.LM_ERR_SIZE
     pen.free()
+
+
+def test_context_params(abi):
+    """lm_create's options: profiling from the start (the build's kernel time is recorded
+    without an lm_stats_reset), the autotuner's HBM rate, and the refusals."""
+    c = abi.Context(0, profile=True, hbm_gbs=6000.0)
+    w = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, th, _, _ = w.inputs()
+    pen = c.build_OG(c.system(6, 3, 3, 24, h, eri), th)
+    st = c.stats()
+    assert st.build_count >= 1 and st.build_ms > 0.0
+    pen.free()
+    c.close()
+    with pytest.raises(abi.LMError) as e:
+        abi.Context(0, hbm_gbs=-1.0)
+    assert e.value.code == abi.LM_ERR_ARG
