@@ -116,6 +116,7 @@ void pencil_release(lm_pencil *p) {
     for (void *b : bufs)
         if (b) cudaFree(b);
     lm_block_release(p);
+    lm_cycle_graphs_release(p);
     if (p->hs) cudaFreeHost(p->hs);
     if (p->hstage) cudaFreeHost(p->hstage);
     delete p;

@@ -20,6 +20,7 @@
 // grid and leaves the other SMs to other instances.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -30,6 +31,13 @@
 #include "internal.cuh"
 
 namespace {
+
+// Pencils of the engines replay captured IRL cycles (irl.cu) unless
+// IRLNQS_CYCLE_GRAPHS=0 (for timing the launch path against them).
+int cycle_graphs_on() {
+    const char *e = getenv("IRLNQS_CYCLE_GRAPHS");
+    return !(e && e[0] == '0');
+}
 
 double now_ms() {
     using namespace std::chrono;
@@ -176,6 +184,7 @@ extern "C" int lm_batch_run(lm_batch *b, int n, const lm_batch_item *items, irl_
         I.fresh = p == nullptr;
         int rc = lm_build_enqueue(ctx, &it.sys, it.theta, it.rows, it.weights, it.n_rows,
                                   (lm_precision)it.precision, I.s, &p);
+        if (!rc) p->cycle_graphs = cycle_graphs_on();
         if (!rc) rc = lm_cuda_check(ctx, cudaEventRecord(I.ev, I.s), "event");
         if (rc) fail(I, rc);
     }
@@ -434,6 +443,7 @@ int server_admit(lm_server *v, Req *q, int stream) {
                               r.weights.empty() ? nullptr : r.weights.data(), r.n_rows,
                               (lm_precision)r.prec, s, &r.p);
     if (rc && fresh && !r.p) v->resident -= r.footprint;
+    if (!rc) r.p->cycle_graphs = cycle_graphs_on();
     q->stream = stream;
     v->stream_busy[stream] = true;
     r.busy = true;

@@ -14,6 +14,17 @@
 #define LM_MAXH 256     // hidden units
 #define LM_MAXKRYLOV 64 // Krylov dimension
 #define LM_HIST_MAX 1024 // IRL cycles recorded per solve (lm_irl_history)
+// Captured IRL cycles kept per pencil (keyed by first step, Krylov dimension and
+// everything the captured launches take by value), least recently used replaced.
+#define LM_CYCLE_GRAPHS 8
+#define LM_CYCLE_KEY 12
+struct CycleGraph {
+    int key[LM_CYCLE_KEY];
+    cudaGraphExec_t exec;
+    int kernels;    // kernel nodes (launch counter per replay)
+    long long used; // last use, for replacement
+};
+void lm_cycle_graphs_release(lm_pencil *p);
 
 // Bound on polls of one mbarrier phase before a kernel gives up (each
 // try_wait may itself suspend for a short, hardware-defined time).
@@ -131,6 +142,17 @@ struct lm_ctx {
 enum { PROF_BUILD = 0, PROF_PENCIL = 1, PROF_LANCZOS = 2, PROF_PREP = 3, PROF_TRI = 4 };
 
 inline void lm_note_launch(lm_ctx *ctx, int n = 1) { ctx->launches += n; }
+
+// The largest dynamic shared memory a launch of func may request on this device:
+// the opt-in limit less the kernel's static shared memory.
+inline int lm_max_dyn_smem(const void *func, int smem_optin) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return smem_optin - (int)fa.sharedSizeBytes;
+}
 // Event pair around one launch of a profiled kernel class (no-op unless profiling).
 inline void lm_prof_begin(lm_ctx *ctx, int cls, cudaStream_t s) {
     if (!ctx->profile || !ctx->ev_ready) return;
@@ -180,6 +202,8 @@ struct lm_pencil {
     int prec;           // low-precision copy kind (LM_FP64 = none)
     int sym;            // resolved default symmetrisation
     int gfree;          // the E_loc estimator's pencil: O_c, E_loc and weights, no G'_c
+    int cycle_graphs;   // 1: IRL cycles on this pencil replay captured CUDA graphs
+    struct CycleGraph *cg;  // [LM_CYCLE_GRAPHS] captured cycles (irl.cu), or null
     double e_core;
     // device buffers (FP64 unless noted)
     uint64_t *rows;

@@ -1415,11 +1415,11 @@ int lanczos_vectors(Run &R, int j) {
         cfg.dynamicSmemBytes = cluster_dyn_smem(j + 1, R.cluster_emax);
         cfg.stream = R.s;
         // The limit is an attribute of the kernel, shared by every pencil whose
-        // jobs may be in flight at once (batches, the server): set it to this
-        // launch's size right before the launch (all launches come from one
-        // host thread).
+        // jobs may be in flight at once (batches, the server) and read again when
+        // a captured cycle replays this launch: the device maximum.
+        const int dmax = lm_max_dyn_smem((const void *)k_lz_cluster, p->ctx->smem_optin);
         if (cudaFuncSetAttribute(k_lz_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cfg.dynamicSmemBytes) != cudaSuccess)
+                                 std::max(dmax, (int)cfg.dynamicSmemBytes)) != cudaSuccess)
             return lm_cuda_check(p->ctx, cudaGetLastError(), "cluster smem attribute");
         cfg.attrs = at;
         cfg.numAttrs = 1;
@@ -1502,11 +1502,107 @@ int job_readback(IrlJob *J) {
     return lm_cuda_check(p->ctx, e, "IRL state read-back");
 }
 
+// Captured cycles. The Lanczos steps j0 .. m-1 of a cycle are the same launches
+// with the same arguments every time a pencil runs that cycle (the pencil's
+// buffers are rebuilt in place), so a pencil with cycle_graphs set captures
+// them once into a CUDA graph and replays it: one graph launch instead of one
+// to five kernel launches per step, the same kernels in the same order, so the
+// same results bit for bit. Not for row shards (a host reduction between the
+// launches) or streamed pencils.
+void cycle_key(const Run &R, int j0, int *key) {
+    const lm_pencil *p = R.p;
+    const int k[LM_CYCLE_KEY] = {j0,           R.m,         R.prec,          R.sym,
+                                 R.lz_mode,    R.cluster,   R.la.nparts,     R.la.deflate,
+                                 R.la.three_term, p->g_pencil, R.cluster_emax, 0};
+    std::memcpy(key, k, sizeof(k));
+}
+
+// Launch the captured cycle (capturing it first if needed); *used = false when
+// this pencil does not take captured cycles.
+int cycle_graph(IrlJob *J, int j0, bool *used) {
+    Run &R = J->R;
+    lm_pencil *p = J->p;
+    lm_ctx *ctx = p->ctx;
+    *used = false;
+    if (!p->cycle_graphs || R.reduce || p->chunk || j0 >= R.m) return LM_OK;
+    if (!p->cg) {
+        p->cg = new CycleGraph[LM_CYCLE_GRAPHS];
+        std::memset(p->cg, 0, sizeof(CycleGraph) * LM_CYCLE_GRAPHS);
+    }
+    int key[LM_CYCLE_KEY];
+    cycle_key(R, j0, key);
+    CycleGraph *slot = nullptr, *victim = &p->cg[0];
+    for (int i = 0; i < LM_CYCLE_GRAPHS; ++i) {
+        CycleGraph &c = p->cg[i];
+        if (c.exec && !std::memcmp(c.key, key, sizeof(key))) slot = &c;
+        if (!c.exec || (victim->exec && c.used < victim->used)) victim = &c;
+    }
+    if (!slot) {
+        // capture: no event records (profiling off), the launch counter kept for
+        // the first replay below
+        const int prof = ctx->profile;
+        const long long launches = ctx->launches;
+        const int nmv = R.n_matvec;
+        ctx->profile = 0;
+        cudaError_t e = cudaStreamBeginCapture(R.s, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            ctx->profile = prof;
+            return lm_cuda_check(ctx, e, "cycle capture");
+        }
+        int rc = LM_OK;
+        for (int j = j0; j < R.m && !rc; ++j) rc = lanczos_step(R, j);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(R.s, &g);
+        ctx->profile = prof;
+        ctx->launches = launches;
+        R.n_matvec = nmv;
+        if (rc || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc ? rc : lm_cuda_check(ctx, e ? e : cudaErrorUnknown, "cycle capture");
+        }
+        size_t n = 0;
+        cudaGraphGetNodes(g, nullptr, &n);
+        int kernels = 0;
+        if (n) {
+            cudaGraphNode_t *nodes = new cudaGraphNode_t[n];
+            cudaGraphGetNodes(g, nodes, &n);
+            for (size_t i = 0; i < n; ++i) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess &&
+                    t == cudaGraphNodeTypeKernel)
+                    ++kernels;
+            }
+            delete[] nodes;
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return lm_cuda_check(ctx, e, "cycle graph instantiate");
+        if (victim->exec) cudaGraphExecDestroy(victim->exec);
+        slot = victim;
+        std::memcpy(slot->key, key, sizeof(key));
+        slot->exec = ex;
+        slot->kernels = kernels;
+    }
+    long long top = 0;
+    for (int i = 0; i < LM_CYCLE_GRAPHS; ++i) top = std::max(top, p->cg[i].used);
+    slot->used = top + 1;
+    if (int rc = lm_cuda_check(ctx, cudaGraphLaunch(slot->exec, R.s), "cycle graph launch"))
+        return rc;
+    lm_note_launch(ctx, slot->kernels);
+    R.n_matvec += R.m - j0;
+    *used = true;
+    return LM_OK;
+}
+
 // Lanczos steps j0 .. m-1 and the tridiagonal work of one cycle
 int job_cycle(IrlJob *J, int j0) {
     Run &R = J->R;
     lm_pencil *p = J->p;
-    for (int j = j0; j < R.m; ++j)
+    bool captured = false;
+    if (int rc = cycle_graph(J, j0, &captured)) return rc;
+    for (int j = j0; j < R.m && !captured; ++j)
         if (int rc = lanczos_step(R, j)) return rc;
     TriArgs ta;
     ta.st = p->st;
@@ -1898,4 +1994,12 @@ extern "C" int lm_debug_wait_timeout(lm_ctx *ctx, int which, int64_t limit_ns) {
     if (flags & FLAG_TIMEOUT)
         return lm_fail(ctx, LM_ERR_TIMEOUT, "the bounded wait gave up (as the test intends)");
     return LM_OK;
+}
+
+void lm_cycle_graphs_release(lm_pencil *p) {
+    if (!p || !p->cg) return;
+    for (int i = 0; i < LM_CYCLE_GRAPHS; ++i)
+        if (p->cg[i].exec) cudaGraphExecDestroy(p->cg[i].exec);
+    delete[] p->cg;
+    p->cg = nullptr;
 }

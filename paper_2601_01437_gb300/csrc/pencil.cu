@@ -490,8 +490,12 @@ int launch_t(lm_pencil *p, const T *O, const T *G, const double *v, double *out,
     a.flags = p->d_flags;
     a.out_df = out_df;
     a.reverse = p->order_rev;
+    // the device maximum rather than this launch's size: the attribute is shared
+    // by every pencil and read again when a captured IRL cycle replays the launch
+    const int dmax = lm_max_dyn_smem((const void *)k_pencil<T, NJ, MODE>, p->ctx->smem_optin);
     cudaError_t e = cudaFuncSetAttribute(k_pencil<T, NJ, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         std::max(dmax, (int)smem));
     if (e != cudaSuccess) return lm_cuda_check(p->ctx, e, "pencil smem attribute");
     lm_prof_begin(p->ctx, PROF_PENCIL, s);
     const int grid = lm_pencil_ctas(p, std::is_same<T, double>::value ? (int)LM_FP64 : p->prec);
@@ -611,8 +615,10 @@ int raw_launch(const double *O, const double *G, const double *w, int64_t n_rows
     a.flags = flags;
     a.out_df = 0;
     a.reverse = 0;
-    if (cudaFuncSetAttribute(k_pencil<double, NJ, MODE>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    // the device maximum (see launch_t): captured IRL cycles replay these kernels
+    const int dmax = lm_max_dyn_smem((const void *)k_pencil<double, NJ, MODE>, smem_optin);
+    if (cudaFuncSetAttribute(k_pencil<double, NJ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             std::max(dmax, (int)smem)) != cudaSuccess)
         return LM_ERR_CUDA;
     k_pencil<double, NJ, MODE><<<grid, NCW * 32 + 32, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;

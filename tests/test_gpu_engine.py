@@ -89,6 +89,41 @@ def test_batch_equals_solo_and_oracle(abi, ctx):
     b.free()
 
 
+def test_batch_restarts_replay_captured_cycles(abi, ctx):
+    """Short Krylov spaces (m = 8, k = 3) force implicit restarts: the batch engine runs
+    every cycle as a captured CUDA graph (the first cycle from j = 0, restarted ones from
+    j = k), replayed across cycles and across two runs. Results are bit-identical to the
+    same instance solved alone by direct launches, restarts and all."""
+    idx = SMALL[:3]
+    b = abi.Batch(ctx, n_streams=2, autotune=False)
+    results = []
+    for _ in range(2):
+        items = _items(abi, ctx, idx, abi.LM_FP64)
+        for it in items:
+            it["irl"] = abi.irl_settings(m=8, k=3, tol=1e-12, prec=abi.LM_FP64)
+        res, grids = b.run(items)
+        results.append((res, items, grids))
+    for k, i in enumerate(idx):
+        w = INSTANCES[i]
+        r1, r2 = results[0][0][k], results[1][0][k]
+        assert r1.status in (abi.IRL_OK, abi.IRL_BREAKDOWN_INVARIANT), (w.name, r1.status)
+        assert r1.n_restart >= 1, w.name
+        assert r2.lambda_ == r1.lambda_ and r2.n_restart == r1.n_restart
+        h, eri, th = _inputs(w)
+        sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri)
+        pen = ctx.build_OG(sysd, th, prec=abi.LM_FP64)
+        pen.set_grid(results[0][2][k])
+        dth = np.zeros(w.n_params)
+        solo = pen.irl_step(m=8, k=3, tol=1e-12, max_restarts=200, prec=abi.LM_FP64,
+                            dtheta_out=dth)
+        pen.free()
+        assert solo.lambda_ == r1.lambda_ and solo.n_restart == r1.n_restart, w.name
+        assert np.array_equal(dth, results[0][1][k]["dtheta_out"]), w.name
+        ref = lm.lm_step(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th, None, None)
+        assert abs(r1.lambda_ - ref["lam"]) <= 1e-10 * max(1.0, abs(ref["lam"])), w.name
+    b.free()
+
+
 def test_batch_fp64_storage_matches_oracle(abi, ctx):
     b = abi.Batch(ctx, n_streams=2, autotune=False)
     items = _items(abi, ctx, SMALL[:3], abi.LM_FP64)
