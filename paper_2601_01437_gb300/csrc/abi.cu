@@ -112,7 +112,7 @@ void pencil_release(lm_pencil *p) {
                     p->Glo,  p->h,    p->eri,   p->theta, p->tabs, p->stats, p->part,
                     p->V,    p->wvec, p->yvec,  p->hy,   p->sy,   p->tvec, p->dots,
                     p->st,   p->tdf,  p->wlo, p->wel, p->wello, p->bar, p->shv, p->blz,
-                    p->cstats};
+                    p->cstats, p->rt, p->rt64, p->psim, p->psie};
     for (void *b : bufs)
         if (b) cudaFree(b);
     lm_block_release(p);

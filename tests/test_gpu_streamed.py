@@ -1,8 +1,12 @@
 """Streamed pencils (lm_build_streamed): O_c and G'_c rebuilt chunk by chunk inside every
 product, against the resident pencil of lm_build_OG and the FP64 oracle.
 
-Bars: products equal the resident pencil's to 1e-12 relative with FP64-accurate factors
-(only the summation order differs), FP32 copies to 1e-6; energy to 1e-13; the IRL
+Bars: ln psi, the rows and (up to the weights' normaliser) the weights equal the resident
+pencil's; E_loc equals it to 1e-12 of each entry's condition scale (a resident sector pencil
+reads its connections' psi and tanh z_j from per-determinant tables, a streamed one forms
+them per connection: the same terms in another order); products equal the resident
+pencil's to 1e-12 relative with FP64-accurate factors, FP32 copies to 1e-6; energy to
+1e-13; the IRL
 eigenvalue to 1e-10 of the oracle's (FP64-accurate factors) or within 1e-9 Ha after the
 FP64 continuation (FP32 factors)."""
 import numpy as np
@@ -11,6 +15,7 @@ import pytest
 import __graft_entry__ as entry
 import synth
 from oracle import lm
+from parity_tools import componentwise
 
 pytestmark = pytest.mark.gpu
 
@@ -60,8 +65,13 @@ def _pair(ctx, abi, name, prec, arith=0):
 def test_streamed_products_equal_resident(ctx, abi, name, prec, arith):
     w, h, eri, th, rows, cnt, full, st = _pair(ctx, abi, name, prec, arith)
     assert st.info().energy == pytest.approx(full.info().energy, rel=1e-13)
-    for what in (abi.EXPORT_LNPSI, abi.EXPORT_ELOC, abi.EXPORT_ROWS):
+    for what in (abi.EXPORT_LNPSI, abi.EXPORT_ROWS):
         assert np.array_equal(st.export(what), full.export(what))
+    pd = lm.build_pencil(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th, rows, cnt)
+    AE, _, _ = lm.condition_scales(pd, w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th,
+                                   union_occ=True)
+    componentwise(st.export(abi.EXPORT_ELOC), full.export(abi.EXPORT_ELOC), AE, 1e-12,
+                  "E_loc, streamed vs resident")
     assert _rel(st.export(abi.EXPORT_W), full.export(abi.EXPORT_W)) <= 1e-13
     P1 = w.n_params + 1
     rng = np.random.default_rng(4)
