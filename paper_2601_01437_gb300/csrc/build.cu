@@ -635,6 +635,7 @@ struct GridDfArgs {
     int ldL;   // stride of an orbital-sum row (odd, >= nh + 1)
     int ns;    // singles, alpha then beta
     int nsl;   // scatter slices (each with its own orbital sums; 0 without G)
+    int sw;    // threads per scatter slice: n_hidden + 1 rounded up to whole warps
     int gfree; // no G row: O, ln psi and E_loc only (the E_loc estimator's build)
     int lookup; // rows are the sector in enumeration order: read k_row_tables' tables
     const float2 *rt;   // [n_rows][nh] tanh z_j per row (lookup)
@@ -659,8 +660,8 @@ struct GridDfArgs {
 
 // Byte offsets of the dynamic shared memory (host and device use the same map).
 struct GridSmem {
-    size_t lists, tgt, tab, F, Sg, arow, ones, V, Hs, Td, Gd, Red, T, Z, L1, Cs, Ve, Sgn, Pi, Sig,
-        binom, rk, total;
+    size_t lists, tgt, tab, F, ix, Sg, arow, ones, V, Hs, Td, Gd, Red, T, Z, L1, Cs, Ve, Sgn, Pi,
+        Sig, binom, rk, total;
 };
 __host__ __device__ inline GridSmem grid_smem(const GridDfArgs &A) {
     GridSmem g;
@@ -674,7 +675,9 @@ __host__ __device__ inline GridSmem grid_smem(const GridDfArgs &A) {
     g.lists = take(sizeof(RowLists));
     g.tgt = take((size_t)A.ntgt * sizeof(int2));
     g.tab = take((size_t)A.ntab * A.ldA * 8);
-    g.F = take(A.gfree ? 0 : (size_t)GDF_K * A.ldF * 8);
+    // connection rows [c, c u_j]; the lookup form keeps c and the row of x' only
+    g.F = take(A.gfree ? 0 : (size_t)GDF_K * (A.lookup ? 1 : A.ldF) * 8);
+    g.ix = take(A.gfree || !A.lookup ? 0 : (size_t)GDF_K * 4);
     g.Sg = take((size_t)A.nsl * (A.M + 1) * A.ldL * 8);
     g.arow = take((size_t)2 * A.narow * A.ldA * 8);
     g.ones = take((size_t)A.ldA * 8);
@@ -847,7 +850,8 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
     RowLists *sL = reinterpret_cast<RowLists *>(smb + lay.lists);
     int2 *sTgt = reinterpret_cast<int2 *>(smb + lay.tgt);        // [ntgt] orbital targets
     float2 *sTab = reinterpret_cast<float2 *>(smb + lay.tab);    // [ntab][ldA]  B_t[j]
-    float2 *sF = reinterpret_cast<float2 *>(smb + lay.F);        // [K][ldF]  c, c u_j
+    float2 *sF = reinterpret_cast<float2 *>(smb + lay.F);        // [K][ldF]  c, c u_j (lookup: [K] c)
+    int *sIx = reinterpret_cast<int *>(smb + lay.ix);            // lookup: [K] the row of x'
     float2 *sSg = reinterpret_cast<float2 *>(smb + lay.Sg);      // [nsl][M + 1][ldL]
     float2 *sArow = reinterpret_cast<float2 *>(smb + lay.arow);  // [2][narow][ldA]
     float2 *sOne = reinterpret_cast<float2 *>(smb + lay.ones);   // [ldA] ones
@@ -891,8 +895,8 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
     constexpr int CPW = 32 / GDF_TPC;
     const int kk = (tid >> 5) * CPW + (lane % CPW), sub = lane / CPW;
     // scatter thread: slice sl, hidden row sr
-    const int sl = tid / nh1, sr = tid - sl * nh1;
-    const bool scatter_thread = sl < A.nsl;
+    const int sl = tid / A.sw, sr = tid - sl * A.sw;
+    const bool scatter_thread = sl < A.nsl && sr < nh1;
     float2 *mySg = sSg + (size_t)sl * (M + 1) * ldL + sr;
     auto next_class = [&](int c) -> int {
         for (++c; c < GC_N; ++c)
@@ -1153,28 +1157,21 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
                         sg = sSgn[s1] * sSgn[s2];
                     }
                 }
-                float2 *Frow = sF + kk * ldF + 1;
                 if constexpr (LK) {
-                    // c = sign <x'|H|x> psi(x') / psi(x), then the row c tanh z_j(x')
-                    df c = df_make(0.f, 0.f);
+                    // c = sign <x'|H|x> psi(x') / psi(x); the scatter forms c tanh z_j(x')
+                    // from the row of x' in the table
                     if (active && sub == 0) {
                         if (sg < 0.f) hv = df_neg(hv);
                         const df ratio = df_mul(ldg_df(A.psim + idx), df_make(sIM.x, sIM.y));
-                        c = df_ldexp(df_mul(hv, ratio), __ldg(A.psie + idx) - sE);
-                        if (!GF) st_df(Frow - 1, c);
+                        const df c = df_ldexp(df_mul(hv, ratio), __ldg(A.psie + idx) - sE);
+                        if (!GF) {
+                            st_df(sF + kk, c);
+                            sIx[kk] = (int)idx;
+                        }
                         df_acc(el_part, c);
                     }
-                    if (!GF) {
-                        c.h = __shfl_sync(0xffffffffu, c.h, lane % CPW);
-                        c.l = __shfl_sync(0xffffffffu, c.l, lane % CPW);
-                        if (active) {
-                            const float2 *tr = A.rt + idx * nh;
-#pragma unroll 4
-                            for (int j = sub; j < nh; j += GDF_TPC)
-                                st_df(Frow + j, df_mul_lazy(c, ldg_df(tr + j)));
-                        }
-                    }
                 } else {
+                    float2 *Frow = sF + kk * ldF + 1;
                     df rp = df_make(1.f, 0.f);
                     int re = 0;
                     if (active) {
@@ -1255,9 +1252,27 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
                             d = mySg + M * ldL;
                             st_df(d, df_add(ld_df(d), racc));
                         };
-                        const float2 *fp = sF + k0 * ldF + sr;
-                        for (int k2 = k0; k2 < k1; ++k2, fp += ldF) {
-                            const df f = ld_df(fp);
+                        // lookup form: the element of connection k is c_k tanh z(x'_k) at
+                        // hidden row sr - 1 (c_k itself at sr = 0); the table rows of the
+                        // next two connections are in flight while one is added
+                        const float2 *tz = A.rt + (sr > 0 ? sr - 1 : 0);
+                        auto trow = [&](int k) {
+                            return k < k1 ? ldg_df(tz + (int64_t)sIx[k] * nh) : df_make(1.f, 0.f);
+                        };
+                        df t0 = df_make(1.f, 0.f), t1 = t0, t2 = t0;
+                        if (LK) {
+                            t1 = trow(k0);
+                            t2 = trow(k0 + 1);
+                        }
+                        const float2 *fp = sF + k0 * (LK ? 1 : ldF) + (LK ? 0 : sr);
+                        for (int k2 = k0; k2 < k1; ++k2, fp += (LK ? 1 : ldF)) {
+                            df f = ld_df(fp);
+                            if (LK) {
+                                t0 = t1;
+                                t1 = t2;
+                                t2 = trow(k2 + 2);
+                                if (sr > 0) f = df_mul_lazy(f, t0);
+                            }
                             df_acc(racc, f);
                             const int2 t = colT[g];
                             if (t.x >= 0) {
@@ -1818,7 +1833,8 @@ static int launch_build_grid(lm_pencil *p, const BuildArgs &A, cudaStream_t s) {
     G.fd_M1 = make_fastdiv(p->M1);
     // the lookup form: the rows are the sector in enumeration order (enumerated by
     // the library, all of them resident), so every connection is a row
-    const bool lookup = p->enumerated && !p->chunk && !p->shard_state;
+    // (row indices of the lookup form are held as int)
+    const bool lookup = p->enumerated && !p->chunk && !p->shard_state && p->n_rows < INT32_MAX;
     G.lookup = lookup;
     G.ntab = lookup ? 0 : std::max(1, std::max(S.ns_a, S.ns_b));
     G.narow = lookup ? 0 : (GDF_K + G.C[GC_AB] - 2) / G.C[GC_AB] + 1;
@@ -1874,18 +1890,32 @@ static int launch_build_grid(lm_pencil *p, const BuildArgs &A, cudaStream_t s) {
     G.flags = p->d_flags;
     G.gfree = p->gfree;
     // 228 KB of shared memory per SM, 1 KB of it reserved per CTA. Scatter slices
-    // q against CTAs per SM: the most CTAs x min(q, 3), then the most slices.
-    // Measured (ms per build): F2-shaped rows q = 1..6 at 4,4,4,3,3,2 CTAs/SM:
-    // 4.06, 3.21, 2.80, 3.13, 3.09, 3.55; LiCl-shaped (65,536 rows) q = 1..4 at
-    // 3,2,2,2: 111.9, 106.3, 93.1, 84.0.
-    auto per_sm_of = [&](size_t bytes) { return (int)(233472 / (bytes + 1024 + 64)); };
+    // q against CTAs per SM: the most CTAs x min(q, 3); on a tie the fewest slices
+    // at 4 or more CTAs per SM (other CTAs fill the scatter's barrier waits, so its
+    // instruction count decides) and the most below (its critical path decides).
+    // Measured (ms per build): F2-shaped rows, products formed per connection,
+    // q = 1..6 at 4,4,4,3,3,2 CTAs/SM: 4.06, 3.21, 2.80, 3.13, 3.09, 3.55;
+    // F2-shaped rows in the lookup form, q = 2..6 at 5,5,5,5,4: 2.35, 1.95, 2.20,
+    // 2.16, 2.12; LiCl-shaped (65,536 rows) q = 1..4 at 3,2,2,2: 111.9, 106.3,
+    // 93.1, 84.0.
+    auto kern = p->gfree ? (lookup ? k_build_rows_dg<true, true> : k_build_rows_dg<true, false>)
+                         : (lookup ? k_build_rows_dg<false, true> : k_build_rows_dg<false, false>);
+    // CTAs per SM that the registers allow (the kernels differ: 46 to 56 per thread)
+    int reg_cap = 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&reg_cap, kern, GDF_THREADS, 0) != cudaSuccess ||
+        reg_cap < 1)
+        return lm_fail(ctx, LM_ERR_CUDA, "df64 build kernel occupancy query failed");
+    auto per_sm_of = [&](size_t bytes) {
+        return std::min(reg_cap, (int)(233472 / (bytes + 1024 + 64)));
+    };
     const int max_sl = std::max(1, GDF_THREADS / (p->nh + 1));
     int best = 1, best_key = -1;
     for (int q = 1; q <= max_sl; ++q) {
         G.nsl = q;
         const size_t b = grid_smem(G).total;
         if (b > (size_t)ctx->smem_optin) break;
-        const int key = (std::min(4, per_sm_of(b)) * std::min(q, 3)) * 16 + q;
+        const int cta = per_sm_of(b);
+        const int key = (cta * std::min(q, 3)) * 256 + (cta >= 4 ? 255 - q : q);
         if (key > best_key) {
             best_key = key;
             best = q;
@@ -1897,15 +1927,21 @@ static int launch_build_grid(lm_pencil *p, const BuildArgs &A, cudaStream_t s) {
         if (q >= 1 && q <= max_sl) best = q;
     }
     G.nsl = p->gfree ? 0 : best;
+    // Slices packed back to back, unless giving each slice whole warps of its own
+    // takes no more warps (then no warp holds two slices' connections): LiCl-shaped
+    // rows (57 threads a slice, 4 slices) 81.8 against 83.3 ms at 65,536 rows;
+    // F2-shaped ones (41 threads, 3 slices) would take 6 warps instead of 4.
+    {
+        const int nh1 = p->nh + 1, wps = (nh1 + 31) / 32, q = std::max(G.nsl, 1);
+        const bool own = q * wps * 32 <= GDF_THREADS && q * wps == (q * nh1 + 31) / 32;
+        G.sw = own ? wps * 32 : nh1;
+    }
     const size_t dsm = grid_smem(G).total;
     if (dsm > (size_t)ctx->smem_optin)
         return lm_fail(ctx, LM_ERR_SIZE, "df64 build kernel needs %zu B shared memory", dsm);
-    auto kern = p->gfree ? (lookup ? k_build_rows_dg<true, true> : k_build_rows_dg<true, false>)
-                         : (lookup ? k_build_rows_dg<false, true> : k_build_rows_dg<false, false>);
     cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
     if (e2 != cudaSuccess) return lm_cuda_check(ctx, e2, "df64 build smem attribute");
-    int per_sm = std::max(1, per_sm_of(dsm));
-    per_sm = std::min(per_sm, 4);
+    const int per_sm = std::max(1, per_sm_of(dsm));
     int64_t grid = std::min<int64_t>(p->n_rows, (int64_t)ctx->sms * per_sm);
     // many rows per resident CTA: one CTA per row instead, so that other streams'
     // kernels can be scheduled as rows finish
