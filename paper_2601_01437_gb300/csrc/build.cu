@@ -766,10 +766,19 @@ __device__ __forceinline__ int2 grid_target(const GridDfArgs &A, const RowLists 
 //   t[x][j]   tanh z_j(x) as double-float (the connection rows) and in FP64
 //             (the row's own O row)
 //   psi(x) = m[x] 2^e[x] with m in [1, 2) (double-float) and e an integer, from
-//   ln psi(x) = a.x + sum_j (|z_j| + ln(1 + e^{-2|z_j|})) (the ln 2 per cosh
-//   cancels in every ratio), which is written to lnpsi as well.
+//   ln psi(x) = a.x + sum_j |z_j| + ln prod_j (1 + e^{-2|z_j|}) (the ln 2 per
+//   cosh cancels in every ratio), which is written to lnpsi as well.
+// The transcendental work per (row, hidden unit) runs in double-float on the FP32
+// pipes (FP64 issues at 1/64 of the FP32 rate here): e^{-2|z_j|} - 1 by
+// df_expm1_neg and tanh as -(e - 1) / (2 + (e - 1)). FP64 keeps what ln psi needs
+// to its last bits and costs few instructions: z_j (a sum of theta entries),
+// sum_j |z_j|, the product of the 1 + e^{-2|z_j|} (one log per row instead of one
+// per hidden unit), a.x and one exp2 per row.
 struct RowTabArgs {
     int n, nh, M, M1;
+    int R;          // rows per CTA pass
+    int ldz;        // stride of a row's per-hidden-unit values in shared memory (odd)
+    FastDiv fd_nh;
     const double *theta;
     const uint64_t *rows;
     int64_t n_rows;
@@ -780,43 +789,121 @@ struct RowTabArgs {
     double *lnpsi;  // [n_rows]
 };
 
-__global__ void k_row_tables(RowTabArgs A) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < A.n_rows;
-         row += nw) {
-        const uint64_t x = A.rows[row];
-        double lp = 0.0;
-        for (int j = lane; j < A.nh; j += 32) {
+// e^y - 1 for y <= 0 in double-float (relative error ~1e-14; FP32 emulation over
+// y in [-90, 0]). Cody and Waite's reduction y = k ln 2 + r, |r| <= ln 2 / 2, with
+// ln 2 in three FP32 parts (the first with 16 significant bits, so k times it is
+// exact); r' = r / 32; e^{r'} - 1 by its Taylor series to r'^7 / 7! (Horner; the
+// three highest coefficients in FP32, whose terms are below 2^-30 relative);
+// five doublings e^{2u} - 1 = (e^u - 1)(2 + e^u - 1); then
+// e^y - 1 = 2^k (e^r - 1) + (2^k - 1), both parts exact in double-float. Below
+// y = -87 the result is -1 to within 2^-125.
+__device__ __forceinline__ df df_expm1_neg(df y) {
+    if (y.h < -87.f) return df_make(-1.f, 0.f);
+    // k = round(y / ln 2) by the FP32 magic number (no conversion instruction)
+    const float kf = __fsub_rn(__fadd_rn(__fmul_rn(y.h, 1.44269504f), 12582912.0f), 12582912.0f);
+    const int k = __float_as_int(__fadd_rn(kf, 12582912.0f)) - 0x4B400000;
+    const float L1 = 0x1.62e4p-1f, L2 = 0x1.7f7d1cp-20f, L3 = 0x1.ef357ap-45f;
+    df r = df_add(y, df_make(-kf * L1, 0.f));  // kf L1 is exact
+    const float p2 = __fmul_rn(kf, L2);
+    r = df_add(r, df_make(-p2, -__fmaf_rn(kf, L2, -p2)));  // exact k L2
+    r = df_add(r, df_make(__fmul_rn(-kf, L3), 0.f));
+    const df rs = df_make(r.h * 0x1p-5f, r.l * 0x1p-5f);
+    float q = __fmaf_rn(rs.h, 0x1.a01a02p-13f, 0x1.6c16c2p-10f);  // 1/7!, 1/6!
+    q = __fmaf_rn(rs.h, q, 0x1.111112p-7f);                        // 1/5!
+    df P = df_add(df_make(0x1.555556p-5f, -0x1.555556p-30f), df_mul(rs, df_make(q, 0.f)));  // 1/4!
+    P = df_add(df_make(0x1.555556p-3f, -0x1.555556p-28f), df_mul(rs, P));                   // 1/3!
+    P = df_add(df_make(0.5f, 0.f), df_mul(rs, P));
+    P = df_add(df_make(1.f, 0.f), df_mul(rs, P));
+    df E = df_mul(rs, P);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) E = df_mul(E, df_add(df_make(2.f, 0.f), E));
+    // 2^k for k in [-126, 0] from its exponent field
+    const float sc = __int_as_float((127 + k) << 23);
+    const df B = k >= -24 ? df_make(__fsub_rn(sc, 1.f), 0.f) : df_make(-1.f, sc);
+    return df_add(df_make(E.h * sc, E.l * sc), B);
+}
+
+// FP32 to FP64 by the exponent field (conversions issue at the FP64 rate here);
+// zero and subnormal inputs take the conversion
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned u = __float_as_uint(x), ex = (u >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)x;
+    const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ double df_to_double_bits(df a) { return f2d_bits(a.h) + f2d_bits(a.l); }
+
+__global__ void __launch_bounds__(256) k_row_tables(RowTabArgs A) {
+    extern __shared__ __align__(16) unsigned char smr[];
+    const int n = A.n, nh = A.nh, M = A.M, M1 = A.M1, R = A.R, ldz = A.ldz;
+    double *sW = reinterpret_cast<double *>(smr);  // [M + nh M1]: a, then b_j, W_j0 .. W_j(M-1)
+    double *sAz = sW + M + (size_t)nh * M1;        // [R][ldz] |z_j|
+    double *sFc = sAz + (size_t)R * ldz;           // [R][ldz] 1 + e^{-2|z_j|}
+    const int tid = threadIdx.x;
+    for (int e = tid; e < M + nh * M1; e += blockDim.x) sW[e] = A.theta[e];
+    __syncthreads();
+    for (int64_t g = blockIdx.x; g * R < A.n_rows; g += gridDim.x) {
+        const int64_t r0 = g * R;
+        const int nr = A.n_rows - r0 < (int64_t)R ? (int)(A.n_rows - r0) : R;
+        // per (row, hidden unit)
+        for (int e = tid; e < nr * nh; e += blockDim.x) {
+            const int rr = fdiv(e, A.fd_nh), j = e - rr * nh;
+            const int64_t row = r0 + rr;
             // z_j = b_j + sum of W_jp over the occupied spin orbitals, alpha then beta
-            // in ascending order (the build's order)
-            const double *wj = A.theta + (size_t)(j + 1) * A.M1;
-            double za = wj[-1], zb = 0.0;
-            for (int p = 0; p < A.n; ++p)
-                if (occ_bit(x, p)) za += wj[p];
-            for (int p = A.n; p < A.M; ++p)
-                if (occ_bit(x, p)) zb += wj[p];
+            // in ascending order, in FP64 (ln psi sums the |z_j| of every hidden unit)
+            const uint64_t x = A.rows[row];
+            const double *wj = sW + M + (size_t)j * M1;
+            double za = wj[0], zb = 0.0;
+            for (int word = 0; word < 2; ++word) {
+                unsigned w = word ? (unsigned)(x >> 32) : (unsigned)x;
+                while (w) {
+                    const int p = __ffs(w) - 1 + 32 * word;
+                    w &= w - 1;
+                    if (p < n) za += wj[1 + p];
+                    else zb += wj[1 + p];
+                }
+            }
             const double z = za + zb;
-            const double em = expm1(-2.0 * fabs(z));
-            const double t = copysign(-em / (2.0 + em), z);
-            lp += fabs(z) + log1p(1.0 + em);
-            const df td = df_from_double(t);
-            A.t[row * A.nh + j] = make_float2(td.h, td.l);
-            A.t64[row * A.nh + j] = t;
+            const df az = df_split_bits(fabs(z));
+            const df em = df_expm1_neg(df_make(-2.f * az.h, -2.f * az.l));  // e^{-2|z|} - 1
+            const df den = df_add(df_make(2.f, 0.f), em);                   // 1 + e^{-2|z|}
+            df t = df_div(df_neg(em), den);
+            if (z < 0.0) t = df_neg(t);
+            A.t[row * nh + j] = make_float2(t.h, t.l);
+            A.t64[row * nh + j] = df_to_double_bits(t);
+            sAz[rr * ldz + j] = fabs(z);
+            sFc[rr * ldz + j] = df_to_double_bits(den);
         }
-        for (int p = lane; p < A.M; p += 32)
-            if (occ_bit(x, p)) lp += A.theta[p];
-        lp = warp_sum(lp);
-        if (lane == 0) {
-            A.lnpsi[row] = lp;
+        __syncthreads();
+        // per row (a thread each): a.x + sum_j |z_j| + ln prod_j (1 + e^{-2|z_j|})
+        // (the product stays below 2^255: no rescaling in FP64), then psi = m 2^e
+        for (int q = tid; q < nr; q += blockDim.x) {
+            const int64_t rw = r0 + q;
+            const uint64_t x = A.rows[rw];
+            double ax = 0.0;
+            for (int word = 0; word < 2; ++word) {
+                unsigned w = word ? (unsigned)(x >> 32) : (unsigned)x;
+                while (w) {
+                    const int p = __ffs(w) - 1 + 32 * word;
+                    w &= w - 1;
+                    ax += sW[p];
+                }
+            }
+            double sz = 0.0, pr = 1.0;
+            for (int jj = 0; jj < nh; ++jj) {
+                sz += sAz[q * ldz + jj];
+                pr *= sFc[q * ldz + jj];
+            }
+            const double lp = ax + sz + log(pr);
+            A.lnpsi[rw] = lp;
             // psi = 2^(lp / ln 2) = 2^k 2^f, f in [0, 1)
-            const double q = lp * 1.4426950408889634;  // 1 / ln 2
-            const double k = floor(q);
-            const double mv = exp2(q - k);
-            const df md = df_from_double(mv);
-            A.psim[row] = make_float2(md.h, md.l);
-            A.psie[row] = (int)k;
+            const double qd = lp * 1.4426950408889634;  // 1 / ln 2
+            const double kd = floor(qd);
+            const df md = df_from_double(exp2(qd - kd));
+            A.psim[rw] = make_float2(md.h, md.l);
+            A.psie[rw] = (int)kd;
         }
+        __syncthreads();
     }
 }
 
@@ -1834,7 +1921,14 @@ static int launch_build_grid(lm_pencil *p, const BuildArgs &A, cudaStream_t s) {
     // the lookup form: the rows are the sector in enumeration order (enumerated by
     // the library, all of them resident), so every connection is a row
     // (row indices of the lookup form are held as int)
-    const bool lookup = p->enumerated && !p->chunk && !p->shard_state && p->n_rows < INT32_MAX;
+    // k_row_tables: R rows per CTA pass (one thread per row for the per-row FP64
+    // steps); theta and the per-row values in shared memory, up to 32 rows in 96 KB
+    // for the latter (the form is not taken where it would not fit)
+    const int tab_ldz = p->nh | 1;
+    const int tab_R = (int)std::max<int64_t>(1, std::min<int64_t>(32, 96 * 1024 / (16 * (int64_t)tab_ldz)));
+    const size_t tsm = ((size_t)p->M + (size_t)p->nh * p->M1 + 2 * (size_t)tab_R * tab_ldz) * sizeof(double);
+    const bool lookup = p->enumerated && !p->chunk && !p->shard_state && p->n_rows < INT32_MAX &&
+                        tsm <= (size_t)ctx->smem_optin;
     G.lookup = lookup;
     G.ntab = lookup ? 0 : std::max(1, std::max(S.ns_a, S.ns_b));
     G.narow = lookup ? 0 : (GDF_K + G.C[GC_AB] - 2) / G.C[GC_AB] + 1;
@@ -1867,8 +1961,16 @@ static int launch_build_grid(lm_pencil *p, const BuildArgs &A, cudaStream_t s) {
         T.psim = p->psim;
         T.psie = p->psie;
         T.lnpsi = p->lnpsi;
-        const int blocks = (int)std::min<int64_t>((p->n_rows + 7) / 8, (int64_t)ctx->sms * 16);
-        k_row_tables<<<std::max(blocks, 1), 256, 0, s>>>(T);
+        T.ldz = tab_ldz;
+        T.R = tab_R;
+        T.fd_nh = make_fastdiv(p->nh);
+        if (tsm > 48 * 1024) {
+            cudaError_t ea = cudaFuncSetAttribute(k_row_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)tsm);
+            if (ea != cudaSuccess) return lm_cuda_check(ctx, ea, "row tables smem attribute");
+        }
+        const int blocks = (int)std::min<int64_t>((p->n_rows + T.R - 1) / T.R, (int64_t)ctx->sms * 8);
+        k_row_tables<<<std::max(blocks, 1), 256, tsm, s>>>(T);
         lm_note_launch(ctx);
         if (int rc = lm_cuda_check(ctx, cudaGetLastError(), "k_row_tables")) return rc;
         G.rt = p->rt;

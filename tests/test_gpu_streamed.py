@@ -1,10 +1,11 @@
 """Streamed pencils (lm_build_streamed): O_c and G'_c rebuilt chunk by chunk inside every
 product, against the resident pencil of lm_build_OG and the FP64 oracle.
 
-Bars: ln psi, the rows and (up to the weights' normaliser) the weights equal the resident
-pencil's; E_loc equals it to 1e-12 of each entry's condition scale (a resident sector pencil
-reads its connections' psi and tanh z_j from per-determinant tables, a streamed one forms
-them per connection: the same terms in another order); products equal the resident
+Bars: the rows equal the resident pencil's; ln psi equals it to 1e-13 of max |ln psi| and
+the weights to 1e-13 (a resident sector pencil takes ln psi, psi and tanh z_j from
+per-determinant tables formed in double-float arithmetic, a streamed one forms them per row
+and per connection in FP64 and double-float); E_loc equals it to 1e-12 of each entry's
+condition scale (the same terms in another order); products equal the resident
 pencil's to 1e-12 relative with FP64-accurate factors, FP32 copies to 1e-6; energy to
 1e-13; the IRL
 eigenvalue to 1e-10 of the oracle's (FP64-accurate factors) or within 1e-9 Ha after the
@@ -65,8 +66,9 @@ def _pair(ctx, abi, name, prec, arith=0):
 def test_streamed_products_equal_resident(ctx, abi, name, prec, arith):
     w, h, eri, th, rows, cnt, full, st = _pair(ctx, abi, name, prec, arith)
     assert st.info().energy == pytest.approx(full.info().energy, rel=1e-13)
-    for what in (abi.EXPORT_LNPSI, abi.EXPORT_ROWS):
-        assert np.array_equal(st.export(what), full.export(what))
+    assert np.array_equal(st.export(abi.EXPORT_ROWS), full.export(abi.EXPORT_ROWS))
+    l_st, l_full = st.export(abi.EXPORT_LNPSI), full.export(abi.EXPORT_LNPSI)
+    assert np.abs(l_st - l_full).max() <= 1e-13 * np.abs(l_full).max()
     pd = lm.build_pencil(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th, rows, cnt)
     AE, _, _ = lm.condition_scales(pd, w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, th,
                                    union_occ=True)
