@@ -13,7 +13,7 @@ import pytest
 import __graft_entry__ as entry
 import synth
 from oracle import lm
-from parity_tools import componentwise
+from parity_tools import componentwise, saturated_theta
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +48,9 @@ def _case(name):
         h, eri = synth.integrals(6, 17)
         th = synth.rbm_theta(6, 127, 17, sigma=0.5)
         return (6, 3, 3, 127), h, eri, th, None, None
+    if name == "saturated":
+        h, eri = synth.integrals(8, 29)
+        return (8, 4, 4, 32), h, eri, saturated_theta(8, 32, 29), None, None
     if name == "empty_alpha":
         h, eri = synth.integrals(4, 17)
         th = synth.rbm_theta(4, 3, 17, sigma=0.2)
@@ -58,11 +61,12 @@ def _case(name):
 
 
 CASES = [("tiny_6o6e", 0), ("tiny_6o6e", 3), ("f2_10o14e", 3), ("mc", 1), ("edge_nh127", 0),
-         ("empty_alpha", 0)]
+         ("empty_alpha", 0), ("saturated", 3)]
 
 
 @pytest.mark.parametrize("name,prec", CASES,
-                         ids=["tiny-fp64", "tiny-df64", "f2-df64", "mc-fp32", "nh127", "empty-alpha"])
+                         ids=["tiny-fp64", "tiny-df64", "f2-df64", "mc-fp32", "nh127", "empty-alpha",
+                              "saturated"])
 def test_gfree_build_against_the_oracle_and_the_full_build(ctx, abi, name, prec):
     shape, h, eri, th, rows, cnt = _case(name)
     n, na, nb, nh = shape

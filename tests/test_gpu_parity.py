@@ -13,7 +13,7 @@ import __graft_entry__ as entry
 import oracle
 import synth
 from oracle import fock, lm, native
-from parity_tools import componentwise
+from parity_tools import componentwise, saturated_theta
 
 pytestmark = pytest.mark.gpu
 
@@ -191,6 +191,22 @@ def test_build_parity_large_theta(ctx, abi, arith):
     h, eri = synth.integrals(10, 23)
     th = synth.rbm_theta(10, 40, 23, sigma=0.5)
     pen, pd = _build_both(ctx, abi, 10, 7, 7, 40, h, eri, th, arith=arith)
+    _check_build(abi, pen, pd)
+    pen.free()
+
+
+@ARITHS
+def test_build_parity_saturated_hidden_units(ctx, abi, arith):
+    """Saturated hidden units (|z_j| near 12, 30, 48 and 66): on an enumerated sector, whose build
+    reads tanh z_j and psi from the per-determinant tables, and on sampled rows of it,
+    whose build forms every connection's ratios itself."""
+    h, eri = synth.integrals(8, 29)
+    th = saturated_theta(8, 32, 29)
+    pen, pd = _build_both(ctx, abi, 8, 4, 4, 32, h, eri, th, arith=arith)
+    _check_build(abi, pen, pd)
+    pen.free()
+    rows, cnt = _mc_rows(8, 4, 4, 300, 29, h)
+    pen, pd = _build_both(ctx, abi, 8, 4, 4, 32, h, eri, th, rows, cnt, arith=arith)
     _check_build(abi, pen, pd)
     pen.free()
 
