@@ -978,9 +978,11 @@ __global__ void __launch_bounds__(GDF_THREADS) k_build_rows_dg(GridDfArgs A) {
     const int ldL = A.ldL, ldF = A.ldF, ldA = A.ldA;
 
     // connection kk of a tile is handled by the GDF_TPC lanes kk % CPW, kk % CPW
-    // + CPW, ... of warp kk / CPW
+    // + CPW, ... of warp kk / CPW; the lookup form has no hidden-unit loop to
+    // share, so thread kk alone decodes connection kk (warps 0 and 1 the whole
+    // tile: a quarter of the decoding's warp instructions)
     constexpr int CPW = 32 / GDF_TPC;
-    const int kk = (tid >> 5) * CPW + (lane % CPW), sub = lane / CPW;
+    const int kk = LK ? tid : (tid >> 5) * CPW + (lane % CPW), sub = LK ? 0 : lane / CPW;
     // scatter thread: slice sl, hidden row sr
     const int sl = tid / A.sw, sr = tid - sl * A.sw;
     const bool scatter_thread = sl < A.nsl && sr < nh1;
