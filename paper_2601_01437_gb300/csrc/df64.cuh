@@ -105,6 +105,11 @@ __device__ __forceinline__ df df_fma(df a, df b, df c) {
     return df_fts(s.h, __fadd_rn(s.l, __fadd_rn(e, c.l)));
 }
 
+// The FP64 route of df_split_bits, out of line: inlined, the compiler may
+// predicate it into the common path, where its conversions would issue for every
+// value at the FP64 rate.
+static __device__ __noinline__ df df_from_double_rare(double x) { return df_from_double(x); }
+
 // Double-float split of an FP64 value by integer operations (no FP64
 // instruction on the common path): the head is the value rounded to 24
 // significant bits (the carry of the rounding increment runs into the
@@ -117,7 +122,7 @@ __device__ __forceinline__ df df_split_bits(double x) {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
     const int ex = (int)((hi >> 20) & 0x7ffu);
     if (((hi << 1) | lo) == 0u) return df_make(__uint_as_float(hi & 0x80000000u), 0.f);  // +-0
-    if (ex < 1023 - 70 || ex > 1023 + 100) return df_from_double(x);
+    if (ex < 1023 - 70 || ex > 1023 + 100) return df_from_double_rare(x);
     const unsigned sign = hi & 0x80000000u;
     const unsigned up = (lo >> 28) & 1u;  // first dropped bit: round the head up
     const unsigned hb = (((unsigned)(ex - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)) + up;
