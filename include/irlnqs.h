@@ -169,8 +169,9 @@ typedef struct {
  * defaults). */
 typedef struct {
     unsigned struct_size;
-    int profile;    /* 1: time the kernel classes with CUDA events from the start
-                       (as lm_stats_reset(ctx, 1)); 0: count launches only    */
+    int profile;    /* nonzero: time kernel classes with CUDA events from the
+                       start, as lm_stats_reset(ctx, profile) (1: every class;
+                       LM_PROF_ONLY | class bits); 0: count launches only    */
     double hbm_gbs; /* streaming rate in GB/s that the grid autotuner of the batch
                        and server engines assumes (its cost model charges each
                        product max(compute, bytes / rate)); 0: 85 % of the
@@ -538,11 +539,24 @@ typedef struct {
     int64_t tri_count;
 } lm_stats;
 
-/* Reset the counters; profile = 1 also brackets every row-build, pencil,
+/* Kernel classes for lm_stats_reset's profile argument */
+#define LM_PROF_ONLY    0x100 /* with class bits: bracket only those classes  */
+#define LM_PROF_BUILD   0x01  /* row build                                    */
+#define LM_PROF_PENCIL  0x02  /* pencil products                              */
+#define LM_PROF_LANCZOS 0x04  /* Lanczos steps                                */
+#define LM_PROF_PREP    0x08  /* preparation (weights, statistics, centring)  */
+#define LM_PROF_TRI     0x10  /* tridiagonal eigen-solve / shifts             */
+
+/* Reset the counters. profile = 1 also brackets every row-build, pencil,
  * Lanczos-step, preparation and tridiagonal launch (or launch sequence) with
  * CUDA events recorded on the launch stream, until the next reset (at most
- * 2048 intervals per class are timed). lm_stats_get synchronises the device
- * before reading the events. */
+ * 2048 intervals per class are timed); profile = LM_PROF_ONLY | class bits
+ * brackets only those classes (each event pair adds a few microseconds to the
+ * stream, so a caller timing whole steps may want only the class it studies);
+ * 0 counts launches only. Timed classes report their timed intervals as
+ * counts, the others their launches. lm_stats_get synchronises the device
+ * before reading the events. Errors: LM_ERR_ARG (null context, or a profile
+ * value other than 0, 1 or LM_PROF_ONLY with class bits). */
 int lm_stats_reset(lm_ctx *ctx, int profile);
 int lm_stats_get(lm_ctx *ctx, lm_stats *out);
 

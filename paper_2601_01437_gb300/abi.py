@@ -24,6 +24,8 @@ LM_ARITH_DF64, LM_ARITH_FP64 = 0, 1
 IRL_REORTH_FULL, IRL_REORTH_NONE = 0, 1
 IRL_MODE_SHEP = 0
 LM_NOALLOC_MAX_LD = 2048
+LM_PROF_ONLY, LM_PROF_BUILD, LM_PROF_PENCIL, LM_PROF_LANCZOS, LM_PROF_PREP, LM_PROF_TRI = \
+    0x100, 0x01, 0x02, 0x04, 0x08, 0x10
 EXPORT_O, EXPORT_G, EXPORT_LNPSI, EXPORT_ELOC, EXPORT_W, EXPORT_OBAR, EXPORT_ROWS = range(7)
 
 c_int, c_double, c_int64, c_uint64, c_vp = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,

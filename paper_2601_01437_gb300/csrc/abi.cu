@@ -173,7 +173,7 @@ extern "C" int lm_create(lm_ctx **out, int device, const lm_ctx_params *params) 
         delete c;
         return LM_ERR_OOM;
     }
-    if (prm.profile && lm_stats_reset(c, 1) != LM_OK) {
+    if (prm.profile && lm_stats_reset(c, prm.profile) != LM_OK) {
         cudaFree(c->d_flags);
         delete c;
         return LM_ERR_CUDA;
@@ -664,6 +664,9 @@ extern "C" int lm_debug_connections(lm_ctx *ctx, const lm_system *sys, const uin
 // ---------------------------------------------------------------- counters
 extern "C" int lm_stats_reset(lm_ctx *ctx, int profile) {
     if (!ctx) return LM_ERR_ARG;
+    const int all = (1 << LM_PROF_CLASSES) - 1;
+    if (profile != 0 && profile != 1 && (!(profile & LM_PROF_ONLY) || (profile & ~(LM_PROF_ONLY | all))))
+        return lm_fail(ctx, LM_ERR_ARG, "profile = %#x: 0, 1 or LM_PROF_ONLY with class bits", profile);
     cudaSetDevice(ctx->device);
     if (profile && !ctx->ev_ready) {
         for (int c = 0; c < LM_PROF_CLASSES; ++c)
@@ -673,7 +676,8 @@ extern "C" int lm_stats_reset(lm_ctx *ctx, int profile) {
                         return lm_fail(ctx, LM_ERR_CUDA, "cudaEventCreate");
         ctx->ev_ready = 1;
     }
-    ctx->profile = profile;
+    ctx->profile = profile != 0;
+    ctx->prof_mask = profile == 1 ? all : profile & all;
     ctx->launches = 0;
     ctx->pencil_rows = 0;
     for (int c = 0; c < LM_PROF_CLASSES; ++c) ctx->ev_used[c] = ctx->ev_count[c] = 0;
@@ -692,11 +696,14 @@ extern "C" int lm_stats_get(lm_ctx *ctx, lm_stats *out) {
         }
     out->launches = ctx->launches;
     out->build_ms = ms[PROF_BUILD];
-    out->build_count = ctx->profile ? ctx->ev_used[PROF_BUILD] : ctx->ev_count[PROF_BUILD];
+    // timed classes report their timed intervals, the others their launches
+    auto count = [&](int c) {
+        return ctx->profile && ((ctx->prof_mask >> c) & 1) ? ctx->ev_used[c] : ctx->ev_count[c];
+    };
+    out->build_count = count(PROF_BUILD);
     out->pencil_ms = ms[PROF_PENCIL];
-    out->pencil_count = ctx->profile ? ctx->ev_used[PROF_PENCIL] : ctx->ev_count[PROF_PENCIL];
+    out->pencil_count = count(PROF_PENCIL);
     out->pencil_rows = ctx->pencil_rows;
-    auto count = [&](int c) { return ctx->profile ? ctx->ev_used[c] : ctx->ev_count[c]; };
     out->lanczos_ms = ms[PROF_LANCZOS];
     out->lanczos_count = count(PROF_LANCZOS);
     out->prep_ms = ms[PROF_PREP];

@@ -132,6 +132,7 @@ struct lm_ctx {
     // counters
     int64_t launches;
     int profile;
+    int prof_mask;  // kernel classes bracketed by events while profile is set (bit = class)
     cudaEvent_t ev[LM_PROF_CLASSES][LM_PROF_EVENTS][2];  // [class][pair][start/end]
     int ev_ready;
     int64_t ev_used[LM_PROF_CLASSES];
@@ -155,12 +156,12 @@ inline int lm_max_dyn_smem(const void *func, int smem_optin) {
 }
 // Event pair around one launch of a profiled kernel class (no-op unless profiling).
 inline void lm_prof_begin(lm_ctx *ctx, int cls, cudaStream_t s) {
-    if (!ctx->profile || !ctx->ev_ready) return;
+    if (!ctx->profile || !ctx->ev_ready || !((ctx->prof_mask >> cls) & 1)) return;
     if (ctx->ev_used[cls] < LM_PROF_EVENTS) cudaEventRecord(ctx->ev[cls][ctx->ev_used[cls]][0], s);
 }
 inline void lm_prof_end(lm_ctx *ctx, int cls, cudaStream_t s) {
     ctx->ev_count[cls]++;
-    if (!ctx->profile || !ctx->ev_ready) return;
+    if (!ctx->profile || !ctx->ev_ready || !((ctx->prof_mask >> cls) & 1)) return;
     if (ctx->ev_used[cls] < LM_PROF_EVENTS) {
         cudaEventRecord(ctx->ev[cls][ctx->ev_used[cls]][1], s);
         ctx->ev_used[cls]++;

@@ -654,3 +654,40 @@ def test_context_params(abi):
     with pytest.raises(abi.LMError) as e:
         abi.Context(0, hbm_gbs=-1.0)
     assert e.value.code == abi.LM_ERR_ARG
+
+
+def test_profile_class_mask(ctx, abi):
+    """lm_stats_reset with LM_PROF_ONLY | class bits times only those classes (the others
+    report their launch counts and no time), 1 times every class, 0 none; other values
+    are refused."""
+    w = synth.WORKLOADS["tiny_6o6e"]
+    h, eri, th, _, _ = w.inputs()
+    sysd = ctx.system(6, 3, 3, 24, h, eri)
+
+    def step():
+        pen = ctx.build_OG(sysd, th)
+        pen.irl_step(m=20, k=1, tol=1e-12)
+        pen.free()
+
+    ctx.stats_reset(abi.LM_PROF_ONLY | abi.LM_PROF_BUILD)
+    step()
+    st = ctx.stats()
+    assert st.build_count == 1 and st.build_ms > 0.0
+    assert st.pencil_count > 0 and st.pencil_ms == 0.0
+    assert st.lanczos_ms == 0.0 and st.tri_ms == 0.0 and st.prep_ms == 0.0
+    ctx.stats_reset(1)
+    step()
+    st = ctx.stats()
+    assert st.build_ms > 0.0 and st.pencil_ms > 0.0 and st.tri_ms > 0.0
+    counts = (st.build_count, st.pencil_count, st.lanczos_count, st.prep_count, st.tri_count)
+    ctx.stats_reset(0)
+    step()
+    st = ctx.stats()
+    assert st.build_ms == 0.0 and st.pencil_ms == 0.0
+    assert (st.build_count, st.pencil_count, st.lanczos_count, st.prep_count,
+            st.tri_count) == counts
+    for bad in (2, 0x20 | abi.LM_PROF_ONLY, 0x200):
+        with pytest.raises(abi.LMError) as e:
+            ctx.stats_reset(bad)
+        assert e.value.code == abi.LM_ERR_ARG
+    ctx.stats_reset(0)
