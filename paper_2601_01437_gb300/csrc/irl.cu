@@ -935,6 +935,7 @@ __global__ void __launch_bounds__(TT) k_tri(TriArgs t) {
         double x = 0.5 * ((double)blo[i] + (double)bhi[i]);
         double pn, pn1, dpn, plo, pl1, dl;
         charpoly(as, b2s, je, lo, plo, pl1, dl);
+        double prev = INFINITY;
         for (int it = 0; it < 12; ++it) {
             charpoly(as, b2s, je, x, pn, pn1, dpn);
             if (pn == 0.0) break;
@@ -944,6 +945,10 @@ __global__ void __launch_bounds__(TT) k_tri(TriArgs t) {
                 x -= step;
                 break;
             }
+            // the rounding noise of p near the root: steps below 1e-12 of the scaled
+            // norm that no longer halve are noise, not convergence still to come
+            if (dpn != 0.0 && fabs(step) <= 1e-12 && fabs(step) > 0.5 * prev) break;
+            prev = fabs(step);
             if ((pn > 0.0) == (plo > 0.0)) lo = x; else hi = x;
             double xn = dpn != 0.0 ? x - step : 0.5 * (lo + hi);
             if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
