@@ -583,18 +583,23 @@ def test_irl_mixed_precision_32k_rows_vs_oracle(ctx, abi, licl_32k, prec):
     pen.free()
 
 
-def test_two_lm_steps_follow_the_oracle(ctx, abi):
-    """theta <- theta + Delta theta twice; energies and eigenvalues track the oracle's own steps."""
-    w = synth.WORKLOADS["tiny_6o6e"]
+@pytest.mark.parametrize("name,prec,steps", [("tiny_6o6e", 0, 2), ("f2_10o14e", 3, 3)],
+                         ids=["tiny-fp64", "f2-df64"])
+def test_lm_steps_follow_the_oracle(ctx, abi, name, prec, steps):
+    """theta <- theta + Delta theta, step after step; energies and eigenvalues track the
+    oracle's own steps. The F2-shaped trajectory is the one bench.py times (double-float
+    build and pencil, m = 30, k = 10); its second step has a gap of 0.012 between the two
+    lowest eigenvalues of the symmetrised operator."""
+    w = synth.WORKLOADS[name]
     h, eri, th, _, _ = w.inputs()
-    sysd = ctx.system(6, 3, 3, 24, h, eri)
+    sysd = ctx.system(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri)
     tg = th.copy()
     to = th.copy()
     pen = None
-    for step in range(2):
-        pen = ctx.build_OG(sysd, tg, pencil=pen)
-        res = pen.irl_step(m=20, k=1, tol=1e-12, theta_inout=tg)
-        ref = lm.lm_step(6, 3, 3, 24, h, eri, to)
+    for step in range(steps):
+        pen = ctx.build_OG(sysd, tg, pencil=pen, prec=prec)
+        res = pen.irl_step(m=w.m, k=w.k, tol=w.tol, prec=prec, theta_inout=tg)
+        ref = lm.lm_step(w.n_orb, w.n_alpha, w.n_beta, w.n_hidden, h, eri, to)
         assert res.energy == pytest.approx(ref["E"], rel=1e-10)
         assert res.lambda_ == pytest.approx(ref["lam"], rel=1e-8)
         to = to + ref["dtheta"]
