@@ -280,6 +280,8 @@ class Context:
         return lib().lm_debug_wait_timeout(self.handle, int(which), int(limit_ns))
 
     def stats_reset(self, profile=False):
+        """lm_stats_reset: profile False/0 counts launches only, True/1 times every kernel
+        class with CUDA events, LM_PROF_ONLY | class bits (LM_PROF_BUILD, ...) only those."""
         self.check(lib().lm_stats_reset(self.handle, int(profile)), "lm_stats_reset")
 
     def stats(self):
